@@ -1,0 +1,99 @@
+/*
+ * pmom_oracle.h -- plain CPU reference of the pre-computed MoM candidate evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the oracle the CUDA library is checked against; it is
+ * used by tests/, by the smoke check and by the CPU-baseline leg of bench.py, never by the
+ * library itself.  It shares no code with the library.  Everything is complex128 and follows the
+ * paper's definitions step by step, with no blocking, fusion or reordering:
+ *
+ *   mesh + basis-function classes ....... Section II-C (four BF categories), Section VI-A
+ *                                          (diagonal-only contact is not a connection),
+ *                                          Section V-A (two alternating triangles per pixel)
+ *   support set and selection ........... Eq. (3)-(5)
+ *   EFIE / MPIE fill of Z(f) ............ Eq. (1)-(2), RWG basis (Section II-B)
+ *   port excitation, S-parameters ....... Eq. (6)-(7)
+ *   figure of merit ..................... Eq. (8)-(9)
+ *
+ * Where the paper is silent (Green's function of the stack-up, quadrature, port stub geometry,
+ * dB convention, band edges) the readings are stated next to the code that takes them.
+ */
+#ifndef PMOM_ORACLE_H
+#define PMOM_ORACLE_H
+
+#include <complex.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int layers, nx, ny;
+  double pitch;            /* pixel side a [m] */
+  int medium;              /* 0: microstrip (one ground plane at z = 0), 1: stripline (planes at 0 and h_total) */
+  const double* layer_z;   /* [layers] metal heights [m] */
+  double h_total;          /* stripline plate spacing [m] (microstrip: unused) */
+  double eps_r, tan_d;
+  int n_states;            /* 2: void/metal */
+  int n_ports;
+  const int32_t* ports;    /* [n_ports][3] = layer, side (0 right, 1 top, 2 left, 3 bottom), pos */
+} or_grid;
+
+/* Basis-function classes (Section II-C). */
+enum { OR_BF_ALWAYS = 0, OR_BF_INNER = 1, OR_BF_INTER = 2, OR_BF_PIXPORT = 3 };
+
+/* One BF-table row = 8 int32:
+ *   [0] class  [1] pixel A  [2] pixel B  [3] port (or -1)
+ *   [4] key of T+  [5] key of T-  [6] free-vertex index in T+  [7] free-vertex index in T-
+ * pixel index = (layer*ny + y)*nx + x; triangle key = (((layer*128 + y+4)*128 + x+4)*2 + half). */
+#define OR_BF_COLS 8
+
+int or_count_bfs(const or_grid* g);
+int or_bf_table(const or_grid* g, int32_t* table);
+/* Eq. (3): ascending indices of the BFs active under `map` ([layers][ny][nx] states).
+ * Returns N >= 0, or -1 if a state is out of range. */
+int or_active_set(const or_grid* g, const int32_t* table, int M, const uint8_t* map, int32_t* idx);
+
+/* Triangle geometry of a key (3 vertices, metres). */
+void or_triangle(const or_grid* g, int32_t key, double v[3][3]);
+
+/* Z(f) of the all-metal parent, complex128, row-major [F][M][M].
+ * mode 0: every triangle pair integrated; mode 1: pairs related by a lattice translation share
+ * one integration.  Returns max |Z - Z^T| / max |Z| before symmetrisation (Z <- (Z + Z^T)/2). */
+double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threads, double complex* Z);
+
+/* Green's function of the stack-up between metal layers lp and lq at lateral distance rho. */
+double complex or_green(const or_grid* g, double freq, int lp, int lq, double rho);
+/* Same, by the slow reference route only (stripline: plain image series with K images). */
+double complex or_green_images(const or_grid* g, double freq, int lp, int lq, double rho, int K);
+double complex or_green_modal(const or_grid* g, double freq, int lp, int lq, double rho);
+double complex or_bessel_k0(double complex w);
+/* Analytic potential integrals over a planar triangle (used by the singular part of the fill). */
+void or_tri_potentials(const double tri[3][3], const double r[3], double* I1, double Iv[3]);
+/* Quadrature rules on the reference triangle: n = 7 or 13; returns barycentric rows and weights. */
+int or_tri_rule(int n, const double** bary, const double** w);
+double or_eps_eff(const or_grid* g);
+void or_pair_integrals(const or_grid* g, double freq, int32_t kp, int32_t kq, double complex out[10]);
+
+/* Dense LU with partial pivoting (|a| modulus, ties to the lowest row), row-major, in place. */
+int or_lu(double complex* A, int n, int32_t* piv);
+void or_lu_solve(const double complex* LU, const int32_t* piv, int n, double complex* B, int nrhs);
+
+/* Per-candidate evaluation (Eq. 5-7): S[F][P][P] for one map.  zc64 != 0: Z is complex64
+ * storage (promoted exactly to complex128).  form 0: unloaded delta-gap solve + Y->S,
+ * form 1: ports loaded with Z0 and Eq. (6).  Returns 0, 1 (singular), -1 (bad state). */
+int or_eval_map(const or_grid* g, const int32_t* table, int M, const void* Z, int zc64, int F,
+                const uint8_t* map, double Z0, int form, double complex* S);
+/* Batch version, threads over (candidate, frequency); status[B]. */
+void or_eval_batch(const or_grid* g, const int32_t* table, int M, const void* Z, int zc64, int F,
+                   const uint8_t* maps, int B, double Z0, int threads, double complex* S, int32_t* status);
+
+/* Eq. (8)-(9).  band[f]: 0 p1, 1 p2, 2 i, 3 s, 255 none. */
+double or_fom(const double complex* S, int F, int P, const uint8_t* band);
+void or_bands(const double* freqs, int F, const double* edges /* p1lo,p1hi,p2lo,p2hi,ilo,ihi,slo,shi */,
+              uint8_t* band);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
