@@ -1,0 +1,295 @@
+"""Benchmark of the candidate evaluator: candidate evaluations per second (all frequencies of a
+candidate = one evaluation) of the mixed-precision refined path, with the plain FP64 GPU path and
+the CPU oracle timed in the same run.
+
+Default workload: 2-layer 16x16 stripline (M = 1484 BFs), 41 frequencies 1-7 GHz, complex64
+parent database filled on the GPU, all 512 single-bit flips of a seeded map (about 700 active BFs
+each).  One step = one evaluation of the whole batch through the C ABI (activation, gather,
+LU + solves + refinement, S-parameters, FoM).  The database (0.72 GB) is larger than L2, so no
+L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload precision|plain]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pmom_inputs as PI  # noqa: E402
+
+METRIC = "candidate evals/sec (all freqs) vs plain FP64 GPU path at |dS|<=1e-6"
+FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(name: str):
+    return PI.workload_precision() if name == "precision" else PI.workload_plain()
+
+
+def lu_flops(N: np.ndarray, F: int, P: int) -> float:
+    """Algorithmic flops of one batch: complex LU (8/3 N^3) + P-RHS solve (8 N^2 P) per task."""
+    N = N.astype(np.float64)
+    return float(F * np.sum(8.0 / 3.0 * N ** 3 + 8.0 * N ** 2 * P))
+
+
+def cpu_baseline(w, seconds_target: float = 15.0):
+    """The oracle (plain C, complex128) on the host cores, on a bounded sample: a few candidates of
+    the same batch at a few of its frequencies, scaled to candidate evaluations per second."""
+    from oracle import oracle as O
+    freqs = w.freqs()
+    fsel = np.linspace(0, w.n_freq - 1, 4).round().astype(int)
+    OG = O.Grid(w.grid)
+    Z, _ = O.fill(OG, freqs[fsel])
+    Z = Z.astype(np.complex64) if w.z_dtype == "c64" else Z
+    maps = PI.workload_maps(w, seed=0)
+    cores = os.cpu_count() or 1
+    nb = max(1, min(maps.shape[0], cores))
+    t0 = time.perf_counter()
+    O.eval_batch(OG, Z, maps[:nb], threads=cores)
+    dt = time.perf_counter() - t0
+    evals = nb * len(fsel) / w.n_freq
+    # grow the sample towards the time target
+    if dt < seconds_target / 4:
+        nb2 = min(maps.shape[0], max(nb, int(nb * seconds_target / max(dt, 1e-3) / 2)))
+        t0 = time.perf_counter()
+        O.eval_batch(OG, Z, maps[:nb2], threads=cores)
+        dt = time.perf_counter() - t0
+        nb = nb2
+        evals = nb * len(fsel) / w.n_freq
+    return {"value": evals / dt, "unit": "candidate evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nb} candidates x {len(fsel)} of {w.n_freq} frequencies (scaled), complex128 LU, all host threads",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    info = None
+    for _ in range(max(1, args.steps)):
+        info = cpu_baseline(w, seconds_target=max(4.0, 60.0 / max(1, args.steps)))
+        vals.append(info["value"])
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidate evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.batch / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": w.name, "global_batch": w.batch, "freqs": w.n_freq},
+            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": v,
+                             "unit": "candidate evals/s"},
+            "e2e": {"value": v, "unit": "candidate evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2412_17617_gb300 import Evaluator, band_codes, build as B
+    B.build()
+    w = workload(args.workload)
+    ev = Evaluator(w.grid)
+    freqs = w.freqs()
+    ev.fill_Z(freqs, w.z_dtype)
+    ev.set_fom(band_codes(freqs, w.bands), w.z0_ohm)
+    # each rank evaluates its own batch (independent candidates): weak scaling, no collective
+    maps_np = PI.workload_maps(w, seed=rank)
+    maps = torch.from_numpy(maps_np).cuda()
+    Bsz = maps.shape[0]
+    idx, n = ev.active_set(maps)
+    N = n.cpu().numpy()
+    S = torch.empty((Bsz, w.n_freq, ev.P, ev.P), dtype=torch.complex128, device="cuda")
+    fom = torch.empty((Bsz,), dtype=torch.float64, device="cuda")
+    status = torch.empty((Bsz,), dtype=torch.int32, device="cuda")
+    out = (S, fom, status)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- mixed refined path (the headline)
+    ev.set_timing(True)
+    for _ in range(args.warmup):
+        ev.eval(maps, "mixed", out=out)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = []
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ev.eval(maps, "mixed", out=out)
+            kern_ms.append(ev.kernel_times()["eval"]) if args.steps <= 64 else None
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    st = ev.stats()
+    status_np = status.cpu().numpy()
+    value = world * Bsz / (ms * 1e-3)
+    # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
+    nfp = min(Bsz, 32)
+    sub = maps[:nfp]
+    sub_out = (S[:nfp], fom[:nfp], status[:nfp])
+    ev.eval(sub, "fp64", out=sub_out)
+    barrier()
+    e0.record(stream)
+    ev.eval(sub, "fp64", out=sub_out)
+    e1.record(stream)
+    barrier()
+    fp64_ms = e0.elapsed_time(e1)
+    fp64_value = world * nfp / (fp64_ms * 1e-3)
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    maps_h = torch.from_numpy(maps_np).pin_memory()
+    S_h = torch.empty((Bsz, w.n_freq, ev.P, ev.P), dtype=torch.complex128).pin_memory()
+    fom_h = torch.empty((Bsz,), dtype=torch.float64).pin_memory()
+    st_h = torch.empty((Bsz,), dtype=torch.int32).pin_memory()
+    ev.eval_host(maps_h.numpy(), "mixed", S=S_h.numpy(), fom=fom_h.numpy(), status=st_h.numpy())
+    n_e2e = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ev.eval_host(maps_h.numpy(), "mixed", S=S_h.numpy(), fom=fom_h.numpy(), status=st_h.numpy())
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_val = world * Bsz / e2e_s
+    # ---- roofline of the dominant kernel (the evaluation kernel)
+    peaks = _peaks()
+    eval_ms = float(np.median(kern_ms)) if kern_ms else ms
+    flops = lu_flops(N, w.n_freq, ev.P)
+    achieved = flops / (eval_ms * 1e-3) / 1e12
+    peak = FP32_LANES_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "eval_kernel<float2,float2,mixed>",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "candidate evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 LU + f64 refinement", "data": "synthetic",
+        "config": {"workload": w.name, "global_batch": Bsz * world, "freqs": w.n_freq, "M": ev.M,
+                   "N_mean": float(N.mean()), "N_min": int(N.min()), "N_max": int(N.max()),
+                   "l2": "inputs larger than L2 (Z database 0.72 GB)", "parallelism": f"replicas x{world}"},
+        "fp64_path": {"value": fp64_value, "unit": "candidate evals/s", "candidates": nfp,
+                      "speedup_mixed_over_fp64": value / fp64_value},
+        "refinement": {"iters_total": st["refine_iters"], "iters_max": st["refine_max"],
+                       "repaired_tasks": st["repaired_tasks"], "tasks": st["tasks"],
+                       "bad_status": int((status_np != 0).sum())},
+        "kernel_ms": {"eval": eval_ms},
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "candidate evals/s", "h2d_bytes_per_step": int(maps_np.nbytes),
+                "d2h_bytes_per_step": int(S_h.numel() * 16 + fom_h.numel() * 8 + st_h.numel() * 4)},
+        "gpu_launches": int(st["launches"]) * args.steps,
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line))
+    ev.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision", choices=["precision", "plain"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

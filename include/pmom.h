@@ -1,0 +1,170 @@
+/*
+ * pmom.h -- C ABI of the GB300 pre-computed MoM candidate evaluator.
+ *
+ * The library implements the evaluation step of the paper's inverse-design loop: for a batch of
+ * candidate pixel maps it selects each candidate's active RWG basis functions, gathers the
+ * corresponding rows and columns of the pre-computed parent interaction matrix Z(f), solves for
+ * every port excitation at every frequency, converts the port currents to S-parameters and
+ * scores the two-passband diplexer figure of merit.
+ *
+ * Conventions shared by every call:
+ *   - All entry points return a pmom_status (0 = PMOM_OK).  On failure pmom_last_error(ctx)
+ *     returns a message owned by the context (valid until the next call on that context).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Device work is
+ *     asynchronous on that stream; CUDA faults surface at the next call or at pmom_sync().
+ *   - "device" pointers are CUDA device (or managed) memory of the current device; "host"
+ *     pointers are ordinary or pinned host memory.  The caller owns every buffer it passes; the
+ *     library owns its copy of Z, its basis-function tables and its workspaces until
+ *     pmom_destroy().
+ *   - A context is bound to the device that is current when pmom_create() runs and must only be
+ *     used from one host thread at a time.
+ *   - Pixel maps are uint8 [layers][ny][nx] per candidate (row-major, x fastest).  State 0 is
+ *     void, 1 is metal.
+ */
+#ifndef PMOM_H
+#define PMOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pmom_status;
+enum {
+  PMOM_OK = 0,
+  PMOM_ERR_INVALID_ARG = 1,      /* null pointer, size out of range, inconsistent grid */
+  PMOM_ERR_OOM = 2,              /* a device allocation failed */
+  PMOM_ERR_BAD_STATE_VALUE = 3,  /* a pixel state >= n_states (reported per candidate as well) */
+  PMOM_ERR_Z_SHAPE_MISMATCH = 4, /* Z / frequency / band shapes disagree with the grid */
+  PMOM_ERR_CUDA = 5,             /* a CUDA runtime call failed; see pmom_last_error */
+  PMOM_ERR_NOT_READY = 6,        /* call order: Z or the FoM bands not loaded yet */
+  PMOM_ERR_UNSUPPORTED = 7       /* feature outside this build (e.g. via states) */
+};
+
+/* Storage of the parent matrix database. */
+enum { PMOM_C64 = 0, PMOM_C128 = 1 };
+/* Where a buffer lives. */
+enum { PMOM_MEM_HOST = 0, PMOM_MEM_DEVICE = 1 };
+/* Arithmetic of the evaluation.
+ *   PMOM_FP64          : complex128 LU with partial pivoting on the CUDA cores (plain path).
+ *   PMOM_MIXED_REFINED : complex64 LU (single precision) + iterative refinement whose residual
+ *                        V - Z_sub x is formed in double-class precision from the exact stored
+ *                        Z entries, until the correction stops shrinking (see pmom_stats). */
+enum { PMOM_FP64 = 0, PMOM_MIXED_REFINED = 1 };
+/* Per-candidate status codes (status_out). */
+enum {
+  PMOM_CAND_OK = 0,
+  PMOM_CAND_SINGULAR = 1,        /* an exactly zero pivot at some frequency */
+  PMOM_CAND_NONFINITE = 2,       /* NaN/Inf in S or FoM */
+  PMOM_CAND_REPAIRED = 3,        /* mixed path did not converge at some frequency; that frequency
+                                    was re-solved on the FP64 path (results are valid) */
+  PMOM_CAND_BAD_STATE = 5        /* a pixel state >= n_states; S/FoM not computed */
+};
+
+typedef struct {
+  int32_t layer; /* metal layer of the feed stub */
+  int32_t side;  /* 0: +x (right), 1: +y (top), 2: -x (left), 3: -y (bottom) */
+  int32_t pos;   /* pixel row (sides 0/2) or column (sides 1/3) the stub leaves through */
+} pmom_port;
+
+/* Pixel grid and stack-up (paper Section II-A/II-D, Table I). */
+typedef struct {
+  int32_t layers, nx, ny;
+  double pitch_m;              /* pixel side a */
+  int32_t medium;              /* 0: microstrip (ground at z = 0), 1: stripline (grounds at 0, h_total) */
+  const double* layer_z_m;     /* [layers], host; heights of the metal layers */
+  double h_total_m;            /* stripline plate spacing */
+  double eps_r, tan_d;         /* homogenised substrate */
+  int32_t n_states;            /* 2 (void / metal) in this build */
+  int32_t n_ports;             /* 1..4 */
+  const pmom_port* ports;      /* [n_ports], host */
+} pmom_grid_desc;
+
+typedef struct pmom_ctx pmom_ctx;
+
+/* Build the basis-function tables of the grid (two alternating triangles per pixel, RWG on every
+ * shared edge, four BF classes: Section II-C; corner-only contact is no connection: Section VI-A).
+ * Copies the descriptor; `out` receives a new context.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+pmom_status pmom_create(const pmom_grid_desc* grid, pmom_ctx** out);
+pmom_status pmom_destroy(pmom_ctx* ctx);
+const char* pmom_last_error(const pmom_ctx* ctx);
+
+/* Number M of basis functions of the all-metal parent (rows of Z), and ports P. */
+pmom_status pmom_num_bfs(const pmom_ctx* ctx, int32_t* M, int32_t* P);
+
+/* BF table, host int32 [M][8]: class (0 always-present, 1 inner-pixel, 2 inter-pixel,
+ * 3 pixel-port), pixel A, pixel B, port, key(T+), key(T-), free vertex in T+, free vertex in T-.
+ * pixel = (layer*ny + y)*nx + x; key = (((layer*128 + y+4)*128 + x+4)*2 + half), half 0 being the
+ * triangle that holds the pixel's lower (-y) side.  Canonical BF order: port stubs (per port: inner
+ * stub diagonal, delta-gap edge, outer stub diagonal), then per layer and pixel (row-major):
+ * diagonal, +x side, +y side, then one pixel-port BF per port. */
+pmom_status pmom_bf_table(const pmom_ctx* ctx, int32_t* table_host);
+
+/* Load the parent database Z[F][M][M] (row-major; complex interleaved re,im) for F frequencies
+ * (Phase 2 of the paper's flow, Section II-A).  dtype: PMOM_C64 or PMOM_C128; mem: where Z lives.
+ * The library copies Z into memory it owns (device-to-device for PMOM_MEM_DEVICE); the caller may
+ * free its buffer when the call returns (after pmom_sync for device sources).
+ * Errors: INVALID_ARG, Z_SHAPE_MISMATCH (F < 1), OOM, CUDA. */
+pmom_status pmom_load_Z(pmom_ctx* ctx, const double* freqs_hz_host, int32_t F, const void* Z, int32_t dtype,
+                        int32_t mem, void* stream);
+
+/* Copy the resident database (as loaded or filled) out to a caller buffer of F*M*M complex
+ * elements of the resident dtype.  mem says where `out` lives. */
+pmom_status pmom_copy_Z(const pmom_ctx* ctx, void* out, int32_t mem, void* stream);
+
+/* Fill the parent database on the GPU (MPIE with RWG basis, Eq. 1-2; homogeneous-medium Green's
+ * function of the stack-up: one ground image for microstrip, the parallel-plate Dirichlet
+ * function for stripline) at F frequencies and keep it resident as dtype.  Replaces a loaded Z. */
+pmom_status pmom_fill_Z(pmom_ctx* ctx, const double* freqs_hz_host, int32_t F, int32_t dtype, void* stream);
+
+/* Figure-of-merit bands (Eq. 8-9): band_of_freq host uint8 [F] with 0 = f_p1, 1 = f_p2,
+ * 2 = f_i, 3 = f_s, 255 = not scored; Z0 = port reference impedance (Eq. 6).
+ * Errors: Z_SHAPE_MISMATCH if F differs from the loaded database. */
+pmom_status pmom_set_fom(pmom_ctx* ctx, const uint8_t* band_of_freq_host, int32_t F, double Z0);
+
+/* Support sets (Eq. 3): for each of B device maps, idx_out[b][0..N_b) = ascending indices of the
+ * active BFs and n_out[b] = N_b (-1 if a state is out of range).  idx_out: device int32 [B][M]. */
+pmom_status pmom_active_set(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t* idx_out_dev,
+                            int32_t* n_out_dev, void* stream);
+
+/* Z_sub = S^T Z(f) S (Eq. 4-5) for one device index list of length N at frequency f, written to
+ * out_dev as N*N complex elements of the resident dtype (row-major).  Bit-exact copy of entries. */
+pmom_status pmom_gather(pmom_ctx* ctx, const int32_t* idx_dev, int32_t N, int32_t f, void* out_dev, void* stream);
+
+/* Evaluate B candidates at every loaded frequency (Eq. 2-9).
+ *   maps_dev   : device uint8 [B][layers][ny][nx]
+ *   precision  : PMOM_FP64 or PMOM_MIXED_REFINED
+ *   S_out_dev  : device double [B][F][P][P][2] (re, im; S[i][j] = response at port i+1 to port j+1),
+ *                or NULL to skip writing S
+ *   fom_out_dev: device double [B] (lower is better)
+ *   status_dev : device int32 [B] (PMOM_CAND_*)
+ * Errors: INVALID_ARG, NOT_READY (no Z or no bands), OOM, CUDA. */
+pmom_status pmom_eval_candidates(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision,
+                                 double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
+
+/* Same computation with host buffers: the call copies the maps to the device, evaluates, copies
+ * S (if S_out_host != NULL), FoM and status back and synchronizes `stream` before returning.
+ * Pinned host buffers make the copies asynchronous DMA. */
+pmom_status pmom_eval_candidates_host(pmom_ctx* ctx, const uint8_t* maps_host, int32_t B, int32_t precision,
+                                      double* S_out_host, double* fom_out_host, int32_t* status_host,
+                                      void* stream);
+
+/* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
+ * max iterations of one task, tasks re-solved in FP64, candidates singular, candidates
+ * non-finite, kernel launches issued, reserved.  Synchronizes the context's last stream. */
+pmom_status pmom_stats(pmom_ctx* ctx, int64_t* out8);
+
+/* Kernel timing of later eval calls: on != 0 makes each eval record CUDA events on its stream
+ * around its kernels; pmom_kernel_times then returns the last call's milliseconds for
+ * [0] activation, [1] evaluation, [2] FP64 repair, [3] FoM (host double [4]; synchronizes). */
+pmom_status pmom_set_timing(pmom_ctx* ctx, int32_t on);
+pmom_status pmom_kernel_times(pmom_ctx* ctx, double* ms4_host);
+
+/* Wait for all work the context issued on `stream`. */
+pmom_status pmom_sync(pmom_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMOM_H */

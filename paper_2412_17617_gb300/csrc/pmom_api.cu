@@ -1,0 +1,429 @@
+// C ABI of the evaluator: context, parent-database residency, FoM bands, and the evaluation
+// pipeline (activation -> persistent evaluation -> FP64 repair of unconverged tasks -> FoM).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pmom_internal.h"
+
+struct pmom_ctx {
+  int device = 0;
+  int num_sms = 0;
+  pmom::Grid grid;
+  int M = 0;
+  std::vector<int32_t> table;
+  int4* d_rules = nullptr;
+  // parent database
+  int F = 0;
+  int dtype = PMOM_C64;
+  void* d_Z = nullptr;
+  size_t z_bytes = 0;
+  std::vector<double> freqs;
+  // figure of merit
+  bool fom_ready = false;
+  uint8_t* d_bands = nullptr;
+  double Z0 = 50.0;
+  // per-batch buffers (grown on demand)
+  int b_cap = 0;
+  int32_t* d_idx = nullptr;
+  int32_t* d_nact = nullptr;
+  uint32_t* d_flags = nullptr;
+  double2* d_S = nullptr;
+  int* d_repair = nullptr;
+  uint8_t* d_maps_stage = nullptr;
+  double* d_fom_stage = nullptr;
+  int32_t* d_status_stage = nullptr;
+  // scalars: [0] task counter, [1] repair count, then 4 x u64 counters
+  void* d_small = nullptr;
+  // slot workspaces
+  void* d_work = nullptr;
+  size_t work_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  int64_t launches = 0;
+  bool timing = false;
+  bool timed = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::string err;
+};
+
+namespace {
+
+pmom_status fail(pmom_ctx* c, pmom_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+pmom_status cuda_fail(pmom_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? PMOM_ERR_OOM : PMOM_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PMOM_CUDA(ctx, call)                                   \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+size_t z_elem(int dtype) { return dtype == PMOM_C128 ? 16 : 8; }
+
+pmom_status ensure_batch(pmom_ctx* c, int B) {
+  if (B <= c->b_cap && c->d_idx) return PMOM_OK;
+  free_dev(c->d_idx);
+  free_dev(c->d_nact);
+  free_dev(c->d_flags);
+  free_dev(c->d_S);
+  free_dev(c->d_repair);
+  free_dev(c->d_maps_stage);
+  free_dev(c->d_fom_stage);
+  free_dev(c->d_status_stage);
+  const int P = c->grid.n_ports;
+  PMOM_CUDA(c, cudaMalloc(&c->d_idx, sizeof(int32_t) * static_cast<size_t>(B) * c->M));
+  PMOM_CUDA(c, cudaMalloc(&c->d_nact, sizeof(int32_t) * B));
+  PMOM_CUDA(c, cudaMalloc(&c->d_flags, sizeof(uint32_t) * B));
+  PMOM_CUDA(c, cudaMalloc(&c->d_S, sizeof(double2) * static_cast<size_t>(B) * c->F * P * P));
+  PMOM_CUDA(c, cudaMalloc(&c->d_repair, sizeof(int) * static_cast<size_t>(B) * c->F));
+  PMOM_CUDA(c, cudaMalloc(&c->d_maps_stage, static_cast<size_t>(B) * c->grid.pixels()));
+  PMOM_CUDA(c, cudaMalloc(&c->d_fom_stage, sizeof(double) * B));
+  PMOM_CUDA(c, cudaMalloc(&c->d_status_stage, sizeof(int32_t) * B));
+  c->b_cap = B;
+  return PMOM_OK;
+}
+
+int slots_for(pmom_ctx* c, int precision, int tasks) {
+  const int per_sm = pmom::eval_blocks_per_sm(precision, c->M, c->dtype == PMOM_C128);
+  int n = (per_sm > 0 ? per_sm : 1) * c->num_sms;
+  if (n > tasks) n = tasks;
+  return n < 1 ? 1 : n;
+}
+
+pmom_status ensure_work(pmom_ctx* c) {
+  size_t need = 0;
+  for (int prec = 0; prec < 2; ++prec) {
+    int lda = 0;
+    const size_t sb = pmom::eval_slot_bytes(prec, c->M, c->grid.n_ports, &lda);
+    const size_t n = static_cast<size_t>(slots_for(c, prec, 1 << 30));
+    if (sb * n > need) need = sb * n;
+  }
+  if (need <= c->work_bytes && c->d_work) return PMOM_OK;
+  free_dev(c->d_work);
+  PMOM_CUDA(c, cudaMalloc(&c->d_work, need));
+  c->work_bytes = need;
+  return PMOM_OK;
+}
+
+// Device-side state is created on first use, so that a context (and its BF table) can be built
+// on a machine without a GPU.
+pmom_status ensure_device(pmom_ctx* c) {
+  if (c->d_rules) return PMOM_OK;
+  PMOM_CUDA(c, cudaGetDevice(&c->device));
+  PMOM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  std::vector<int4> rules(c->M);
+  for (int m = 0; m < c->M; ++m) {
+    const int32_t* r = &c->table[static_cast<size_t>(m) * pmom::kTableCols];
+    rules[m] = make_int4(r[0], r[1], r[2], 0);
+  }
+  PMOM_CUDA(c, cudaMalloc(&c->d_small, 256));
+  PMOM_CUDA(c, cudaMalloc(&c->d_rules, sizeof(int4) * c->M));
+  PMOM_CUDA(c, cudaMemcpy(c->d_rules, rules.data(), sizeof(int4) * c->M, cudaMemcpyHostToDevice));
+  return PMOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
+  if (!g || !out) return PMOM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (g->layers < 1 || g->layers > 8 || g->nx < 1 || g->ny < 1 || g->nx > 100 || g->ny > 100 || g->pitch_m <= 0 ||
+      g->n_ports < 1 || g->n_ports > pmom::kMaxPorts || !g->ports || !g->layer_z_m || (g->medium != 0 && g->medium != 1))
+    return PMOM_ERR_INVALID_ARG;
+  if (g->n_states != 2) return PMOM_ERR_UNSUPPORTED;
+  for (int p = 0; p < g->n_ports; ++p) {
+    const pmom_port& q = g->ports[p];
+    const int lim = (q.side == 0 || q.side == 2) ? g->ny : g->nx;
+    if (q.layer < 0 || q.layer >= g->layers || q.side < 0 || q.side > 3 || q.pos < 0 || q.pos >= lim)
+      return PMOM_ERR_INVALID_ARG;
+  }
+  pmom_ctx* c = new pmom_ctx();
+  pmom::Grid& gr = c->grid;
+  gr.layers = g->layers; gr.nx = g->nx; gr.ny = g->ny; gr.medium = g->medium; gr.n_states = g->n_states;
+  gr.n_ports = g->n_ports; gr.pitch = g->pitch_m; gr.h_total = g->h_total_m; gr.eps_r = g->eps_r; gr.tan_d = g->tan_d;
+  gr.layer_z.assign(g->layer_z_m, g->layer_z_m + g->layers);
+  gr.ports.assign(g->ports, g->ports + g->n_ports);
+  c->M = pmom::build_bf_table(gr, c->table);
+  *out = c;
+  return PMOM_OK;
+}
+
+pmom_status pmom_destroy(pmom_ctx* c) {
+  if (!c) return PMOM_OK;
+  free_dev(c->d_rules);
+  free_dev(c->d_Z);
+  free_dev(c->d_bands);
+  free_dev(c->d_idx);
+  free_dev(c->d_nact);
+  free_dev(c->d_flags);
+  free_dev(c->d_S);
+  free_dev(c->d_repair);
+  free_dev(c->d_maps_stage);
+  free_dev(c->d_fom_stage);
+  free_dev(c->d_status_stage);
+  free_dev(c->d_small);
+  free_dev(c->d_work);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+  return PMOM_OK;
+}
+
+const char* pmom_last_error(const pmom_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+pmom_status pmom_num_bfs(const pmom_ctx* c, int32_t* M, int32_t* P) {
+  if (!c || !M) return PMOM_ERR_INVALID_ARG;
+  *M = c->M;
+  if (P) *P = c->grid.n_ports;
+  return PMOM_OK;
+}
+
+pmom_status pmom_bf_table(const pmom_ctx* c, int32_t* out) {
+  if (!c || !out) return PMOM_ERR_INVALID_ARG;
+  std::memcpy(out, c->table.data(), sizeof(int32_t) * c->table.size());
+  return PMOM_OK;
+}
+
+pmom_status pmom_load_Z(pmom_ctx* c, const double* freqs, int32_t F, const void* Z, int32_t dtype, int32_t mem,
+                        void* stream) {
+  if (!c) return PMOM_ERR_INVALID_ARG;
+  if (c) {
+    const pmom_status dv = ensure_device(c);
+    if (dv) return dv;
+  }
+  if (!freqs || !Z || (dtype != PMOM_C64 && dtype != PMOM_C128) || (mem != PMOM_MEM_HOST && mem != PMOM_MEM_DEVICE))
+    return fail(c, PMOM_ERR_INVALID_ARG, "load_Z: bad argument");
+  if (F < 1) return fail(c, PMOM_ERR_Z_SHAPE_MISMATCH, "load_Z: F < 1");
+  const size_t bytes = static_cast<size_t>(F) * c->M * c->M * z_elem(dtype);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (bytes != c->z_bytes) {
+    free_dev(c->d_Z);
+    PMOM_CUDA(c, cudaMalloc(&c->d_Z, bytes));
+    c->z_bytes = bytes;
+  }
+  PMOM_CUDA(c, cudaMemcpyAsync(c->d_Z, Z, bytes, mem == PMOM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  if (mem == PMOM_MEM_HOST) PMOM_CUDA(c, cudaStreamSynchronize(s));
+  if (F != c->F) {
+    c->fom_ready = false;
+    free_dev(c->d_S);
+    free_dev(c->d_repair);
+    c->b_cap = 0;
+    free_dev(c->d_idx);
+  }
+  c->F = F;
+  c->dtype = dtype;
+  c->freqs.assign(freqs, freqs + F);
+  return PMOM_OK;
+}
+
+pmom_status pmom_copy_Z(const pmom_ctx* c, void* out, int32_t mem, void* stream) {
+  if (!c || !out) return PMOM_ERR_INVALID_ARG;
+  if (!c->d_Z) return PMOM_ERR_NOT_READY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out, c->d_Z, c->z_bytes, mem == PMOM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && mem == PMOM_MEM_HOST) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? PMOM_OK : PMOM_ERR_CUDA;
+}
+
+pmom_status pmom_set_fom(pmom_ctx* c, const uint8_t* bands, int32_t F, double Z0) {
+  if (!c || !bands || !(Z0 > 0)) return fail(c, PMOM_ERR_INVALID_ARG, "set_fom: bad argument");
+  if (!c->d_Z) return fail(c, PMOM_ERR_NOT_READY, "set_fom: load or fill Z first");
+  if (F != c->F) return fail(c, PMOM_ERR_Z_SHAPE_MISMATCH, "set_fom: band count differs from the database");
+  for (int f = 0; f < F; ++f)
+    if (bands[f] > 3 && bands[f] != 255) return fail(c, PMOM_ERR_INVALID_ARG, "set_fom: band code");
+  free_dev(c->d_bands);
+  PMOM_CUDA(c, cudaMalloc(&c->d_bands, F));
+  PMOM_CUDA(c, cudaMemcpy(c->d_bands, bands, F, cudaMemcpyHostToDevice));
+  c->Z0 = Z0;
+  c->fom_ready = true;
+  return PMOM_OK;
+}
+
+pmom_status pmom_active_set(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t* idx_out, int32_t* n_out, void* stream) {
+  if (!c || !maps || !idx_out || !n_out || B < 1) return fail(c, PMOM_ERR_INVALID_ARG, "active_set: bad argument");
+  pmom_status st = ensure_device(c);
+  if (st) return st;
+  st = ensure_batch(c, B);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pmom::EvalArgs a{};
+  a.rules = c->d_rules; a.M = c->M; a.B = B; a.npix = c->grid.pixels(); a.n_states = c->grid.n_states;
+  a.maps = maps; a.idx = idx_out; a.n_act = n_out; a.flags = c->d_flags;
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
+  PMOM_CUDA(c, pmom::launch_activate(a, s));
+  return PMOM_OK;
+}
+
+pmom_status pmom_gather(pmom_ctx* c, const int32_t* idx, int32_t N, int32_t f, void* out, void* stream) {
+  if (!c || !idx || !out || N < 1 || N > c->M) return fail(c, PMOM_ERR_INVALID_ARG, "gather: bad argument");
+  if (!c->d_Z) return fail(c, PMOM_ERR_NOT_READY, "gather: no database");
+  if (f < 0 || f >= c->F) return fail(c, PMOM_ERR_INVALID_ARG, "gather: frequency index");
+  PMOM_CUDA(c, pmom::launch_gather(c->d_Z, c->dtype == PMOM_C128, c->M, f, idx, N, out, static_cast<cudaStream_t>(stream)));
+  return PMOM_OK;
+}
+
+pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
+                                 double* fom_out, int32_t* status, void* stream) {
+  if (!c || !maps || !fom_out || !status || B < 1 || (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
+    return fail(c, PMOM_ERR_INVALID_ARG, "eval: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval: load Z and set the FoM bands first");
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  st = ensure_work(c);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  const int P = c->grid.n_ports;
+  pmom::EvalArgs a{};
+  a.rules = c->d_rules; a.M = c->M; a.P = P; a.F = c->F; a.B = B; a.npix = c->grid.pixels();
+  a.n_states = c->grid.n_states; a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.Z = c->d_Z;
+  a.z_c128 = c->dtype == PMOM_C128;
+  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch;   // delta-gap edges are pixel sides
+  a.Z0 = c->Z0;
+  a.S = S_out ? reinterpret_cast<double2*>(S_out) : c->d_S;
+  a.flags = c->d_flags;
+  int* small = static_cast<int*>(c->d_small);
+  a.task_counter = small;
+  a.repair_count = small + 1;
+  a.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
+  a.repair_list = c->d_repair;
+  a.work = c->d_work;
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_small, 0, 256, s));
+  const bool tm = c->timing;
+  c->timed = tm;
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
+  PMOM_CUDA(c, pmom::launch_activate(a, s));
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
+  c->launches = 1;
+  const int tasks = B * c->F;
+  a.slot_bytes = pmom::eval_slot_bytes(precision, c->M, P, &a.lda);
+  a.ntasks_list = 0;
+  PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks), s));
+  ++c->launches;
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[2], s));
+  if (precision == PMOM_MIXED_REFINED) {
+    // tasks whose refinement did not converge are solved again on the FP64 path
+    PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
+    a.slot_bytes = pmom::eval_slot_bytes(PMOM_FP64, c->M, P, &a.lda);
+    a.ntasks_list = 1;
+    PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, slots_for(c, PMOM_FP64, tasks), s));
+    ++c->launches;
+  }
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[3], s));
+  PMOM_CUDA(c, pmom::launch_fom(a.S, c->d_bands, c->F, P, B, c->d_flags, c->d_nact, fom_out, status, s));
+  ++c->launches;
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
+  return PMOM_OK;
+}
+
+pmom_status pmom_eval_candidates_host(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
+                                      double* fom_out, int32_t* status, void* stream) {
+  if (!c || !maps || !fom_out || !status || B < 1) return fail(c, PMOM_ERR_INVALID_ARG, "eval_host: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval_host: load Z and set the FoM bands first");
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = c->grid.n_ports;
+  PMOM_CUDA(c, cudaMemcpyAsync(c->d_maps_stage, maps, static_cast<size_t>(B) * c->grid.pixels(), cudaMemcpyHostToDevice, s));
+  st = pmom_eval_candidates(c, c->d_maps_stage, B, precision, nullptr, c->d_fom_stage, c->d_status_stage, stream);
+  if (st) return st;
+  if (S_out)
+    PMOM_CUDA(c, cudaMemcpyAsync(S_out, c->d_S, sizeof(double2) * static_cast<size_t>(B) * c->F * P * P, cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaMemcpyAsync(fom_out, c->d_fom_stage, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaMemcpyAsync(status, c->d_status_stage, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaStreamSynchronize(s));
+  return PMOM_OK;
+}
+
+pmom_status pmom_stats(pmom_ctx* c, int64_t* out8) {
+  if (!c || !out8) return PMOM_ERR_INVALID_ARG;
+  PMOM_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  PMOM_CUDA(c, cudaMemcpy(cnt, static_cast<char*>(c->d_small) + 64, sizeof(cnt), cudaMemcpyDeviceToHost));
+  out8[0] = static_cast<int64_t>(cnt[3]);
+  out8[1] = static_cast<int64_t>(cnt[0]);
+  out8[2] = static_cast<int64_t>(cnt[1]);
+  out8[3] = static_cast<int64_t>(cnt[2]);
+  out8[4] = 0;
+  out8[5] = 0;
+  out8[6] = c->launches;
+  out8[7] = 0;
+  return PMOM_OK;
+}
+
+pmom_status pmom_set_timing(pmom_ctx* c, int32_t on) {
+  if (!c) return PMOM_ERR_INVALID_ARG;
+  if (on && !c->ev[0])
+    for (auto& e : c->ev) PMOM_CUDA(c, cudaEventCreate(&e));
+  c->timing = on != 0;
+  return PMOM_OK;
+}
+
+pmom_status pmom_kernel_times(pmom_ctx* c, double* ms4) {
+  if (!c || !ms4) return PMOM_ERR_INVALID_ARG;
+  if (!c->timed) return fail(c, PMOM_ERR_NOT_READY, "kernel_times: no timed eval call yet");
+  PMOM_CUDA(c, cudaEventSynchronize(c->ev[4]));
+  for (int i = 0; i < 4; ++i) {
+    float ms = 0.f;
+    PMOM_CUDA(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    ms4[i] = ms;
+  }
+  return PMOM_OK;
+}
+
+pmom_status pmom_sync(pmom_ctx* c, void* stream) {
+  if (!c) return PMOM_ERR_INVALID_ARG;
+  PMOM_CUDA(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  PMOM_CUDA(c, cudaGetLastError());
+  return PMOM_OK;
+}
+
+pmom_status pmom_fill_Z(pmom_ctx* c, const double* freqs, int32_t F, int32_t dtype, void* stream) {
+  if (c) {
+    const pmom_status dv = ensure_device(c);
+    if (dv) return dv;
+  }
+  if (!c || !freqs || F < 1 || (dtype != PMOM_C64 && dtype != PMOM_C128))
+    return fail(c, PMOM_ERR_INVALID_ARG, "fill_Z: bad argument");
+  for (int f = 0; f < F; ++f)
+    if (!(freqs[f] > 0)) return fail(c, PMOM_ERR_INVALID_ARG, "fill_Z: frequencies must be positive");
+  if (c->grid.medium == 1)
+    for (double z : c->grid.layer_z)
+      if (!(z > 0 && z < c->grid.h_total)) return fail(c, PMOM_ERR_INVALID_ARG, "fill_Z: layer outside the plates");
+  void* dz = nullptr;
+  std::string msg;
+  pmom_status st = pmom::fill_Z(c->grid, c->table, c->M, freqs, F, dtype, static_cast<cudaStream_t>(stream), &dz, &msg);
+  if (st) return fail(c, st, msg);
+  free_dev(c->d_Z);
+  c->d_Z = dz;
+  c->z_bytes = static_cast<size_t>(F) * c->M * c->M * z_elem(dtype);
+  if (F != c->F) {
+    c->fom_ready = false;
+    free_dev(c->d_S);
+    free_dev(c->d_repair);
+    free_dev(c->d_idx);
+    c->b_cap = 0;
+  }
+  c->F = F;
+  c->dtype = dtype;
+  c->freqs.assign(freqs, freqs + F);
+  return PMOM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,852 @@
+// Candidate-evaluation kernels for sm_103a.
+//
+//   activate_kernel : pixel map -> active-BF indices I (Eq. 3, ascending) by a block-wide ballot scan
+//   eval_kernel     : persistent; one CTA per (frequency, candidate) task at a time, frequency-major
+//                     so the parent Z(f) being read stays resident in L2.  Per task:
+//                       gather Z_sub = Z(f)[I, I]                           (Eq. 4-5)
+//                       blocked right-looking LU, partial pivoting          (Eq. 2)
+//                       forward/back substitution for the P port excitations
+//                       [mixed] iterative refinement: residual V - Z_sub x in double from the
+//                               exact stored Z entries, correction with the single-precision LU
+//                       Y_ij = l_i x_i^(j), S = (1 + Z0 Y)^-1 (1 - Z0 Y)   (Eq. 6-7)
+//   fom_kernel      : FoM of Eq. (8)-(9) per candidate, frequencies summed in order.
+#include <cfloat>
+#include <cstdint>
+
+#include "pmom_internal.h"
+
+namespace pmom {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kTile = 64;        // trailing-update tile (rows and columns)
+constexpr int kMaxRefine = 10;
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c - a*b
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  c.x = fmaf(-a.x, b.x, c.x); c.x = fmaf(a.y, b.y, c.x);
+  c.y = fmaf(-a.x, b.y, c.y); c.y = fmaf(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+  c.x = fma(-a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+// c + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ float2 cinv(float2 a) {
+  const float d = cabs2(a);
+  return make_float2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double2 cinv(double2 a) {
+  const double d = cabs2(a);
+  return make_double2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ float2 czero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 czero(double2) { return make_double2(0.0, 0.0); }
+
+template <typename T> __device__ __forceinline__ T from_f2(float2 z);
+template <> __device__ __forceinline__ float2 from_f2<float2>(float2 z) { return z; }
+template <> __device__ __forceinline__ double2 from_f2<double2>(float2 z) { return make_double2(z.x, z.y); }
+template <typename T> __device__ __forceinline__ T from_d2(double2 z);
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 z) {
+  return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
+}
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 z) { return z; }
+__device__ __forceinline__ double2 to_d2(float2 z) { return make_double2(z.x, z.y); }
+__device__ __forceinline__ double2 to_d2(double2 z) { return z; }
+
+template <typename ZT, typename T> __device__ __forceinline__ T zload(const ZT* p);
+template <> __device__ __forceinline__ float2 zload<float2, float2>(const float2* p) { return __ldg(p); }
+template <> __device__ __forceinline__ double2 zload<float2, double2>(const float2* p) { return to_d2(__ldg(p)); }
+template <> __device__ __forceinline__ double2 zload<double2, double2>(const double2* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float2 zload<double2, float2>(const double2* p) {
+  return from_d2<float2>(__ldg(p));
+}
+
+__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_f(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <typename T> __device__ __forceinline__ T shfl_c(T v, int src) {
+  v.x = shfl_f(v.x, src);
+  v.y = shfl_f(v.y, src);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T shfl_c_down(T v, int d) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+  return v;
+}
+
+template <typename T> struct Real;
+template <> struct Real<float2> { using type = float; };
+template <> struct Real<double2> { using type = double; };
+
+template <typename CT> struct Cfg;
+template <> struct Cfg<float2> { static constexpr int NB = 16; };
+template <> struct Cfg<double2> { static constexpr int NB = 8; };
+
+// ------------------------------------------------------------------ activation (Eq. 3)
+__global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restrict__ rules, int M,
+                                                           const uint8_t* __restrict__ maps, int npix, int n_states,
+                                                           int32_t* __restrict__ idx, int32_t* __restrict__ n_act,
+                                                           uint32_t* __restrict__ flags) {
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint8_t* map = maps + static_cast<size_t>(b) * npix;
+  __shared__ int s_bad;
+  __shared__ int s_warp[kWarps];
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int i = tid; i < npix; i += kThreads)
+    if (map[i] >= n_states) s_bad = 1;
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) {
+      n_act[b] = -1;
+      atomicOr(&flags[b], kFlagBadState);
+    }
+    return;
+  }
+  int32_t* out = idx + static_cast<size_t>(b) * M;
+  int base = 0;
+  for (int m0 = 0; m0 < M; m0 += kThreads) {
+    const int m = m0 + tid;
+    bool on = false;
+    if (m < M) {
+      const int4 r = __ldg(&rules[m]);
+      switch (r.x) {
+        case kAlways: on = true; break;
+        case kInner: on = map[r.y] >= 1; break;
+        case kInter: on = map[r.y] >= 1 && map[r.z] >= 1; break;
+        case kPixPort: on = map[r.y] >= 1; break;
+        default: on = false;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int woff = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int c = s_warp[w];
+      woff += (w < warp) ? c : 0;
+      total += c;
+    }
+    if (on) out[base + woff + before] = m;
+    base += total;
+    __syncthreads();
+  }
+  if (tid == 0) n_act[b] = base;
+}
+
+// ------------------------------------------------------------------ block argmax of |a|^2
+template <typename R>
+__device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const R ov = __shfl_down_sync(0xffffffffu, v, d);
+    const int orow = __shfl_down_sync(0xffffffffu, row, d);
+    if (ov > v || (ov == v && orow >= 0 && (row < 0 || orow < row))) { v = ov; row = orow; }
+  }
+  if (lane == 0) { s_val[warp] = v; s_row[warp] = row; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R bv = s_val[0];
+    int br = s_row[0];
+    for (int w = 1; w < kWarps; ++w) {
+      if (s_val[w] > bv || (s_val[w] == bv && s_row[w] >= 0 && (br < 0 || s_row[w] < br))) { bv = s_val[w]; br = s_row[w]; }
+    }
+    s_row[kWarps] = br;
+  }
+  __syncthreads();
+  return s_row[kWarps];
+}
+
+// ------------------------------------------------------------------ blocked LU in global memory
+// A: row-major N x N (leading dimension lda).  Panel of NB columns factored in shared memory;
+// row interchanges applied to whole rows (LAPACK convention: P A = L U, unit-diagonal L).
+// Returns true if an exactly zero pivot occurred.
+template <typename CT>
+__device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ piv, CT* __restrict__ Pn,
+                          CT* __restrict__ Ut, typename Real<CT>::type* s_val, int* s_row) {
+  using R = typename Real<CT>::type;
+  constexpr int NB = Cfg<CT>::NB;
+  constexpr int LDP = NB + 1;
+  constexpr int LDU = kTile + 1;
+  const int tid = threadIdx.x;
+  bool singular = false;
+  for (int k0 = 0; k0 < N; k0 += NB) {
+    const int kb = min(NB, N - k0);
+    const int nr = N - k0;
+    // 1. panel -> shared memory
+    for (int e = tid; e < nr * NB; e += kThreads) {
+      const int r = e / NB, c = e % NB;
+      if (c < kb) Pn[r * LDP + c] = A[static_cast<size_t>(k0 + r) * lda + k0 + c];
+    }
+    __syncthreads();
+    // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row)
+    for (int j = 0; j < kb; ++j) {
+      R best = -1;
+      int brow = -1;
+      for (int r = j + tid; r < nr; r += kThreads) {
+        const R v = cabs2(Pn[r * LDP + j]);
+        if (v > best) { best = v; brow = r; }
+      }
+      const int p = block_argmax<R>(best, brow, s_val, s_row);
+      if (tid == 0) piv[k0 + j] = k0 + p;
+      if (p != j && tid < kb) {
+        const CT t = Pn[j * LDP + tid];
+        Pn[j * LDP + tid] = Pn[p * LDP + tid];
+        Pn[p * LDP + tid] = t;
+      }
+      __syncthreads();
+      const CT d = Pn[j * LDP + j];
+      const bool zero = cabs2(d) == R(0);
+      if (zero) singular = true;
+      const CT inv = zero ? czero(d) : cinv(d);
+      for (int r = j + 1 + tid; r < nr; r += kThreads) {
+        const CT l = cmul(Pn[r * LDP + j], inv);
+        Pn[r * LDP + j] = l;
+        for (int c = j + 1; c < kb; ++c) Pn[r * LDP + c] = cfms(l, Pn[j * LDP + c], Pn[r * LDP + c]);
+      }
+      __syncthreads();
+    }
+    // 3. panel back to global memory
+    for (int e = tid; e < nr * NB; e += kThreads) {
+      const int r = e / NB, c = e % NB;
+      if (c < kb) A[static_cast<size_t>(k0 + r) * lda + k0 + c] = Pn[r * LDP + c];
+    }
+    // 4. the panel's row interchanges on the columns outside it
+    for (int j = 0; j < kb; ++j) {
+      const int p = piv[k0 + j];
+      if (p != k0 + j) {
+        CT* ra = A + static_cast<size_t>(k0 + j) * lda;
+        CT* rb = A + static_cast<size_t>(p) * lda;
+        for (int c = tid; c < N; c += kThreads) {
+          if (c >= k0 && c < k0 + kb) continue;
+          const CT t = ra[c];
+          ra[c] = rb[c];
+          rb[c] = t;
+        }
+      }
+      __syncthreads();
+    }
+    // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory)
+    for (int c = k0 + kb + tid; c < N; c += kThreads) {
+      CT u[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) u[i] = i < kb ? A[static_cast<size_t>(k0 + i) * lda + c] : czero(u[0]);
+#pragma unroll
+      for (int i = 1; i < NB; ++i)
+#pragma unroll
+        for (int t = 0; t < i; ++t) u[i] = cfms(Pn[i * LDP + t], u[t], u[i]);
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < kb) A[static_cast<size_t>(k0 + i) * lda + c] = u[i];
+    }
+    __syncthreads();
+    // 6. trailing update A22 -= L21 U12, 64 x 64 tiles, 4 x 4 complex outputs per thread
+    const int r_begin = k0 + kb, n2 = N - r_begin;
+    if (n2 > 0) {
+      const int ty = tid >> 4, tx = tid & 15;
+      const int ntile = (n2 + kTile - 1) / kTile;
+      for (int tc = 0; tc < ntile; ++tc) {
+        const int c0 = r_begin + tc * kTile;
+        for (int e = tid; e < NB * kTile; e += kThreads) {
+          const int t = e / kTile, cc = e % kTile;
+          Ut[t * LDU + cc] = (t < kb && c0 + cc < N) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
+        }
+        __syncthreads();
+        for (int tr = 0; tr < ntile; ++tr) {
+          const int r0 = tr * kTile;   // relative to r_begin
+          CT acc[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
+              acc[i][jj] = (r < n2 && c < N) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
+            }
+#pragma unroll 4
+          for (int t = 0; t < NB; ++t) {
+            if (t >= kb) break;
+            CT a[4], u[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int r = r0 + ty + 16 * i;
+              a[i] = r < n2 ? Pn[(kb + r) * LDP + t] : czero(a[0]);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) u[jj] = Ut[t * LDU + tx + 16 * jj];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cfms(a[i], u[jj], acc[i][jj]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
+              if (r < n2 && c < N) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
+            }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  return singular;
+}
+
+// ------------------------------------------------------------------ triangular solves
+// W (shared, N x P) holds the right-hand sides on entry and the solution on exit.
+template <typename CT>
+__device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
+                         int P) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    for (int k = 0; k < N; ++k) {
+      const int p = piv[k];
+      if (p != k && lane < P) {
+        const CT t = W[k * P + lane];
+        W[k * P + lane] = W[p * P + lane];
+        W[p * P + lane] = t;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // forward: L y = P b, unit diagonal, blocks of 32 rows
+  for (int i0 = 0; i0 < N; i0 += 32) {
+    const int bs = min(32, N - i0);
+    if (i0 > 0) {
+      for (int ii = warp; ii < bs; ii += kWarps) {
+        const int i = i0 + ii;
+        CT acc[kMaxPorts];
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
+        const CT* row = A + static_cast<size_t>(i) * lda;
+        for (int t = lane; t < i0; t += 32) {
+          const CT l = row[t];
+#pragma unroll
+          for (int p = 0; p < kMaxPorts; ++p)
+            if (p < P) acc[p] = cfms(l, W[t * P + p], acc[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) {
+          if (p >= P) break;
+          CT v = acc[p];
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) {
+            const CT o = shfl_c_down(v, d);
+            v.x += o.x;
+            v.y += o.y;
+          }
+          if (lane == 0) {
+            CT w = W[i * P + p];
+            w.x += v.x;   // acc holds -sum, so adding applies the subtraction
+            w.y += v.y;
+            W[i * P + p] = w;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      const int i = i0 + lane;
+      CT w[kMaxPorts];
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
+      for (int t = 0; t < bs; ++t) {
+        const CT l = (lane < bs && lane > t) ? A[static_cast<size_t>(i) * lda + i0 + t] : czero(w[0]);
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) {
+          const CT y = shfl_c(w[p], t);
+          if (lane > t) w[p] = cfms(l, y, w[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p)
+        if (lane < bs && p < P) W[i * P + p] = w[p];
+    }
+    __syncthreads();
+  }
+  // backward: U x = y, blocks of 32 rows from the bottom
+  for (int i1 = N; i1 > 0; i1 -= 32) {
+    const int i0 = max(0, i1 - 32), bs = i1 - i0;
+    if (i1 < N) {
+      for (int ii = warp; ii < bs; ii += kWarps) {
+        const int i = i0 + ii;
+        CT acc[kMaxPorts];
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
+        const CT* row = A + static_cast<size_t>(i) * lda;
+        for (int t = i1 + lane; t < N; t += 32) {
+          const CT u = row[t];
+#pragma unroll
+          for (int p = 0; p < kMaxPorts; ++p)
+            if (p < P) acc[p] = cfms(u, W[t * P + p], acc[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) {
+          if (p >= P) break;
+          CT v = acc[p];
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) {
+            const CT o = shfl_c_down(v, d);
+            v.x += o.x;
+            v.y += o.y;
+          }
+          if (lane == 0) {
+            CT w = W[i * P + p];
+            w.x += v.x;
+            w.y += v.y;
+            W[i * P + p] = w;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      const int i = i0 + lane;
+      CT w[kMaxPorts];
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
+      for (int t = bs - 1; t >= 0; --t) {
+        if (lane == t) {
+          const CT d = A[static_cast<size_t>(i) * lda + i];
+          const CT inv = cabs2(d) > 0 ? cinv(d) : czero(d);
+#pragma unroll
+          for (int p = 0; p < kMaxPorts; ++p) w[p] = cmul(w[p], inv);
+        }
+        const CT u = (lane < t) ? A[static_cast<size_t>(i) * lda + i0 + t] : czero(w[0]);
+#pragma unroll
+        for (int p = 0; p < kMaxPorts; ++p) {
+          const CT y = shfl_c(w[p], t);
+          if (lane < t) w[p] = cfms(u, y, w[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p)
+        if (lane < bs && p < P) W[i * P + p] = w[p];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ refinement residual
+// r = V - Z_sub x in double from the stored entries; returns ||r||_inf (|re|+|im| norm) and
+// ||Z_sub||_inf in s_out[0..1].  x_s: shared copy of x (N x P double2).
+template <typename ZT>
+__device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N, const double2* x_s,
+                         int P, const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double rmax = 0.0, zmax = 0.0;
+  for (int i = warp; i < N; i += kWarps) {
+    const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
+    double2 acc[kMaxPorts];
+#pragma unroll
+    for (int p = 0; p < kMaxPorts; ++p) acc[p] = make_double2(0.0, 0.0);
+    double rowabs = 0.0;
+    for (int t = lane; t < N; t += 32) {
+      const double2 z = zload<ZT, double2>(zrow + s_idx[t]);
+      rowabs += fabs(z.x) + fabs(z.y);
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p)
+        if (p < P) acc[p] = cfma(z, x_s[t * P + p], acc[p]);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) rowabs += __shfl_down_sync(0xffffffffu, rowabs, d);
+#pragma unroll
+    for (int p = 0; p < kMaxPorts; ++p) {
+      if (p >= P) break;
+      double2 v = acc[p];
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, d);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, d);
+      }
+      if (lane == 0) {
+        const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
+        const double2 ri = make_double2(vv - v.x, -v.y);
+        r[i * P + p] = ri;
+        rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
+      }
+    }
+    if (lane == 0) zmax = fmax(zmax, rowabs);
+  }
+  if (lane == 0) {
+    s_red[warp] = rmax;
+    s_red[kWarps + warp] = zmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      a = fmax(a, s_red[w]);
+      b = fmax(b, s_red[kWarps + w]);
+    }
+    s_out[0] = a;
+    s_out[1] = b;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ Y -> S (Eq. 6-7), one thread
+__device__ void ports_to_s(const double2* x, int P, const double* lport, double Z0, double2* S, bool* nonfinite) {
+  double2 Am[kMaxPorts][kMaxPorts], Bm[kMaxPorts][kMaxPorts];
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      const double2 xv = x[(3 * i + 1) * P + j];
+      const double2 y = make_double2(lport[i] * xv.x, lport[i] * xv.y);
+      const double d = (i == j) ? 1.0 : 0.0;
+      Am[i][j] = make_double2(d + Z0 * y.x, Z0 * y.y);
+      Bm[i][j] = make_double2(d - Z0 * y.x, -Z0 * y.y);
+    }
+  // Gauss-Jordan with partial pivoting on (1 + Z0 Y) S = (1 - Z0 Y)
+  for (int k = 0; k < P; ++k) {
+    int p = k;
+    double best = cabs2(Am[k][k]);
+    for (int i = k + 1; i < P; ++i)
+      if (cabs2(Am[i][k]) > best) { best = cabs2(Am[i][k]); p = i; }
+    if (p != k)
+      for (int j = 0; j < P; ++j) {
+        double2 t = Am[k][j]; Am[k][j] = Am[p][j]; Am[p][j] = t;
+        t = Bm[k][j]; Bm[k][j] = Bm[p][j]; Bm[p][j] = t;
+      }
+    const double2 inv = cinv(Am[k][k]);
+    for (int j = 0; j < P; ++j) {
+      Am[k][j] = cmul(Am[k][j], inv);
+      Bm[k][j] = cmul(Bm[k][j], inv);
+    }
+    for (int i = 0; i < P; ++i) {
+      if (i == k) continue;
+      const double2 f = Am[i][k];
+      for (int j = 0; j < P; ++j) {
+        Am[i][j] = cfms(f, Am[k][j], Am[i][j]);
+        Bm[i][j] = cfms(f, Bm[k][j], Bm[i][j]);
+      }
+    }
+  }
+  bool bad = false;
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      S[i * P + j] = Bm[i][j];
+      if (!isfinite(Bm[i][j].x) || !isfinite(Bm[i][j].y)) bad = true;
+    }
+  *nonfinite = bad;
+}
+
+// ------------------------------------------------------------------ the evaluation kernel
+struct Slot {
+  size_t a_off, piv_off, x_off, r_off;
+};
+__host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_bytes) {
+  Slot s;
+  s.a_off = 0;
+  s.piv_off = s.a_off + static_cast<size_t>(M) * lda * ct_bytes;
+  s.piv_off = (s.piv_off + 255) & ~size_t(255);
+  s.x_off = s.piv_off + static_cast<size_t>(M) * sizeof(int);
+  s.x_off = (s.x_off + 255) & ~size_t(255);
+  s.r_off = s.x_off + static_cast<size_t>(M) * P * sizeof(double2);
+  s.r_off = (s.r_off + 255) & ~size_t(255);
+  return s;
+}
+
+template <typename CT>
+__host__ __device__ inline size_t smem_layout(int M, size_t* u_off, size_t* idx_off) {
+  constexpr int NB = Cfg<CT>::NB;
+  size_t panel = static_cast<size_t>(M) * (NB + 1) * sizeof(CT);
+  const size_t xcache = static_cast<size_t>(M) * kMaxPorts * sizeof(double2);
+  if (xcache > panel) panel = xcache;
+  panel = (panel + 15) & ~size_t(15);
+  *u_off = panel;
+  const size_t u = static_cast<size_t>(NB) * (kTile + 1) * sizeof(CT);
+  *idx_off = panel + ((u + 15) & ~size_t(15));
+  return *idx_off + static_cast<size_t>(M) * sizeof(int);
+}
+
+template <typename CT, typename ZT, bool MIXED>
+__global__ void __launch_bounds__(kThreads) eval_kernel(EvalArgs a) {
+  using R = typename Real<CT>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ R s_val[kWarps + 1];
+  __shared__ int s_row[kWarps + 1];
+  __shared__ double s_red[2 * kWarps];
+  __shared__ double s_norm[2];
+  __shared__ int s_task;
+  __shared__ int s_flag;
+  size_t u_off, idx_off;
+  smem_layout<CT>(a.M, &u_off, &idx_off);
+  CT* Pn = reinterpret_cast<CT*>(smem);
+  CT* Ut = reinterpret_cast<CT*>(smem + u_off);
+  int* s_idx = reinterpret_cast<int*>(smem + idx_off);
+  const int tid = threadIdx.x;
+  const int P = a.P, M = a.M, lda = a.lda;
+  const Slot sl = slot_layout(M, lda, P, sizeof(CT));
+  unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * blockIdx.x;
+  CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
+  int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
+  double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
+  double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
+  const ZT* Zall = static_cast<const ZT*>(a.Z);
+  const int ntasks = a.ntasks_list ? *a.repair_count : a.B * a.F;
+  double lport[kMaxPorts];
+#pragma unroll
+  for (int p = 0; p < kMaxPorts; ++p) lport[p] = a.port_len[p];
+
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(a.task_counter, 1);
+    __syncthreads();
+    const int tq = s_task;
+    __syncthreads();
+    if (tq >= ntasks) break;
+    const int t = a.ntasks_list ? a.repair_list[tq] : tq;
+    const int f = t / a.B, b = t % a.B;
+    const int N = a.n_act[b];
+    double2* Sout = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
+    if (N <= 0) {
+      if (tid < P * P) Sout[tid] = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
+      continue;
+    }
+    const ZT* Zf = Zall + static_cast<size_t>(f) * M * M;
+    const int32_t* gidx = a.idx + static_cast<size_t>(b) * M;
+    for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
+    __syncthreads();
+    // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
+    for (int i = 0; i < N; ++i) {
+      const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
+      CT* arow = A + static_cast<size_t>(i) * lda;
+      for (int j = tid; j < N; j += kThreads) arow[j] = zload<ZT, CT>(zrow + s_idx[j]);
+    }
+    __syncthreads();
+    const bool singular = lu_factor<CT>(A, lda, N, piv, Pn, Ut, s_val, s_row);
+    // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
+    CT* W = Pn;
+    for (int e = tid; e < N * P; e += kThreads) {
+      const int i = e / P, p = e % P;
+      W[e] = from_d2<CT>(make_double2(i == 3 * p + 1 ? lport[p] : 0.0, 0.0));
+    }
+    __syncthreads();
+    lu_solve<CT>(A, lda, N, piv, W, P);
+    for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
+    __syncthreads();
+    int iters = 0;
+    bool repaired = false;
+    if (MIXED) {
+      double rprev = 0.0;
+      double2* xs = reinterpret_cast<double2*>(Pn);
+      const double vnorm = fmax(fmax(lport[0], P > 1 ? lport[1] : 0.0), fmax(P > 2 ? lport[2] : 0.0, P > 3 ? lport[3] : 0.0));
+      bool converged = false;
+      for (int it = 0; it <= kMaxRefine; ++it) {
+        for (int e = tid; e < N * P; e += kThreads) xs[e] = X[e];
+        __syncthreads();
+        residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
+        double xmax = 0.0;
+        // ||x||_inf (|re|+|im|), reduced over the block
+        for (int e = tid; e < N * P; e += kThreads) xmax = fmax(xmax, fabs(xs[e].x) + fabs(xs[e].y));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
+        if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
+        __syncthreads();
+        if (tid == 0) {
+          double m = 0.0;
+          for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
+          const double rn = s_norm[0], zn = s_norm[1];
+          const double eta = rn / (zn * m + vnorm);
+          int flag = 0;   // 0 continue, 1 converged, 2 stop (stagnated or out of iterations)
+          if (eta <= 4.0 * DBL_EPSILON) flag = 1;
+          else if (it > 0 && rn > 0.5 * rprev) flag = (eta <= 1e-12) ? 1 : 2;
+          else if (it == kMaxRefine) flag = (eta <= 1e-12) ? 1 : 2;
+          s_flag = flag;
+          s_norm[0] = rn;
+        }
+        __syncthreads();
+        const int flag = s_flag;
+        rprev = s_norm[0];
+        if (flag != 0) {
+          converged = flag == 1;
+          break;
+        }
+        for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
+        __syncthreads();
+        lu_solve<CT>(A, lda, N, piv, W, P);
+        for (int e = tid; e < N * P; e += kThreads) {
+          const double2 d = to_d2(W[e]);
+          X[e] = make_double2(X[e].x + d.x, X[e].y + d.y);
+        }
+        __syncthreads();
+        ++iters;
+      }
+      if (!converged) repaired = true;
+    }
+    if (tid == 0) {
+      if (MIXED) {
+        atomicAdd(&a.counters[0], static_cast<unsigned long long>(iters));
+        atomicMax(&a.counters[1], static_cast<unsigned long long>(iters));
+      }
+      atomicAdd(&a.counters[3], 1ull);
+      if (repaired) {
+        const int slot = atomicAdd(a.repair_count, 1);
+        a.repair_list[slot] = t;
+        atomicAdd(&a.counters[2], 1ull);
+        atomicOr(&a.flags[b], kFlagRepaired);
+      } else {
+        bool nonfinite = false;
+        ports_to_s(X, P, lport, a.Z0, Sout, &nonfinite);
+        if (nonfinite) atomicOr(&a.flags[b], kFlagNonfinite);
+        if (singular) atomicOr(&a.flags[b], kFlagSingular);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ FoM (Eq. 8-9)
+__device__ __forceinline__ double sdb(double2 s) {
+  double m = sqrt(s.x * s.x + s.y * s.y);
+  if (m < 1e-15) m = 1e-15;
+  return 20.0 * log10(m);
+}
+
+__global__ void fom_kernel(const double2* __restrict__ S, const uint8_t* __restrict__ bands, int F, int P, int B,
+                           const uint32_t* __restrict__ flags, const int32_t* __restrict__ n_act, double* __restrict__ fom,
+                           int32_t* __restrict__ status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double sum = 0.0;
+  if (P >= 3 && n_act[b] >= 0) {
+    for (int f = 0; f < F; ++f) {
+      const double2* s = S + (static_cast<size_t>(b) * F + f) * P * P;
+      const double s11 = sdb(s[0]), s21 = sdb(s[1 * P + 0]), s31 = sdb(s[2 * P + 0]), s32 = sdb(s[2 * P + 1]);
+      switch (bands[f]) {
+        case 0:  // 1/rw_p1 + 1/rw_m1 + 1/rw_s2
+          sum += pow(10.0, -(s21 + 1.0) / 10.0) + pow(10.0, (15.0 + s11) / 10.0) + pow(10.0, (s31 + 35.0) / 15.0);
+          break;
+        case 1:  // 1/rw_p2 + 1/rw_m2 + 1/rw_s1
+          sum += pow(10.0, -(s31 + 1.0) / 10.0) + pow(10.0, (15.0 + s11) / 10.0) + pow(10.0, (s21 + 35.0) / 15.0);
+          break;
+        case 2:  // 1/rw_oi
+          sum += pow(10.0, (s32 + 20.0) / 15.0);
+          break;
+        case 3:  // 1/rw_s3 + 1/rw_s4
+          sum += pow(10.0, (s21 + 20.0) / 18.0) + pow(10.0, (s31 + 20.0) / 18.0);
+          break;
+        default: break;
+      }
+    }
+  }
+  const uint32_t fl = flags[b];
+  int32_t st = PMOM_CAND_OK;
+  if (n_act[b] < 0 || (fl & kFlagBadState)) {
+    st = PMOM_CAND_BAD_STATE;
+    sum = __longlong_as_double(0x7ff8000000000000ll);
+  } else if ((fl & kFlagNonfinite) || !isfinite(sum)) st = PMOM_CAND_NONFINITE;
+  else if (fl & kFlagSingular) st = PMOM_CAND_SINGULAR;
+  else if (fl & kFlagRepaired) st = PMOM_CAND_REPAIRED;
+  fom[b] = sum;
+  status[b] = st;
+}
+
+template <typename ZT>
+__global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int32_t* __restrict__ idx, int N,
+                              ZT* __restrict__ out) {
+  const ZT* Zf = Z + static_cast<size_t>(f) * M * M;
+  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    const ZT* zrow = Zf + static_cast<size_t>(idx[i]) * M;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) out[static_cast<size_t>(i) * N + j] = zrow[idx[j]];
+  }
+}
+
+template <typename CT, typename ZT, bool MIXED>
+cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
+  size_t u_off, idx_off;
+  const size_t smem = smem_layout<CT>(a.M, &u_off, &idx_off);
+  auto k = eval_kernel<CT, ZT, MIXED>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k<<<nslots, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename CT, typename ZT, bool MIXED>
+int blocks_per_sm_t(int M) {
+  size_t u_off, idx_off;
+  const size_t smem = smem_layout<CT>(M, &u_off, &idx_off);
+  auto k = eval_kernel<CT, ZT, MIXED>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
+  activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.idx, a.n_act, a.flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {
+  if (precision == PMOM_FP64) {
+    return a.z_c128 ? launch_eval_t<double2, double2, false>(a, nslots, s)
+                    : launch_eval_t<double2, float2, false>(a, nslots, s);
+  }
+  return a.z_c128 ? launch_eval_t<float2, double2, true>(a, nslots, s) : launch_eval_t<float2, float2, true>(a, nslots, s);
+}
+
+int eval_blocks_per_sm(int precision, int M, int z_c128) {
+  if (precision == PMOM_FP64)
+    return z_c128 ? blocks_per_sm_t<double2, double2, false>(M) : blocks_per_sm_t<double2, float2, false>(M);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true>(M) : blocks_per_sm_t<float2, float2, true>(M);
+}
+
+size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
+  *lda = (M + 3) & ~3;
+  const size_t ct = precision == PMOM_FP64 ? sizeof(double2) : sizeof(float2);
+  const Slot s = slot_layout(M, *lda, P, ct);
+  size_t bytes = s.r_off + static_cast<size_t>(M) * P * sizeof(double2);
+  return (bytes + 255) & ~size_t(255);
+}
+
+size_t eval_smem_bytes(int precision, int M, int P) {
+  (void)P;
+  size_t u_off, idx_off;
+  return precision == PMOM_FP64 ? smem_layout<double2>(M, &u_off, &idx_off) : smem_layout<float2>(M, &u_off, &idx_off);
+}
+
+cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int B, const uint32_t* flags,
+                       const int32_t* n_act, double* fom, int32_t* status, cudaStream_t s) {
+  fom_kernel<<<(B + 127) / 128, 128, 0, s>>>(S, bands, F, P, B, flags, n_act, fom, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
+                          cudaStream_t s) {
+  const int grid = N < 1024 ? (N > 0 ? N : 1) : 1024;
+  if (z_c128)
+    gather_kernel<double2><<<grid, 256, 0, s>>>(static_cast<const double2*>(Z), M, f, idx, N, static_cast<double2*>(out));
+  else
+    gather_kernel<float2><<<grid, 256, 0, s>>>(static_cast<const float2*>(Z), M, f, idx, N, static_cast<float2*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace pmom

@@ -1,0 +1,525 @@
+// GPU fill of the parent interaction matrix Z(f) (paper Phase 2, Eq. 1-2, RWG basis).
+//
+// Galerkin MPIE, e^{+jwt}:  Z_mn = jw mu0 <f_m, G f_n> + <div f_m, G div f_n> / (jw eps),
+// eps = eps0 eps_r (1 - j tan d) (microstrip: Hammerstad-Jensen eps_eff of a strip w = pitch).
+// Green's function of the homogeneous stack-up:
+//   microstrip  G = g(R) - g(R'), R' to the image below the ground plane z = 0
+//   stripline   Dirichlet function of the plates z = 0, H: for lateral distance rho >= H/2 the
+//               waveguide-mode sum (1/(pi H)) sum_m sin(m pi z/H) sin(m pi z'/H) K0(gamma_m rho);
+//               below H/2 the images with |n| <= 16 plus a quadratic in rho^2 matched to the mode
+//               sum at rho = H/2, 3H/4, H (the remaining images are smooth and even in rho).
+// Triangle pairs related by a lattice translation (same layers, orientations, halves and
+// offset) share one integration: one thread integrates one such class at one frequency
+// (7-point rule x 7-point rule when the centroids are at least two longest edges apart; else
+// 13 x 13 with the 1/(4 pi R) part of the direct term integrated analytically over the source
+// triangle).  A second kernel assembles Z_mn from the class table and stores (Z_mn + Z_nm)/2.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "pmom_internal.h"
+
+namespace pmom {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 4.0e-7 * kPi;
+constexpr int kImages = 16;
+constexpr int kMaxLayers = 8;
+
+struct FillTri {
+  double v[3][3];
+  double c[3];
+  double area, lmax;
+  int layer;
+};
+
+struct Medium {
+  double omega, H, rho_s;
+  double2 k;       // complex wavenumber
+  double2 eps;     // complex permittivity
+  int stripline;
+  double z[kMaxLayers];
+  int layers;
+};
+
+// ------------------------------------------------------------------ complex double helpers
+__device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 ca(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cs(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cexp_(double2 a) {
+  double s, c;
+  sincos(a.y, &s, &c);
+  const double e = exp(a.x);
+  return make_double2(e * c, e * s);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 csqrt_(double2 a) {
+  const double r = hypot(a.x, a.y);
+  double re = sqrt(0.5 * (r + a.x));
+  double im = sqrt(0.5 * (r - a.x));
+  if (a.y < 0) im = -im;
+  return make_double2(re, im);
+}
+
+// exp(-j k R) / (4 pi R)
+__device__ __forceinline__ double2 g_free(double2 k, double R) {
+  // -j k R = (k.y R) + j(-k.x R)
+  return cscale(cexp_(make_double2(k.y * R, -k.x * R)), 1.0 / (4.0 * kPi * R));
+}
+// (exp(-j k R) - 1) / (4 pi R), finite as R -> 0
+__device__ __forceinline__ double2 g_free_smooth(double2 k, double R) {
+  const double2 x = make_double2(k.y * R, -k.x * R);
+  if (x.x * x.x + x.y * x.y < 1e-6) {
+    // -jk (1 + x/2 + x^2/6 + x^3/24)
+    double2 t = ca(make_double2(1.0, 0.0), cscale(x, 0.5));
+    const double2 x2 = cm(x, x);
+    t = ca(t, cscale(x2, 1.0 / 6.0));
+    t = ca(t, cscale(cm(x2, x), 1.0 / 24.0));
+    return cscale(cm(make_double2(k.y, -k.x), t), 1.0 / (4.0 * kPi));
+  }
+  const double2 e = cexp_(x);
+  return cscale(make_double2(e.x - 1.0, e.y), 1.0 / (4.0 * kPi * R));
+}
+
+// K0(w), Re w > 0: trapezoidal rule on K0(w) = int_0^inf exp(-w cosh t) dt.
+__device__ double2 bessel_k0(double2 w) {
+  const double aw = hypot(w.x, w.y);
+  double h = 0.6 / sqrt(aw);
+  h = h > 0.2 ? 0.2 : h;
+  double2 sum = cscale(cexp_(make_double2(-w.x, -w.y)), 0.5);
+  for (int j = 1; j < 20000; ++j) {
+    const double ch = cosh(j * h);
+    if (w.x * (ch - 1.0) > 40.0) break;
+    sum = ca(sum, cexp_(make_double2(-w.x * ch, -w.y * ch)));
+  }
+  return cscale(sum, h);
+}
+
+__device__ double2 strip_modes(const Medium& md, double zp, double zq, double rho) {
+  double2 s = make_double2(0.0, 0.0);
+  const double2 k2 = cm(md.k, md.k);
+  for (int m = 1; m < 4000; ++m) {
+    const double km = m * kPi / md.H;
+    const double2 gam = csqrt_(make_double2(km * km - k2.x, -k2.y));
+    if (gam.x * rho > 40.0) break;
+    const double w = sin(km * zp) * sin(km * zq);
+    s = ca(s, cscale(bessel_k0(cscale(gam, rho)), w));
+  }
+  return cscale(s, 1.0 / (kPi * md.H));
+}
+
+// image sum |n| <= kImages; `smooth` replaces the direct term by its R -> 0 regular part
+__device__ double2 strip_images(const Medium& md, double zp, double zq, double rho, bool smooth) {
+  double2 s = make_double2(0.0, 0.0);
+  const double r2 = rho * rho;
+  for (int n = -kImages; n <= kImages; ++n) {
+    const double a = zp - zq + 2.0 * n * md.H, b = zp + zq + 2.0 * n * md.H;
+    const double Ra = sqrt(r2 + a * a), Rb = sqrt(r2 + b * b);
+    s = ca(s, (n == 0 && smooth) ? g_free_smooth(md.k, Ra) : g_free(md.k, Ra));
+    s = cs(s, g_free(md.k, Rb));
+  }
+  return s;
+}
+
+// G(rho) between layers lp, lq; smooth = true returns G - 1/(4 pi R_direct).
+__device__ double2 green(const Medium& md, const double2* fit, int lp, int lq, double rho, bool smooth) {
+  const double zp = md.z[lp], zq = md.z[lq];
+  if (!md.stripline) {
+    const double Rd = sqrt(rho * rho + (zp - zq) * (zp - zq)), Ri = sqrt(rho * rho + (zp + zq) * (zp + zq));
+    return cs(smooth ? g_free_smooth(md.k, Rd) : g_free(md.k, Rd), g_free(md.k, Ri));
+  }
+  if (rho >= md.rho_s) {
+    double2 G = strip_modes(md, zp, zq, rho);
+    if (smooth) G.x -= 1.0 / (4.0 * kPi * sqrt(rho * rho + (zp - zq) * (zp - zq)));
+    return G;
+  }
+  const double2* c = fit + 3 * (lp * md.layers + lq);
+  const double x = rho * rho;
+  return ca(strip_images(md, zp, zq, rho, smooth), ca(c[0], cscale(ca(c[1], cscale(c[2], x)), x)));
+}
+
+// ------------------------------------------------------------------ quadrature (barycentric)
+// Radon 7-point, degree 5; Dunavant 13-point, degree 7.
+__constant__ double kQ7[7][4];
+__constant__ double kQ13[13][4];
+
+void host_rules(double q7[7][4], double q13[13][4]) {
+  const double s = std::sqrt(15.0);
+  const double a1 = (6.0 - s) / 21.0, w1 = (155.0 - s) / 1200.0;
+  const double a2 = (6.0 + s) / 21.0, w2 = (155.0 + s) / 1200.0;
+  double r7[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 0.225},
+                     {1 - 2 * a1, a1, a1, w1}, {a1, 1 - 2 * a1, a1, w1}, {a1, a1, 1 - 2 * a1, w1},
+                     {1 - 2 * a2, a2, a2, w2}, {a2, 1 - 2 * a2, a2, w2}, {a2, a2, 1 - 2 * a2, w2}};
+  std::memcpy(q7, r7, sizeof(r7));
+  const double b1 = 0.260345966079040, v1 = 0.175615257433208;
+  const double b2 = 0.065130102902216, v2 = 0.053347235608838;
+  const double c1 = 0.048690315425316, c2 = 0.312865496004874, c3 = 0.638444188569810, v3 = 0.077113760890257;
+  double r13[13][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, -0.149570044467682},
+                       {1 - 2 * b1, b1, b1, v1}, {b1, 1 - 2 * b1, b1, v1}, {b1, b1, 1 - 2 * b1, v1},
+                       {1 - 2 * b2, b2, b2, v2}, {b2, 1 - 2 * b2, b2, v2}, {b2, b2, 1 - 2 * b2, v2},
+                       {c1, c2, c3, v3}, {c1, c3, c2, v3}, {c2, c1, c3, v3},
+                       {c2, c3, c1, v3}, {c3, c1, c2, v3}, {c3, c2, c1, v3}};
+  std::memcpy(q13, r13, sizeof(r13));
+}
+
+// Analytic integrals over planar triangle T of 1/R and (rho' - rho)/R for observation point r
+// (Wilton et al. 1984): I1 and the in-plane vector Iv.
+__device__ void potentials(const FillTri& t, const double r[3], double* I1, double Iv[3]) {
+  double e1[3], e2[3], n[3];
+  for (int i = 0; i < 3; ++i) { e1[i] = t.v[1][i] - t.v[0][i]; e2[i] = t.v[2][i] - t.v[0][i]; }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int i = 0; i < 3; ++i) n[i] /= nn;
+  const double d = n[0] * (r[0] - t.v[0][0]) + n[1] * (r[1] - t.v[0][1]) + n[2] * (r[2] - t.v[0][2]);
+  const double ad = fabs(d);
+  const double p[3] = {r[0] - d * n[0], r[1] - d * n[1], r[2] - d * n[2]};
+  double s = 0.0, sv[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i) {
+    const double* A = t.v[i];
+    const double* B = t.v[(i + 1) % 3];
+    double l[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double len = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    for (int k = 0; k < 3; ++k) l[k] /= len;
+    const double u[3] = {l[1] * n[2] - l[2] * n[1], l[2] * n[0] - l[0] * n[2], l[0] * n[1] - l[1] * n[0]};
+    const double am[3] = {A[0] - p[0], A[1] - p[1], A[2] - p[2]};
+    const double bm[3] = {B[0] - p[0], B[1] - p[1], B[2] - p[2]};
+    const double lm = am[0] * l[0] + am[1] * l[1] + am[2] * l[2];
+    const double lp = bm[0] * l[0] + bm[1] * l[1] + bm[2] * l[2];
+    const double tt = am[0] * u[0] + am[1] * u[1] + am[2] * u[2];
+    const double R02 = tt * tt + d * d;
+    const double Rm = sqrt(R02 + lm * lm), Rp = sqrt(R02 + lp * lp);
+    double lg = 0.0;
+    if (R02 > 1e-30 * len * len) {
+      const double num = lp >= 0 ? Rp + lp : R02 / (Rp - lp);
+      const double den = lm >= 0 ? Rm + lm : R02 / (Rm - lm);
+      lg = log(num / den);
+      s += tt * lg;
+      if (ad > 0) s -= ad * (atan(tt * lp / (R02 + ad * Rp)) - atan(tt * lm / (R02 + ad * Rm)));
+    }
+    const double vv = R02 * lg + lp * Rp - lm * Rm;
+    for (int k = 0; k < 3; ++k) sv[k] += 0.5 * u[k] * vv;
+  }
+  *I1 = s;
+  Iv[0] = sv[0]; Iv[1] = sv[1]; Iv[2] = sv[2];
+}
+
+__global__ void fit_kernel(const Medium* __restrict__ media, double2* __restrict__ fits, int L) {
+  const int f = blockIdx.x, pq = threadIdx.x;
+  if (pq >= L * L) return;
+  const Medium md = media[f];
+  double2* c = fits + (static_cast<size_t>(f) * L * L + pq) * 3;
+  if (!md.stripline) {
+    c[0] = c[1] = c[2] = make_double2(0.0, 0.0);
+    return;
+  }
+  const int lp = pq / L, lq = pq % L;
+  double x[3];
+  double2 y[3];
+  for (int i = 0; i < 3; ++i) {
+    const double rho = md.rho_s * (1.0 + 0.5 * i);
+    x[i] = rho * rho;
+    y[i] = cs(strip_modes(md, md.z[lp], md.z[lq], rho), strip_images(md, md.z[lp], md.z[lq], rho, false));
+  }
+  // Lagrange form of the quadratic in x through the three points, expanded to c0 + c1 x + c2 x^2
+  double2 c0 = make_double2(0, 0), c1 = c0, c2 = c0;
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    const double den = (x[i] - x[j]) * (x[i] - x[k]);
+    c2 = ca(c2, cscale(y[i], 1.0 / den));
+    c1 = ca(c1, cscale(y[i], -(x[j] + x[k]) / den));
+    c0 = ca(c0, cscale(y[i], x[j] * x[k] / den));
+  }
+  c[0] = c0; c[1] = c1; c[2] = c2;
+}
+
+// One thread: integrals of one translation class at one frequency.
+// out[0] = int int G, out[1 + 3a + b] = int int (r - v_a).(r' - v_b) G.
+__global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ tris, const int2* __restrict__ rep, int U,
+                                                     const Medium* __restrict__ media, const double2* __restrict__ fits,
+                                                     int L, int F, double2* __restrict__ out) {
+  const long gid = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= static_cast<long>(U) * F) return;
+  const int f = static_cast<int>(gid / U), u = static_cast<int>(gid % U);
+  const Medium md = media[f];
+  const double2* fit = fits + static_cast<size_t>(f) * L * L * 3;
+  const FillTri p = tris[rep[u].x];
+  const FillTri q = tris[rep[u].y];
+  double2 acc[10];
+  for (int i = 0; i < 10; ++i) acc[i] = make_double2(0.0, 0.0);
+  const double dc = sqrt((p.c[0] - q.c[0]) * (p.c[0] - q.c[0]) + (p.c[1] - q.c[1]) * (p.c[1] - q.c[1]) +
+                         (p.c[2] - q.c[2]) * (p.c[2] - q.c[2]));
+  const double lmax = fmax(p.lmax, q.lmax);
+  const bool near = dc < 2.0 * lmax * (1.0 + 1e-9);
+  const int nq = near ? 13 : 7;
+  const double(*Q)[4] = near ? kQ13 : kQ7;
+  for (int i = 0; i < nq; ++i) {
+    double r[3];
+    for (int k = 0; k < 3; ++k) r[k] = Q[i][0] * p.v[0][k] + Q[i][1] * p.v[1][k] + Q[i][2] * p.v[2][k];
+    const double wo = Q[i][3] * p.area;
+    double ra[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) ra[a][k] = r[k] - p.v[a][k];
+    if (near) {
+      double I1, Iv[3];
+      potentials(q, r, &I1, Iv);
+      const double s = wo / (4.0 * kPi);
+      acc[0].x += s * I1;
+      const double r0[3] = {r[0], r[1], q.v[0][2]};
+      for (int b = 0; b < 3; ++b) {
+        double tv[3];
+        for (int k = 0; k < 3; ++k) tv[k] = Iv[k] + (r0[k] - q.v[b][k]) * I1;
+        for (int a = 0; a < 3; ++a) acc[1 + 3 * a + b].x += s * (ra[a][0] * tv[0] + ra[a][1] * tv[1] + ra[a][2] * tv[2]);
+      }
+    }
+    for (int j = 0; j < nq; ++j) {
+      double rq[3];
+      for (int k = 0; k < 3; ++k) rq[k] = Q[j][0] * q.v[0][k] + Q[j][1] * q.v[1][k] + Q[j][2] * q.v[2][k];
+      const double rho = hypot(r[0] - rq[0], r[1] - rq[1]);
+      const double2 G = cscale(green(md, fit, p.layer, q.layer, rho, near), wo * Q[j][3] * q.area);
+      acc[0] = ca(acc[0], G);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          const double dd = ra[a][0] * (rq[0] - q.v[b][0]) + ra[a][1] * (rq[1] - q.v[b][1]) + ra[a][2] * (rq[2] - q.v[b][2]);
+          acc[1 + 3 * a + b] = ca(acc[1 + 3 * a + b], cscale(G, dd));
+        }
+    }
+  }
+  double2* o = out + gid * 10;
+  for (int i = 0; i < 10; ++i) o[i] = acc[i];
+}
+
+struct BfGeom {
+  int tp, tm;        // triangle indices of T+ and T-
+  int fp, fm;        // free vertex indices
+  double len;        // edge length
+};
+
+__device__ __forceinline__ double2 zmn(const BfGeom& m, const BfGeom& n, const FillTri* tris, const int* pair_class, int T,
+                                       const double2* cls, double2 jwmu, double2 inv_jweps) {
+  double2 z = make_double2(0.0, 0.0);
+  const int tm[2] = {m.tp, m.tm}, fm[2] = {m.fp, m.fm};
+  const int tn[2] = {n.tp, n.tm}, fn[2] = {n.fp, n.fm};
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 2; ++t) {
+      const double2* v = cls + static_cast<size_t>(pair_class[tm[s] * T + tn[t]]) * 10;
+      const double aa = tris[tm[s]].area * tris[tn[t]].area;
+      const double sg = (s == t ? 1.0 : -1.0) * m.len * n.len;
+      const double2 vec = cm(cscale(jwmu, 0.25 / aa), v[1 + 3 * fm[s] + fn[t]]);
+      const double2 sca = cm(cscale(inv_jweps, 1.0 / aa), v[0]);
+      z = ca(z, cscale(ca(vec, sca), sg));
+    }
+  return z;
+}
+
+template <typename ZT>
+__global__ void assemble_kernel(const BfGeom* __restrict__ bfs, int M, const FillTri* __restrict__ tris,
+                                const int* __restrict__ pair_class, int T, const double2* __restrict__ cls_all, int U,
+                                const Medium* __restrict__ media, ZT* __restrict__ Z) {
+  const int f = blockIdx.y;
+  const long e = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= static_cast<long>(M) * M) return;
+  const int m = static_cast<int>(e / M), n = static_cast<int>(e % M);
+  const Medium md = media[f];
+  const double2 jwmu = make_double2(0.0, md.omega * kMu0);
+  const double2 inv_jweps = cdiv(make_double2(1.0, 0.0), cm(make_double2(0.0, md.omega), md.eps));
+  const double2* cls = cls_all + static_cast<size_t>(f) * U * 10;
+  const BfGeom bm = bfs[m], bn = bfs[n];
+  const double2 a = zmn(bm, bn, tris, pair_class, T, cls, jwmu, inv_jweps);
+  const double2 b = zmn(bn, bm, tris, pair_class, T, cls, jwmu, inv_jweps);
+  const double2 z = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+  ZT out;
+  out.x = z.x;
+  out.y = z.y;
+  Z[static_cast<size_t>(f) * M * M + e] = out;
+}
+
+double hj_eps_eff(const Grid& g) {
+  double h = 0.0;
+  for (double z : g.layer_z) h = std::max(h, z);
+  const double u = g.pitch / h, er = g.eps_r;
+  const double a = 1.0 + std::log((std::pow(u, 4) + std::pow(u / 52.0, 2)) / (std::pow(u, 4) + 0.432)) / 49.0 +
+                   std::log(1.0 + std::pow(u / 18.1, 3)) / 18.7;
+  const double b = 0.564 * std::pow((er - 0.9) / (er + 3.0), 0.053);
+  return 0.5 * (er + 1.0) + 0.5 * (er - 1.0) * std::pow(1.0 + 10.0 / u, -a * b);
+}
+
+void key_triangle(const Grid& g, int32_t key, FillTri* t) {
+  const int half = key & 1;
+  int k = key >> 1;
+  const int x = k % 128 - 4;
+  k /= 128;
+  const int y = k % 128 - 4;
+  const int layer = k / 128;
+  static const int corner[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
+  static const int tri[2][2][3] = {{{0, 1, 2}, {1, 3, 2}}, {{0, 1, 3}, {0, 3, 2}}};
+  const int o = (x + y) & 1;
+  double lmax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const int cc = tri[o][half][i];
+    t->v[i][0] = (x + corner[cc][0]) * g.pitch;
+    t->v[i][1] = (y + corner[cc][1]) * g.pitch;
+    t->v[i][2] = g.layer_z[layer];
+  }
+  for (int i = 0; i < 3; ++i) {
+    t->c[i] = (t->v[0][i] + t->v[1][i] + t->v[2][i]) / 3.0;
+    const double dx = t->v[(i + 1) % 3][0] - t->v[i][0], dy = t->v[(i + 1) % 3][1] - t->v[i][1];
+    lmax = std::max(lmax, std::sqrt(dx * dx + dy * dy));
+  }
+  t->area = 0.5 * g.pitch * g.pitch;
+  t->lmax = lmax;
+  t->layer = layer;
+}
+
+}  // namespace
+}  // namespace pmom
+
+namespace pmom {
+
+pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,
+                   cudaStream_t s, void** d_Z_out, std::string* err) {
+  if (g.layers > kMaxLayers) return PMOM_ERR_UNSUPPORTED;
+  // distinct triangles
+  std::unordered_map<int32_t, int> tri_of;
+  std::vector<FillTri> tris;
+  std::vector<int32_t> keys;
+  for (int m = 0; m < M; ++m)
+    for (int sd = 0; sd < 2; ++sd) {
+      const int32_t k = table[static_cast<size_t>(m) * kTableCols + 4 + sd];
+      if (!tri_of.count(k)) {
+        tri_of[k] = static_cast<int>(tris.size());
+        FillTri t;
+        key_triangle(g, k, &t);
+        tris.push_back(t);
+        keys.push_back(k);
+      }
+    }
+  const int T = static_cast<int>(tris.size());
+  // translation classes
+  std::unordered_map<long long, int> cls_of;
+  std::vector<int2> rep;
+  std::vector<int> pair_class(static_cast<size_t>(T) * T);
+  for (int p = 0; p < T; ++p) {
+    const int32_t kp = keys[p];
+    const int hp = kp & 1, xp = (kp >> 1) % 128, yp = ((kp >> 1) / 128) % 128, lp = (kp >> 1) / (128 * 128);
+    for (int q = 0; q < T; ++q) {
+      const int32_t kq = keys[q];
+      const int hq = kq & 1, xq = (kq >> 1) % 128, yq = ((kq >> 1) / 128) % 128, lq = (kq >> 1) / (128 * 128);
+      const long long key = ((((((static_cast<long long>(lp) * 8 + lq) * 2 + ((xp + yp) & 1)) * 2 + hp) * 2 + hq) * 512 +
+                              (xq - xp + 256)) * 512) + (yq - yp + 256);
+      auto it = cls_of.find(key);
+      int c;
+      if (it == cls_of.end()) {
+        c = static_cast<int>(rep.size());
+        cls_of.emplace(key, c);
+        rep.push_back(make_int2(p, q));
+      } else {
+        c = it->second;
+      }
+      pair_class[static_cast<size_t>(p) * T + q] = c;
+    }
+  }
+  const int U = static_cast<int>(rep.size());
+  std::vector<BfGeom> bfs(M);
+  for (int m = 0; m < M; ++m) {
+    const int32_t* r = &table[static_cast<size_t>(m) * kTableCols];
+    BfGeom b;
+    b.tp = tri_of[r[4]];
+    b.tm = tri_of[r[5]];
+    b.fp = r[6];
+    b.fm = r[7];
+    const FillTri& t = tris[b.tp];
+    const double* v1 = t.v[(b.fp + 1) % 3];
+    const double* v2 = t.v[(b.fp + 2) % 3];
+    b.len = std::sqrt((v1[0] - v2[0]) * (v1[0] - v2[0]) + (v1[1] - v2[1]) * (v1[1] - v2[1]) + (v1[2] - v2[2]) * (v1[2] - v2[2]));
+    bfs[m] = b;
+  }
+  std::vector<Medium> media(F);
+  const double er = g.medium == 0 ? hj_eps_eff(g) : g.eps_r;
+  const double eps0 = 1.0 / (kMu0 * kC0 * kC0);
+  for (int f = 0; f < F; ++f) {
+    Medium& md = media[f];
+    md.omega = 2.0 * kPi * freqs[f];
+    md.eps = make_double2(eps0 * er, -eps0 * er * g.tan_d);
+    // k = w sqrt(mu0 eps): principal square root of mu0 eps
+    const double ar = kMu0 * md.eps.x, ai = kMu0 * md.eps.y;
+    const double r = std::hypot(ar, ai);
+    double sr = std::sqrt(0.5 * (r + ar)), si = std::sqrt(0.5 * (r - ar));
+    if (ai < 0) si = -si;
+    md.k = make_double2(md.omega * sr, md.omega * si);
+    md.stripline = g.medium == 1;
+    md.H = g.h_total;
+    md.rho_s = 0.5 * g.h_total;
+    md.layers = g.layers;
+    for (int l = 0; l < kMaxLayers; ++l) md.z[l] = l < g.layers ? g.layer_z[l] : 0.0;
+  }
+  double q7[7][4], q13[13][4];
+  host_rules(q7, q13);
+  FillTri* d_tris = nullptr;
+  int2* d_rep = nullptr;
+  int* d_pc = nullptr;
+  BfGeom* d_bfs = nullptr;
+  Medium* d_media = nullptr;
+  double2* d_fit = nullptr;
+  double2* d_cls = nullptr;
+  void* d_Z = nullptr;
+  const size_t zel = dtype == PMOM_C128 ? sizeof(double2) : sizeof(float2);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(cudaMemcpyToSymbolAsync(kQ7, q7, sizeof(q7), 0, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyToSymbolAsync(kQ13, q13, sizeof(q13), 0, cudaMemcpyHostToDevice, s));
+  chk(cudaMalloc(&d_tris, sizeof(FillTri) * T));
+  chk(cudaMalloc(&d_rep, sizeof(int2) * U));
+  chk(cudaMalloc(&d_pc, sizeof(int) * pair_class.size()));
+  chk(cudaMalloc(&d_bfs, sizeof(BfGeom) * M));
+  chk(cudaMalloc(&d_media, sizeof(Medium) * F));
+  chk(cudaMalloc(&d_fit, sizeof(double2) * 3 * g.layers * g.layers * F));
+  chk(cudaMalloc(&d_cls, sizeof(double2) * 10 * static_cast<size_t>(U) * F));
+  chk(cudaMalloc(&d_Z, zel * static_cast<size_t>(F) * M * M));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(d_tris, tris.data(), sizeof(FillTri) * T, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(d_rep, rep.data(), sizeof(int2) * U, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(d_pc, pair_class.data(), sizeof(int) * pair_class.size(), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(d_bfs, bfs.data(), sizeof(BfGeom) * M, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(d_media, media.data(), sizeof(Medium) * F, cudaMemcpyHostToDevice, s));
+  }
+  if (e == cudaSuccess) {
+    fit_kernel<<<F, 64, 0, s>>>(d_media, d_fit, g.layers);
+    chk(cudaGetLastError());
+    const long work = static_cast<long>(U) * F;
+    class_kernel<<<static_cast<unsigned>((work + 127) / 128), 128, 0, s>>>(d_tris, d_rep, U, d_media, d_fit, g.layers, F, d_cls);
+    chk(cudaGetLastError());
+    const dim3 grid(static_cast<unsigned>((static_cast<long>(M) * M + 255) / 256), F);
+    if (dtype == PMOM_C128)
+      assemble_kernel<double2><<<grid, 256, 0, s>>>(d_bfs, M, d_tris, d_pc, T, d_cls, U, d_media, static_cast<double2*>(d_Z));
+    else
+      assemble_kernel<float2><<<grid, 256, 0, s>>>(d_bfs, M, d_tris, d_pc, T, d_cls, U, d_media, static_cast<float2*>(d_Z));
+    chk(cudaGetLastError());
+    chk(cudaStreamSynchronize(s));
+  }
+  cudaFree(d_tris);
+  cudaFree(d_rep);
+  cudaFree(d_pc);
+  cudaFree(d_bfs);
+  cudaFree(d_media);
+  cudaFree(d_fit);
+  cudaFree(d_cls);
+  if (e != cudaSuccess) {
+    if (d_Z) cudaFree(d_Z);
+    *err = std::string("fill_Z: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PMOM_ERR_OOM : PMOM_ERR_CUDA;
+  }
+  *d_Z_out = d_Z;
+  return PMOM_OK;
+}
+
+}  // namespace pmom

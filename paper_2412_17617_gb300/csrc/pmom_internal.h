@@ -1,0 +1,71 @@
+// Internal declarations of the GB300 candidate evaluator (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pmom.h"
+
+namespace pmom {
+
+constexpr int kMaxPorts = 4;
+constexpr int kTableCols = 8;
+
+// Activation rule of one basis function, as the kernels read it.
+enum RuleKind : int32_t { kAlways = 0, kInner = 1, kInter = 2, kPixPort = 3 };
+
+struct Grid {
+  int layers = 0, nx = 0, ny = 0, medium = 0, n_states = 2, n_ports = 0;
+  double pitch = 0, h_total = 0, eps_r = 1, tan_d = 0;
+  std::vector<double> layer_z;
+  std::vector<pmom_port> ports;
+  int pixels() const { return layers * nx * ny; }
+};
+
+// Builds the canonical BF table (see pmom_bf_table in pmom.h).  Returns M.
+int build_bf_table(const Grid& g, std::vector<int32_t>& table);
+
+// Device-side launch parameters of the evaluation kernels.
+struct EvalArgs {
+  const int4* rules;       // [M] {kind, pixA, pixB, 0}
+  int M, P, F, B, npix, n_states;
+  const uint8_t* maps;     // [B][npix]
+  int32_t* idx;            // [B][M]
+  int32_t* n_act;          // [B]
+  const void* Z;           // [F][M][M] resident database
+  int z_c128;              // 1: double2 storage, 0: float2
+  double port_len[kMaxPorts];
+  double Z0;
+  double2* S;              // [B][F][P][P]
+  uint32_t* flags;         // [B] bit flags per candidate
+  int* task_counter;       // persistent queue head
+  int* repair_list;        // [B*F] tasks the mixed path hands to FP64
+  int* repair_count;
+  unsigned long long* counters;  // [4]: refinement iterations, max iterations, repaired, tasks
+  void* work;              // slot workspaces
+  size_t slot_bytes;
+  int lda;                 // leading dimension of the per-slot matrix
+  int ntasks_list;         // 0: all B*F tasks; 1: tasks from repair_list
+};
+
+enum CandFlag : uint32_t { kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u };
+
+// Launchers (pmom_eval.cu).
+cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
+cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int B, const uint32_t* flags,
+                       const int32_t* n_act, double* fom, int32_t* status, cudaStream_t s);
+cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
+                          cudaStream_t s);
+size_t eval_slot_bytes(int precision, int M, int P, int* lda);
+size_t eval_smem_bytes(int precision, int M, int P);
+int eval_blocks_per_sm(int precision, int M, int z_c128);
+
+// GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
+pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,
+                   cudaStream_t s, void** d_Z_out, std::string* err);
+
+}  // namespace pmom

@@ -1,0 +1,103 @@
+// Basis-function table of the pixel grid (paper Section II-C; alternating 2-triangle pixels of
+// Section V-A; corner-only contact is no connection, Section VI-A).  Table-driven: the two
+// halves of a pixel, which half owns each pixel side, and which triangle corner is the free RWG
+// vertex are fixed per diagonal orientation and looked up instead of searched.
+#include "pmom_internal.h"
+
+namespace pmom {
+namespace {
+
+// Pixel sides.
+enum Side { kBottom = 0, kRight = 1, kTop = 2, kLeft = 3 };
+
+// Orientation o = (x + y) & 1: o = 0 -> diagonal (x, y+1)-(x+1, y); o = 1 -> (x, y)-(x+1, y+1).
+// Triangle corners in canonical order, as corner codes 0:(x,y) 1:(x+1,y) 2:(x,y+1) 3:(x+1,y+1):
+//   o = 0: half 0 = {0, 1, 2}, half 1 = {1, 3, 2};  o = 1: half 0 = {0, 1, 3}, half 1 = {0, 3, 2}.
+// For each orientation and side: the half holding that side and the index of the corner opposite it.
+struct HalfFree {
+  int8_t half, free_vertex;
+};
+constexpr HalfFree kSideOwner[2][4] = {
+    /* o = 0 */ {{0, 2}, {1, 2}, {1, 0}, {0, 1}},
+    /* o = 1 */ {{0, 2}, {0, 0}, {1, 0}, {1, 1}},
+};
+// Free vertex of each half for the pixel's own diagonal.
+constexpr int8_t kDiagFree[2][2] = {{0, 1}, {1, 2}};
+
+int32_t tri_key(int layer, int x, int y, int half) { return ((layer * 128 + (y + 4)) * 128 + (x + 4)) * 2 + half; }
+
+void put_diag(int32_t* r, int layer, int x, int y) {
+  const int o = (x + y) & 1;
+  r[4] = tri_key(layer, x, y, 0);
+  r[5] = tri_key(layer, x, y, 1);
+  r[6] = kDiagFree[o][0];
+  r[7] = kDiagFree[o][1];
+}
+
+// BF on the side shared by lattice neighbours P (positive triangle) and Q (negative triangle).
+void put_side(int32_t* r, int layer, int px, int py, int qx, int qy) {
+  Side sp, sq;
+  if (qx == px + 1) { sp = kRight; sq = kLeft; }
+  else if (qx == px - 1) { sp = kLeft; sq = kRight; }
+  else if (qy == py + 1) { sp = kTop; sq = kBottom; }
+  else { sp = kBottom; sq = kTop; }
+  const HalfFree a = kSideOwner[(px + py) & 1][sp];
+  const HalfFree b = kSideOwner[(qx + qy) & 1][sq];
+  r[4] = tri_key(layer, px, py, a.half);
+  r[5] = tri_key(layer, qx, qy, b.half);
+  r[6] = a.free_vertex;
+  r[7] = b.free_vertex;
+}
+
+// Feed stub of a port: s1 touches the grid, s2 lies outside it, g is the grid pixel touched.
+void stub(const Grid& g, const pmom_port& p, int s1[2], int s2[2], int gp[2]) {
+  static const int dir[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+  const int dx = dir[p.side][0], dy = dir[p.side][1];
+  if (dx != 0) {
+    gp[0] = dx > 0 ? g.nx - 1 : 0;
+    gp[1] = p.pos;
+  } else {
+    gp[0] = p.pos;
+    gp[1] = dy > 0 ? g.ny - 1 : 0;
+  }
+  s1[0] = gp[0] + dx; s1[1] = gp[1] + dy;
+  s2[0] = s1[0] + dx; s2[1] = s1[1] + dy;
+}
+
+}  // namespace
+
+int build_bf_table(const Grid& g, std::vector<int32_t>& t) {
+  const int M = 4 * g.n_ports + g.layers * (g.nx * g.ny + (g.nx - 1) * g.ny + g.nx * (g.ny - 1));
+  t.assign(static_cast<size_t>(M) * kTableCols, -1);
+  int m = 0;
+  auto row = [&](int kind, int pa, int pb, int port) {
+    int32_t* r = &t[static_cast<size_t>(m++) * kTableCols];
+    r[0] = kind; r[1] = pa; r[2] = pb; r[3] = port;
+    return r;
+  };
+  auto pix = [&](int l, int x, int y) { return (l * g.ny + y) * g.nx + x; };
+  for (int p = 0; p < g.n_ports; ++p) {
+    int s1[2], s2[2], gp[2];
+    const int l = g.ports[p].layer;
+    stub(g, g.ports[p], s1, s2, gp);
+    put_diag(row(kAlways, -1, -1, p), l, s1[0], s1[1]);
+    put_side(row(kAlways, -1, -1, p), l, s2[0], s2[1], s1[0], s1[1]);   // delta-gap edge, + outside
+    put_diag(row(kAlways, -1, -1, p), l, s2[0], s2[1]);
+  }
+  for (int l = 0; l < g.layers; ++l)
+    for (int y = 0; y < g.ny; ++y)
+      for (int x = 0; x < g.nx; ++x) {
+        put_diag(row(kInner, pix(l, x, y), -1, -1), l, x, y);
+        if (x + 1 < g.nx) put_side(row(kInter, pix(l, x, y), pix(l, x + 1, y), -1), l, x, y, x + 1, y);
+        if (y + 1 < g.ny) put_side(row(kInter, pix(l, x, y), pix(l, x, y + 1), -1), l, x, y, x, y + 1);
+      }
+  for (int p = 0; p < g.n_ports; ++p) {
+    int s1[2], s2[2], gp[2];
+    const int l = g.ports[p].layer;
+    stub(g, g.ports[p], s1, s2, gp);
+    put_side(row(kPixPort, pix(l, gp[0], gp[1]), -1, p), l, s1[0], s1[1], gp[0], gp[1]);
+  }
+  return M;
+}
+
+}  // namespace pmom

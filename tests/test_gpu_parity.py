@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path against the oracle, through the C ABI, on the same seeded inputs.
+
+Tolerances (from the accuracy targets of the method's two paths):
+  FP64 path : max |S_gpu - S_oracle| <= 1e-10 * max(1, |S_oracle|) per entry, FoM relative 1e-10
+  mixed path: max |S_gpu - S_oracle| <= 1e-6 per complex entry, FoM relative 1e-6
+  support sets, counts and gathered Z entries: bit-exact.
+"""
+import numpy as np
+import pytest
+
+import pmom_inputs as PI
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-10, 1e-10), "mixed": (1e-6, 1e-6)}
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2412_17617_gb300 import build as B
+    B.build()
+    from paper_2412_17617_gb300 import pmom
+    return pmom
+
+
+def _check(S_gpu, fom_gpu, S_ref, fom_ref, prec):
+    ts, tf = TOL[prec]
+    err = np.abs(S_gpu - S_ref)
+    if prec == "fp64":
+        assert (err <= ts * np.maximum(1.0, np.abs(S_ref))).all(), float(err.max())
+    else:
+        assert err.max() <= ts, float(err.max())
+    rel = np.abs(fom_gpu - fom_ref) / np.abs(fom_ref)
+    assert rel.max() <= tf, float(rel.max())
+
+
+@pytest.fixture(scope="module")
+def plain(built):
+    w = PI.workload_plain()
+    OG = O.Grid(w.grid)
+    Z, _ = O.fill(OG, w.freqs())
+    maps = PI.workload_maps(w, seed=0)
+    S_ref, st = O.eval_batch(OG, Z, maps)
+    assert (st == 0).all()
+    band = O.bands(w.freqs(), w.bands)
+    fom_ref = O.fom_batch(S_ref, band)
+    ev = built.Evaluator(w.grid)
+    ev.load_Z(w.freqs(), torch.from_numpy(Z).cuda())
+    ev.set_fom(built.band_codes(w.freqs(), w.bands))
+    yield w, OG, Z, maps, S_ref, fom_ref, ev
+    ev.close()
+
+
+def test_active_set_bit_exact(plain, built):
+    w, OG, Z, maps, *_ , ev = plain
+    extra = PI.random_maps(w.grid, 32, 0.3, 7)
+    allm = np.concatenate([maps, extra, np.zeros_like(extra[:1]), np.ones_like(extra[:1])])
+    idx, n = ev.active_set(torch.from_numpy(allm).cuda())
+    idx, n = idx.cpu().numpy(), n.cpu().numpy()
+    for b in range(allm.shape[0]):
+        ref = O.active_set(OG, allm[b])
+        assert n[b] == len(ref)
+        assert np.array_equal(idx[b, : n[b]], ref)
+
+
+def test_gather_bit_exact(plain, built):
+    w, OG, Z, maps, *_ , ev = plain
+    ref_idx = O.active_set(OG, maps[5])
+    idx = torch.from_numpy(ref_idx).cuda()
+    for f in (0, 4, 10):
+        sub = ev.gather(idx, f).cpu().numpy()
+        assert np.array_equal(sub.view(np.uint64), Z[f][np.ix_(ref_idx, ref_idx)].view(np.uint64))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_plain_workload_parity(plain, prec):
+    w, OG, Z, maps, S_ref, fom_ref, ev = plain
+    S, fom, status = ev.eval(torch.from_numpy(maps).cuda(), prec)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    _check(S.cpu().numpy(), fom.cpu().numpy(), S_ref, fom_ref, prec)
+    # identical decision: the best single flip is the same
+    assert int(np.argmin(fom.cpu().numpy())) == int(np.argmin(fom_ref))
+    st = ev.stats()
+    assert st["tasks"] == maps.shape[0] * w.n_freq
+    if prec == "mixed":
+        assert st["repaired_tasks"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_3x3_map(built, prec):
+    g = PI.grid_tiny(3)
+    freqs = np.array([1.7e9, 5.3e9])
+    OG = O.Grid(g)
+    Z, _ = O.fill(OG, freqs)
+    maps = PI.all_maps(g)
+    S_ref, _ = O.eval_batch(OG, Z, maps)
+    band = np.array([0, 1], np.uint8)
+    fom_ref = O.fom_batch(S_ref, band)
+    ev = built.Evaluator(g)
+    ev.load_Z(freqs, torch.from_numpy(Z).cuda())
+    ev.set_fom(band)
+    S, fom, status = ev.eval(torch.from_numpy(maps).cuda(), prec)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    _check(S.cpu().numpy(), fom.cpu().numpy(), S_ref, fom_ref, prec)
+    assert int(np.argmin(fom.cpu().numpy())) == int(np.argmin(fom_ref))
+    ev.close()
+
+
+def test_edge_cases(plain, built):
+    """Bad pixel states are isolated per candidate; a batch of one, the empty map (ports only) and
+    the all-metal map evaluate; host-buffer entry point equals the device one."""
+    w, OG, Z, maps, S_ref, fom_ref, ev = plain
+    m = maps[:4].copy()
+    m[2, 0, 3, 3] = 9
+    S, fom, status = ev.eval(torch.from_numpy(m).cuda(), "mixed")
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    assert st.tolist() == [0, 0, 5, 0]
+    assert np.isnan(fom.cpu().numpy()[2])
+    _check(S.cpu().numpy()[[0, 1, 3]], fom.cpu().numpy()[[0, 1, 3]], S_ref[[0, 1, 3]], fom_ref[[0, 1, 3]], "mixed")
+    special = np.stack([np.zeros_like(maps[0]), np.ones_like(maps[0])])
+    S2_ref, _ = O.eval_batch(OG, Z, special)
+    for b in range(2):
+        S1, f1, s1 = ev.eval(torch.from_numpy(special[b:b + 1]).cuda(), "fp64")
+        torch.cuda.synchronize()
+        assert int(s1.item()) == 0
+        assert np.abs(S1.cpu().numpy()[0] - S2_ref[b]).max() <= 1e-10
+    Sh = np.zeros((maps.shape[0], w.n_freq, 3, 3), np.complex128)
+    _, fh, sh = ev.eval_host(np.ascontiguousarray(maps), "mixed", S=Sh)
+    assert (sh == 0).all()
+    _check(Sh, fh, S_ref, fom_ref, "mixed")
+
+
+@pytest.fixture(scope="module")
+def precision_case(built):
+    """2-layer 16x16 stripline, 41 frequencies, all 512 single flips of a seeded map; the oracle fills
+    Z (complex128, stored as complex64 as the database of this workload) and evaluates a sample."""
+    w = PI.workload_precision()
+    OG = O.Grid(w.grid)
+    Z, _ = O.fill(OG, w.freqs())
+    Z64 = Z.astype(np.complex64)
+    del Z
+    maps = PI.workload_maps(w, seed=0)
+    ev = built.Evaluator(w.grid)
+    ev.load_Z(w.freqs(), torch.from_numpy(Z64).cuda())
+    ev.set_fom(built.band_codes(w.freqs(), w.bands))
+    sample = np.array([0, 1, 97, 255, 256, 300, 480, 511])
+    S_ref, st = O.eval_batch(OG, Z64, maps[sample])
+    assert (st == 0).all()
+    fom_ref = O.fom_batch(S_ref, O.bands(w.freqs(), w.bands))
+    yield w, Z64, maps, ev, sample, S_ref, fom_ref
+    ev.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_precision_workload_full_batch_sampled(precision_case, prec):
+    """Full 512-candidate x 41-frequency batch in the launch configuration the benchmark times;
+    sampled candidates compared with the oracle entry by entry."""
+    w, Z64, maps, ev, sample, S_ref, fom_ref = precision_case
+    dm = torch.from_numpy(maps).cuda()
+    if prec == "fp64":
+        dm = dm[: 64]
+        sample = sample[sample < 64]
+        S_ref, fom_ref = S_ref[: len(sample)], fom_ref[: len(sample)]
+    S, fom, status = ev.eval(dm, prec)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    _check(S.cpu().numpy()[sample], fom.cpu().numpy()[sample], S_ref, fom_ref, prec)
+    assert int(np.argmin(fom.cpu().numpy()[sample])) == int(np.argmin(fom_ref))
+    st = ev.stats()
+    if prec == "mixed":
+        assert st["repaired_tasks"] == 0
+        assert st["refine_max"] <= 10
+
+
+def test_gpu_fill_matches_oracle_fill(built):
+    for g, freqs in ((PI.grid_plain_8x8(), [1.0e9, 3.5e9, 6.0e9]),
+                     (PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2), [1.0e9, 7.0e9])):
+        OG = O.Grid(g)
+        Zr, _ = O.fill(OG, freqs)
+        ev = built.Evaluator(g)
+        ev.fill_Z(freqs, "c128")
+        Zg = ev.copy_Z().cpu().numpy()
+        for f in range(len(freqs)):
+            assert np.abs(Zg[f] - Zr[f]).max() <= 1e-9 * np.abs(Zr[f]).max()
+        ev.close()

@@ -1,0 +1,72 @@
+"""Host-side checks of the CUDA library (no GPU needed): exported symbols, the basis-function
+table against the oracle's (bit-exact), FoM band assignment, argument validation."""
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+import pmom_inputs as PI
+from oracle import oracle as O
+from paper_2412_17617_gb300 import build as B
+from paper_2412_17617_gb300 import pmom
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pmom.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(B.HEADERS[1]).read()
+    declared = set(re.findall(r"^(?:pmom_status|const char\*)\s+(pmom_\w+)\(", hdr, re.M))
+    assert declared == set(pmom.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _grids():
+    gs = [PI.grid_plain_8x8(), PI.grid_stripline_16x16x2(), PI.grid_tiny(3), PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2),
+          PI.grid_stripline_32x32x4()]
+    # every port side, several positions, non-square grid
+    ports = (PI.Port(0, 0, 0), PI.Port(0, 1, 4), PI.Port(1, 2, 2), PI.Port(1, 3, 0))
+    gs.append(PI.Grid("sides_5x3x2", 2, 5, 3, 1e-3, PI.MEDIUM_STRIPLINE, (0.5e-3, 1.0e-3), 1.5e-3, 3.66, 0.004, 2,
+                      ports))
+    return gs
+
+
+@pytest.mark.parametrize("g", _grids(), ids=lambda g: g.name)
+def test_bf_table_bit_exact_vs_oracle(lib, g):
+    ev = pmom.Evaluator(g)
+    ours = ev.bf_table()
+    ref = O.Grid(g).table
+    assert ours.shape == ref.shape
+    assert np.array_equal(ours, ref)
+    ev.close()
+
+
+@pytest.mark.parametrize("w", [PI.workload_plain(), PI.workload_precision()], ids=lambda w: w.name)
+def test_band_codes_match_oracle(w):
+    assert np.array_equal(pmom.band_codes(w.freqs(), w.bands), O.bands(w.freqs(), w.bands))
+
+
+def test_argument_validation(lib):
+    g = PI.grid_tiny(3)
+    bad = PI.Grid("bad", 1, 3, 3, 1e-3, 0, (0.5e-3,), 0.5e-3, 3.5, 0.0, 2, (PI.Port(0, 0, 7),))
+    with pytest.raises(pmom.PmomError) as e:
+        pmom.Evaluator(bad)
+    assert e.value.status == 1
+    three = PI.Grid("via", 1, 3, 3, 1e-3, 0, (0.5e-3,), 0.5e-3, 3.5, 0.0, 3, (PI.Port(0, 0, 1),))
+    with pytest.raises(pmom.PmomError) as e:
+        pmom.Evaluator(three)
+    assert e.value.status == 7
+    ev = pmom.Evaluator(g)
+    with pytest.raises(pmom.PmomError) as e:
+        ev.set_fom(np.zeros(2, np.uint8))
+    assert e.value.status == 6   # NOT_READY: no database yet
+    st = lib.pmom_eval_candidates(ev.h, ctypes.c_void_p(1), 4, 1, None, ctypes.c_void_p(1), ctypes.c_void_p(1), None)
+    assert st == 6
+    st = lib.pmom_eval_candidates(ev.h, None, 4, 1, None, None, None, None)
+    assert st == 1
+    ev.close()
