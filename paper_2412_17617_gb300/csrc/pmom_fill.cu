@@ -15,6 +15,7 @@
 // triangle).  A second kernel assembles Z_mn from the class table and stores (Z_mn + Z_nm)/2.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <unordered_map>
 #include <vector>
@@ -61,12 +62,18 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   const double d = b.x * b.x + b.y * b.y;
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
+// principal square root; the part that would cancel (r - |a.x| when |a.y| << |a.x|) is formed
+// from the other one, so nearly real arguments never take sqrt of a rounded-negative number
 __device__ __forceinline__ double2 csqrt_(double2 a) {
   const double r = hypot(a.x, a.y);
-  double re = sqrt(0.5 * (r + a.x));
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  if (a.x >= 0.0) {
+    const double re = sqrt(0.5 * (r + a.x));
+    return make_double2(re, a.y / (2.0 * re));
+  }
   double im = sqrt(0.5 * (r - a.x));
-  if (a.y < 0) im = -im;
-  return make_double2(re, im);
+  if (a.y < 0.0) im = -im;
+  return make_double2(a.y / (2.0 * im), im);
 }
 
 // exp(-j k R) / (4 pi R)
@@ -450,12 +457,9 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
     Medium& md = media[f];
     md.omega = 2.0 * kPi * freqs[f];
     md.eps = make_double2(eps0 * er, -eps0 * er * g.tan_d);
-    // k = w sqrt(mu0 eps): principal square root of mu0 eps
-    const double ar = kMu0 * md.eps.x, ai = kMu0 * md.eps.y;
-    const double r = std::hypot(ar, ai);
-    double sr = std::sqrt(0.5 * (r + ar)), si = std::sqrt(0.5 * (r - ar));
-    if (ai < 0) si = -si;
-    md.k = make_double2(md.omega * sr, md.omega * si);
+    // k = w sqrt(mu0 eps), principal root
+    const std::complex<double> kk = md.omega * std::sqrt(std::complex<double>(kMu0 * md.eps.x, kMu0 * md.eps.y));
+    md.k = make_double2(kk.real(), kk.imag());
     md.stripline = g.medium == 1;
     md.H = g.h_total;
     md.rho_s = 0.5 * g.h_total;
