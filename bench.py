@@ -96,7 +96,7 @@ class Clocks:
 
 
 def workload(name: str):
-    return PI.workload_precision() if name == "precision" else PI.workload_plain()
+    return {"precision": PI.workload_precision, "plain": PI.workload_plain, "profile": PI.workload_profile}[name]()
 
 
 def lu_flops(N: np.ndarray, F: int, P: int) -> float:
@@ -174,6 +174,8 @@ def run_ours(args):
     ev.set_fom(band_codes(freqs, w.bands), w.z0_ohm)
     # each rank evaluates its own batch (independent candidates): weak scaling, no collective
     maps_np = PI.workload_maps(w, seed=rank)
+    if args.batch > 0:
+        maps_np = np.ascontiguousarray(maps_np[: args.batch])
     maps = torch.from_numpy(maps_np).cuda()
     Bsz = maps.shape[0]
     idx, n = ev.active_set(maps)
@@ -282,7 +284,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="precision", choices=["precision", "plain"])
+    ap.add_argument("--workload", default="precision", choices=["precision", "plain", "profile"],
+                    help="profile: a smaller grid running the same kernels, for counter captures")
+    ap.add_argument("--batch", type=int, default=0, help="evaluate only the first B candidates")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -148,6 +148,15 @@ def workload_precision() -> Workload:
                     UNII_BANDS)
 
 
+def workload_profile() -> Workload:
+    """A smaller stripline case (2-layer 10x10, 41 frequencies, complex64) that runs the same
+    kernels as the 16x16x2 case with a device footprint small enough for counter captures."""
+    h = H_RO4350
+    g = Grid("stripline_10x10x2", 2, 10, 10, 0.9e-3, MEDIUM_STRIPLINE, (h, 2 * h), 3 * h, 3.66, 0.004, 2,
+             (Port(0, SIDE_RIGHT, 5), Port(0, SIDE_LEFT, 5), Port(1, SIDE_LEFT, 5)))
+    return Workload("stripline_10x10x2_f41_b200", g, 1e9, 7e9, 41, 0.65, 200, "c64", UNII_BANDS)
+
+
 def workload_batching() -> Workload:
     return Workload("stripline_20x20x3_f101_b4096", grid_stripline_20x20x3(), 0.5e9, 8e9, 101, 0.5, 4096, "c64",
                     UNII_BANDS)
