@@ -150,6 +150,28 @@ pmom_status pmom_eval_candidates_host(pmom_ctx* ctx, const uint8_t* maps_host, i
                                       double* S_out_host, double* fom_out_host, int32_t* status_host,
                                       void* stream);
 
+/* Allocation-free evaluation, for callers that must not allocate device memory during the
+ * call: code running inside a CUDA-graph capture or another framework's memory pool, real-time
+ * loops that forbid allocator latency, and hosts whose device memory is fully reserved up front.
+ * The paper has no counterpart to this entry point; it is a deployment convenience.
+ * Same arguments and results as pmom_eval_candidates (S_out_dev may be NULL only if the batch's
+ * S still fits the scratch), but every temporary (support sets, per-task workspaces, counters)
+ * lives in one fixed array of PMOM_NOALLOC_SCRATCH_BYTES (32 MiB) that the library declares in
+ * device memory and that stays reserved on every GPU that loads the library until the process
+ * exits.  The call issues no cudaMalloc/cudaFree.  Preconditions: Z loaded or filled and the
+ * FoM bands set on `ctx` (those earlier calls may allocate).  A batch whose scratch does not fit
+ * is rejected with PMOM_ERR_INVALID_ARG and a message stating the bytes needed (in practice the
+ * FP64 workspace of one task must fit: M up to about 1400 for the mixed path).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call outside any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents: the entry point clears the parts that must start at zero itself,
+ * but two calls that overlap on the GPU (different streams, contexts or host threads without
+ * ordering) race on the array and corrupt each other.  pmom_stats / pmom_kernel_times do not
+ * report these calls. */
+#define PMOM_NOALLOC_SCRATCH_BYTES (32u << 20)
+pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision,
+                                         double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
+
 /* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
  * max iterations of one task, tasks re-solved in FP64, candidates singular, candidates
  * non-finite, kernel launches issued, reserved.  Synchronizes the context's last stream. */

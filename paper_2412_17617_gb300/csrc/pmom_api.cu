@@ -2,6 +2,7 @@
 // pipeline (activation -> persistent evaluation -> FP64 repair of unconverged tasks -> FoM).
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -427,3 +428,103 @@ pmom_status pmom_fill_Z(pmom_ctx* c, const double* freqs, int32_t F, int32_t dty
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free evaluation
+// Some callers cannot let the library allocate device memory inside a call (graph capture,
+// pools owned by another framework, real-time loops).  For them every temporary of the
+// evaluation comes out of one fixed device array declared here; the kernels are the same ones
+// pmom_eval_candidates launches, given pointers into this array instead of context workspaces.
+namespace {
+
+constexpr size_t kNoAllocBytes = PMOM_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision,
+                                                    double* S_out, double* fom_out, int32_t* status, void* stream) {
+  if (!c || !maps || !fom_out || !status || B < 1 || (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
+    return fail(c, PMOM_ERR_INVALID_ARG, "eval_noalloc: bad argument");
+  if (!c->d_Z || !c->fom_ready || !c->d_rules)
+    return fail(c, PMOM_ERR_NOT_READY, "eval_noalloc: load Z and set the FoM bands first");
+  int dev = 0;
+  PMOM_CUDA(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(c, PMOM_ERR_INVALID_ARG, "eval_noalloc: device index");
+  unsigned char* base = nullptr;
+  {
+    // once per device, with that device current: the host-side symbol is not a device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+      g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+    }
+    base = g_noalloc_base[dev];
+  }
+  const int P = c->grid.n_ports, F = c->F, M = c->M;
+  // carve the scratch: counters | idx | N | flags | repair list | S (if the caller passed none) | slots
+  size_t off = 0;
+  const size_t o_small = off; off = align256(off + 256);
+  const size_t o_idx = off; off = align256(off + sizeof(int32_t) * static_cast<size_t>(B) * M);
+  const size_t o_nact = off; off = align256(off + sizeof(int32_t) * B);
+  const size_t o_flags = off; off = align256(off + sizeof(uint32_t) * B);
+  const size_t o_rep = off; off = align256(off + sizeof(int) * static_cast<size_t>(B) * F);
+  const size_t o_S = off;
+  if (!S_out) off = align256(off + sizeof(double2) * static_cast<size_t>(B) * F * P * P);
+  const size_t o_work = off;
+  int lda = 0;   // the same leading dimension for both precisions
+  const size_t slot_main = pmom::eval_slot_bytes(precision, M, P, &lda);
+  const size_t slot_fp64 = pmom::eval_slot_bytes(PMOM_FP64, M, P, &lda);
+  const size_t slot_max = slot_main > slot_fp64 ? slot_main : slot_fp64;
+  if (o_work + slot_max > kNoAllocBytes) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg,
+                  "eval_noalloc: batch needs %zu bytes of scratch (one task workspace %zu) but the fixed array holds %zu",
+                  o_work + slot_max, slot_max, kNoAllocBytes);
+    return fail(c, PMOM_ERR_INVALID_ARG, msg);
+  }
+  const int fit = static_cast<int>((kNoAllocBytes - o_work) / slot_max);
+  const int tasks = B * F;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* small = reinterpret_cast<int*>(base + o_small);
+  pmom::EvalArgs a{};
+  a.rules = c->d_rules; a.M = M; a.P = P; a.F = F; a.B = B; a.npix = c->grid.pixels();
+  a.n_states = c->grid.n_states; a.maps = maps;
+  a.idx = reinterpret_cast<int32_t*>(base + o_idx);
+  a.n_act = reinterpret_cast<int32_t*>(base + o_nact);
+  a.flags = reinterpret_cast<uint32_t*>(base + o_flags);
+  a.Z = c->d_Z;
+  a.z_c128 = c->dtype == PMOM_C128;
+  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch;
+  a.Z0 = c->Z0;
+  a.S = S_out ? reinterpret_cast<double2*>(S_out) : reinterpret_cast<double2*>(base + o_S);
+  a.task_counter = small;
+  a.repair_count = small + 1;
+  a.counters = reinterpret_cast<unsigned long long*>(base + o_small + 64);
+  a.repair_list = reinterpret_cast<int*>(base + o_rep);
+  a.work = base + o_work;
+  a.lda = lda;
+  // the array keeps the previous call's contents: zero what the kernels accumulate into
+  PMOM_CUDA(c, cudaMemsetAsync(base + o_small, 0, 256, s));
+  PMOM_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * B, s));
+  PMOM_CUDA(c, pmom::launch_activate(a, s));
+  a.slot_bytes = slot_main;
+  a.ntasks_list = 0;
+  int n = slots_for(c, precision, tasks);
+  PMOM_CUDA(c, pmom::launch_eval(a, precision, n < fit ? n : fit, s));
+  if (precision == PMOM_MIXED_REFINED) {
+    PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
+    a.slot_bytes = slot_fp64;
+    a.ntasks_list = 1;
+    n = slots_for(c, PMOM_FP64, tasks);
+    PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, n < fit ? n : fit, s));
+  }
+  PMOM_CUDA(c, pmom::launch_fom(a.S, c->d_bands, F, P, B, a.flags, a.n_act, fom_out, status, s));
+  return PMOM_OK;
+}

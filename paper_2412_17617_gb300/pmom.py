@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z
 # names exported by libpmom.so, one per declaration in include/pmom.h
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
-           "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync")
+           "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
+           "pmom_eval_candidates_noalloc")
 
 
 class PmomError(RuntimeError):
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_set_timing": [V, I32],
         "pmom_kernel_times": [V, P],
         "pmom_sync": [V, V],
+        "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -235,6 +237,23 @@ class Evaluator:
         self._check(self.L.pmom_eval_candidates_host(
             self.h, ctypes.c_void_p(maps.ctypes.data), B, prec, ctypes.c_void_p(sp), ctypes.c_void_p(fom.ctypes.data),
             ctypes.c_void_p(status.ctypes.data), ctypes.c_void_p(_stream_ptr(stream))))
+        return S, fom, status
+
+    def eval_noalloc(self, maps, precision: str = "mixed", out=None, stream=None):
+        """Like eval(), through the entry point that allocates no device memory during the call
+        (temporaries live in the library's fixed 32 MiB device array; see include/pmom.h)."""
+        import torch
+        B = maps.shape[0]
+        prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED
+        if out is None:
+            S = torch.empty((B, self.F, self.P, self.P), dtype=torch.complex128, device="cuda")
+            fom = torch.empty((B,), dtype=torch.float64, device="cuda")
+            status = torch.empty((B,), dtype=torch.int32, device="cuda")
+        else:
+            S, fom, status = out
+        self._check(self.L.pmom_eval_candidates_noalloc(
+            self.h, ctypes.c_void_p(maps.data_ptr()), B, prec, ctypes.c_void_p(S.data_ptr() if S is not None else 0),
+            ctypes.c_void_p(fom.data_ptr()), ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
 
     def stats(self) -> dict:
