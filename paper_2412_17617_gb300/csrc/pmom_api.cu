@@ -97,19 +97,22 @@ pmom_status ensure_batch(pmom_ctx* c, int B) {
   return PMOM_OK;
 }
 
-int slots_for(pmom_ctx* c, int precision, int tasks) {
-  const int per_sm = pmom::eval_blocks_per_sm(precision, c->M, c->dtype == PMOM_C128);
+int slots_for(pmom_ctx* c, int precision, int tasks, int ncap) {
+  const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128);
   int n = (per_sm > 0 ? per_sm : 1) * c->num_sms;
   if (n > tasks) n = tasks;
   return n < 1 ? 1 : n;
 }
 
-pmom_status ensure_work(pmom_ctx* c) {
+// Slot workspaces for this call: the launch of `precision` and, for the mixed path, the FP64
+// repair launch that follows it (they reuse the same memory one after the other).
+pmom_status ensure_work(pmom_ctx* c, int precision, int tasks, int ncap) {
   size_t need = 0;
   for (int prec = 0; prec < 2; ++prec) {
+    if (prec != precision && prec != PMOM_FP64) continue;
     int lda = 0;
     const size_t sb = pmom::eval_slot_bytes(prec, c->M, c->grid.n_ports, &lda);
-    const size_t n = static_cast<size_t>(slots_for(c, prec, 1 << 30));
+    const size_t n = static_cast<size_t>(slots_for(c, prec, tasks, ncap));
     if (sb * n > need) need = sb * n;
   }
   if (need <= c->work_bytes && c->d_work) return PMOM_OK;
@@ -285,8 +288,6 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval: load Z and set the FoM bands first");
   pmom_status st = ensure_batch(c, B);
   if (st) return st;
-  st = ensure_work(c);
-  if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
   const int P = c->grid.n_ports;
@@ -303,19 +304,27 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   a.repair_count = small + 1;
   a.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
   a.repair_list = c->d_repair;
-  a.work = c->d_work;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, cudaMemsetAsync(c->d_small, 0, 256, s));
   const bool tm = c->timing;
   c->timed = tm;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
+  a.n_max = small + 2;
   PMOM_CUDA(c, pmom::launch_activate(a, s));
-  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
   c->launches = 1;
+  // the largest support set of the batch sizes the kernels' shared memory and their occupancy
+  int ncap = 0;
+  PMOM_CUDA(c, cudaMemcpyAsync(&ncap, small + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaStreamSynchronize(s));
+  a.ncap = ncap < 1 ? 1 : ncap;
   const int tasks = B * c->F;
+  st = ensure_work(c, precision, tasks, a.ncap);
+  if (st) return st;
+  a.work = c->d_work;
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
   a.slot_bytes = pmom::eval_slot_bytes(precision, c->M, P, &a.lda);
   a.ntasks_list = 0;
-  PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks), s));
+  PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks, a.ncap), s));
   ++c->launches;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[2], s));
   if (precision == PMOM_MIXED_REFINED) {
@@ -323,12 +332,13 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
     PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
     a.slot_bytes = pmom::eval_slot_bytes(PMOM_FP64, c->M, P, &a.lda);
     a.ntasks_list = 1;
-    PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, slots_for(c, PMOM_FP64, tasks), s));
+    PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, slots_for(c, PMOM_FP64, tasks, a.ncap), s));
     ++c->launches;
   }
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[3], s));
+  PMOM_CUDA(c, pmom::launch_ys(a.S, B, c->F, P, c->Z0, c->d_flags, s));
   PMOM_CUDA(c, pmom::launch_fom(a.S, c->d_bands, c->F, P, B, c->d_flags, c->d_nact, fom_out, status, s));
-  ++c->launches;
+  c->launches += 2;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
   return PMOM_OK;
 }
@@ -510,21 +520,23 @@ extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* 
   a.repair_list = reinterpret_cast<int*>(base + o_rep);
   a.work = base + o_work;
   a.lda = lda;
+  a.ncap = M;   // no host round trip here: shared memory sized for the whole parent
   // the array keeps the previous call's contents: zero what the kernels accumulate into
   PMOM_CUDA(c, cudaMemsetAsync(base + o_small, 0, 256, s));
   PMOM_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, pmom::launch_activate(a, s));
   a.slot_bytes = slot_main;
   a.ntasks_list = 0;
-  int n = slots_for(c, precision, tasks);
+  int n = slots_for(c, precision, tasks, M);
   PMOM_CUDA(c, pmom::launch_eval(a, precision, n < fit ? n : fit, s));
   if (precision == PMOM_MIXED_REFINED) {
     PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
     a.slot_bytes = slot_fp64;
     a.ntasks_list = 1;
-    n = slots_for(c, PMOM_FP64, tasks);
+    n = slots_for(c, PMOM_FP64, tasks, M);
     PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, n < fit ? n : fit, s));
   }
+  PMOM_CUDA(c, pmom::launch_ys(a.S, B, F, P, c->Z0, a.flags, s));
   PMOM_CUDA(c, pmom::launch_fom(a.S, c->d_bands, F, P, B, a.flags, a.n_act, fom_out, status, s));
   return PMOM_OK;
 }

@@ -12,6 +12,7 @@
 //   fom_kernel      : FoM of Eq. (8)-(9) per candidate, frequencies summed in order.
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "pmom_internal.h"
 
@@ -104,7 +105,7 @@ template <> struct Cfg<double2> { static constexpr int NB = 8; };
 __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restrict__ rules, int M,
                                                            const uint8_t* __restrict__ maps, int npix, int n_states,
                                                            int32_t* __restrict__ idx, int32_t* __restrict__ n_act,
-                                                           uint32_t* __restrict__ flags) {
+                                                           uint32_t* __restrict__ flags, int* __restrict__ n_max) {
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint8_t* map = maps + static_cast<size_t>(b) * npix;
   __shared__ int s_bad;
@@ -151,7 +152,10 @@ __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restri
     base += total;
     __syncthreads();
   }
-  if (tid == 0) n_act[b] = base;
+  if (tid == 0) {
+    n_act[b] = base;
+    if (n_max) atomicMax(n_max, base);
+  }
 }
 
 // ------------------------------------------------------------------ block argmax of |a|^2
@@ -452,6 +456,90 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
 }
 
 // ------------------------------------------------------------------ refinement residual
+// Error-free transformations on the FP32 pipe (Knuth's TwoSum, FMA-based TwoProduct); the
+// explicit _rn intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += z * (xh + xl): z is an exact float, xh + xl the two-float split of a double
+__device__ __forceinline__ void df_mac(float z, float xh, float xl, float& hi, float& lo) {
+  const float p = __fmul_rn(z, xh);
+  const float e = __fmaf_rn(z, xh, -p);
+  float sum, err;
+  two_sum(hi, p, sum, err);
+  hi = sum;
+  lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(z, xl, e)));
+}
+
+// r = V - Z_sub x for complex64 storage in float-float arithmetic (about 2^-44 relative per lane
+// partial sum, combined in double across the warp).  xs: x split as (re_hi, re_lo, im_hi, im_lo).
+__device__ void residual_df(const float2* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N,
+                            const float4* xs, int P, const double* lport, double2* __restrict__ r, double* s_red,
+                            double* s_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double rmax = 0.0, zmax = 0.0;
+  for (int i = warp; i < N; i += kWarps) {
+    const float2* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
+    float rh[kMaxPorts], rl[kMaxPorts], ih[kMaxPorts], il[kMaxPorts];
+#pragma unroll
+    for (int p = 0; p < kMaxPorts; ++p) rh[p] = rl[p] = ih[p] = il[p] = 0.f;
+    float rowabs = 0.f;
+    for (int t = lane; t < N; t += 32) {
+      const float2 z = __ldg(zrow + s_idx[t]);
+      rowabs += fabsf(z.x) + fabsf(z.y);
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) {
+        if (p < P) {
+          const float4 x = xs[t * P + p];
+          df_mac(z.x, x.x, x.y, rh[p], rl[p]);
+          df_mac(-z.y, x.z, x.w, rh[p], rl[p]);
+          df_mac(z.x, x.z, x.w, ih[p], il[p]);
+          df_mac(z.y, x.x, x.y, ih[p], il[p]);
+        }
+      }
+    }
+    double ra = rowabs;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) ra += __shfl_down_sync(0xffffffffu, ra, d);
+#pragma unroll
+    for (int p = 0; p < kMaxPorts; ++p) {
+      if (p >= P) break;
+      double vx = static_cast<double>(rh[p]) + static_cast<double>(rl[p]);
+      double vy = static_cast<double>(ih[p]) + static_cast<double>(il[p]);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        vx += __shfl_down_sync(0xffffffffu, vx, d);
+        vy += __shfl_down_sync(0xffffffffu, vy, d);
+      }
+      if (lane == 0) {
+        const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
+        const double2 ri = make_double2(vv - vx, -vy);
+        r[i * P + p] = ri;
+        rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
+      }
+    }
+    if (lane == 0) zmax = fmax(zmax, ra);
+  }
+  if (lane == 0) {
+    s_red[warp] = rmax;
+    s_red[kWarps + warp] = zmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      a = fmax(a, s_red[w]);
+      b = fmax(b, s_red[kWarps + w]);
+    }
+    s_out[0] = a;
+    s_out[1] = b;
+  }
+  __syncthreads();
+}
+
+// double-storage residual (complex128 database): plain FP64
 // r = V - Z_sub x in double from the stored entries; returns ||r||_inf (|re|+|im| norm) and
 // ||Z_sub||_inf in s_out[0..1].  x_s: shared copy of x (N x P double2).
 template <typename ZT>
@@ -509,13 +597,17 @@ __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict
   __syncthreads();
 }
 
-// ------------------------------------------------------------------ Y -> S (Eq. 6-7), one thread
-__device__ void ports_to_s(const double2* x, int P, const double* lport, double Z0, double2* S, bool* nonfinite) {
+// ------------------------------------------------------------------ Y -> S (Eq. 6-7)
+// One thread per task converts the port admittance matrix Y (written by the evaluation kernel
+// into the S slot) to S = (1 + Z0 Y)^-1 (1 - Z0 Y) in place.
+__global__ void ys_kernel(double2* __restrict__ S, int ntask, int F, int P, double Z0, uint32_t* __restrict__ flags) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntask) return;
+  double2* s = S + static_cast<size_t>(t) * P * P;
   double2 Am[kMaxPorts][kMaxPorts], Bm[kMaxPorts][kMaxPorts];
   for (int i = 0; i < P; ++i)
     for (int j = 0; j < P; ++j) {
-      const double2 xv = x[(3 * i + 1) * P + j];
-      const double2 y = make_double2(lport[i] * xv.x, lport[i] * xv.y);
+      const double2 y = s[i * P + j];
       const double d = (i == j) ? 1.0 : 0.0;
       Am[i][j] = make_double2(d + Z0 * y.x, Z0 * y.y);
       Bm[i][j] = make_double2(d - Z0 * y.x, -Z0 * y.y);
@@ -528,8 +620,8 @@ __device__ void ports_to_s(const double2* x, int P, const double* lport, double 
       if (cabs2(Am[i][k]) > best) { best = cabs2(Am[i][k]); p = i; }
     if (p != k)
       for (int j = 0; j < P; ++j) {
-        double2 t = Am[k][j]; Am[k][j] = Am[p][j]; Am[p][j] = t;
-        t = Bm[k][j]; Bm[k][j] = Bm[p][j]; Bm[p][j] = t;
+        double2 tt = Am[k][j]; Am[k][j] = Am[p][j]; Am[p][j] = tt;
+        tt = Bm[k][j]; Bm[k][j] = Bm[p][j]; Bm[p][j] = tt;
       }
     const double2 inv = cinv(Am[k][k]);
     for (int j = 0; j < P; ++j) {
@@ -548,10 +640,10 @@ __device__ void ports_to_s(const double2* x, int P, const double* lport, double 
   bool bad = false;
   for (int i = 0; i < P; ++i)
     for (int j = 0; j < P; ++j) {
-      S[i * P + j] = Bm[i][j];
+      s[i * P + j] = Bm[i][j];
       if (!isfinite(Bm[i][j].x) || !isfinite(Bm[i][j].y)) bad = true;
     }
-  *nonfinite = bad;
+  if (bad) atomicOr(&flags[t / F], kFlagNonfinite);
 }
 
 // ------------------------------------------------------------------ the evaluation kernel
@@ -583,8 +675,12 @@ __host__ __device__ inline size_t smem_layout(int M, size_t* u_off, size_t* idx_
   return *idx_off + static_cast<size_t>(M) * sizeof(int);
 }
 
+template <typename ZT> struct XCache;
+template <> struct XCache<float2> { using type = float4; };
+template <> struct XCache<double2> { using type = double2; };
+
 template <typename CT, typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kThreads) eval_kernel(EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
   using R = typename Real<CT>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ R s_val[kWarps + 1];
@@ -594,7 +690,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(EvalArgs a) {
   __shared__ int s_task;
   __shared__ int s_flag;
   size_t u_off, idx_off;
-  smem_layout<CT>(a.M, &u_off, &idx_off);
+  smem_layout<CT>(a.ncap, &u_off, &idx_off);
   CT* Pn = reinterpret_cast<CT*>(smem);
   CT* Ut = reinterpret_cast<CT*>(smem + u_off);
   int* s_idx = reinterpret_cast<int*>(smem + idx_off);
@@ -656,12 +752,25 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(EvalArgs a) {
       const double vnorm = fmax(fmax(lport[0], P > 1 ? lport[1] : 0.0), fmax(P > 2 ? lport[2] : 0.0, P > 3 ? lport[3] : 0.0));
       bool converged = false;
       for (int it = 0; it <= kMaxRefine; ++it) {
-        for (int e = tid; e < N * P; e += kThreads) xs[e] = X[e];
-        __syncthreads();
-        residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
-        double xmax = 0.0;
-        // ||x||_inf (|re|+|im|), reduced over the block
-        for (int e = tid; e < N * P; e += kThreads) xmax = fmax(xmax, fabs(xs[e].x) + fabs(xs[e].y));
+        double xmax = 0.0;   // ||x||_inf (|re|+|im|), reduced over the block
+        if constexpr (std::is_same<ZT, float2>::value) {
+          float4* xf = reinterpret_cast<float4*>(Pn);
+          for (int e = tid; e < N * P; e += kThreads) {
+            const double2 v = X[e];
+            const float hx = static_cast<float>(v.x), hy = static_cast<float>(v.y);
+            xf[e] = make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
+            xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
+          }
+          __syncthreads();
+          residual_df(Zf, M, s_idx, N, xf, P, lport, Rv, s_red, s_norm);
+        } else {
+          for (int e = tid; e < N * P; e += kThreads) {
+            xs[e] = X[e];
+            xmax = fmax(xmax, fabs(X[e].x) + fabs(X[e].y));
+          }
+          __syncthreads();
+          residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
+        }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
         if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
@@ -708,12 +817,15 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(EvalArgs a) {
         a.repair_list[slot] = t;
         atomicAdd(&a.counters[2], 1ull);
         atomicOr(&a.flags[b], kFlagRepaired);
-      } else {
-        bool nonfinite = false;
-        ports_to_s(X, P, lport, a.Z0, Sout, &nonfinite);
-        if (nonfinite) atomicOr(&a.flags[b], kFlagNonfinite);
-        if (singular) atomicOr(&a.flags[b], kFlagSingular);
+      } else if (singular) {
+        atomicOr(&a.flags[b], kFlagSingular);
       }
+    }
+    // port admittances Y_ij = l_i x_i^(j) (Eq. 7) into the S slot; ys_kernel converts them
+    if (!repaired && tid < P * P) {
+      const int i = tid / P, j = tid % P;
+      const double2 xv = X[(3 * i + 1) * P + j];
+      Sout[tid] = make_double2(lport[i] * xv.x, lport[i] * xv.y);
     }
     __syncthreads();
   }
@@ -777,8 +889,9 @@ __global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int3
 
 template <typename CT, typename ZT, bool MIXED>
 cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
+  if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M) return cudaErrorInvalidValue;
   size_t u_off, idx_off;
-  const size_t smem = smem_layout<CT>(a.M, &u_off, &idx_off);
+  const size_t smem = smem_layout<CT>(a.ncap, &u_off, &idx_off);
   auto k = eval_kernel<CT, ZT, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -801,7 +914,8 @@ int blocks_per_sm_t(int M) {
 }  // namespace
 
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
-  activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.idx, a.n_act, a.flags);
+  activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.idx, a.n_act, a.flags,
+                                            a.n_max);
   return cudaGetLastError();
 }
 
@@ -813,10 +927,10 @@ cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream
   return a.z_c128 ? launch_eval_t<float2, double2, true>(a, nslots, s) : launch_eval_t<float2, float2, true>(a, nslots, s);
 }
 
-int eval_blocks_per_sm(int precision, int M, int z_c128) {
+int eval_blocks_per_sm(int precision, int ncap, int z_c128) {
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false>(M) : blocks_per_sm_t<double2, float2, false>(M);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true>(M) : blocks_per_sm_t<float2, float2, true>(M);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false>(ncap) : blocks_per_sm_t<double2, float2, false>(ncap);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true>(ncap) : blocks_per_sm_t<float2, float2, true>(ncap);
 }
 
 size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
@@ -827,10 +941,17 @@ size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
   return (bytes + 255) & ~size_t(255);
 }
 
-size_t eval_smem_bytes(int precision, int M, int P) {
+size_t eval_smem_bytes(int precision, int ncap, int P) {
   (void)P;
   size_t u_off, idx_off;
-  return precision == PMOM_FP64 ? smem_layout<double2>(M, &u_off, &idx_off) : smem_layout<float2>(M, &u_off, &idx_off);
+  return precision == PMOM_FP64 ? smem_layout<double2>(ncap, &u_off, &idx_off)
+                                : smem_layout<float2>(ncap, &u_off, &idx_off);
+}
+
+cudaError_t launch_ys(double2* S, int B, int F, int P, double Z0, uint32_t* flags, cudaStream_t s) {
+  const int n = B * F;
+  ys_kernel<<<(n + 127) / 128, 128, 0, s>>>(S, n, F, P, Z0, flags);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int B, const uint32_t* flags,

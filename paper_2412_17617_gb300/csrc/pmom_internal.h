@@ -49,6 +49,8 @@ struct EvalArgs {
   size_t slot_bytes;
   int lda;                 // leading dimension of the per-slot matrix
   int ntasks_list;         // 0: all B*F tasks; 1: tasks from repair_list
+  int ncap;                // largest N of the batch (sizes the shared-memory panel); <= M
+  int* n_max;              // activation writes max N here (atomicMax)
 };
 
 enum CandFlag : uint32_t { kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u };
@@ -56,13 +58,15 @@ enum CandFlag : uint32_t { kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaire
 // Launchers (pmom_eval.cu).
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
+// Y -> S in place for every (candidate, frequency) task of the batch (Eq. 6-7).
+cudaError_t launch_ys(double2* S, int B, int F, int P, double Z0, uint32_t* flags, cudaStream_t s);
 cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int B, const uint32_t* flags,
                        const int32_t* n_act, double* fom, int32_t* status, cudaStream_t s);
 cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
                           cudaStream_t s);
 size_t eval_slot_bytes(int precision, int M, int P, int* lda);
-size_t eval_smem_bytes(int precision, int M, int P);
-int eval_blocks_per_sm(int precision, int M, int z_c128);
+size_t eval_smem_bytes(int precision, int ncap, int P);
+int eval_blocks_per_sm(int precision, int ncap, int z_c128);
 
 // GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
 pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,
