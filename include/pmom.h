@@ -172,9 +172,15 @@ pmom_status pmom_eval_candidates_host(pmom_ctx* ctx, const uint8_t* maps_host, i
 pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision,
                                          double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
 
+/* Single-precision LU variant: on != 0 (default) runs the trailing-matrix updates on the
+ * tensor cores (tcgen05, TF32 operands split hi + lo, fp32 accumulation in TMEM); 0 runs them on
+ * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning. */
+pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
+
 /* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
- * max iterations of one task, tasks re-solved in FP64, candidates singular, candidates
- * non-finite, kernel launches issued, reserved.  Synchronizes the context's last stream. */
+ * max iterations of one task, tasks re-solved in FP64, tensor-core waits that ran out (the
+ * task's candidate then reports PMOM_CAND_NONFINITE), reserved, kernel launches issued,
+ * reserved.  Synchronizes the context's last stream. */
 pmom_status pmom_stats(pmom_ctx* ctx, int64_t* out8);
 
 /* Kernel timing of later eval calls: on != 0 makes each eval record CUDA events on its stream

@@ -44,6 +44,7 @@ struct pmom_ctx {
   int64_t launches = 0;
   bool timing = false;
   bool timed = false;
+  int use_tc = 1;    // tensor-core trailing updates in the single-precision LU
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::string err;
 };
@@ -98,7 +99,7 @@ pmom_status ensure_batch(pmom_ctx* c, int B) {
 }
 
 int slots_for(pmom_ctx* c, int precision, int tasks, int ncap) {
-  const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128);
+  const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128, c->use_tc);
   int n = (per_sm > 0 ? per_sm : 1) * c->num_sms;
   if (n > tasks) n = tasks;
   return n < 1 ? 1 : n;
@@ -310,6 +311,7 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   c->timed = tm;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
   a.n_max = small + 2;
+  a.use_tc = c->use_tc;
   PMOM_CUDA(c, pmom::launch_activate(a, s));
   c->launches = 1;
   // the largest support set of the batch sizes the kernels' shared memory and their occupancy
@@ -365,16 +367,22 @@ pmom_status pmom_eval_candidates_host(pmom_ctx* c, const uint8_t* maps, int32_t 
 pmom_status pmom_stats(pmom_ctx* c, int64_t* out8) {
   if (!c || !out8) return PMOM_ERR_INVALID_ARG;
   PMOM_CUDA(c, cudaStreamSynchronize(c->last_stream));
-  unsigned long long cnt[4] = {0, 0, 0, 0};
+  unsigned long long cnt[5] = {0, 0, 0, 0, 0};
   PMOM_CUDA(c, cudaMemcpy(cnt, static_cast<char*>(c->d_small) + 64, sizeof(cnt), cudaMemcpyDeviceToHost));
   out8[0] = static_cast<int64_t>(cnt[3]);
   out8[1] = static_cast<int64_t>(cnt[0]);
   out8[2] = static_cast<int64_t>(cnt[1]);
   out8[3] = static_cast<int64_t>(cnt[2]);
-  out8[4] = 0;
+  out8[4] = static_cast<int64_t>(cnt[4]);
   out8[5] = 0;
   out8[6] = c->launches;
   out8[7] = 0;
+  return PMOM_OK;
+}
+
+pmom_status pmom_set_tensor_cores(pmom_ctx* c, int32_t on) {
+  if (!c) return PMOM_ERR_INVALID_ARG;
+  c->use_tc = on != 0;
   return PMOM_OK;
 }
 
@@ -521,6 +529,7 @@ extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* 
   a.work = base + o_work;
   a.lda = lda;
   a.ncap = M;   // no host round trip here: shared memory sized for the whole parent
+  a.use_tc = c->use_tc;
   // the array keeps the previous call's contents: zero what the kernels accumulate into
   PMOM_CUDA(c, cudaMemsetAsync(base + o_small, 0, 256, s));
   PMOM_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * B, s));

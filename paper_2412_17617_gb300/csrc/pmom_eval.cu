@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "pmom_internal.h"
+#include "pmom_tc.cuh"
 
 namespace pmom {
 namespace {
@@ -22,7 +23,11 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 64;        // trailing-update tile (rows and columns)
+constexpr int kOuter = 64;       // outer panel width of the two-level (tensor-core) LU
 constexpr int kMaxRefine = 10;
+// Refinement target on the normwise backward error: reachable by the float-float residual
+// (about 2^-44 per partial sum) and, with cond(Z_sub) ~ 1e4-1e5, far below |dS| = 1e-6.
+constexpr double kEtaTarget = 1e-12;
 
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -182,22 +187,189 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
   return s_row[kWarps];
 }
 
+// ------------------------------------------------------------------ tensor-core trailing update
+// State of the CTA's tensor-core pipeline: 64 KB operand staging (A_hi | A_lo | B_hi | B_lo, each
+// a 128 x 32 K-major fp32 tile), a 128-column TMEM accumulator and the MMA-completion barrier.
+struct TcState {
+  unsigned char* stage;
+  uint32_t tmem;
+  uint64_t* mbar;
+  uint32_t phase;
+  bool failed;
+};
+constexpr long long kTcWaitPolls = 1ll << 26;   // bounded wait; a stall flags the task instead of hanging
+
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float v) {
+  const float h = tc::to_tf32(v);
+  const uint32_t off = tc::kmajor_off(row, k);
+  *reinterpret_cast<float*>(hi + off) = h;
+  *reinterpret_cast<float*>(lo + off) = tc::to_tf32(v - h);
+}
+
+// Outer-panel update A22 -= L21 U12 on the tensor cores, with K = jb <= 64 complex columns taken
+// in chunks of 16.  Per 128 x 64 complex output tile, each chunk is one real GEMM
+// [Lr | Li] (128 x 32) times B (32 x 128), B's first 64 columns being [Ur; -Ui] (real parts of the
+// product) and its last 64 [Ui; Ur] (imaginary parts).  Every fp32 operand is split into two TF32
+// terms (hi + lo) and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32 in
+// TMEM across all chunks, which keeps fp32-level accuracy; the tile is then subtracted from A22
+// once.  L21 = A[rb.., j0..j0+jb), U12 = A[j0..j0+jb, rb..), A22 = A[rb.., rb..], rb = j0 + jb.
+__device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int jb, TcState& st) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rb = j0 + jb, n2 = N - rb;
+  const int nk = (jb + 15) >> 4;
+  unsigned char* Ah = st.stage;
+  unsigned char* Al = st.stage + 16384;
+  unsigned char* Bh = st.stage + 32768;
+  unsigned char* Bl = st.stage + 49152;
+  const uint32_t idesc = tc::idesc_tf32(128, 128);
+  for (int c0 = rb; c0 < N; c0 += 64) {
+    for (int r0 = 0; r0 < n2; r0 += 128) {
+      for (int kc = 0; kc < nk; ++kc) {
+        const int kbase = j0 + 16 * kc, kw = min(16, jb - 16 * kc);
+        {
+          // all loads first (independent, in flight together), then the split stores
+          float2 u[4], l[8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
+            u[i] = (t < kw && c0 + c < N) ? A[static_cast<size_t>(kbase + t) * lda + c0 + c] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
+            l[i] = (t < kw && r0 + r < n2) ? A[static_cast<size_t>(rb + r0 + r) * lda + kbase + t] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
+            put_split(Bh, Bl, c, t, u[i].x);
+            put_split(Bh, Bl, c, 16 + t, -u[i].y);
+            put_split(Bh, Bl, 64 + c, t, u[i].y);
+            put_split(Bh, Bl, 64 + c, 16 + t, u[i].x);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
+            put_split(Ah, Al, r, t, l[i].x);
+            put_split(Ah, Al, r, 16 + t, l[i].y);
+          }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+          const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al), bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
+          uint32_t acc = kc > 0 ? 1u : 0u;
+#pragma unroll
+          for (int term = 0; term < 3; ++term) {
+            const uint32_t ao = term == 0 ? al : ah;     // small terms first: lo*hi, hi*lo, hi*hi
+            const uint32_t bo = term == 1 ? bl : bh;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              tc::mma_tf32(st.tmem, tc::smem_desc(ao + ks * 256), tc::smem_desc(bo + ks * 256), idesc, acc);
+              acc = 1;
+            }
+          }
+          tc::commit(st.mbar);
+        }
+        // one warp waits for the MMAs (they read the staged operands); the barrier releases the rest
+        if (warp == 0) {
+          if (!tc::mbar_wait(st.mbar, st.phase, kTcWaitPolls)) st.failed = true;
+        }
+        st.phase ^= 1u;
+        __syncthreads();
+      }
+      tc::fence_after_sync();
+      // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update
+      float2* T = reinterpret_cast<float2*>(st.stage);
+      constexpr int LDT = 65;
+      {
+        const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
+        float re[32], im[32];
+        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * h, re);
+        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 + 32 * h, im);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      // 32 elements per thread in two batches of 16 independent loads, then the stores
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float2 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
+          v[i] = (r0 + r < n2 && c0 + c < N) ? A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
+          if (r0 + r < n2 && c0 + c < N) {
+            const float2 d = T[r * LDT + c];
+            A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] = make_float2(v[i].x - d.x, v[i].y - d.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// U12 = L11^-1 A12 for an outer panel: L11 = unit lower A[j0..j0+jb, j0..j0+jb) (jb <= 64, staged in
+// shared memory), A12 = A[j0..j0+jb, cb..N); one column per thread, 16 rows at a time.
+__device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int jb, float2* __restrict__ Ls) {
+  constexpr int LDL = 65;
+  const int tid = threadIdx.x, cb = j0 + jb;
+  for (int e = tid; e < jb * 64; e += kThreads) {
+    const int r = e >> 6, c = e & 63;
+    Ls[r * LDL + c] = c < jb ? A[static_cast<size_t>(j0 + r) * lda + j0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int c = cb + tid; c < N; c += kThreads) {
+    for (int ch = 0; ch * 16 < jb; ++ch) {
+      const int rw = min(16, jb - 16 * ch);
+      float2 u[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) u[i] = i < rw ? A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] : make_float2(0.f, 0.f);
+      for (int t = 0; t < 16 * ch; ++t) {   // contributions of the rows already solved
+        const float2 y = A[static_cast<size_t>(j0 + t) * lda + c];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) u[i] = cfms(Ls[(16 * ch + i) * LDL + t], y, u[i]);
+      }
+#pragma unroll
+      for (int i = 1; i < 16; ++i)
+#pragma unroll
+        for (int t = 0; t < i; ++t) u[i] = cfms(Ls[(16 * ch + i) * LDL + 16 * ch + t], u[t], u[i]);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < rw) A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] = u[i];
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ blocked LU in global memory
 // A: row-major N x N (leading dimension lda).  Panel of NB columns factored in shared memory;
 // row interchanges applied to whole rows (LAPACK convention: P A = L U, unit-diagonal L).
 // Returns true if an exactly zero pivot occurred.
 template <typename CT>
 __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ piv, CT* __restrict__ Pn,
-                          CT* __restrict__ Ut, typename Real<CT>::type* s_val, int* s_row) {
+                          CT* __restrict__ Ut, typename Real<CT>::type* s_val, int* s_row, TcState* tcs) {
   using R = typename Real<CT>::type;
   constexpr int NB = Cfg<CT>::NB;
   constexpr int LDP = NB + 1;
   constexpr int LDU = kTile + 1;
   const int tid = threadIdx.x;
   bool singular = false;
+  // Updates made by each NB-column panel stop at column `cend`: N for the one-level CUDA-core
+  // path; the end of the current kOuter-column outer panel for the two-level tensor-core path
+  int cend = N;
   for (int k0 = 0; k0 < N; k0 += NB) {
     const int kb = min(NB, N - k0);
     const int nr = N - k0;
+    if (tcs != nullptr && k0 % kOuter == 0) cend = min(N, k0 + kOuter);
     // 1. panel -> shared memory
     for (int e = tid; e < nr * NB; e += kThreads) {
       const int r = e / NB, c = e % NB;
@@ -251,8 +423,9 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
       __syncthreads();
     }
-    // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory)
-    for (int c = k0 + kb + tid; c < N; c += kThreads) {
+    // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory), columns up
+    //    to the end of the current outer panel
+    for (int c = k0 + kb + tid; c < cend; c += kThreads) {
       CT u[NB];
 #pragma unroll
       for (int i = 0; i < NB; ++i) u[i] = i < kb ? A[static_cast<size_t>(k0 + i) * lda + c] : czero(u[0]);
@@ -265,16 +438,18 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         if (i < kb) A[static_cast<size_t>(k0 + i) * lda + c] = u[i];
     }
     __syncthreads();
-    // 6. trailing update A22 -= L21 U12, 64 x 64 tiles, 4 x 4 complex outputs per thread
+    // 6. trailing update A22 -= L21 U12 on the CUDA cores (64 x 64 tiles, 4 x 4 complex outputs per
+    //    thread), for the columns up to the end of the current outer panel
     const int r_begin = k0 + kb, n2 = N - r_begin;
-    if (n2 > 0) {
+    if (n2 > 0 && cend > r_begin) {
       const int ty = tid >> 4, tx = tid & 15;
       const int ntile = (n2 + kTile - 1) / kTile;
-      for (int tc = 0; tc < ntile; ++tc) {
+      const int ntile_c = (cend - r_begin + kTile - 1) / kTile;
+      for (int tc = 0; tc < ntile_c; ++tc) {
         const int c0 = r_begin + tc * kTile;
         for (int e = tid; e < NB * kTile; e += kThreads) {
           const int t = e / kTile, cc = e % kTile;
-          Ut[t * LDU + cc] = (t < kb && c0 + cc < N) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
+          Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
         }
         __syncthreads();
         for (int tr = 0; tr < ntile; ++tr) {
@@ -285,7 +460,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              acc[i][jj] = (r < n2 && c < N) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
+              acc[i][jj] = (r < n2 && c < cend) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
             }
 #pragma unroll 4
           for (int t = 0; t < NB; ++t) {
@@ -308,22 +483,33 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              if (r < n2 && c < N) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
+              if (r < n2 && c < cend) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
             }
         }
         __syncthreads();
       }
     }
     __syncthreads();
+    // 7-8. end of an outer panel (tensor-core path): U12 for the columns to its right, then one
+    //      K = 64 update of the remaining matrix on the tensor cores
+    if constexpr (std::is_same<CT, float2>::value) {
+      if (tcs != nullptr && k0 + kb == cend && cend < N) {
+        const int j0 = cend - ((cend - 1) % kOuter + 1);
+        outer_trsm(A, lda, N, j0, cend - j0, reinterpret_cast<float2*>(tcs->stage));
+        trailing_tc(A, lda, N, j0, cend - j0, *tcs);
+        __syncthreads();
+      }
+    }
   }
   return singular;
 }
 
 // ------------------------------------------------------------------ triangular solves
 // W (shared, N x P) holds the right-hand sides on entry and the solution on exit.
+// D: shared 32 x 33 staging of the current diagonal block (read once, coalesced).
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
-                         int P) {
+                         int P, CT* __restrict__ D) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
     for (int k = 0; k < N; ++k) {
@@ -375,11 +561,14 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (warp == 0) {
       const int i = i0 + lane;
+      for (int r = 0; r < bs; ++r)
+        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
+      __syncwarp();
       CT w[kMaxPorts];
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
       for (int t = 0; t < bs; ++t) {
-        const CT l = (lane < bs && lane > t) ? A[static_cast<size_t>(i) * lda + i0 + t] : czero(w[0]);
+        const CT l = (lane < bs && lane > t) ? D[lane * 33 + t] : czero(w[0]);
 #pragma unroll
         for (int p = 0; p < kMaxPorts; ++p) {
           const CT y = shfl_c(w[p], t);
@@ -430,17 +619,20 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (warp == 0) {
       const int i = i0 + lane;
+      for (int r = 0; r < bs; ++r)
+        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
+      __syncwarp();
       CT w[kMaxPorts];
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
       for (int t = bs - 1; t >= 0; --t) {
         if (lane == t) {
-          const CT d = A[static_cast<size_t>(i) * lda + i];
+          const CT d = D[lane * 33 + lane];
           const CT inv = cabs2(d) > 0 ? cinv(d) : czero(d);
 #pragma unroll
           for (int p = 0; p < kMaxPorts; ++p) w[p] = cmul(w[p], inv);
         }
-        const CT u = (lane < t) ? A[static_cast<size_t>(i) * lda + i0 + t] : czero(w[0]);
+        const CT u = (lane < t) ? D[lane * 33 + t] : czero(w[0]);
 #pragma unroll
         for (int p = 0; p < kMaxPorts; ++p) {
           const CT y = shfl_c(w[p], t);
@@ -475,19 +667,18 @@ __device__ __forceinline__ void df_mac(float z, float xh, float xl, float& hi, f
 
 // r = V - Z_sub x for complex64 storage in float-float arithmetic (about 2^-44 relative per lane
 // partial sum, combined in double across the warp).  xs: x split as (re_hi, re_lo, im_hi, im_lo).
-__device__ void residual_df(const float2* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N,
-                            const float4* xs, int P, const double* lport, double2* __restrict__ r, double* s_red,
-                            double* s_out) {
+__device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
+                            const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
   for (int i = warp; i < N; i += kWarps) {
-    const float2* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
+    const float2* zrow = Zs + static_cast<size_t>(i) * lda;
     float rh[kMaxPorts], rl[kMaxPorts], ih[kMaxPorts], il[kMaxPorts];
 #pragma unroll
     for (int p = 0; p < kMaxPorts; ++p) rh[p] = rl[p] = ih[p] = il[p] = 0.f;
     float rowabs = 0.f;
     for (int t = lane; t < N; t += 32) {
-      const float2 z = __ldg(zrow + s_idx[t]);
+      const float2 z = zrow[t];
       rowabs += fabsf(z.x) + fabsf(z.y);
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) {
@@ -647,13 +838,17 @@ __global__ void ys_kernel(double2* __restrict__ S, int ntask, int F, int P, doub
 }
 
 // ------------------------------------------------------------------ the evaluation kernel
+// Per-slot workspace: [LU matrix | exact complex64 copy of Z_sub (mixed path with complex64
+// storage: the refinement residual reads it row by row) | pivots | x | residual].
 struct Slot {
-  size_t a_off, piv_off, x_off, r_off;
+  size_t a_off, zs_off, piv_off, x_off, r_off;
 };
 __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_bytes) {
   Slot s;
   s.a_off = 0;
-  s.piv_off = s.a_off + static_cast<size_t>(M) * lda * ct_bytes;
+  s.zs_off = s.a_off + static_cast<size_t>(M) * lda * ct_bytes;
+  s.zs_off = (s.zs_off + 255) & ~size_t(255);
+  s.piv_off = s.zs_off + static_cast<size_t>(M) * lda * sizeof(float2);
   s.piv_off = (s.piv_off + 255) & ~size_t(255);
   s.x_off = s.piv_off + static_cast<size_t>(M) * sizeof(int);
   s.x_off = (s.x_off + 255) & ~size_t(255);
@@ -662,17 +857,23 @@ __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_byt
   return s;
 }
 
+// Dynamic shared memory: [panel (M x (NB+1)) | U tile | idx (M ints) | tensor-core staging
+// (64 KB + 2 KB alignment slack, single-precision tensor-core path only)].
+constexpr size_t kTcStageBytes = 65536 + 2048;   // 64 KB operands (or the 128 x 65 result tile) + alignment
+
 template <typename CT>
-__host__ __device__ inline size_t smem_layout(int M, size_t* u_off, size_t* idx_off) {
+__host__ __device__ inline size_t smem_layout(int M, int use_tc, size_t* u_off, size_t* idx_off, size_t* tc_off) {
   constexpr int NB = Cfg<CT>::NB;
   size_t panel = static_cast<size_t>(M) * (NB + 1) * sizeof(CT);
   const size_t xcache = static_cast<size_t>(M) * kMaxPorts * sizeof(double2);
   if (xcache > panel) panel = xcache;
   panel = (panel + 15) & ~size_t(15);
   *u_off = panel;
-  const size_t u = static_cast<size_t>(NB) * (kTile + 1) * sizeof(CT);
+  size_t u = static_cast<size_t>(NB) * (kTile + 1) * sizeof(CT);
+  if (u < 32 * 33 * sizeof(CT)) u = 32 * 33 * sizeof(CT);
   *idx_off = panel + ((u + 15) & ~size_t(15));
-  return *idx_off + static_cast<size_t>(M) * sizeof(int);
+  *tc_off = *idx_off + ((static_cast<size_t>(M) * sizeof(int) + 15) & ~size_t(15));
+  return *tc_off + (use_tc ? kTcStageBytes : 0);
 }
 
 template <typename ZT> struct XCache;
@@ -689,16 +890,43 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
   __shared__ double s_norm[2];
   __shared__ int s_task;
   __shared__ int s_flag;
-  size_t u_off, idx_off;
-  smem_layout<CT>(a.ncap, &u_off, &idx_off);
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const bool use_tc = std::is_same<CT, float2>::value && a.use_tc != 0;
+  size_t u_off, idx_off, tc_off;
+  smem_layout<CT>(a.ncap, use_tc, &u_off, &idx_off, &tc_off);
   CT* Pn = reinterpret_cast<CT*>(smem);
   CT* Ut = reinterpret_cast<CT*>(smem + u_off);
   int* s_idx = reinterpret_cast<int*>(smem + idx_off);
   const int tid = threadIdx.x;
+  TcState tcs;
+  tcs.stage = nullptr;
+  tcs.tmem = 0;
+  tcs.mbar = &s_mbar;
+  tcs.phase = 0;
+  tcs.failed = false;
+  if (use_tc) {
+    // 1024-byte aligned operand staging inside the slack of the tensor-core region
+    const uint32_t base = tc::smem_u32(smem + tc_off);
+    tcs.stage = smem + tc_off + ((1024u - (base & 1023u)) & 1023u);
+    if ((tid >> 5) == 0) {
+      tc::tmem_alloc(&s_tmem, 128);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+      tc::mbar_init(&s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tcs.tmem = s_tmem;
+  }
   const int P = a.P, M = a.M, lda = a.lda;
   const Slot sl = slot_layout(M, lda, P, sizeof(CT));
   unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * blockIdx.x;
   CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
+  float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
   int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
   double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
   double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
@@ -727,13 +955,19 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
     for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
     __syncthreads();
     // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
+    constexpr bool kZsCopy = MIXED && std::is_same<ZT, float2>::value;
     for (int i = 0; i < N; ++i) {
       const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
       CT* arow = A + static_cast<size_t>(i) * lda;
-      for (int j = tid; j < N; j += kThreads) arow[j] = zload<ZT, CT>(zrow + s_idx[j]);
+      float2* zsrow = Zs + static_cast<size_t>(i) * lda;
+      for (int j = tid; j < N; j += kThreads) {
+        const CT v = zload<ZT, CT>(zrow + s_idx[j]);
+        arow[j] = v;
+        if constexpr (kZsCopy) zsrow[j] = v;
+      }
     }
     __syncthreads();
-    const bool singular = lu_factor<CT>(A, lda, N, piv, Pn, Ut, s_val, s_row);
+    const bool singular = lu_factor<CT>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
     // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
     CT* W = Pn;
     for (int e = tid; e < N * P; e += kThreads) {
@@ -741,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
       W[e] = from_d2<CT>(make_double2(i == 3 * p + 1 ? lport[p] : 0.0, 0.0));
     }
     __syncthreads();
-    lu_solve<CT>(A, lda, N, piv, W, P);
+    lu_solve<CT>(A, lda, N, piv, W, P, Ut);
     for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
     __syncthreads();
     int iters = 0;
@@ -762,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
             xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
           }
           __syncthreads();
-          residual_df(Zf, M, s_idx, N, xf, P, lport, Rv, s_red, s_norm);
+          residual_df(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm);
         } else {
           for (int e = tid; e < N * P; e += kThreads) {
             xs[e] = X[e];
@@ -781,9 +1015,9 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
           const double rn = s_norm[0], zn = s_norm[1];
           const double eta = rn / (zn * m + vnorm);
           int flag = 0;   // 0 continue, 1 converged, 2 stop (stagnated or out of iterations)
-          if (eta <= 4.0 * DBL_EPSILON) flag = 1;
-          else if (it > 0 && rn > 0.5 * rprev) flag = (eta <= 1e-12) ? 1 : 2;
-          else if (it == kMaxRefine) flag = (eta <= 1e-12) ? 1 : 2;
+          if (eta <= kEtaTarget) flag = 1;
+          else if (it > 0 && rn > 0.5 * rprev) flag = 2;      // stagnated above the target
+          else if (it == kMaxRefine) flag = 2;
           s_flag = flag;
           s_norm[0] = rn;
         }
@@ -796,7 +1030,7 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
         }
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
         __syncthreads();
-        lu_solve<CT>(A, lda, N, piv, W, P);
+        lu_solve<CT>(A, lda, N, piv, W, P, Ut);
         for (int e = tid; e < N * P; e += kThreads) {
           const double2 d = to_d2(W[e]);
           X[e] = make_double2(X[e].x + d.x, X[e].y + d.y);
@@ -820,7 +1054,12 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
       } else if (singular) {
         atomicOr(&a.flags[b], kFlagSingular);
       }
+      if (tcs.failed) {   // a tensor-core completion wait ran out: the task's numbers are not trusted
+        atomicOr(&a.flags[b], kFlagNonfinite);
+        atomicAdd(&a.counters[4], 1ull);
+      }
     }
+    tcs.failed = false;
     // port admittances Y_ij = l_i x_i^(j) (Eq. 7) into the S slot; ys_kernel converts them
     if (!repaired && tid < P * P) {
       const int i = tid / P, j = tid % P;
@@ -828,6 +1067,11 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
       Sout[tid] = make_double2(lport[i] * xv.x, lport[i] * xv.y);
     }
     __syncthreads();
+  }
+  if (use_tc) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((tid >> 5) == 0) tc::tmem_dealloc(tcs.tmem, 128);
   }
 }
 
@@ -890,8 +1134,8 @@ __global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int3
 template <typename CT, typename ZT, bool MIXED>
 cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
   if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M) return cudaErrorInvalidValue;
-  size_t u_off, idx_off;
-  const size_t smem = smem_layout<CT>(a.ncap, &u_off, &idx_off);
+  size_t u_off, idx_off, tc_off;
+  const size_t smem = smem_layout<CT>(a.ncap, std::is_same<CT, float2>::value && a.use_tc, &u_off, &idx_off, &tc_off);
   auto k = eval_kernel<CT, ZT, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -900,9 +1144,9 @@ cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
 }
 
 template <typename CT, typename ZT, bool MIXED>
-int blocks_per_sm_t(int M) {
-  size_t u_off, idx_off;
-  const size_t smem = smem_layout<CT>(M, &u_off, &idx_off);
+int blocks_per_sm_t(int M, int use_tc) {
+  size_t u_off, idx_off, tc_off;
+  const size_t smem = smem_layout<CT>(M, std::is_same<CT, float2>::value && use_tc, &u_off, &idx_off, &tc_off);
   auto k = eval_kernel<CT, ZT, MIXED>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
     return 0;
@@ -927,25 +1171,24 @@ cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream
   return a.z_c128 ? launch_eval_t<float2, double2, true>(a, nslots, s) : launch_eval_t<float2, float2, true>(a, nslots, s);
 }
 
-int eval_blocks_per_sm(int precision, int ncap, int z_c128) {
+int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc) {
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false>(ncap) : blocks_per_sm_t<double2, float2, false>(ncap);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true>(ncap) : blocks_per_sm_t<float2, float2, true>(ncap);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false>(ncap, 0) : blocks_per_sm_t<double2, float2, false>(ncap, 0);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true>(ncap, use_tc) : blocks_per_sm_t<float2, float2, true>(ncap, use_tc);
 }
 
 size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
   *lda = (M + 3) & ~3;
   const size_t ct = precision == PMOM_FP64 ? sizeof(double2) : sizeof(float2);
   const Slot s = slot_layout(M, *lda, P, ct);
-  size_t bytes = s.r_off + static_cast<size_t>(M) * P * sizeof(double2);
+  size_t bytes = s.r_off + static_cast<size_t>(M) * P * sizeof(double2);   // includes the Z_sub copy
   return (bytes + 255) & ~size_t(255);
 }
 
-size_t eval_smem_bytes(int precision, int ncap, int P) {
-  (void)P;
-  size_t u_off, idx_off;
-  return precision == PMOM_FP64 ? smem_layout<double2>(ncap, &u_off, &idx_off)
-                                : smem_layout<float2>(ncap, &u_off, &idx_off);
+size_t eval_smem_bytes(int precision, int ncap, int use_tc) {
+  size_t u_off, idx_off, tc_off;
+  return precision == PMOM_FP64 ? smem_layout<double2>(ncap, 0, &u_off, &idx_off, &tc_off)
+                                : smem_layout<float2>(ncap, use_tc, &u_off, &idx_off, &tc_off);
 }
 
 cudaError_t launch_ys(double2* S, int B, int F, int P, double Z0, uint32_t* flags, cudaStream_t s) {

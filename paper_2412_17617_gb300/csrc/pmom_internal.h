@@ -44,13 +44,14 @@ struct EvalArgs {
   int* task_counter;       // persistent queue head
   int* repair_list;        // [B*F] tasks the mixed path hands to FP64
   int* repair_count;
-  unsigned long long* counters;  // [4]: refinement iterations, max iterations, repaired, tasks
+  unsigned long long* counters;  // [5]: refinement iterations, max iterations, repaired, tasks, tensor-core wait timeouts
   void* work;              // slot workspaces
   size_t slot_bytes;
   int lda;                 // leading dimension of the per-slot matrix
   int ntasks_list;         // 0: all B*F tasks; 1: tasks from repair_list
   int ncap;                // largest N of the batch (sizes the shared-memory panel); <= M
   int* n_max;              // activation writes max N here (atomicMax)
+  int use_tc;              // single-precision LU: trailing updates on the tensor cores (tcgen05)
 };
 
 enum CandFlag : uint32_t { kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u };
@@ -65,8 +66,8 @@ cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int
 cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
                           cudaStream_t s);
 size_t eval_slot_bytes(int precision, int M, int P, int* lda);
-size_t eval_smem_bytes(int precision, int ncap, int P);
-int eval_blocks_per_sm(int precision, int ncap, int z_c128);
+size_t eval_smem_bytes(int precision, int ncap, int use_tc);
+int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc);
 
 // GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
 pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
-           "pmom_eval_candidates_noalloc")
+           "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores")
 
 
 class PmomError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_kernel_times": [V, P],
         "pmom_sync": [V, V],
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
+        "pmom_set_tensor_cores": [V, I32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -260,7 +261,10 @@ class Evaluator:
         out = np.zeros(8, dtype=np.int64)
         self._check(self.L.pmom_stats(self.h, out.ctypes.data_as(ctypes.c_void_p)))
         return {"tasks": int(out[0]), "refine_iters": int(out[1]), "refine_max": int(out[2]),
-                "repaired_tasks": int(out[3]), "launches": int(out[6])}
+                "repaired_tasks": int(out[3]), "tc_wait_timeouts": int(out[4]), "launches": int(out[6])}
+
+    def set_tensor_cores(self, on: bool = True):
+        self._check(self.L.pmom_set_tensor_cores(self.h, 1 if on else 0))
 
     def set_timing(self, on: bool = True):
         self._check(self.L.pmom_set_timing(self.h, 1 if on else 0))
