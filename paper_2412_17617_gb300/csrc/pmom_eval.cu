@@ -533,7 +533,18 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
 #pragma unroll
         for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
         const CT* row = A + static_cast<size_t>(i) * lda;
-        for (int t = lane; t < i0; t += 32) {
+        int t = lane;
+        for (; t + 96 < i0; t += 128) {   // four independent loads in flight
+          CT l[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) l[u] = row[t + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int p = 0; p < kMaxPorts; ++p)
+              if (p < P) acc[p] = cfms(l[u], W[(t + 32 * u) * P + p], acc[p]);
+        }
+        for (; t < i0; t += 32) {
           const CT l = row[t];
 #pragma unroll
           for (int p = 0; p < kMaxPorts; ++p)
@@ -591,7 +602,18 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
 #pragma unroll
         for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
         const CT* row = A + static_cast<size_t>(i) * lda;
-        for (int t = i1 + lane; t < N; t += 32) {
+        int t = i1 + lane;
+        for (; t + 96 < N; t += 128) {   // four independent loads in flight
+          CT uu[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) uu[u] = row[t + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int p = 0; p < kMaxPorts; ++p)
+              if (p < P) acc[p] = cfms(uu[u], W[(t + 32 * u) * P + p], acc[p]);
+        }
+        for (; t < N; t += 32) {
           const CT u = row[t];
 #pragma unroll
           for (int p = 0; p < kMaxPorts; ++p)
@@ -669,49 +691,70 @@ __device__ __forceinline__ void df_mac(float z, float xh, float xl, float& hi, f
 // partial sum, combined in double across the warp).  xs: x split as (re_hi, re_lo, im_hi, im_lo).
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
                             const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
+  // four rows per warp at a time: independent float-float chains interleave and each x load
+  // serves four rows
+  constexpr int R = 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
-  for (int i = warp; i < N; i += kWarps) {
-    const float2* zrow = Zs + static_cast<size_t>(i) * lda;
-    float rh[kMaxPorts], rl[kMaxPorts], ih[kMaxPorts], il[kMaxPorts];
+  for (int i0 = warp; i0 < N; i0 += kWarps * R) {
+    float rh[R][kMaxPorts], rl[R][kMaxPorts], ih[R][kMaxPorts], il[R][kMaxPorts], ra[R];
 #pragma unroll
-    for (int p = 0; p < kMaxPorts; ++p) rh[p] = rl[p] = ih[p] = il[p] = 0.f;
-    float rowabs = 0.f;
+    for (int q = 0; q < R; ++q) {
+      ra[q] = 0.f;
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) rh[q][p] = rl[q][p] = ih[q][p] = il[q][p] = 0.f;
+    }
+    const float2* zrow[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = i0 + q * kWarps;
+      zrow[q] = Zs + static_cast<size_t>(i < N ? i : 0) * lda;
+    }
     for (int t = lane; t < N; t += 32) {
-      const float2 z = zrow[t];
-      rowabs += fabsf(z.x) + fabsf(z.y);
+      float2 z[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) z[q] = (i0 + q * kWarps < N) ? zrow[q][t] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) {
         if (p < P) {
           const float4 x = xs[t * P + p];
-          df_mac(z.x, x.x, x.y, rh[p], rl[p]);
-          df_mac(-z.y, x.z, x.w, rh[p], rl[p]);
-          df_mac(z.x, x.z, x.w, ih[p], il[p]);
-          df_mac(z.y, x.x, x.y, ih[p], il[p]);
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            df_mac(z[q].x, x.x, x.y, rh[q][p], rl[q][p]);
+            df_mac(-z[q].y, x.z, x.w, rh[q][p], rl[q][p]);
+            df_mac(z[q].x, x.z, x.w, ih[q][p], il[q][p]);
+            df_mac(z[q].y, x.x, x.y, ih[q][p], il[q][p]);
+          }
         }
       }
+#pragma unroll
+      for (int q = 0; q < R; ++q) ra[q] += fabsf(z[q].x) + fabsf(z[q].y);
     }
-    double ra = rowabs;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) ra += __shfl_down_sync(0xffffffffu, ra, d);
+    for (int q = 0; q < R; ++q) {
+      const int i = i0 + q * kWarps;
+      double rs = ra[q];
 #pragma unroll
-    for (int p = 0; p < kMaxPorts; ++p) {
-      if (p >= P) break;
-      double vx = static_cast<double>(rh[p]) + static_cast<double>(rl[p]);
-      double vy = static_cast<double>(ih[p]) + static_cast<double>(il[p]);
+      for (int d = 16; d > 0; d >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, d);
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        vx += __shfl_down_sync(0xffffffffu, vx, d);
-        vy += __shfl_down_sync(0xffffffffu, vy, d);
+      for (int p = 0; p < kMaxPorts; ++p) {
+        if (p >= P) break;
+        double vx = static_cast<double>(rh[q][p]) + static_cast<double>(rl[q][p]);
+        double vy = static_cast<double>(ih[q][p]) + static_cast<double>(il[q][p]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          vx += __shfl_down_sync(0xffffffffu, vx, d);
+          vy += __shfl_down_sync(0xffffffffu, vy, d);
+        }
+        if (lane == 0 && i < N) {
+          const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
+          const double2 ri = make_double2(vv - vx, -vy);
+          r[i * P + p] = ri;
+          rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
+        }
       }
-      if (lane == 0) {
-        const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
-        const double2 ri = make_double2(vv - vx, -vy);
-        r[i * P + p] = ri;
-        rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
-      }
+      if (lane == 0 && i < N) zmax = fmax(zmax, rs);
     }
-    if (lane == 0) zmax = fmax(zmax, ra);
   }
   if (lane == 0) {
     s_red[warp] = rmax;
@@ -880,8 +923,10 @@ template <typename ZT> struct XCache;
 template <> struct XCache<float2> { using type = float4; };
 template <> struct XCache<double2> { using type = double2; };
 
-template <typename CT, typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
+// TC: the single-precision LU runs its outer-panel updates on the tensor cores.  That variant holds
+// 66 KB more shared memory and runs one CTA per SM, so it may use the full register file.
+template <typename CT, typename ZT, bool MIXED, bool TC>
+__global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) {
   using R = typename Real<CT>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ R s_val[kWarps + 1];
@@ -892,7 +937,7 @@ __global__ void __launch_bounds__(kThreads, 2) eval_kernel(EvalArgs a) {
   __shared__ int s_flag;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mbar;
-  const bool use_tc = std::is_same<CT, float2>::value && a.use_tc != 0;
+  constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
   size_t u_off, idx_off, tc_off;
   smem_layout<CT>(a.ncap, use_tc, &u_off, &idx_off, &tc_off);
   CT* Pn = reinterpret_cast<CT*>(smem);
@@ -1131,23 +1176,23 @@ __global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int3
   }
 }
 
-template <typename CT, typename ZT, bool MIXED>
+template <typename CT, typename ZT, bool MIXED, bool TC>
 cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
   if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M) return cudaErrorInvalidValue;
   size_t u_off, idx_off, tc_off;
-  const size_t smem = smem_layout<CT>(a.ncap, std::is_same<CT, float2>::value && a.use_tc, &u_off, &idx_off, &tc_off);
-  auto k = eval_kernel<CT, ZT, MIXED>;
+  const size_t smem = smem_layout<CT>(a.ncap, TC, &u_off, &idx_off, &tc_off);
+  auto k = eval_kernel<CT, ZT, MIXED, TC>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k<<<nslots, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename CT, typename ZT, bool MIXED>
-int blocks_per_sm_t(int M, int use_tc) {
+template <typename CT, typename ZT, bool MIXED, bool TC>
+int blocks_per_sm_t(int M) {
   size_t u_off, idx_off, tc_off;
-  const size_t smem = smem_layout<CT>(M, std::is_same<CT, float2>::value && use_tc, &u_off, &idx_off, &tc_off);
-  auto k = eval_kernel<CT, ZT, MIXED>;
+  const size_t smem = smem_layout<CT>(M, TC, &u_off, &idx_off, &tc_off);
+  auto k = eval_kernel<CT, ZT, MIXED, TC>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int n = 0;
@@ -1165,16 +1210,22 @@ cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
 
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {
   if (precision == PMOM_FP64) {
-    return a.z_c128 ? launch_eval_t<double2, double2, false>(a, nslots, s)
-                    : launch_eval_t<double2, float2, false>(a, nslots, s);
+    return a.z_c128 ? launch_eval_t<double2, double2, false, false>(a, nslots, s)
+                    : launch_eval_t<double2, float2, false, false>(a, nslots, s);
   }
-  return a.z_c128 ? launch_eval_t<float2, double2, true>(a, nslots, s) : launch_eval_t<float2, float2, true>(a, nslots, s);
+  if (a.use_tc)
+    return a.z_c128 ? launch_eval_t<float2, double2, true, true>(a, nslots, s)
+                    : launch_eval_t<float2, float2, true, true>(a, nslots, s);
+  return a.z_c128 ? launch_eval_t<float2, double2, true, false>(a, nslots, s)
+                  : launch_eval_t<float2, float2, true, false>(a, nslots, s);
 }
 
 int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc) {
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false>(ncap, 0) : blocks_per_sm_t<double2, float2, false>(ncap, 0);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true>(ncap, use_tc) : blocks_per_sm_t<float2, float2, true>(ncap, use_tc);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false, false>(ncap) : blocks_per_sm_t<double2, float2, false, false>(ncap);
+  if (use_tc)
+    return z_c128 ? blocks_per_sm_t<float2, double2, true, true>(ncap) : blocks_per_sm_t<float2, float2, true, true>(ncap);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true, false>(ncap) : blocks_per_sm_t<float2, float2, true, false>(ncap);
 }
 
 size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
