@@ -59,7 +59,8 @@ enum {
   PMOM_CAND_NONFINITE = 2,       /* NaN/Inf in S or FoM */
   PMOM_CAND_REPAIRED = 3,        /* mixed path did not converge at some frequency; that frequency
                                     was re-solved on the FP64 path (results are valid) */
-  PMOM_CAND_BAD_STATE = 5        /* a pixel state >= n_states; S/FoM not computed */
+  PMOM_CAND_BAD_STATE = 5,       /* a pixel state >= n_states; S/FoM not computed */
+  PMOM_CAND_CAPACITY = 6         /* support set larger than a captured graph's capacity; not computed */
 };
 
 typedef struct {
@@ -142,6 +143,24 @@ pmom_status pmom_gather(pmom_ctx* ctx, const int32_t* idx_dev, int32_t N, int32_
  * Errors: INVALID_ARG, NOT_READY (no Z or no bands), OOM, CUDA. */
 pmom_status pmom_eval_candidates(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision,
                                  double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
+
+/* CUDA-graph form of pmom_eval_candidates for repeated evaluation of same-shaped batches (the
+ * inner loop of the tree search): records the whole pipeline (activation, ordering, persistent
+ * evaluation, FP64 repair, Y->S, FoM) for these device buffers into one graph; pmom_graph_launch
+ * replays it on `stream` with no host synchronisation.  The maps' contents may change between
+ * launches; the pointers and B may not.  ncap: the largest support set the graph must handle
+ * (0 = M); a candidate with more active BFs reports PMOM_CAND_CAPACITY instead of being solved.
+ * All allocations happen before the capture starts.  Capturing replaces a previous graph. */
+pmom_status pmom_graph_capture(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision,
+                               double* S_out_dev, double* fom_out_dev, int32_t* status_dev, int32_t ncap,
+                               void* stream);
+pmom_status pmom_graph_launch(pmom_ctx* ctx, void* stream);
+
+/* Autotuner: times the single-precision LU variants (tensor-core or CUDA-core trailing updates)
+ * on this batch and keeps the faster for later calls; *choice_out = 1 if the tensor cores won.
+ * Synchronous; FP64 has a single variant. */
+pmom_status pmom_autotune(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision, int32_t* choice_out,
+                          void* stream);
 
 /* Same computation with host buffers: the call copies the maps to the device, evaluates, copies
  * S (if S_out_host != NULL), FoM and status back and synchronizes `stream` before returning.

@@ -32,6 +32,7 @@ struct pmom_ctx {
   uint32_t* d_flags = nullptr;
   double2* d_S = nullptr;
   int* d_repair = nullptr;
+  int* d_order = nullptr;
   uint8_t* d_maps_stage = nullptr;
   double* d_fom_stage = nullptr;
   int32_t* d_status_stage = nullptr;
@@ -45,6 +46,10 @@ struct pmom_ctx {
   bool timing = false;
   bool timed = false;
   int use_tc = 1;    // tensor-core trailing updates in the single-precision LU
+  // captured evaluation pipeline (pmom_graph_capture / pmom_graph_launch)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // capture stream (the legacy default stream cannot be captured)
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::string err;
 };
@@ -82,6 +87,7 @@ pmom_status ensure_batch(pmom_ctx* c, int B) {
   free_dev(c->d_flags);
   free_dev(c->d_S);
   free_dev(c->d_repair);
+  free_dev(c->d_order);
   free_dev(c->d_maps_stage);
   free_dev(c->d_fom_stage);
   free_dev(c->d_status_stage);
@@ -91,6 +97,7 @@ pmom_status ensure_batch(pmom_ctx* c, int B) {
   PMOM_CUDA(c, cudaMalloc(&c->d_flags, sizeof(uint32_t) * B));
   PMOM_CUDA(c, cudaMalloc(&c->d_S, sizeof(double2) * static_cast<size_t>(B) * c->F * P * P));
   PMOM_CUDA(c, cudaMalloc(&c->d_repair, sizeof(int) * static_cast<size_t>(B) * c->F));
+  PMOM_CUDA(c, cudaMalloc(&c->d_order, sizeof(int) * static_cast<size_t>(B)));
   PMOM_CUDA(c, cudaMalloc(&c->d_maps_stage, static_cast<size_t>(B) * c->grid.pixels()));
   PMOM_CUDA(c, cudaMalloc(&c->d_fom_stage, sizeof(double) * B));
   PMOM_CUDA(c, cudaMalloc(&c->d_status_stage, sizeof(int32_t) * B));
@@ -183,6 +190,10 @@ pmom_status pmom_destroy(pmom_ctx* c) {
   free_dev(c->d_status_stage);
   free_dev(c->d_small);
   free_dev(c->d_work);
+  free_dev(c->d_order);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   delete c;
@@ -282,15 +293,12 @@ pmom_status pmom_gather(pmom_ctx* c, const int32_t* idx, int32_t N, int32_t f, v
   return PMOM_OK;
 }
 
-pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
-                                 double* fom_out, int32_t* status, void* stream) {
-  if (!c || !maps || !fom_out || !status || B < 1 || (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
-    return fail(c, PMOM_ERR_INVALID_ARG, "eval: bad argument");
-  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval: load Z and set the FoM bands first");
-  pmom_status st = ensure_batch(c, B);
-  if (st) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  c->last_stream = s;
+namespace {
+
+// Enqueue the whole evaluation on stream s.  ncap > 0: the caller fixes the shared-memory capacity
+// (graph capture: no host round trip); ncap == 0: read the batch's largest support set back first.
+pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision, double* S_out, double* fom_out,
+                         int32_t* status, cudaStream_t s, int ncap_fixed) {
   const int P = c->grid.n_ports;
   pmom::EvalArgs a{};
   a.rules = c->d_rules; a.M = c->M; a.P = P; a.F = c->F; a.B = B; a.npix = c->grid.pixels();
@@ -305,22 +313,26 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   a.repair_count = small + 1;
   a.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
   a.repair_list = c->d_repair;
+  a.order = c->d_order;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, cudaMemsetAsync(c->d_small, 0, 256, s));
-  const bool tm = c->timing;
+  const bool tm = c->timing && ncap_fixed == 0;
   c->timed = tm;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
   a.n_max = small + 2;
   a.use_tc = c->use_tc;
   PMOM_CUDA(c, pmom::launch_activate(a, s));
-  c->launches = 1;
-  // the largest support set of the batch sizes the kernels' shared memory and their occupancy
-  int ncap = 0;
-  PMOM_CUDA(c, cudaMemcpyAsync(&ncap, small + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PMOM_CUDA(c, cudaStreamSynchronize(s));
-  a.ncap = ncap < 1 ? 1 : ncap;
+  PMOM_CUDA(c, pmom::launch_order(c->d_nact, B, c->M, c->d_order, s));
+  c->launches = 2;
+  int ncap = ncap_fixed;
+  if (ncap <= 0) {
+    // the largest support set of the batch sizes the kernels' shared memory and their occupancy
+    PMOM_CUDA(c, cudaMemcpyAsync(&ncap, small + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMOM_CUDA(c, cudaStreamSynchronize(s));
+  }
+  a.ncap = ncap < 1 ? 1 : (ncap > c->M ? c->M : ncap);
   const int tasks = B * c->F;
-  st = ensure_work(c, precision, tasks, a.ncap);
+  pmom_status st = ensure_work(c, precision, tasks, a.ncap);
   if (st) return st;
   a.work = c->d_work;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
@@ -343,6 +355,101 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   c->launches += 2;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
   return PMOM_OK;
+}
+
+}  // namespace
+
+pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
+                                 double* fom_out, int32_t* status, void* stream) {
+  if (!c || !maps || !fom_out || !status || B < 1 || (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
+    return fail(c, PMOM_ERR_INVALID_ARG, "eval: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval: load Z and set the FoM bands first");
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  return enqueue_eval(c, maps, B, precision, S_out, fom_out, status, s, 0);
+}
+
+pmom_status pmom_graph_capture(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
+                               double* fom_out, int32_t* status, int32_t ncap, void* stream) {
+  if (!c || !maps || !fom_out || !status || B < 1 || ncap < 0 ||
+      (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
+    return fail(c, PMOM_ERR_INVALID_ARG, "graph_capture: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "graph_capture: load Z and set the FoM bands first");
+  const int cap = (ncap == 0 || ncap > c->M) ? c->M : ncap;
+  // every allocation and launch attribute is settled before the capture starts
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  st = ensure_work(c, precision, B * c->F, cap);
+  if (st) return st;
+  slots_for(c, PMOM_FP64, B * c->F, cap);
+  slots_for(c, precision, B * c->F, cap);
+  // recording executes nothing, so the graph is captured on the context's own stream; launches may
+  // use any stream
+  (void)stream;
+  if (!c->cap_stream) PMOM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = c->cap_stream;
+  if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  PMOM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  st = enqueue_eval(c, maps, B, precision, S_out, fom_out, status, s, cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  c->graph = g;
+  PMOM_CUDA(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+  return PMOM_OK;
+}
+
+pmom_status pmom_graph_launch(pmom_ctx* c, void* stream) {
+  if (!c) return PMOM_ERR_INVALID_ARG;
+  if (!c->graph_exec) return fail(c, PMOM_ERR_NOT_READY, "graph_launch: no captured graph");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  PMOM_CUDA(c, cudaGraphLaunch(c->graph_exec, s));
+  return PMOM_OK;
+}
+
+pmom_status pmom_autotune(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, int32_t* choice,
+                          void* stream) {
+  if (!c || !maps || B < 1) return fail(c, PMOM_ERR_INVALID_ARG, "autotune: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "autotune: load Z and set the FoM bands first");
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  if (precision != PMOM_MIXED_REFINED) {   // one variant only
+    if (choice) *choice = c->use_tc;
+    return PMOM_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  PMOM_CUDA(c, cudaEventCreate(&e0));
+  PMOM_CUDA(c, cudaEventCreate(&e1));
+  float best = 3.4e38f;
+  int best_tc = c->use_tc;
+  for (int tc = 1; tc >= 0; --tc) {
+    c->use_tc = tc;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and sizes workspaces
+      PMOM_CUDA(c, cudaEventRecord(e0, s));
+      st = enqueue_eval(c, maps, B, precision, nullptr, c->d_fom_stage, c->d_status_stage, s, 0);
+      if (st) break;
+      PMOM_CUDA(c, cudaEventRecord(e1, s));
+      PMOM_CUDA(c, cudaEventSynchronize(e1));
+      PMOM_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    }
+    if (st) break;
+    if (ms < best) { best = ms; best_tc = tc; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->use_tc = best_tc;
+  if (choice) *choice = best_tc;
+  return st;
 }
 
 pmom_status pmom_eval_candidates_host(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,

@@ -988,11 +988,14 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
     __syncthreads();
     if (tq >= ntasks) break;
     const int t = a.ntasks_list ? a.repair_list[tq] : tq;
-    const int f = t / a.B, b = t % a.B;
+    const int f = t / a.B, b = a.order ? a.order[t % a.B] : t % a.B;
     const int N = a.n_act[b];
     double2* Sout = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
-    if (N <= 0) {
+    if (N <= 0 || N > a.ncap) {
+      // bad pixel states, or a support set larger than the shared memory this launch was sized
+      // for (a graph captured with a smaller capacity): no solve, NaN S, flagged candidate
       if (tid < P * P) Sout[tid] = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
+      if (tid == 0 && N > a.ncap) atomicOr(&a.flags[b], kFlagCapacity);
       continue;
     }
     const ZT* Zf = Zall + static_cast<size_t>(f) * M * M;
@@ -1159,11 +1162,33 @@ __global__ void fom_kernel(const double2* __restrict__ S, const uint8_t* __restr
   if (n_act[b] < 0 || (fl & kFlagBadState)) {
     st = PMOM_CAND_BAD_STATE;
     sum = __longlong_as_double(0x7ff8000000000000ll);
+  } else if (fl & kFlagCapacity) {
+    st = PMOM_CAND_CAPACITY;
+    sum = __longlong_as_double(0x7ff8000000000000ll);
   } else if ((fl & kFlagNonfinite) || !isfinite(sum)) st = PMOM_CAND_NONFINITE;
   else if (fl & kFlagSingular) st = PMOM_CAND_SINGULAR;
   else if (fl & kFlagRepaired) st = PMOM_CAND_REPAIRED;
   fom[b] = sum;
   status[b] = st;
+}
+
+// Counting sort of candidates by support-set size, descending (stable).  One block.
+__global__ void order_kernel(const int32_t* __restrict__ n_act, int B, int M, int* __restrict__ order) {
+  extern __shared__ int cnt[];   // M + 2 bins: N = -1 (bad) .. M
+  const int nb = M + 2;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) atomicAdd(&cnt[M - max(n_act[b], -1)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int i = 0; i < nb; ++i) {
+      const int c = cnt[i];
+      cnt[i] = run;
+      run += c;
+    }
+    for (int b = 0; b < B; ++b) order[cnt[M - max(n_act[b], -1)]++] = b;
+  }
 }
 
 template <typename ZT>
@@ -1240,6 +1265,11 @@ size_t eval_smem_bytes(int precision, int ncap, int use_tc) {
   size_t u_off, idx_off, tc_off;
   return precision == PMOM_FP64 ? smem_layout<double2>(ncap, 0, &u_off, &idx_off, &tc_off)
                                 : smem_layout<float2>(ncap, use_tc, &u_off, &idx_off, &tc_off);
+}
+
+cudaError_t launch_order(const int32_t* n_act, int B, int M, int* order, cudaStream_t s) {
+  order_kernel<<<1, 256, sizeof(int) * (M + 2), s>>>(n_act, B, M, order);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ys(double2* S, int B, int F, int P, double Z0, uint32_t* flags, cudaStream_t s) {

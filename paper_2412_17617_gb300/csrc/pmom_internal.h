@@ -52,13 +52,19 @@ struct EvalArgs {
   int ncap;                // largest N of the batch (sizes the shared-memory panel); <= M
   int* n_max;              // activation writes max N here (atomicMax)
   int use_tc;              // single-precision LU: trailing updates on the tensor cores (tcgen05)
+  const int* order;        // [B] candidates in task order (largest support set first), or null
 };
 
-enum CandFlag : uint32_t { kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u };
+enum CandFlag : uint32_t {
+  kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u, kFlagCapacity = 16u
+};
 
 // Launchers (pmom_eval.cu).
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
+// Candidates sorted by support-set size, largest first (longest-processing-time order for the
+// persistent queue); one block, B <= 65536.
+cudaError_t launch_order(const int32_t* n_act, int B, int M, int* order, cudaStream_t s);
 // Y -> S in place for every (candidate, frequency) task of the batch (Eq. 6-7).
 cudaError_t launch_ys(double2* S, int B, int F, int P, double Z0, uint32_t* flags, cudaStream_t s);
 cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int B, const uint32_t* flags,

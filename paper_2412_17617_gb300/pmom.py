@@ -19,14 +19,15 @@ PMOM_OK = 0
 PMOM_C64, PMOM_C128 = 0, 1
 PMOM_MEM_HOST, PMOM_MEM_DEVICE = 0, 1
 PMOM_FP64, PMOM_MIXED_REFINED = 0, 1
-CAND_OK, CAND_SINGULAR, CAND_NONFINITE, CAND_REPAIRED, CAND_BAD_STATE = 0, 1, 2, 3, 5
+CAND_OK, CAND_SINGULAR, CAND_NONFINITE, CAND_REPAIRED, CAND_BAD_STATE, CAND_CAPACITY = 0, 1, 2, 3, 5, 6
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z_SHAPE_MISMATCH", 5: "CUDA",
                 6: "NOT_READY", 7: "UNSUPPORTED"}
 # names exported by libpmom.so, one per declaration in include/pmom.h
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
-           "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores")
+           "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_graph_capture", "pmom_graph_launch",
+           "pmom_autotune")
 
 
 class PmomError(RuntimeError):
@@ -80,6 +81,9 @@ def load_library(path: str = LIB_PATH):
         "pmom_sync": [V, V],
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
         "pmom_set_tensor_cores": [V, I32],
+        "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
+        "pmom_graph_launch": [V, V],
+        "pmom_autotune": [V, P, I32, I32, P, V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -239,6 +243,35 @@ class Evaluator:
             self.h, ctypes.c_void_p(maps.ctypes.data), B, prec, ctypes.c_void_p(sp), ctypes.c_void_p(fom.ctypes.data),
             ctypes.c_void_p(status.ctypes.data), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
+
+    def graph_capture(self, maps, precision: str = "mixed", out=None, ncap: int = 0, stream=None):
+        """Record the evaluation of this batch into a CUDA graph; returns the output tensors that
+        each graph_launch() refills."""
+        import torch
+        B = maps.shape[0]
+        prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED
+        if out is None:
+            out = (torch.empty((B, self.F, self.P, self.P), dtype=torch.complex128, device="cuda"),
+                   torch.empty((B,), dtype=torch.float64, device="cuda"),
+                   torch.empty((B,), dtype=torch.int32, device="cuda"))
+        S, fom, status = out
+        self._check(self.L.pmom_graph_capture(
+            self.h, ctypes.c_void_p(maps.data_ptr()), B, prec, ctypes.c_void_p(S.data_ptr() if S is not None else 0),
+            ctypes.c_void_p(fom.data_ptr()), ctypes.c_void_p(status.data_ptr()), int(ncap),
+            ctypes.c_void_p(_stream_ptr(stream))))
+        self._graph_out = out
+        return out
+
+    def graph_launch(self, stream=None):
+        self._check(self.L.pmom_graph_launch(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+        return self._graph_out
+
+    def autotune(self, maps, precision: str = "mixed", stream=None) -> int:
+        prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED
+        ch = ctypes.c_int32(0)
+        self._check(self.L.pmom_autotune(self.h, ctypes.c_void_p(maps.data_ptr()), maps.shape[0], prec, ctypes.byref(ch),
+                                         ctypes.c_void_p(_stream_ptr(stream))))
+        return ch.value
 
     def eval_noalloc(self, maps, precision: str = "mixed", out=None, stream=None):
         """Like eval(), through the entry point that allocates no device memory during the call
