@@ -22,6 +22,16 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// The evaluation kernel runs up to two independent task groups of kThreads threads per CTA: a
+// kernel that allocates tensor memory gets one CTA per SM, and two groups keep two tasks in flight
+// per SM (one overlapping the other's latency-bound phases).  Each group synchronises on its own
+// named barrier and owns a shared-memory region, a workspace slot and 128 TMEM columns.
+constexpr int kMaxGroups = 2;
+__device__ __forceinline__ int gtid() { return threadIdx.x & (kThreads - 1); }
+__device__ __forceinline__ int group_id() { return threadIdx.x / kThreads; }
+__device__ __forceinline__ void gsync() {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "r"(kThreads) : "memory");
+}
 constexpr int kTile = 64;        // trailing-update tile (rows and columns)
 constexpr int kOuter = 64;       // outer panel width of the two-level (tensor-core) LU
 constexpr int kMaxRefine = 10;
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restri
 // ------------------------------------------------------------------ block argmax of |a|^2
 template <typename R>
 __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = gtid() & 31, warp = gtid() >> 5;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     const R ov = __shfl_down_sync(0xffffffffu, v, d);
@@ -174,8 +184,8 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
     if (ov > v || (ov == v && orow >= 0 && (row < 0 || orow < row))) { v = ov; row = orow; }
   }
   if (lane == 0) { s_val[warp] = v; s_row[warp] = row; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  gsync();
+  if (gtid() == 0) {
     R bv = s_val[0];
     int br = s_row[0];
     for (int w = 1; w < kWarps; ++w) {
@@ -183,7 +193,7 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
     }
     s_row[kWarps] = br;
   }
-  __syncthreads();
+  gsync();
   return s_row[kWarps];
 }
 
@@ -214,7 +224,7 @@ __device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, 
 // TMEM across all chunks, which keeps fp32-level accuracy; the tile is then subtracted from A22
 // once.  L21 = A[rb.., j0..j0+jb), U12 = A[j0..j0+jb, rb..), A22 = A[rb.., rb..], rb = j0 + jb.
 __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int jb, TcState& st) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = gtid(), warp = tid >> 5, lane = tid & 31;
   const int rb = j0 + jb, n2 = N - rb;
   const int nk = (jb + 15) >> 4;
   unsigned char* Ah = st.stage;
@@ -256,7 +266,7 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        gsync();
         tc::fence_after_sync();
         if (tid == 0) {
           const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al), bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
@@ -278,7 +288,7 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
           if (!tc::mbar_wait(st.mbar, st.phase, kTcWaitPolls)) st.failed = true;
         }
         st.phase ^= 1u;
-        __syncthreads();
+        gsync();
       }
       tc::fence_after_sync();
       // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update
@@ -293,7 +303,7 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
         for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
       }
       tc::fence_before_sync();
-      __syncthreads();
+      gsync();
       // 32 elements per thread in two batches of 16 independent loads, then the stores
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
@@ -312,7 +322,7 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
           }
         }
       }
-      __syncthreads();
+      gsync();
     }
   }
 }
@@ -321,12 +331,12 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
 // shared memory), A12 = A[j0..j0+jb, cb..N); one column per thread, 16 rows at a time.
 __device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int jb, float2* __restrict__ Ls) {
   constexpr int LDL = 65;
-  const int tid = threadIdx.x, cb = j0 + jb;
+  const int tid = gtid(), cb = j0 + jb;
   for (int e = tid; e < jb * 64; e += kThreads) {
     const int r = e >> 6, c = e & 63;
     Ls[r * LDL + c] = c < jb ? A[static_cast<size_t>(j0 + r) * lda + j0 + c] : make_float2(0.f, 0.f);
   }
-  __syncthreads();
+  gsync();
   for (int c = cb + tid; c < N; c += kThreads) {
     for (int ch = 0; ch * 16 < jb; ++ch) {
       const int rw = min(16, jb - 16 * ch);
@@ -347,7 +357,7 @@ __device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int j
         if (i < rw) A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] = u[i];
     }
   }
-  __syncthreads();
+  gsync();
 }
 
 // ------------------------------------------------------------------ blocked LU in global memory
@@ -361,7 +371,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
   constexpr int NB = Cfg<CT>::NB;
   constexpr int LDP = NB + 1;
   constexpr int LDU = kTile + 1;
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   bool singular = false;
   // Updates made by each NB-column panel stop at column `cend`: N for the one-level CUDA-core
   // path; the end of the current kOuter-column outer panel for the two-level tensor-core path
@@ -375,7 +385,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       const int r = e / NB, c = e % NB;
       if (c < kb) Pn[r * LDP + c] = A[static_cast<size_t>(k0 + r) * lda + k0 + c];
     }
-    __syncthreads();
+    gsync();
     // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row)
     for (int j = 0; j < kb; ++j) {
       R best = -1;
@@ -391,7 +401,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         Pn[j * LDP + tid] = Pn[p * LDP + tid];
         Pn[p * LDP + tid] = t;
       }
-      __syncthreads();
+      gsync();
       const CT d = Pn[j * LDP + j];
       const bool zero = cabs2(d) == R(0);
       if (zero) singular = true;
@@ -401,7 +411,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         Pn[r * LDP + j] = l;
         for (int c = j + 1; c < kb; ++c) Pn[r * LDP + c] = cfms(l, Pn[j * LDP + c], Pn[r * LDP + c]);
       }
-      __syncthreads();
+      gsync();
     }
     // 3. panel back to global memory
     for (int e = tid; e < nr * NB; e += kThreads) {
@@ -421,7 +431,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
           rb[c] = t;
         }
       }
-      __syncthreads();
+      gsync();
     }
     // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory), columns up
     //    to the end of the current outer panel
@@ -437,7 +447,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       for (int i = 0; i < NB; ++i)
         if (i < kb) A[static_cast<size_t>(k0 + i) * lda + c] = u[i];
     }
-    __syncthreads();
+    gsync();
     // 6. trailing update A22 -= L21 U12 on the CUDA cores (64 x 64 tiles, 4 x 4 complex outputs per
     //    thread), for the columns up to the end of the current outer panel
     const int r_begin = k0 + kb, n2 = N - r_begin;
@@ -451,7 +461,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
           const int t = e / kTile, cc = e % kTile;
           Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
         }
-        __syncthreads();
+        gsync();
         for (int tr = 0; tr < ntile; ++tr) {
           const int r0 = tr * kTile;   // relative to r_begin
           CT acc[4][4];
@@ -486,10 +496,10 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
               if (r < n2 && c < cend) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
             }
         }
-        __syncthreads();
+        gsync();
       }
     }
-    __syncthreads();
+    gsync();
     // 7-8. end of an outer panel (tensor-core path): U12 for the columns to its right, then one
     //      K = 64 update of the remaining matrix on the tensor cores
     if constexpr (std::is_same<CT, float2>::value) {
@@ -497,7 +507,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         const int j0 = cend - ((cend - 1) % kOuter + 1);
         outer_trsm(A, lda, N, j0, cend - j0, reinterpret_cast<float2*>(tcs->stage));
         trailing_tc(A, lda, N, j0, cend - j0, *tcs);
-        __syncthreads();
+        gsync();
       }
     }
   }
@@ -510,7 +520,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
                          int P, CT* __restrict__ D) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
     for (int k = 0; k < N; ++k) {
       const int p = piv[k];
@@ -522,7 +532,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
       __syncwarp();
     }
   }
-  __syncthreads();
+  gsync();
   // forward: L y = P b, unit diagonal, blocks of 32 rows
   for (int i0 = 0; i0 < N; i0 += 32) {
     const int bs = min(32, N - i0);
@@ -568,7 +578,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
           }
         }
       }
-      __syncthreads();
+      gsync();
     }
     if (warp == 0) {
       const int i = i0 + lane;
@@ -590,7 +600,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
       for (int p = 0; p < kMaxPorts; ++p)
         if (lane < bs && p < P) W[i * P + p] = w[p];
     }
-    __syncthreads();
+    gsync();
   }
   // backward: U x = y, blocks of 32 rows from the bottom
   for (int i1 = N; i1 > 0; i1 -= 32) {
@@ -637,7 +647,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
           }
         }
       }
-      __syncthreads();
+      gsync();
     }
     if (warp == 0) {
       const int i = i0 + lane;
@@ -665,7 +675,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
       for (int p = 0; p < kMaxPorts; ++p)
         if (lane < bs && p < P) W[i * P + p] = w[p];
     }
-    __syncthreads();
+    gsync();
   }
 }
 
@@ -694,7 +704,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
   for (int i0 = warp; i0 < N; i0 += kWarps * R) {
     float rh[R][kMaxPorts], rl[R][kMaxPorts], ih[R][kMaxPorts], il[R][kMaxPorts], ra[R];
@@ -760,7 +770,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
     s_red[warp] = rmax;
     s_red[kWarps + warp] = zmax;
   }
-  __syncthreads();
+  gsync();
   if (tid == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < kWarps; ++w) {
@@ -770,7 +780,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
     s_out[0] = a;
     s_out[1] = b;
   }
-  __syncthreads();
+  gsync();
 }
 
 // double-storage residual (complex128 database): plain FP64
@@ -779,7 +789,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
 template <typename ZT>
 __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N, const double2* x_s,
                          int P, const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
   for (int i = warp; i < N; i += kWarps) {
     const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
@@ -818,7 +828,7 @@ __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict
     s_red[warp] = rmax;
     s_red[kWarps + warp] = zmax;
   }
-  __syncthreads();
+  gsync();
   if (tid == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < kWarps; ++w) {
@@ -828,7 +838,7 @@ __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict
     s_out[0] = a;
     s_out[1] = b;
   }
-  __syncthreads();
+  gsync();
 }
 
 // ------------------------------------------------------------------ Y -> S (Eq. 6-7)
@@ -900,8 +910,10 @@ __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_byt
   return s;
 }
 
-// Dynamic shared memory: [panel (M x (NB+1)) | U tile | idx (M ints) | tensor-core staging
-// (64 KB + 2 KB alignment slack, single-precision tensor-core path only)].
+// Dynamic shared memory: [union of the panel (M x (NB+1)), the x cache and, for the tensor-core
+// path, the operand staging (64 KB + 2 KB alignment slack) | U tile / diagonal block | idx (M ints)].
+// The staging is only live during the outer-panel steps, when the panel has been written back, so
+// the two share memory and the tensor-core variant still fits two CTAs per SM.
 constexpr size_t kTcStageBytes = 65536 + 2048;   // 64 KB operands (or the 128 x 65 result tile) + alignment
 
 template <typename CT>
@@ -910,66 +922,86 @@ __host__ __device__ inline size_t smem_layout(int M, int use_tc, size_t* u_off, 
   size_t panel = static_cast<size_t>(M) * (NB + 1) * sizeof(CT);
   const size_t xcache = static_cast<size_t>(M) * kMaxPorts * sizeof(double2);
   if (xcache > panel) panel = xcache;
+  if (use_tc && panel < kTcStageBytes) panel = kTcStageBytes;
   panel = (panel + 15) & ~size_t(15);
+  *tc_off = 0;
   *u_off = panel;
   size_t u = static_cast<size_t>(NB) * (kTile + 1) * sizeof(CT);
   if (u < 32 * 33 * sizeof(CT)) u = 32 * 33 * sizeof(CT);
   *idx_off = panel + ((u + 15) & ~size_t(15));
-  *tc_off = *idx_off + ((static_cast<size_t>(M) * sizeof(int) + 15) & ~size_t(15));
-  return *tc_off + (use_tc ? kTcStageBytes : 0);
+  return *idx_off + static_cast<size_t>(M) * sizeof(int);
+}
+
+// One group's share of the dynamic shared memory (1024-byte multiple so every group's region
+// starts aligned like the first).
+template <typename CT>
+__host__ __device__ inline size_t group_smem_bytes(int M, int use_tc) {
+  size_t u_off, idx_off, tc_off;
+  const size_t b = smem_layout<CT>(M, use_tc, &u_off, &idx_off, &tc_off);
+  return (b + 1023) & ~size_t(1023);
 }
 
 template <typename ZT> struct XCache;
 template <> struct XCache<float2> { using type = float4; };
 template <> struct XCache<double2> { using type = double2; };
 
-// TC: the single-precision LU runs its outer-panel updates on the tensor cores.  That variant holds
-// 66 KB more shared memory and runs one CTA per SM, so it may use the full register file.
+// TC: the single-precision LU runs its outer-panel updates on the tensor cores.
 template <typename CT, typename ZT, bool MIXED, bool TC>
-__global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) {
+__global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs a) {
   using R = typename Real<CT>::type;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ R s_val[kWarps + 1];
-  __shared__ int s_row[kWarps + 1];
-  __shared__ double s_red[2 * kWarps];
-  __shared__ double s_norm[2];
-  __shared__ int s_task;
-  __shared__ int s_flag;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  __shared__ R s_val_g[kMaxGroups][kWarps + 1];
+  __shared__ int s_row_g[kMaxGroups][kWarps + 1];
+  __shared__ double s_red_g[kMaxGroups][2 * kWarps];
+  __shared__ double s_norm_g[kMaxGroups][2];
+  __shared__ int s_task_g[kMaxGroups];
+  __shared__ int s_flag_g[kMaxGroups];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups];
   constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
+  const int g = group_id();
+  const int ngroups = blockDim.x / kThreads;
+  R* s_val = s_val_g[g];
+  int* s_row = s_row_g[g];
+  double* s_red = s_red_g[g];
+  double* s_norm = s_norm_g[g];
+  int& s_task = s_task_g[g];
+  int& s_flag = s_flag_g[g];
   size_t u_off, idx_off, tc_off;
+  const size_t group_bytes = group_smem_bytes<CT>(a.ncap, use_tc);
   smem_layout<CT>(a.ncap, use_tc, &u_off, &idx_off, &tc_off);
+  unsigned char* smem = smem_all + g * group_bytes;
   CT* Pn = reinterpret_cast<CT*>(smem);
   CT* Ut = reinterpret_cast<CT*>(smem + u_off);
   int* s_idx = reinterpret_cast<int*>(smem + idx_off);
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   TcState tcs;
   tcs.stage = nullptr;
   tcs.tmem = 0;
-  tcs.mbar = &s_mbar;
+  tcs.mbar = &s_mbar_g[g];
   tcs.phase = 0;
   tcs.failed = false;
   if (use_tc) {
-    // 1024-byte aligned operand staging inside the slack of the tensor-core region
+    // 1024-byte aligned operand staging inside this group's tensor-core region
     const uint32_t base = tc::smem_u32(smem + tc_off);
     tcs.stage = smem + tc_off + ((1024u - (base & 1023u)) & 1023u);
-    if ((tid >> 5) == 0) {
-      tc::tmem_alloc(&s_tmem, 128);
+    if (threadIdx.x < 32) {   // one warp allocates 128 TMEM columns per group for the whole CTA
+      tc::tmem_alloc(&s_tmem, 128u * ngroups);
       tc::tmem_relinquish();
     }
-    if (tid == 0) {
-      tc::mbar_init(&s_mbar, 1);
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < ngroups; ++i) tc::mbar_init(&s_mbar_g[i], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    tcs.tmem = s_tmem;
+    tcs.tmem = s_tmem + 128u * g;
   }
   const int P = a.P, M = a.M, lda = a.lda;
   const Slot sl = slot_layout(M, lda, P, sizeof(CT));
-  unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * blockIdx.x;
+  const int slot = blockIdx.x * ngroups + g;
+  unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * slot;
   CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
   float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
   int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
@@ -982,10 +1014,11 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
   for (int p = 0; p < kMaxPorts; ++p) lport[p] = a.port_len[p];
 
   for (;;) {
+    if (slot >= a.nslots) break;   // a spare group (odd slot count): no workspace
     if (tid == 0) s_task = atomicAdd(a.task_counter, 1);
-    __syncthreads();
+    gsync();
     const int tq = s_task;
-    __syncthreads();
+    gsync();
     if (tq >= ntasks) break;
     const int t = a.ntasks_list ? a.repair_list[tq] : tq;
     const int f = t / a.B, b = a.order ? a.order[t % a.B] : t % a.B;
@@ -1001,7 +1034,7 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
     const ZT* Zf = Zall + static_cast<size_t>(f) * M * M;
     const int32_t* gidx = a.idx + static_cast<size_t>(b) * M;
     for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
-    __syncthreads();
+    gsync();
     // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
     constexpr bool kZsCopy = MIXED && std::is_same<ZT, float2>::value;
     for (int i = 0; i < N; ++i) {
@@ -1014,7 +1047,7 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
         if constexpr (kZsCopy) zsrow[j] = v;
       }
     }
-    __syncthreads();
+    gsync();
     const bool singular = lu_factor<CT>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
     // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
     CT* W = Pn;
@@ -1022,10 +1055,10 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
       const int i = e / P, p = e % P;
       W[e] = from_d2<CT>(make_double2(i == 3 * p + 1 ? lport[p] : 0.0, 0.0));
     }
-    __syncthreads();
+    gsync();
     lu_solve<CT>(A, lda, N, piv, W, P, Ut);
     for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
-    __syncthreads();
+    gsync();
     int iters = 0;
     bool repaired = false;
     if (MIXED) {
@@ -1043,20 +1076,20 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
             xf[e] = make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
             xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
           }
-          __syncthreads();
+          gsync();
           residual_df(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm);
         } else {
           for (int e = tid; e < N * P; e += kThreads) {
             xs[e] = X[e];
             xmax = fmax(xmax, fabs(X[e].x) + fabs(X[e].y));
           }
-          __syncthreads();
+          gsync();
           residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
         if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
-        __syncthreads();
+        gsync();
         if (tid == 0) {
           double m = 0.0;
           for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
@@ -1069,7 +1102,7 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
           s_flag = flag;
           s_norm[0] = rn;
         }
-        __syncthreads();
+        gsync();
         const int flag = s_flag;
         rprev = s_norm[0];
         if (flag != 0) {
@@ -1077,13 +1110,13 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
           break;
         }
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
-        __syncthreads();
+        gsync();
         lu_solve<CT>(A, lda, N, piv, W, P, Ut);
         for (int e = tid; e < N * P; e += kThreads) {
           const double2 d = to_d2(W[e]);
           X[e] = make_double2(X[e].x + d.x, X[e].y + d.y);
         }
-        __syncthreads();
+        gsync();
         ++iters;
       }
       if (!converged) repaired = true;
@@ -1114,12 +1147,12 @@ __global__ void __launch_bounds__(kThreads, TC ? 1 : 2) eval_kernel(EvalArgs a) 
       const double2 xv = X[(3 * i + 1) * P + j];
       Sout[tid] = make_double2(lport[i] * xv.x, lport[i] * xv.y);
     }
-    __syncthreads();
+    gsync();
   }
-  if (use_tc) {
+  if (use_tc) {   // both groups are done with the tensor memory
     tc::fence_before_sync();
     __syncthreads();
-    if ((tid >> 5) == 0) tc::tmem_dealloc(tcs.tmem, 128);
+    if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, 128u * ngroups);
   }
 }
 
@@ -1201,28 +1234,42 @@ __global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int3
   }
 }
 
-template <typename CT, typename ZT, bool MIXED, bool TC>
-cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
-  if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M) return cudaErrorInvalidValue;
-  size_t u_off, idx_off, tc_off;
-  const size_t smem = smem_layout<CT>(a.ncap, TC, &u_off, &idx_off, &tc_off);
-  auto k = eval_kernel<CT, ZT, MIXED, TC>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  k<<<nslots, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+// Task groups per CTA: two when both groups' shared memory fits one CTA, else one.
+template <typename CT>
+int groups_for(int ncap, bool tc) {
+  int optin = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t gb = group_smem_bytes<CT>(ncap, tc);
+  return (2 * gb + 2048 <= static_cast<size_t>(optin)) ? 2 : 1;
 }
 
 template <typename CT, typename ZT, bool MIXED, bool TC>
+cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
+  if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M || nslots < 1) return cudaErrorInvalidValue;
+  const int groups = groups_for<CT>(a.ncap, TC);
+  const size_t smem = groups * group_smem_bytes<CT>(a.ncap, TC);
+  auto k = eval_kernel<CT, ZT, MIXED, TC>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  EvalArgs b = a;
+  b.nslots = nslots;
+  k<<<(nslots + groups - 1) / groups, kThreads * groups, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+// Resident task groups per SM (CTAs per SM x groups per CTA).
+template <typename CT, typename ZT, bool MIXED, bool TC>
 int blocks_per_sm_t(int M) {
-  size_t u_off, idx_off, tc_off;
-  const size_t smem = smem_layout<CT>(M, TC, &u_off, &idx_off, &tc_off);
+  const int groups = groups_for<CT>(M, TC);
+  const size_t smem = groups * group_smem_bytes<CT>(M, TC);
   auto k = eval_kernel<CT, ZT, MIXED, TC>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) return 0;
-  return n;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads * groups, smem) != cudaSuccess) return 0;
+  return n * groups;
 }
 
 }  // namespace

@@ -53,6 +53,7 @@ struct EvalArgs {
   int* n_max;              // activation writes max N here (atomicMax)
   int use_tc;              // single-precision LU: trailing updates on the tensor cores (tcgen05)
   const int* order;        // [B] candidates in task order (largest support set first), or null
+  int nslots;              // workspace slots of this launch (set by the launcher)
 };
 
 enum CandFlag : uint32_t {
