@@ -196,6 +196,27 @@ pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev,
  * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning. */
 pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
 
+/* Depth-increasing all-way tree search (paper Algorithm 1, Section III-A; hyper-parameters of
+ * Section III-D: Dmax = 2 with M(1) = 10, M(2) = 3 for the 8-state case).  A pixel is an (x, y)
+ * column whose state is the bit pattern of its layers; every tree node branches into all other
+ * states of one column drawn uniformly (counter-based SplitMix64 keyed by seed, restart,
+ * iteration, depth and node) among the columns not yet on its path; each tree level is one
+ * evaluator batch.  The best depth-D leaf is accepted only if its FoM is strictly lower; after
+ * m_of_d[D-1] failures the depth grows; past d_max the search restarts from a random half-filled
+ * map.  Stops when max_evals evaluations are used (a started tree is finished).
+ *   init_map_host / best_map_host: uint8 [layers][ny][nx]; trace_host (optional): the current
+ *   FoM after each iteration, up to trace_cap entries. */
+typedef struct {
+  uint64_t seed;
+  int32_t d_max;          /* 1..8 */
+  int32_t m_of_d[8];      /* non-improving iterations tolerated at each depth */
+  int64_t max_evals;      /* FoM evaluation budget */
+  int32_t precision;      /* PMOM_FP64 or PMOM_MIXED_REFINED */
+} pmom_search_params;
+pmom_status pmom_search(pmom_ctx* ctx, const pmom_search_params* params, const uint8_t* init_map_host,
+                        uint8_t* best_map_host, double* best_fom, int64_t* evals_used, double* trace_host,
+                        int32_t trace_cap, int32_t* trace_len, void* stream);
+
 /* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
  * max iterations of one task, tasks re-solved in FP64, tensor-core waits that ran out (the
  * task's candidate then reports PMOM_CAND_NONFINITE), reserved, kernel launches issued,

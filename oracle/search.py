@@ -1,0 +1,117 @@
+"""Plain reference of the paper's depth-increasing all-way tree search (Algorithm 1, Section III-A).
+
+TEST INFRASTRUCTURE ONLY (oracle side): it evaluates candidates with the CPU oracle.  The
+library's native search (pmom_search) is checked against it decision by decision.
+
+Readings where Algorithm 1 leaves a choice open:
+  * a pixel is one (x, y) column; its state is the bit pattern of its layers (K = 2**layers
+    states), so a node has K - 1 children, one per other state of the chosen column;
+  * the column j of node (d, k) is drawn uniformly from the columns not yet on the node's path,
+    with the counter-based SplitMix64 generator keyed by (seed, restart, iteration, d, k);
+  * every child at every depth is evaluated; the best leaf is the argmin over depth-D leaves
+    only (ties: lowest leaf index); it is accepted if strictly better than the current F;
+  * after M(D) consecutive non-improving iterations the depth grows; when it would exceed Dmax
+    the search restarts from a random map (each layer pixel metal with probability 1/2, drawn by
+    the same generator) at depth 1, keeping the global best;
+  * the search stops once the evaluation budget is used up (a started tree is finished);
+  * a candidate whose evaluation failed (non-finite FoM) counts as +infinity.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASK = (1 << 64) - 1
+GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64(x: int) -> int:
+    """One output of SplitMix64 (Steele, Lea and Flood, 2014) from state x (state advanced first)."""
+    z = (x + GOLDEN) & MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK
+    return z ^ (z >> 31)
+
+
+def key(*parts: int) -> int:
+    h = 0
+    for p in parts:
+        h = splitmix64(h ^ (p & MASK))
+    return h
+
+
+def random_map(seed: int, restart: int, shape) -> np.ndarray:
+    L, ny, nx = shape
+    out = np.zeros(shape, np.uint8)
+    for i in range(L * ny * nx):
+        out.flat[i] = key(seed, 0xA5A5, restart, i) >> 63
+    return out
+
+
+def column_state(m: np.ndarray, j: int) -> int:
+    L, ny, nx = m.shape
+    y, x = divmod(j, nx)
+    return sum(int(m[l, y, x]) << l for l in range(L))
+
+
+def set_column(m: np.ndarray, j: int, s: int) -> np.ndarray:
+    L, ny, nx = m.shape
+    y, x = divmod(j, nx)
+    c = m.copy()
+    for l in range(L):
+        c[l, y, x] = (s >> l) & 1
+    return c
+
+
+def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, max_evals: int):
+    """evaluate(maps[B][L][ny][nx]) -> FoM[B].  Returns (best_map, best_F, evals, trace) where
+    trace[i] is the current F after iteration i."""
+    L, ny, nx = init_map.shape
+    ncol, K = ny * nx, 1 << L
+
+    def F_of(maps):
+        f = np.asarray(evaluate(np.ascontiguousarray(maps)), dtype=np.float64)
+        return np.where(np.isfinite(f), f, np.inf)
+
+    P = init_map.copy()
+    F = float(F_of(P[None])[0])
+    evals = 1
+    best_P, best_F = P.copy(), F
+    D, counter, restart, it = 1, 0, 0, 0
+    trace = []
+    while evals < max_evals:
+        nodes = [(frozenset(), P)]
+        Fs = None
+        for d in range(D):
+            children = []
+            for k, (S, Pn) in enumerate(nodes):
+                free = [c for c in range(ncol) if c not in S]
+                j = free[key(seed, restart, it, d, k) % len(free)]
+                cur = column_state(Pn, j)
+                for s in range(K):
+                    if s != cur:
+                        children.append((S | {j}, set_column(Pn, j, s)))
+            Fs = F_of(np.stack([c[1] for c in children]))
+            evals += len(children)
+            nodes = children
+        b = int(np.argmin(Fs))
+        if Fs[b] < F:
+            P, F = nodes[b][1], float(Fs[b])
+            counter = 0
+        else:
+            counter += 1
+        if F < best_F:
+            best_P, best_F = P.copy(), F
+        if counter >= m_of_d[D - 1]:
+            D += 1
+            counter = 0
+        if D > d_max:
+            restart += 1
+            P = random_map(seed, restart, (L, ny, nx))
+            F = float(F_of(P[None])[0])
+            evals += 1
+            D, counter = 1, 0
+            if F < best_F:
+                best_P, best_F = P.copy(), F
+        trace.append(F)
+        it += 1
+    return best_P, best_F, evals, trace

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpmom.so")
-SOURCES = ["pmom_api.cu", "pmom_eval.cu", "pmom_fill.cu", "pmom_mesh.cpp"]
+SOURCES = ["pmom_api.cu", "pmom_eval.cu", "pmom_fill.cu", "pmom_mesh.cpp", "pmom_search.cpp"]
 HEADERS = [os.path.join(CSRC, "pmom_internal.h"), os.path.join(os.path.dirname(HERE), "include", "pmom.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]

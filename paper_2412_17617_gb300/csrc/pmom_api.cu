@@ -54,6 +54,10 @@ struct pmom_ctx {
   std::string err;
 };
 
+namespace pmom {
+const Grid& grid_of(const pmom_ctx* c) { return c->grid; }
+}  // namespace pmom
+
 namespace {
 
 pmom_status fail(pmom_ctx* c, pmom_status st, const std::string& msg) {

@@ -25,6 +25,9 @@ struct Grid {
   int pixels() const { return layers * nx * ny; }
 };
 
+// Grid of a context (pmom_api.cu).
+const Grid& grid_of(const pmom_ctx* c);
+
 // Builds the canonical BF table (see pmom_bf_table in pmom.h).  Returns M.
 int build_bf_table(const Grid& g, std::vector<int32_t>& table);
 

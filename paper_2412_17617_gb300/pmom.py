@@ -27,7 +27,7 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
            "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_graph_capture", "pmom_graph_launch",
-           "pmom_autotune")
+           "pmom_autotune", "pmom_search")
 
 
 class PmomError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
+        "pmom_search": [V, P, P, P, P, P, P, I32, P, V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -115,6 +116,11 @@ def band_codes(freqs, bands) -> np.ndarray:
         elif bands.s[0] <= f <= bands.s[1]:
             out[i] = 3
     return out
+
+
+class _SearchParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("d_max", ctypes.c_int32), ("m_of_d", ctypes.c_int32 * 8),
+                ("max_evals", ctypes.c_int64), ("precision", ctypes.c_int32)]
 
 
 class Evaluator:
@@ -289,6 +295,24 @@ class Evaluator:
             self.h, ctypes.c_void_p(maps.data_ptr()), B, prec, ctypes.c_void_p(S.data_ptr() if S is not None else 0),
             ctypes.c_void_p(fom.data_ptr()), ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
+
+    def search(self, init_map: np.ndarray, seed: int, d_max: int = 2, m_of_d=(10, 3), max_evals: int = 1000,
+               precision: str = "mixed", trace_cap: int = 100000, stream=None):
+        """Algorithm 1 on the GPU evaluator.  Returns (best_map, best_fom, evals, trace)."""
+        m = list(m_of_d) + [m_of_d[-1]] * (8 - len(m_of_d))
+        prm = _SearchParams(seed, d_max, (ctypes.c_int32 * 8)(*m[:8]), max_evals,
+                            PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED)
+        init = np.ascontiguousarray(init_map, dtype=np.uint8)
+        best = np.zeros_like(init)
+        bf = ctypes.c_double(0.0)
+        ev = ctypes.c_int64(0)
+        tr = np.zeros(trace_cap, np.float64)
+        tl = ctypes.c_int32(0)
+        self._check(self.L.pmom_search(self.h, ctypes.byref(prm), ctypes.c_void_p(init.ctypes.data),
+                                       ctypes.c_void_p(best.ctypes.data), ctypes.byref(bf), ctypes.byref(ev),
+                                       ctypes.c_void_p(tr.ctypes.data), trace_cap, ctypes.byref(tl),
+                                       ctypes.c_void_p(_stream_ptr(stream))))
+        return best, bf.value, ev.value, tr[: tl.value].copy()
 
     def stats(self) -> dict:
         out = np.zeros(8, dtype=np.int64)

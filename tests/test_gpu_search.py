@@ -1,0 +1,55 @@
+"""Decision parity of the native tree search (Algorithm 1 on the GPU evaluator) with the oracle's."""
+import numpy as np
+import pytest
+
+import pmom_inputs as PI
+from oracle import oracle as O
+from oracle import search as OS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2412_17617_gb300 import build as B
+    B.build()
+    from paper_2412_17617_gb300 import pmom
+    return pmom
+
+
+def _problem(g, freqs, bands):
+    OG = O.Grid(g)
+    Z, _ = O.fill(OG, freqs)
+    band = O.bands(freqs, bands)
+
+    def evaluate(maps):
+        S, _ = O.eval_batch(OG, Z, maps)
+        return O.fom_batch(S, band)
+    return Z, band, evaluate
+
+
+@pytest.mark.parametrize("case", ["tiny_3x3", "plain_8x8", "stripline_4x4x2"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_search_decisions_match_oracle(built, case, prec):
+    if case == "tiny_3x3":
+        g, freqs, bands, budget = PI.grid_tiny(3), np.array([2.0e9, 2.5e9, 3.5e9, 5.0e9]), PI.PLAIN_BANDS, 300
+    elif case == "plain_8x8":
+        g, freqs, bands, budget = PI.grid_plain_8x8(), np.array([2.0e9, 3.0e9, 5.0e9]), PI.PLAIN_BANDS, 120
+    else:
+        g = PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5625e-3)
+        freqs, bands, budget = np.array([5.5e9, 6.2e9, 6.8e9, 8.0e9]), PI.UNII_BANDS, 150
+    Z, band, evaluate = _problem(g, freqs, bands)
+    ev = built.Evaluator(g)
+    ev.load_Z(freqs, torch.from_numpy(Z).cuda())
+    ev.set_fom(band)
+    init = PI.seed_map(g, 0.5, 5)
+    m_ref, f_ref, e_ref, t_ref = OS.tree_search(evaluate, init, seed=42, d_max=2, m_of_d=(10, 3), max_evals=budget)
+    m_gpu, f_gpu, e_gpu, t_gpu = ev.search(init, seed=42, d_max=2, m_of_d=(10, 3), max_evals=budget, precision=prec)
+    ev.close()
+    tol = 1e-6 if prec == "mixed" else 1e-10
+    assert e_gpu == e_ref
+    assert len(t_gpu) == len(t_ref)
+    assert np.allclose(t_gpu, t_ref, rtol=tol, atol=0)      # identical decisions, same FoM path
+    assert np.array_equal(m_gpu, m_ref)
+    assert f_gpu == pytest.approx(f_ref, rel=tol)
