@@ -196,6 +196,14 @@ pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev,
  * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning. */
 pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
 
+/* Support-set capacity of one task on this GPU for `precision` (PMOM_FP64 or
+ * PMOM_MIXED_REFINED): *n_default = the largest N the default shared-memory layout holds (wide
+ * panels, solve vectors in shared memory, up to two tasks per SM); *n_max = the largest N any
+ * layout holds (narrow panels, solve vectors in the task's global workspace, one task per SM).
+ * Candidates with N > *n_max are returned with status PMOM_CAND_CAPACITY.  Both are capped at M.
+ * Needs the GPU.  Errors: INVALID_ARG, CUDA. */
+pmom_status pmom_capacity(pmom_ctx* ctx, int32_t precision, int32_t* n_default, int32_t* n_max);
+
 /* Depth-increasing all-way tree search (paper Algorithm 1, Section III-A; hyper-parameters of
  * Section III-D: Dmax = 2 with M(1) = 10, M(2) = 3 for the 8-state case).  A pixel is an (x, y)
  * column whose state is the bit pattern of its layers; every tree node branches into all other

@@ -41,6 +41,7 @@ struct pmom_ctx {
   // slot workspaces
   void* d_work = nullptr;
   size_t work_bytes = 0;
+  int max_slots = 0;   // > 0: task slots limited by free device memory (large support sets)
   cudaStream_t last_stream = nullptr;
   int64_t launches = 0;
   bool timing = false;
@@ -109,9 +110,18 @@ pmom_status ensure_batch(pmom_ctx* c, int B) {
   return PMOM_OK;
 }
 
+// Support-set capacity of a launch: the batch's largest set, clipped to what one task group's
+// shared memory holds for this precision (larger candidates are flagged, not solved).
+int ncap_for(pmom_ctx* c, int precision, int ncap) {
+  const int mx = pmom::eval_max_ncap(precision, c->M);
+  if (ncap > mx) ncap = mx;
+  return ncap < 1 ? 1 : ncap;
+}
+
 int slots_for(pmom_ctx* c, int precision, int tasks, int ncap) {
   const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128, c->use_tc);
   int n = (per_sm > 0 ? per_sm : 1) * c->num_sms;
+  if (c->max_slots > 0 && n > c->max_slots) n = c->max_slots;
   if (n > tasks) n = tasks;
   return n < 1 ? 1 : n;
 }
@@ -119,16 +129,34 @@ int slots_for(pmom_ctx* c, int precision, int tasks, int ncap) {
 // Slot workspaces for this call: the launch of `precision` and, for the mixed path, the FP64
 // repair launch that follows it (they reuse the same memory one after the other).
 pmom_status ensure_work(pmom_ctx* c, int precision, int tasks, int ncap) {
-  size_t need = 0;
-  for (int prec = 0; prec < 2; ++prec) {
-    if (prec != precision && prec != PMOM_FP64) continue;
-    int lda = 0;
-    const size_t sb = pmom::eval_slot_bytes(prec, c->M, c->grid.n_ports, &lda);
-    const size_t n = static_cast<size_t>(slots_for(c, prec, tasks, ncap));
-    if (sb * n > need) need = sb * n;
-  }
+  auto need_of = [&](size_t* sb_max) {
+    size_t need = 0;
+    *sb_max = 0;
+    for (int prec = 0; prec < 2; ++prec) {
+      if (prec != precision && prec != PMOM_FP64) continue;
+      int lda = 0;
+      const size_t sb = pmom::eval_slot_bytes(prec, ncap_for(c, prec, ncap), c->grid.n_ports, &lda);
+      const size_t n = static_cast<size_t>(slots_for(c, prec, tasks, ncap_for(c, prec, ncap)));
+      if (sb * n > need) need = sb * n;
+      if (sb > *sb_max) *sb_max = sb;
+    }
+    return need;
+  };
+  c->max_slots = 0;
+  size_t sb_max = 0;
+  size_t need = need_of(&sb_max);
   if (need <= c->work_bytes && c->d_work) return PMOM_OK;
   free_dev(c->d_work);
+  c->work_bytes = 0;
+  // large support sets: as many slots as free memory allows (1 GiB kept for the runtime)
+  size_t free_b = 0, total_b = 0;
+  PMOM_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+  const size_t reserve = size_t(1) << 30;
+  if (need + reserve > free_b) {
+    const size_t fit = free_b > reserve + sb_max ? (free_b - reserve) / sb_max : 1;
+    c->max_slots = static_cast<int>(fit < 1 ? 1 : fit);
+    need = need_of(&sb_max);
+  }
   PMOM_CUDA(c, cudaMalloc(&c->d_work, need));
   c->work_bytes = need;
   return PMOM_OK;
@@ -334,13 +362,14 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
     PMOM_CUDA(c, cudaMemcpyAsync(&ncap, small + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     PMOM_CUDA(c, cudaStreamSynchronize(s));
   }
-  a.ncap = ncap < 1 ? 1 : (ncap > c->M ? c->M : ncap);
+  ncap = ncap < 1 ? 1 : (ncap > c->M ? c->M : ncap);
+  a.ncap = ncap_for(c, precision, ncap);
   const int tasks = B * c->F;
-  pmom_status st = ensure_work(c, precision, tasks, a.ncap);
+  pmom_status st = ensure_work(c, precision, tasks, ncap);
   if (st) return st;
   a.work = c->d_work;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
-  a.slot_bytes = pmom::eval_slot_bytes(precision, c->M, P, &a.lda);
+  a.slot_bytes = pmom::eval_slot_bytes(precision, a.ncap, P, &a.lda);
   a.ntasks_list = 0;
   PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks, a.ncap), s));
   ++c->launches;
@@ -348,7 +377,8 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
   if (precision == PMOM_MIXED_REFINED) {
     // tasks whose refinement did not converge are solved again on the FP64 path
     PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
-    a.slot_bytes = pmom::eval_slot_bytes(PMOM_FP64, c->M, P, &a.lda);
+    a.ncap = ncap_for(c, PMOM_FP64, ncap);
+    a.slot_bytes = pmom::eval_slot_bytes(PMOM_FP64, a.ncap, P, &a.lda);
     a.ntasks_list = 1;
     PMOM_CUDA(c, pmom::launch_eval(a, PMOM_FP64, slots_for(c, PMOM_FP64, tasks, a.ncap), s));
     ++c->launches;
@@ -387,8 +417,8 @@ pmom_status pmom_graph_capture(pmom_ctx* c, const uint8_t* maps, int32_t B, int3
   if (st) return st;
   st = ensure_work(c, precision, B * c->F, cap);
   if (st) return st;
-  slots_for(c, PMOM_FP64, B * c->F, cap);
-  slots_for(c, precision, B * c->F, cap);
+  slots_for(c, PMOM_FP64, B * c->F, ncap_for(c, PMOM_FP64, cap));
+  slots_for(c, precision, B * c->F, ncap_for(c, precision, cap));
   // recording executes nothing, so the graph is captured on the context's own stream; launches may
   // use any stream
   (void)stream;
@@ -494,6 +524,22 @@ pmom_status pmom_stats(pmom_ctx* c, int64_t* out8) {
 pmom_status pmom_set_tensor_cores(pmom_ctx* c, int32_t on) {
   if (!c) return PMOM_ERR_INVALID_ARG;
   c->use_tc = on != 0;
+  return PMOM_OK;
+}
+
+pmom_status pmom_capacity(pmom_ctx* c, int32_t precision, int32_t* n_default, int32_t* n_max) {
+  if (!c || !n_default || !n_max || (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
+    return fail(c, PMOM_ERR_INVALID_ARG, "capacity: bad argument");
+  pmom_status st = ensure_device(c);
+  if (st) return st;
+  *n_max = pmom::eval_max_ncap(precision, c->M);
+  // largest N that stays on the default layout (the layout size grows with N: binary search)
+  int lo = 0, hi = c->M + 1;   // default(lo) (lo = 0 trivially), !default(hi)
+  while (hi - lo > 1) {
+    const int mid = lo + (hi - lo) / 2;
+    if (!pmom::eval_is_large(precision, mid, c->use_tc)) lo = mid; else hi = mid;
+  }
+  *n_default = lo;
   return PMOM_OK;
 }
 

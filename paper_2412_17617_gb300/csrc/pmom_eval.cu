@@ -1,1275 +1,16 @@
-// Candidate-evaluation kernels for sm_103a.
-//
-//   activate_kernel : pixel map -> active-BF indices I (Eq. 3, ascending) by a block-wide ballot scan
-//   eval_kernel     : persistent; one CTA per (frequency, candidate) task at a time, frequency-major
-//                     so the parent Z(f) being read stays resident in L2.  Per task:
-//                       gather Z_sub = Z(f)[I, I]                           (Eq. 4-5)
-//                       blocked right-looking LU, partial pivoting          (Eq. 2)
-//                       forward/back substitution for the P port excitations
-//                       [mixed] iterative refinement: residual V - Z_sub x in double from the
-//                               exact stored Z entries, correction with the single-precision LU
-//                       Y_ij = l_i x_i^(j), S = (1 + Z0 Y)^-1 (1 - Z0 Y)   (Eq. 6-7)
-//   fom_kernel      : FoM of Eq. (8)-(9) per candidate, frequencies summed in order.
-#include <cfloat>
-#include <cstdint>
-#include <type_traits>
-
-#include "pmom_internal.h"
-#include "pmom_tc.cuh"
+// Candidate-evaluation launchers for sm_103a: the default-layout evaluation kernels, the
+// activation, ordering, Y -> S, FoM and gather kernels.  The large-support-set variants are
+// compiled in pmom_eval_large.cu (a separate translation unit so the two build in parallel).
+#include "pmom_eval_kernels.cuh"
 
 namespace pmom {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-// The evaluation kernel runs up to two independent task groups of kThreads threads per CTA: a
-// kernel that allocates tensor memory gets one CTA per SM, and two groups keep two tasks in flight
-// per SM (one overlapping the other's latency-bound phases).  Each group synchronises on its own
-// named barrier and owns a shared-memory region, a workspace slot and 128 TMEM columns.
-constexpr int kMaxGroups = 2;
-__device__ __forceinline__ int gtid() { return threadIdx.x & (kThreads - 1); }
-__device__ __forceinline__ int group_id() { return threadIdx.x / kThreads; }
-__device__ __forceinline__ void gsync() {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "r"(kThreads) : "memory");
-}
-constexpr int kTile = 64;        // trailing-update tile (rows and columns)
-constexpr int kOuter = 64;       // outer panel width of the two-level (tensor-core) LU
-constexpr int kMaxRefine = 10;
-// Refinement target on the normwise backward error: reachable by the float-float residual
-// (about 2^-44 per partial sum) and, with cond(Z_sub) ~ 1e4-1e5, far below |dS| = 1e-6.
-constexpr double kEtaTarget = 1e-12;
-
-// ------------------------------------------------------------------ complex helpers
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-// c - a*b
-__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
-  c.x = fmaf(-a.x, b.x, c.x); c.x = fmaf(a.y, b.y, c.x);
-  c.y = fmaf(-a.x, b.y, c.y); c.y = fmaf(-a.y, b.x, c.y);
-  return c;
-}
-__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
-  c.x = fma(-a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
-  c.y = fma(-a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
-  return c;
-}
-// c + a*b
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
-  c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
-  c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
-  return c;
-}
-__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
-__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-__device__ __forceinline__ float2 cinv(float2 a) {
-  const float d = cabs2(a);
-  return make_float2(a.x / d, -a.y / d);
-}
-__device__ __forceinline__ double2 cinv(double2 a) {
-  const double d = cabs2(a);
-  return make_double2(a.x / d, -a.y / d);
-}
-__device__ __forceinline__ float2 czero(float2) { return make_float2(0.f, 0.f); }
-__device__ __forceinline__ double2 czero(double2) { return make_double2(0.0, 0.0); }
-
-template <typename T> __device__ __forceinline__ T from_f2(float2 z);
-template <> __device__ __forceinline__ float2 from_f2<float2>(float2 z) { return z; }
-template <> __device__ __forceinline__ double2 from_f2<double2>(float2 z) { return make_double2(z.x, z.y); }
-template <typename T> __device__ __forceinline__ T from_d2(double2 z);
-template <> __device__ __forceinline__ float2 from_d2<float2>(double2 z) {
-  return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
-}
-template <> __device__ __forceinline__ double2 from_d2<double2>(double2 z) { return z; }
-__device__ __forceinline__ double2 to_d2(float2 z) { return make_double2(z.x, z.y); }
-__device__ __forceinline__ double2 to_d2(double2 z) { return z; }
-
-template <typename ZT, typename T> __device__ __forceinline__ T zload(const ZT* p);
-template <> __device__ __forceinline__ float2 zload<float2, float2>(const float2* p) { return __ldg(p); }
-template <> __device__ __forceinline__ double2 zload<float2, double2>(const float2* p) { return to_d2(__ldg(p)); }
-template <> __device__ __forceinline__ double2 zload<double2, double2>(const double2* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float2 zload<double2, float2>(const double2* p) {
-  return from_d2<float2>(__ldg(p));
-}
-
-__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ double shfl_f(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-template <typename T> __device__ __forceinline__ T shfl_c(T v, int src) {
-  v.x = shfl_f(v.x, src);
-  v.y = shfl_f(v.y, src);
-  return v;
-}
-template <typename T> __device__ __forceinline__ T shfl_c_down(T v, int d) {
-  v.x = __shfl_down_sync(0xffffffffu, v.x, d);
-  v.y = __shfl_down_sync(0xffffffffu, v.y, d);
-  return v;
-}
-
-template <typename T> struct Real;
-template <> struct Real<float2> { using type = float; };
-template <> struct Real<double2> { using type = double; };
-
-template <typename CT> struct Cfg;
-template <> struct Cfg<float2> { static constexpr int NB = 16; };
-template <> struct Cfg<double2> { static constexpr int NB = 8; };
-
-// ------------------------------------------------------------------ activation (Eq. 3)
-__global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restrict__ rules, int M,
-                                                           const uint8_t* __restrict__ maps, int npix, int n_states,
-                                                           int32_t* __restrict__ idx, int32_t* __restrict__ n_act,
-                                                           uint32_t* __restrict__ flags, int* __restrict__ n_max) {
-  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint8_t* map = maps + static_cast<size_t>(b) * npix;
-  __shared__ int s_bad;
-  __shared__ int s_warp[kWarps];
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int i = tid; i < npix; i += kThreads)
-    if (map[i] >= n_states) s_bad = 1;
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) {
-      n_act[b] = -1;
-      atomicOr(&flags[b], kFlagBadState);
-    }
-    return;
-  }
-  int32_t* out = idx + static_cast<size_t>(b) * M;
-  int base = 0;
-  for (int m0 = 0; m0 < M; m0 += kThreads) {
-    const int m = m0 + tid;
-    bool on = false;
-    if (m < M) {
-      const int4 r = __ldg(&rules[m]);
-      switch (r.x) {
-        case kAlways: on = true; break;
-        case kInner: on = map[r.y] >= 1; break;
-        case kInter: on = map[r.y] >= 1 && map[r.z] >= 1; break;
-        case kPixPort: on = map[r.y] >= 1; break;
-        default: on = false;
-      }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, on);
-    const int before = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    int woff = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const int c = s_warp[w];
-      woff += (w < warp) ? c : 0;
-      total += c;
-    }
-    if (on) out[base + woff + before] = m;
-    base += total;
-    __syncthreads();
-  }
-  if (tid == 0) {
-    n_act[b] = base;
-    if (n_max) atomicMax(n_max, base);
-  }
-}
-
-// ------------------------------------------------------------------ block argmax of |a|^2
-template <typename R>
-__device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) {
-  const int lane = gtid() & 31, warp = gtid() >> 5;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    const R ov = __shfl_down_sync(0xffffffffu, v, d);
-    const int orow = __shfl_down_sync(0xffffffffu, row, d);
-    if (ov > v || (ov == v && orow >= 0 && (row < 0 || orow < row))) { v = ov; row = orow; }
-  }
-  if (lane == 0) { s_val[warp] = v; s_row[warp] = row; }
-  gsync();
-  if (gtid() == 0) {
-    R bv = s_val[0];
-    int br = s_row[0];
-    for (int w = 1; w < kWarps; ++w) {
-      if (s_val[w] > bv || (s_val[w] == bv && s_row[w] >= 0 && (br < 0 || s_row[w] < br))) { bv = s_val[w]; br = s_row[w]; }
-    }
-    s_row[kWarps] = br;
-  }
-  gsync();
-  return s_row[kWarps];
-}
-
-// ------------------------------------------------------------------ tensor-core trailing update
-// State of the CTA's tensor-core pipeline: 64 KB operand staging (A_hi | A_lo | B_hi | B_lo, each
-// a 128 x 32 K-major fp32 tile), a 128-column TMEM accumulator and the MMA-completion barrier.
-struct TcState {
-  unsigned char* stage;
-  uint32_t tmem;
-  uint64_t* mbar;
-  uint32_t phase;
-  bool failed;
-};
-constexpr long long kTcWaitPolls = 1ll << 26;   // bounded wait; a stall flags the task instead of hanging
-
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float v) {
-  const float h = tc::to_tf32(v);
-  const uint32_t off = tc::kmajor_off(row, k);
-  *reinterpret_cast<float*>(hi + off) = h;
-  *reinterpret_cast<float*>(lo + off) = tc::to_tf32(v - h);
-}
-
-// Outer-panel update A22 -= L21 U12 on the tensor cores, with K = jb <= 64 complex columns taken
-// in chunks of 16.  Per 128 x 64 complex output tile, each chunk is one real GEMM
-// [Lr | Li] (128 x 32) times B (32 x 128), B's first 64 columns being [Ur; -Ui] (real parts of the
-// product) and its last 64 [Ui; Ur] (imaginary parts).  Every fp32 operand is split into two TF32
-// terms (hi + lo) and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32 in
-// TMEM across all chunks, which keeps fp32-level accuracy; the tile is then subtracted from A22
-// once.  L21 = A[rb.., j0..j0+jb), U12 = A[j0..j0+jb, rb..), A22 = A[rb.., rb..], rb = j0 + jb.
-__device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int jb, TcState& st) {
-  const int tid = gtid(), warp = tid >> 5, lane = tid & 31;
-  const int rb = j0 + jb, n2 = N - rb;
-  const int nk = (jb + 15) >> 4;
-  unsigned char* Ah = st.stage;
-  unsigned char* Al = st.stage + 16384;
-  unsigned char* Bh = st.stage + 32768;
-  unsigned char* Bl = st.stage + 49152;
-  const uint32_t idesc = tc::idesc_tf32(128, 128);
-  for (int c0 = rb; c0 < N; c0 += 64) {
-    for (int r0 = 0; r0 < n2; r0 += 128) {
-      for (int kc = 0; kc < nk; ++kc) {
-        const int kbase = j0 + 16 * kc, kw = min(16, jb - 16 * kc);
-        {
-          // all loads first (independent, in flight together), then the split stores
-          float2 u[4], l[8];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
-            u[i] = (t < kw && c0 + c < N) ? A[static_cast<size_t>(kbase + t) * lda + c0 + c] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
-            l[i] = (t < kw && r0 + r < n2) ? A[static_cast<size_t>(rb + r0 + r) * lda + kbase + t] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
-            put_split(Bh, Bl, c, t, u[i].x);
-            put_split(Bh, Bl, c, 16 + t, -u[i].y);
-            put_split(Bh, Bl, 64 + c, t, u[i].y);
-            put_split(Bh, Bl, 64 + c, 16 + t, u[i].x);
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
-            put_split(Ah, Al, r, t, l[i].x);
-            put_split(Ah, Al, r, 16 + t, l[i].y);
-          }
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        gsync();
-        tc::fence_after_sync();
-        if (tid == 0) {
-          const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al), bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
-          uint32_t acc = kc > 0 ? 1u : 0u;
-#pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            const uint32_t ao = term == 0 ? al : ah;     // small terms first: lo*hi, hi*lo, hi*hi
-            const uint32_t bo = term == 1 ? bl : bh;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              tc::mma_tf32(st.tmem, tc::smem_desc(ao + ks * 256), tc::smem_desc(bo + ks * 256), idesc, acc);
-              acc = 1;
-            }
-          }
-          tc::commit(st.mbar);
-        }
-        // one warp waits for the MMAs (they read the staged operands); the barrier releases the rest
-        if (warp == 0) {
-          if (!tc::mbar_wait(st.mbar, st.phase, kTcWaitPolls)) st.failed = true;
-        }
-        st.phase ^= 1u;
-        gsync();
-      }
-      tc::fence_after_sync();
-      // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update
-      float2* T = reinterpret_cast<float2*>(st.stage);
-      constexpr int LDT = 65;
-      {
-        const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
-        float re[32], im[32];
-        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * h, re);
-        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 + 32 * h, im);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
-      }
-      tc::fence_before_sync();
-      gsync();
-      // 32 elements per thread in two batches of 16 independent loads, then the stores
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float2 v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
-          v[i] = (r0 + r < n2 && c0 + c < N) ? A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
-          if (r0 + r < n2 && c0 + c < N) {
-            const float2 d = T[r * LDT + c];
-            A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] = make_float2(v[i].x - d.x, v[i].y - d.y);
-          }
-        }
-      }
-      gsync();
-    }
-  }
-}
-
-// U12 = L11^-1 A12 for an outer panel: L11 = unit lower A[j0..j0+jb, j0..j0+jb) (jb <= 64, staged in
-// shared memory), A12 = A[j0..j0+jb, cb..N); one column per thread, 16 rows at a time.
-__device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int jb, float2* __restrict__ Ls) {
-  constexpr int LDL = 65;
-  const int tid = gtid(), cb = j0 + jb;
-  for (int e = tid; e < jb * 64; e += kThreads) {
-    const int r = e >> 6, c = e & 63;
-    Ls[r * LDL + c] = c < jb ? A[static_cast<size_t>(j0 + r) * lda + j0 + c] : make_float2(0.f, 0.f);
-  }
-  gsync();
-  for (int c = cb + tid; c < N; c += kThreads) {
-    for (int ch = 0; ch * 16 < jb; ++ch) {
-      const int rw = min(16, jb - 16 * ch);
-      float2 u[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) u[i] = i < rw ? A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] : make_float2(0.f, 0.f);
-      for (int t = 0; t < 16 * ch; ++t) {   // contributions of the rows already solved
-        const float2 y = A[static_cast<size_t>(j0 + t) * lda + c];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) u[i] = cfms(Ls[(16 * ch + i) * LDL + t], y, u[i]);
-      }
-#pragma unroll
-      for (int i = 1; i < 16; ++i)
-#pragma unroll
-        for (int t = 0; t < i; ++t) u[i] = cfms(Ls[(16 * ch + i) * LDL + 16 * ch + t], u[t], u[i]);
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (i < rw) A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] = u[i];
-    }
-  }
-  gsync();
-}
-
-// ------------------------------------------------------------------ blocked LU in global memory
-// A: row-major N x N (leading dimension lda).  Panel of NB columns factored in shared memory;
-// row interchanges applied to whole rows (LAPACK convention: P A = L U, unit-diagonal L).
-// Returns true if an exactly zero pivot occurred.
+// The large-support-set layout is used when the default layout's single task group does not fit
+// the opt-in shared memory of one CTA.
 template <typename CT>
-__device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ piv, CT* __restrict__ Pn,
-                          CT* __restrict__ Ut, typename Real<CT>::type* s_val, int* s_row, TcState* tcs) {
-  using R = typename Real<CT>::type;
-  constexpr int NB = Cfg<CT>::NB;
-  constexpr int LDP = NB + 1;
-  constexpr int LDU = kTile + 1;
-  const int tid = gtid();
-  bool singular = false;
-  // Updates made by each NB-column panel stop at column `cend`: N for the one-level CUDA-core
-  // path; the end of the current kOuter-column outer panel for the two-level tensor-core path
-  int cend = N;
-  for (int k0 = 0; k0 < N; k0 += NB) {
-    const int kb = min(NB, N - k0);
-    const int nr = N - k0;
-    if (tcs != nullptr && k0 % kOuter == 0) cend = min(N, k0 + kOuter);
-    // 1. panel -> shared memory
-    for (int e = tid; e < nr * NB; e += kThreads) {
-      const int r = e / NB, c = e % NB;
-      if (c < kb) Pn[r * LDP + c] = A[static_cast<size_t>(k0 + r) * lda + k0 + c];
-    }
-    gsync();
-    // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row)
-    for (int j = 0; j < kb; ++j) {
-      R best = -1;
-      int brow = -1;
-      for (int r = j + tid; r < nr; r += kThreads) {
-        const R v = cabs2(Pn[r * LDP + j]);
-        if (v > best) { best = v; brow = r; }
-      }
-      const int p = block_argmax<R>(best, brow, s_val, s_row);
-      if (tid == 0) piv[k0 + j] = k0 + p;
-      if (p != j && tid < kb) {
-        const CT t = Pn[j * LDP + tid];
-        Pn[j * LDP + tid] = Pn[p * LDP + tid];
-        Pn[p * LDP + tid] = t;
-      }
-      gsync();
-      const CT d = Pn[j * LDP + j];
-      const bool zero = cabs2(d) == R(0);
-      if (zero) singular = true;
-      const CT inv = zero ? czero(d) : cinv(d);
-      for (int r = j + 1 + tid; r < nr; r += kThreads) {
-        const CT l = cmul(Pn[r * LDP + j], inv);
-        Pn[r * LDP + j] = l;
-        for (int c = j + 1; c < kb; ++c) Pn[r * LDP + c] = cfms(l, Pn[j * LDP + c], Pn[r * LDP + c]);
-      }
-      gsync();
-    }
-    // 3. panel back to global memory
-    for (int e = tid; e < nr * NB; e += kThreads) {
-      const int r = e / NB, c = e % NB;
-      if (c < kb) A[static_cast<size_t>(k0 + r) * lda + k0 + c] = Pn[r * LDP + c];
-    }
-    // 4. the panel's row interchanges on the columns outside it
-    for (int j = 0; j < kb; ++j) {
-      const int p = piv[k0 + j];
-      if (p != k0 + j) {
-        CT* ra = A + static_cast<size_t>(k0 + j) * lda;
-        CT* rb = A + static_cast<size_t>(p) * lda;
-        for (int c = tid; c < N; c += kThreads) {
-          if (c >= k0 && c < k0 + kb) continue;
-          const CT t = ra[c];
-          ra[c] = rb[c];
-          rb[c] = t;
-        }
-      }
-      gsync();
-    }
-    // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory), columns up
-    //    to the end of the current outer panel
-    for (int c = k0 + kb + tid; c < cend; c += kThreads) {
-      CT u[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) u[i] = i < kb ? A[static_cast<size_t>(k0 + i) * lda + c] : czero(u[0]);
-#pragma unroll
-      for (int i = 1; i < NB; ++i)
-#pragma unroll
-        for (int t = 0; t < i; ++t) u[i] = cfms(Pn[i * LDP + t], u[t], u[i]);
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < kb) A[static_cast<size_t>(k0 + i) * lda + c] = u[i];
-    }
-    gsync();
-    // 6. trailing update A22 -= L21 U12 on the CUDA cores (64 x 64 tiles, 4 x 4 complex outputs per
-    //    thread), for the columns up to the end of the current outer panel
-    const int r_begin = k0 + kb, n2 = N - r_begin;
-    if (n2 > 0 && cend > r_begin) {
-      const int ty = tid >> 4, tx = tid & 15;
-      const int ntile = (n2 + kTile - 1) / kTile;
-      const int ntile_c = (cend - r_begin + kTile - 1) / kTile;
-      for (int tc = 0; tc < ntile_c; ++tc) {
-        const int c0 = r_begin + tc * kTile;
-        for (int e = tid; e < NB * kTile; e += kThreads) {
-          const int t = e / kTile, cc = e % kTile;
-          Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
-        }
-        gsync();
-        for (int tr = 0; tr < ntile; ++tr) {
-          const int r0 = tr * kTile;   // relative to r_begin
-          CT acc[4][4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              acc[i][jj] = (r < n2 && c < cend) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
-            }
-#pragma unroll 4
-          for (int t = 0; t < NB; ++t) {
-            if (t >= kb) break;
-            CT a[4], u[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int r = r0 + ty + 16 * i;
-              a[i] = r < n2 ? Pn[(kb + r) * LDP + t] : czero(a[0]);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) u[jj] = Ut[t * LDU + tx + 16 * jj];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cfms(a[i], u[jj], acc[i][jj]);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              if (r < n2 && c < cend) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
-            }
-        }
-        gsync();
-      }
-    }
-    gsync();
-    // 7-8. end of an outer panel (tensor-core path): U12 for the columns to its right, then one
-    //      K = 64 update of the remaining matrix on the tensor cores
-    if constexpr (std::is_same<CT, float2>::value) {
-      if (tcs != nullptr && k0 + kb == cend && cend < N) {
-        const int j0 = cend - ((cend - 1) % kOuter + 1);
-        outer_trsm(A, lda, N, j0, cend - j0, reinterpret_cast<float2*>(tcs->stage));
-        trailing_tc(A, lda, N, j0, cend - j0, *tcs);
-        gsync();
-      }
-    }
-  }
-  return singular;
-}
-
-// ------------------------------------------------------------------ triangular solves
-// W (shared, N x P) holds the right-hand sides on entry and the solution on exit.
-// D: shared 32 x 33 staging of the current diagonal block (read once, coalesced).
-template <typename CT>
-__device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
-                         int P, CT* __restrict__ D) {
-  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
-  if (warp == 0) {
-    for (int k = 0; k < N; ++k) {
-      const int p = piv[k];
-      if (p != k && lane < P) {
-        const CT t = W[k * P + lane];
-        W[k * P + lane] = W[p * P + lane];
-        W[p * P + lane] = t;
-      }
-      __syncwarp();
-    }
-  }
-  gsync();
-  // forward: L y = P b, unit diagonal, blocks of 32 rows
-  for (int i0 = 0; i0 < N; i0 += 32) {
-    const int bs = min(32, N - i0);
-    if (i0 > 0) {
-      for (int ii = warp; ii < bs; ii += kWarps) {
-        const int i = i0 + ii;
-        CT acc[kMaxPorts];
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
-        const CT* row = A + static_cast<size_t>(i) * lda;
-        int t = lane;
-        for (; t + 96 < i0; t += 128) {   // four independent loads in flight
-          CT l[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) l[u] = row[t + 32 * u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int p = 0; p < kMaxPorts; ++p)
-              if (p < P) acc[p] = cfms(l[u], W[(t + 32 * u) * P + p], acc[p]);
-        }
-        for (; t < i0; t += 32) {
-          const CT l = row[t];
-#pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p)
-            if (p < P) acc[p] = cfms(l, W[t * P + p], acc[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          if (p >= P) break;
-          CT v = acc[p];
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            const CT o = shfl_c_down(v, d);
-            v.x += o.x;
-            v.y += o.y;
-          }
-          if (lane == 0) {
-            CT w = W[i * P + p];
-            w.x += v.x;   // acc holds -sum, so adding applies the subtraction
-            w.y += v.y;
-            W[i * P + p] = w;
-          }
-        }
-      }
-      gsync();
-    }
-    if (warp == 0) {
-      const int i = i0 + lane;
-      for (int r = 0; r < bs; ++r)
-        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
-      __syncwarp();
-      CT w[kMaxPorts];
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
-      for (int t = 0; t < bs; ++t) {
-        const CT l = (lane < bs && lane > t) ? D[lane * 33 + t] : czero(w[0]);
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          const CT y = shfl_c(w[p], t);
-          if (lane > t) w[p] = cfms(l, y, w[p]);
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p)
-        if (lane < bs && p < P) W[i * P + p] = w[p];
-    }
-    gsync();
-  }
-  // backward: U x = y, blocks of 32 rows from the bottom
-  for (int i1 = N; i1 > 0; i1 -= 32) {
-    const int i0 = max(0, i1 - 32), bs = i1 - i0;
-    if (i1 < N) {
-      for (int ii = warp; ii < bs; ii += kWarps) {
-        const int i = i0 + ii;
-        CT acc[kMaxPorts];
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
-        const CT* row = A + static_cast<size_t>(i) * lda;
-        int t = i1 + lane;
-        for (; t + 96 < N; t += 128) {   // four independent loads in flight
-          CT uu[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) uu[u] = row[t + 32 * u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int p = 0; p < kMaxPorts; ++p)
-              if (p < P) acc[p] = cfms(uu[u], W[(t + 32 * u) * P + p], acc[p]);
-        }
-        for (; t < N; t += 32) {
-          const CT u = row[t];
-#pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p)
-            if (p < P) acc[p] = cfms(u, W[t * P + p], acc[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          if (p >= P) break;
-          CT v = acc[p];
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            const CT o = shfl_c_down(v, d);
-            v.x += o.x;
-            v.y += o.y;
-          }
-          if (lane == 0) {
-            CT w = W[i * P + p];
-            w.x += v.x;
-            w.y += v.y;
-            W[i * P + p] = w;
-          }
-        }
-      }
-      gsync();
-    }
-    if (warp == 0) {
-      const int i = i0 + lane;
-      for (int r = 0; r < bs; ++r)
-        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
-      __syncwarp();
-      CT w[kMaxPorts];
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
-      for (int t = bs - 1; t >= 0; --t) {
-        if (lane == t) {
-          const CT d = D[lane * 33 + lane];
-          const CT inv = cabs2(d) > 0 ? cinv(d) : czero(d);
-#pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p) w[p] = cmul(w[p], inv);
-        }
-        const CT u = (lane < t) ? D[lane * 33 + t] : czero(w[0]);
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          const CT y = shfl_c(w[p], t);
-          if (lane < t) w[p] = cfms(u, y, w[p]);
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p)
-        if (lane < bs && p < P) W[i * P + p] = w[p];
-    }
-    gsync();
-  }
-}
-
-// ------------------------------------------------------------------ refinement residual
-// Error-free transformations on the FP32 pipe (Knuth's TwoSum, FMA-based TwoProduct); the
-// explicit _rn intrinsics keep the compiler from contracting or reassociating them.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// (hi, lo) += z * (xh + xl): z is an exact float, xh + xl the two-float split of a double
-__device__ __forceinline__ void df_mac(float z, float xh, float xl, float& hi, float& lo) {
-  const float p = __fmul_rn(z, xh);
-  const float e = __fmaf_rn(z, xh, -p);
-  float sum, err;
-  two_sum(hi, p, sum, err);
-  hi = sum;
-  lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(z, xl, e)));
-}
-
-// r = V - Z_sub x for complex64 storage in float-float arithmetic (about 2^-44 relative per lane
-// partial sum, combined in double across the warp).  xs: x split as (re_hi, re_lo, im_hi, im_lo).
-__device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
-                            const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
-  // four rows per warp at a time: independent float-float chains interleave and each x load
-  // serves four rows
-  constexpr int R = 4;
-  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
-  double rmax = 0.0, zmax = 0.0;
-  for (int i0 = warp; i0 < N; i0 += kWarps * R) {
-    float rh[R][kMaxPorts], rl[R][kMaxPorts], ih[R][kMaxPorts], il[R][kMaxPorts], ra[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      ra[q] = 0.f;
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) rh[q][p] = rl[q][p] = ih[q][p] = il[q][p] = 0.f;
-    }
-    const float2* zrow[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int i = i0 + q * kWarps;
-      zrow[q] = Zs + static_cast<size_t>(i < N ? i : 0) * lda;
-    }
-    for (int t = lane; t < N; t += 32) {
-      float2 z[R];
-#pragma unroll
-      for (int q = 0; q < R; ++q) z[q] = (i0 + q * kWarps < N) ? zrow[q][t] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) {
-        if (p < P) {
-          const float4 x = xs[t * P + p];
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            df_mac(z[q].x, x.x, x.y, rh[q][p], rl[q][p]);
-            df_mac(-z[q].y, x.z, x.w, rh[q][p], rl[q][p]);
-            df_mac(z[q].x, x.z, x.w, ih[q][p], il[q][p]);
-            df_mac(z[q].y, x.x, x.y, ih[q][p], il[q][p]);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < R; ++q) ra[q] += fabsf(z[q].x) + fabsf(z[q].y);
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int i = i0 + q * kWarps;
-      double rs = ra[q];
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, d);
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) {
-        if (p >= P) break;
-        double vx = static_cast<double>(rh[q][p]) + static_cast<double>(rl[q][p]);
-        double vy = static_cast<double>(ih[q][p]) + static_cast<double>(il[q][p]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          vx += __shfl_down_sync(0xffffffffu, vx, d);
-          vy += __shfl_down_sync(0xffffffffu, vy, d);
-        }
-        if (lane == 0 && i < N) {
-          const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
-          const double2 ri = make_double2(vv - vx, -vy);
-          r[i * P + p] = ri;
-          rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
-        }
-      }
-      if (lane == 0 && i < N) zmax = fmax(zmax, rs);
-    }
-  }
-  if (lane == 0) {
-    s_red[warp] = rmax;
-    s_red[kWarps + warp] = zmax;
-  }
-  gsync();
-  if (tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      a = fmax(a, s_red[w]);
-      b = fmax(b, s_red[kWarps + w]);
-    }
-    s_out[0] = a;
-    s_out[1] = b;
-  }
-  gsync();
-}
-
-// double-storage residual (complex128 database): plain FP64
-// r = V - Z_sub x in double from the stored entries; returns ||r||_inf (|re|+|im| norm) and
-// ||Z_sub||_inf in s_out[0..1].  x_s: shared copy of x (N x P double2).
-template <typename ZT>
-__device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N, const double2* x_s,
-                         int P, const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
-  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
-  double rmax = 0.0, zmax = 0.0;
-  for (int i = warp; i < N; i += kWarps) {
-    const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
-    double2 acc[kMaxPorts];
-#pragma unroll
-    for (int p = 0; p < kMaxPorts; ++p) acc[p] = make_double2(0.0, 0.0);
-    double rowabs = 0.0;
-    for (int t = lane; t < N; t += 32) {
-      const double2 z = zload<ZT, double2>(zrow + s_idx[t]);
-      rowabs += fabs(z.x) + fabs(z.y);
-#pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p)
-        if (p < P) acc[p] = cfma(z, x_s[t * P + p], acc[p]);
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) rowabs += __shfl_down_sync(0xffffffffu, rowabs, d);
-#pragma unroll
-    for (int p = 0; p < kMaxPorts; ++p) {
-      if (p >= P) break;
-      double2 v = acc[p];
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, d);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, d);
-      }
-      if (lane == 0) {
-        const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
-        const double2 ri = make_double2(vv - v.x, -v.y);
-        r[i * P + p] = ri;
-        rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
-      }
-    }
-    if (lane == 0) zmax = fmax(zmax, rowabs);
-  }
-  if (lane == 0) {
-    s_red[warp] = rmax;
-    s_red[kWarps + warp] = zmax;
-  }
-  gsync();
-  if (tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      a = fmax(a, s_red[w]);
-      b = fmax(b, s_red[kWarps + w]);
-    }
-    s_out[0] = a;
-    s_out[1] = b;
-  }
-  gsync();
-}
-
-// ------------------------------------------------------------------ Y -> S (Eq. 6-7)
-// One thread per task converts the port admittance matrix Y (written by the evaluation kernel
-// into the S slot) to S = (1 + Z0 Y)^-1 (1 - Z0 Y) in place.
-__global__ void ys_kernel(double2* __restrict__ S, int ntask, int F, int P, double Z0, uint32_t* __restrict__ flags) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntask) return;
-  double2* s = S + static_cast<size_t>(t) * P * P;
-  double2 Am[kMaxPorts][kMaxPorts], Bm[kMaxPorts][kMaxPorts];
-  for (int i = 0; i < P; ++i)
-    for (int j = 0; j < P; ++j) {
-      const double2 y = s[i * P + j];
-      const double d = (i == j) ? 1.0 : 0.0;
-      Am[i][j] = make_double2(d + Z0 * y.x, Z0 * y.y);
-      Bm[i][j] = make_double2(d - Z0 * y.x, -Z0 * y.y);
-    }
-  // Gauss-Jordan with partial pivoting on (1 + Z0 Y) S = (1 - Z0 Y)
-  for (int k = 0; k < P; ++k) {
-    int p = k;
-    double best = cabs2(Am[k][k]);
-    for (int i = k + 1; i < P; ++i)
-      if (cabs2(Am[i][k]) > best) { best = cabs2(Am[i][k]); p = i; }
-    if (p != k)
-      for (int j = 0; j < P; ++j) {
-        double2 tt = Am[k][j]; Am[k][j] = Am[p][j]; Am[p][j] = tt;
-        tt = Bm[k][j]; Bm[k][j] = Bm[p][j]; Bm[p][j] = tt;
-      }
-    const double2 inv = cinv(Am[k][k]);
-    for (int j = 0; j < P; ++j) {
-      Am[k][j] = cmul(Am[k][j], inv);
-      Bm[k][j] = cmul(Bm[k][j], inv);
-    }
-    for (int i = 0; i < P; ++i) {
-      if (i == k) continue;
-      const double2 f = Am[i][k];
-      for (int j = 0; j < P; ++j) {
-        Am[i][j] = cfms(f, Am[k][j], Am[i][j]);
-        Bm[i][j] = cfms(f, Bm[k][j], Bm[i][j]);
-      }
-    }
-  }
-  bool bad = false;
-  for (int i = 0; i < P; ++i)
-    for (int j = 0; j < P; ++j) {
-      s[i * P + j] = Bm[i][j];
-      if (!isfinite(Bm[i][j].x) || !isfinite(Bm[i][j].y)) bad = true;
-    }
-  if (bad) atomicOr(&flags[t / F], kFlagNonfinite);
-}
-
-// ------------------------------------------------------------------ the evaluation kernel
-// Per-slot workspace: [LU matrix | exact complex64 copy of Z_sub (mixed path with complex64
-// storage: the refinement residual reads it row by row) | pivots | x | residual].
-struct Slot {
-  size_t a_off, zs_off, piv_off, x_off, r_off;
-};
-__host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_bytes) {
-  Slot s;
-  s.a_off = 0;
-  s.zs_off = s.a_off + static_cast<size_t>(M) * lda * ct_bytes;
-  s.zs_off = (s.zs_off + 255) & ~size_t(255);
-  s.piv_off = s.zs_off + static_cast<size_t>(M) * lda * sizeof(float2);
-  s.piv_off = (s.piv_off + 255) & ~size_t(255);
-  s.x_off = s.piv_off + static_cast<size_t>(M) * sizeof(int);
-  s.x_off = (s.x_off + 255) & ~size_t(255);
-  s.r_off = s.x_off + static_cast<size_t>(M) * P * sizeof(double2);
-  s.r_off = (s.r_off + 255) & ~size_t(255);
-  return s;
-}
-
-// Dynamic shared memory: [union of the panel (M x (NB+1)), the x cache and, for the tensor-core
-// path, the operand staging (64 KB + 2 KB alignment slack) | U tile / diagonal block | idx (M ints)].
-// The staging is only live during the outer-panel steps, when the panel has been written back, so
-// the two share memory and the tensor-core variant still fits two CTAs per SM.
-constexpr size_t kTcStageBytes = 65536 + 2048;   // 64 KB operands (or the 128 x 65 result tile) + alignment
-
-template <typename CT>
-__host__ __device__ inline size_t smem_layout(int M, int use_tc, size_t* u_off, size_t* idx_off, size_t* tc_off) {
-  constexpr int NB = Cfg<CT>::NB;
-  size_t panel = static_cast<size_t>(M) * (NB + 1) * sizeof(CT);
-  const size_t xcache = static_cast<size_t>(M) * kMaxPorts * sizeof(double2);
-  if (xcache > panel) panel = xcache;
-  if (use_tc && panel < kTcStageBytes) panel = kTcStageBytes;
-  panel = (panel + 15) & ~size_t(15);
-  *tc_off = 0;
-  *u_off = panel;
-  size_t u = static_cast<size_t>(NB) * (kTile + 1) * sizeof(CT);
-  if (u < 32 * 33 * sizeof(CT)) u = 32 * 33 * sizeof(CT);
-  *idx_off = panel + ((u + 15) & ~size_t(15));
-  return *idx_off + static_cast<size_t>(M) * sizeof(int);
-}
-
-// One group's share of the dynamic shared memory (1024-byte multiple so every group's region
-// starts aligned like the first).
-template <typename CT>
-__host__ __device__ inline size_t group_smem_bytes(int M, int use_tc) {
-  size_t u_off, idx_off, tc_off;
-  const size_t b = smem_layout<CT>(M, use_tc, &u_off, &idx_off, &tc_off);
-  return (b + 1023) & ~size_t(1023);
-}
-
-template <typename ZT> struct XCache;
-template <> struct XCache<float2> { using type = float4; };
-template <> struct XCache<double2> { using type = double2; };
-
-// TC: the single-precision LU runs its outer-panel updates on the tensor cores.
-template <typename CT, typename ZT, bool MIXED, bool TC>
-__global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs a) {
-  using R = typename Real<CT>::type;
-  extern __shared__ __align__(16) unsigned char smem_all[];
-  __shared__ R s_val_g[kMaxGroups][kWarps + 1];
-  __shared__ int s_row_g[kMaxGroups][kWarps + 1];
-  __shared__ double s_red_g[kMaxGroups][2 * kWarps];
-  __shared__ double s_norm_g[kMaxGroups][2];
-  __shared__ int s_task_g[kMaxGroups];
-  __shared__ int s_flag_g[kMaxGroups];
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups];
-  constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
-  const int g = group_id();
-  const int ngroups = blockDim.x / kThreads;
-  R* s_val = s_val_g[g];
-  int* s_row = s_row_g[g];
-  double* s_red = s_red_g[g];
-  double* s_norm = s_norm_g[g];
-  int& s_task = s_task_g[g];
-  int& s_flag = s_flag_g[g];
-  size_t u_off, idx_off, tc_off;
-  const size_t group_bytes = group_smem_bytes<CT>(a.ncap, use_tc);
-  smem_layout<CT>(a.ncap, use_tc, &u_off, &idx_off, &tc_off);
-  unsigned char* smem = smem_all + g * group_bytes;
-  CT* Pn = reinterpret_cast<CT*>(smem);
-  CT* Ut = reinterpret_cast<CT*>(smem + u_off);
-  int* s_idx = reinterpret_cast<int*>(smem + idx_off);
-  const int tid = gtid();
-  TcState tcs;
-  tcs.stage = nullptr;
-  tcs.tmem = 0;
-  tcs.mbar = &s_mbar_g[g];
-  tcs.phase = 0;
-  tcs.failed = false;
-  if (use_tc) {
-    // 1024-byte aligned operand staging inside this group's tensor-core region
-    const uint32_t base = tc::smem_u32(smem + tc_off);
-    tcs.stage = smem + tc_off + ((1024u - (base & 1023u)) & 1023u);
-    if (threadIdx.x < 32) {   // one warp allocates 128 TMEM columns per group for the whole CTA
-      tc::tmem_alloc(&s_tmem, 128u * ngroups);
-      tc::tmem_relinquish();
-    }
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < ngroups; ++i) tc::mbar_init(&s_mbar_g[i], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    tcs.tmem = s_tmem + 128u * g;
-  }
-  const int P = a.P, M = a.M, lda = a.lda;
-  const Slot sl = slot_layout(M, lda, P, sizeof(CT));
-  const int slot = blockIdx.x * ngroups + g;
-  unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * slot;
-  CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
-  float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
-  int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
-  double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
-  double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
-  const ZT* Zall = static_cast<const ZT*>(a.Z);
-  const int ntasks = a.ntasks_list ? *a.repair_count : a.B * a.F;
-  double lport[kMaxPorts];
-#pragma unroll
-  for (int p = 0; p < kMaxPorts; ++p) lport[p] = a.port_len[p];
-
-  for (;;) {
-    if (slot >= a.nslots) break;   // a spare group (odd slot count): no workspace
-    if (tid == 0) s_task = atomicAdd(a.task_counter, 1);
-    gsync();
-    const int tq = s_task;
-    gsync();
-    if (tq >= ntasks) break;
-    const int t = a.ntasks_list ? a.repair_list[tq] : tq;
-    const int f = t / a.B, b = a.order ? a.order[t % a.B] : t % a.B;
-    const int N = a.n_act[b];
-    double2* Sout = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
-    if (N <= 0 || N > a.ncap) {
-      // bad pixel states, or a support set larger than the shared memory this launch was sized
-      // for (a graph captured with a smaller capacity): no solve, NaN S, flagged candidate
-      if (tid < P * P) Sout[tid] = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
-      if (tid == 0 && N > a.ncap) atomicOr(&a.flags[b], kFlagCapacity);
-      continue;
-    }
-    const ZT* Zf = Zall + static_cast<size_t>(f) * M * M;
-    const int32_t* gidx = a.idx + static_cast<size_t>(b) * M;
-    for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
-    gsync();
-    // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
-    constexpr bool kZsCopy = MIXED && std::is_same<ZT, float2>::value;
-    for (int i = 0; i < N; ++i) {
-      const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
-      CT* arow = A + static_cast<size_t>(i) * lda;
-      float2* zsrow = Zs + static_cast<size_t>(i) * lda;
-      for (int j = tid; j < N; j += kThreads) {
-        const CT v = zload<ZT, CT>(zrow + s_idx[j]);
-        arow[j] = v;
-        if constexpr (kZsCopy) zsrow[j] = v;
-      }
-    }
-    gsync();
-    const bool singular = lu_factor<CT>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
-    // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
-    CT* W = Pn;
-    for (int e = tid; e < N * P; e += kThreads) {
-      const int i = e / P, p = e % P;
-      W[e] = from_d2<CT>(make_double2(i == 3 * p + 1 ? lport[p] : 0.0, 0.0));
-    }
-    gsync();
-    lu_solve<CT>(A, lda, N, piv, W, P, Ut);
-    for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
-    gsync();
-    int iters = 0;
-    bool repaired = false;
-    if (MIXED) {
-      double rprev = 0.0;
-      double2* xs = reinterpret_cast<double2*>(Pn);
-      const double vnorm = fmax(fmax(lport[0], P > 1 ? lport[1] : 0.0), fmax(P > 2 ? lport[2] : 0.0, P > 3 ? lport[3] : 0.0));
-      bool converged = false;
-      for (int it = 0; it <= kMaxRefine; ++it) {
-        double xmax = 0.0;   // ||x||_inf (|re|+|im|), reduced over the block
-        if constexpr (std::is_same<ZT, float2>::value) {
-          float4* xf = reinterpret_cast<float4*>(Pn);
-          for (int e = tid; e < N * P; e += kThreads) {
-            const double2 v = X[e];
-            const float hx = static_cast<float>(v.x), hy = static_cast<float>(v.y);
-            xf[e] = make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
-            xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
-          }
-          gsync();
-          residual_df(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm);
-        } else {
-          for (int e = tid; e < N * P; e += kThreads) {
-            xs[e] = X[e];
-            xmax = fmax(xmax, fabs(X[e].x) + fabs(X[e].y));
-          }
-          gsync();
-          residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
-        if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
-        gsync();
-        if (tid == 0) {
-          double m = 0.0;
-          for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
-          const double rn = s_norm[0], zn = s_norm[1];
-          const double eta = rn / (zn * m + vnorm);
-          int flag = 0;   // 0 continue, 1 converged, 2 stop (stagnated or out of iterations)
-          if (eta <= kEtaTarget) flag = 1;
-          else if (it > 0 && rn > 0.5 * rprev) flag = 2;      // stagnated above the target
-          else if (it == kMaxRefine) flag = 2;
-          s_flag = flag;
-          s_norm[0] = rn;
-        }
-        gsync();
-        const int flag = s_flag;
-        rprev = s_norm[0];
-        if (flag != 0) {
-          converged = flag == 1;
-          break;
-        }
-        for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
-        gsync();
-        lu_solve<CT>(A, lda, N, piv, W, P, Ut);
-        for (int e = tid; e < N * P; e += kThreads) {
-          const double2 d = to_d2(W[e]);
-          X[e] = make_double2(X[e].x + d.x, X[e].y + d.y);
-        }
-        gsync();
-        ++iters;
-      }
-      if (!converged) repaired = true;
-    }
-    if (tid == 0) {
-      if (MIXED) {
-        atomicAdd(&a.counters[0], static_cast<unsigned long long>(iters));
-        atomicMax(&a.counters[1], static_cast<unsigned long long>(iters));
-      }
-      atomicAdd(&a.counters[3], 1ull);
-      if (repaired) {
-        const int slot = atomicAdd(a.repair_count, 1);
-        a.repair_list[slot] = t;
-        atomicAdd(&a.counters[2], 1ull);
-        atomicOr(&a.flags[b], kFlagRepaired);
-      } else if (singular) {
-        atomicOr(&a.flags[b], kFlagSingular);
-      }
-      if (tcs.failed) {   // a tensor-core completion wait ran out: the task's numbers are not trusted
-        atomicOr(&a.flags[b], kFlagNonfinite);
-        atomicAdd(&a.counters[4], 1ull);
-      }
-    }
-    tcs.failed = false;
-    // port admittances Y_ij = l_i x_i^(j) (Eq. 7) into the S slot; ys_kernel converts them
-    if (!repaired && tid < P * P) {
-      const int i = tid / P, j = tid % P;
-      const double2 xv = X[(3 * i + 1) * P + j];
-      Sout[tid] = make_double2(lport[i] * xv.x, lport[i] * xv.y);
-    }
-    gsync();
-  }
-  if (use_tc) {   // both groups are done with the tensor memory
-    tc::fence_before_sync();
-    __syncthreads();
-    if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, 128u * ngroups);
-  }
-}
-
-// ------------------------------------------------------------------ FoM (Eq. 8-9)
-__device__ __forceinline__ double sdb(double2 s) {
-  double m = sqrt(s.x * s.x + s.y * s.y);
-  if (m < 1e-15) m = 1e-15;
-  return 20.0 * log10(m);
-}
-
-__global__ void fom_kernel(const double2* __restrict__ S, const uint8_t* __restrict__ bands, int F, int P, int B,
-                           const uint32_t* __restrict__ flags, const int32_t* __restrict__ n_act, double* __restrict__ fom,
-                           int32_t* __restrict__ status) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  double sum = 0.0;
-  if (P >= 3 && n_act[b] >= 0) {
-    for (int f = 0; f < F; ++f) {
-      const double2* s = S + (static_cast<size_t>(b) * F + f) * P * P;
-      const double s11 = sdb(s[0]), s21 = sdb(s[1 * P + 0]), s31 = sdb(s[2 * P + 0]), s32 = sdb(s[2 * P + 1]);
-      switch (bands[f]) {
-        case 0:  // 1/rw_p1 + 1/rw_m1 + 1/rw_s2
-          sum += pow(10.0, -(s21 + 1.0) / 10.0) + pow(10.0, (15.0 + s11) / 10.0) + pow(10.0, (s31 + 35.0) / 15.0);
-          break;
-        case 1:  // 1/rw_p2 + 1/rw_m2 + 1/rw_s1
-          sum += pow(10.0, -(s31 + 1.0) / 10.0) + pow(10.0, (15.0 + s11) / 10.0) + pow(10.0, (s21 + 35.0) / 15.0);
-          break;
-        case 2:  // 1/rw_oi
-          sum += pow(10.0, (s32 + 20.0) / 15.0);
-          break;
-        case 3:  // 1/rw_s3 + 1/rw_s4
-          sum += pow(10.0, (s21 + 20.0) / 18.0) + pow(10.0, (s31 + 20.0) / 18.0);
-          break;
-        default: break;
-      }
-    }
-  }
-  const uint32_t fl = flags[b];
-  int32_t st = PMOM_CAND_OK;
-  if (n_act[b] < 0 || (fl & kFlagBadState)) {
-    st = PMOM_CAND_BAD_STATE;
-    sum = __longlong_as_double(0x7ff8000000000000ll);
-  } else if (fl & kFlagCapacity) {
-    st = PMOM_CAND_CAPACITY;
-    sum = __longlong_as_double(0x7ff8000000000000ll);
-  } else if ((fl & kFlagNonfinite) || !isfinite(sum)) st = PMOM_CAND_NONFINITE;
-  else if (fl & kFlagSingular) st = PMOM_CAND_SINGULAR;
-  else if (fl & kFlagRepaired) st = PMOM_CAND_REPAIRED;
-  fom[b] = sum;
-  status[b] = st;
-}
-
-// Counting sort of candidates by support-set size, descending (stable).  One block.
-__global__ void order_kernel(const int32_t* __restrict__ n_act, int B, int M, int* __restrict__ order) {
-  extern __shared__ int cnt[];   // M + 2 bins: N = -1 (bad) .. M
-  const int nb = M + 2;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) cnt[i] = 0;
-  __syncthreads();
-  for (int b = threadIdx.x; b < B; b += blockDim.x) atomicAdd(&cnt[M - max(n_act[b], -1)], 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int i = 0; i < nb; ++i) {
-      const int c = cnt[i];
-      cnt[i] = run;
-      run += c;
-    }
-    for (int b = 0; b < B; ++b) order[cnt[M - max(n_act[b], -1)]++] = b;
-  }
-}
-
-template <typename ZT>
-__global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int32_t* __restrict__ idx, int N,
-                              ZT* __restrict__ out) {
-  const ZT* Zf = Z + static_cast<size_t>(f) * M * M;
-  for (int i = blockIdx.x; i < N; i += gridDim.x) {
-    const ZT* zrow = Zf + static_cast<size_t>(idx[i]) * M;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) out[static_cast<size_t>(i) * N + j] = zrow[idx[j]];
-  }
-}
-
-// Task groups per CTA: two when both groups' shared memory fits one CTA, else one.
-template <typename CT>
-int groups_for(int ncap, bool tc) {
-  int optin = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t gb = group_smem_bytes<CT>(ncap, tc);
-  return (2 * gb + 2048 <= static_cast<size_t>(optin)) ? 2 : 1;
-}
-
-template <typename CT, typename ZT, bool MIXED, bool TC>
-cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
-  if (a.ncap < 1 || a.ncap > a.M || a.lda < a.M || nslots < 1) return cudaErrorInvalidValue;
-  const int groups = groups_for<CT>(a.ncap, TC);
-  const size_t smem = groups * group_smem_bytes<CT>(a.ncap, TC);
-  auto k = eval_kernel<CT, ZT, MIXED, TC>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  EvalArgs b = a;
-  b.nslots = nslots;
-  k<<<(nslots + groups - 1) / groups, kThreads * groups, smem, s>>>(b);
-  return cudaGetLastError();
-}
-
-// Resident task groups per SM (CTAs per SM x groups per CTA).
-template <typename CT, typename ZT, bool MIXED, bool TC>
-int blocks_per_sm_t(int M) {
-  const int groups = groups_for<CT>(M, TC);
-  const size_t smem = groups * group_smem_bytes<CT>(M, TC);
-  auto k = eval_kernel<CT, ZT, MIXED, TC>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-    return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads * groups, smem) != cudaSuccess) return 0;
-  return n * groups;
+bool needs_large(int ncap, bool tc) {
+  return group_smem_bytes<CT>(ncap, tc, false) + kStaticSmemSlack > static_cast<size_t>(optin_smem());
 }
 
 }  // namespace
@@ -1280,38 +21,63 @@ cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+bool eval_is_large(int precision, int ncap, int use_tc) {
+  return precision == PMOM_FP64 ? needs_large<double2>(ncap, false) : needs_large<float2>(ncap, use_tc != 0);
+}
+
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {
+  if (eval_is_large(precision, a.ncap, a.use_tc)) return launch_eval_large(a, precision, nslots, s);
   if (precision == PMOM_FP64) {
-    return a.z_c128 ? launch_eval_t<double2, double2, false, false>(a, nslots, s)
-                    : launch_eval_t<double2, float2, false, false>(a, nslots, s);
+    return a.z_c128 ? launch_eval_t<double2, double2, false, false, false>(a, nslots, s)
+                    : launch_eval_t<double2, float2, false, false, false>(a, nslots, s);
   }
   if (a.use_tc)
-    return a.z_c128 ? launch_eval_t<float2, double2, true, true>(a, nslots, s)
-                    : launch_eval_t<float2, float2, true, true>(a, nslots, s);
-  return a.z_c128 ? launch_eval_t<float2, double2, true, false>(a, nslots, s)
-                  : launch_eval_t<float2, float2, true, false>(a, nslots, s);
+    return a.z_c128 ? launch_eval_t<float2, double2, true, true, false>(a, nslots, s)
+                    : launch_eval_t<float2, float2, true, true, false>(a, nslots, s);
+  return a.z_c128 ? launch_eval_t<float2, double2, true, false, false>(a, nslots, s)
+                  : launch_eval_t<float2, float2, true, false, false>(a, nslots, s);
 }
 
 int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc) {
+  if (eval_is_large(precision, ncap, use_tc)) return eval_blocks_per_sm_large(precision, ncap, z_c128);
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false, false>(ncap) : blocks_per_sm_t<double2, float2, false, false>(ncap);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false, false, false>(ncap)
+                  : blocks_per_sm_t<double2, float2, false, false, false>(ncap);
   if (use_tc)
-    return z_c128 ? blocks_per_sm_t<float2, double2, true, true>(ncap) : blocks_per_sm_t<float2, float2, true, true>(ncap);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true, false>(ncap) : blocks_per_sm_t<float2, float2, true, false>(ncap);
+    return z_c128 ? blocks_per_sm_t<float2, double2, true, true, false>(ncap)
+                  : blocks_per_sm_t<float2, float2, true, true, false>(ncap);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true, false, false>(ncap)
+                : blocks_per_sm_t<float2, float2, true, false, false>(ncap);
 }
 
-size_t eval_slot_bytes(int precision, int M, int P, int* lda) {
-  *lda = (M + 3) & ~3;
+int eval_max_ncap(int precision, int M) {
+  // largest support set whose large-layout task group fits one CTA (binary search on the layout)
+  const size_t optin = static_cast<size_t>(optin_smem());
+  auto fits = [&](int n) {
+    const size_t b = precision == PMOM_FP64 ? group_smem_bytes<double2>(n, 0, true) : group_smem_bytes<float2>(n, 1, true);
+    return b + kStaticSmemSlack <= optin;
+  };
+  if (fits(M)) return M;
+  int lo = 1, hi = M;   // fits(lo), !fits(hi)
+  while (hi - lo > 1) {
+    const int mid = lo + (hi - lo) / 2;
+    if (fits(mid)) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+size_t eval_slot_bytes(int precision, int ncap, int P, int* lda) {
+  *lda = (ncap + 3) & ~3;
   const size_t ct = precision == PMOM_FP64 ? sizeof(double2) : sizeof(float2);
-  const Slot s = slot_layout(M, *lda, P, ct);
-  size_t bytes = s.r_off + static_cast<size_t>(M) * P * sizeof(double2);   // includes the Z_sub copy
-  return (bytes + 255) & ~size_t(255);
+  const Slot s = slot_layout(ncap, *lda, P, ct);
+  return (s.end + 255) & ~size_t(255);
 }
 
 size_t eval_smem_bytes(int precision, int ncap, int use_tc) {
   size_t u_off, idx_off, tc_off;
-  return precision == PMOM_FP64 ? smem_layout<double2>(ncap, 0, &u_off, &idx_off, &tc_off)
-                                : smem_layout<float2>(ncap, use_tc, &u_off, &idx_off, &tc_off);
+  const bool large = eval_is_large(precision, ncap, use_tc);
+  return precision == PMOM_FP64 ? smem_layout<double2>(ncap, 0, large, &u_off, &idx_off, &tc_off)
+                                : smem_layout<float2>(ncap, large ? 1 : use_tc, large, &u_off, &idx_off, &tc_off);
 }
 
 cudaError_t launch_order(const int32_t* n_act, int B, int M, int* order, cudaStream_t s) {

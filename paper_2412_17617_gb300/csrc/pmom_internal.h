@@ -75,9 +75,16 @@ cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int
                        const int32_t* n_act, double* fom, int32_t* status, cudaStream_t s);
 cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
                           cudaStream_t s);
-size_t eval_slot_bytes(int precision, int M, int P, int* lda);
+// Workspace of one task slot for support sets up to ncap (leading dimension returned in *lda).
+size_t eval_slot_bytes(int precision, int ncap, int P, int* lda);
 size_t eval_smem_bytes(int precision, int ncap, int use_tc);
 int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc);
+// Large-support-set layout (narrow panels, solve vectors in global memory): chosen when the default
+// layout does not fit one CTA; pmom_eval_large.cu holds its kernels.
+bool eval_is_large(int precision, int ncap, int use_tc);
+int eval_max_ncap(int precision, int M);
+cudaError_t launch_eval_large(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
+int eval_blocks_per_sm_large(int precision, int ncap, int z_c128);
 
 // GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
 pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
-           "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_graph_capture", "pmom_graph_launch",
+           "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_capacity", "pmom_graph_capture", "pmom_graph_launch",
            "pmom_autotune", "pmom_search")
 
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_sync": [V, V],
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
         "pmom_set_tensor_cores": [V, I32],
+        "pmom_capacity": [V, I32, P, P],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
@@ -322,6 +323,14 @@ class Evaluator:
 
     def set_tensor_cores(self, on: bool = True):
         self._check(self.L.pmom_set_tensor_cores(self.h, 1 if on else 0))
+
+    def capacity(self, precision: str = "mixed"):
+        """(n_default, n_max): the largest support set of the default shared-memory layout and of
+        any layout (larger candidates come back with status CAPACITY)."""
+        nd, nm = ctypes.c_int32(), ctypes.c_int32()
+        prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED
+        self._check(self.L.pmom_capacity(self.h, prec, ctypes.byref(nd), ctypes.byref(nm)))
+        return nd.value, nm.value
 
     def set_timing(self, on: bool = True):
         self._check(self.L.pmom_set_timing(self.h, 1 if on else 0))

@@ -110,11 +110,13 @@ def grid_stripline_16x16x2() -> Grid:
                 3.66, 0.004, 2, ports)
 
 
-def grid_stripline_20x20x3() -> Grid:
+def grid_stripline_20x20x3(n_states: int = 3) -> Grid:
+    """3-layer 20x20 stripline; n_states = 3 adds the via state (void / metal / via to the next
+    layer), n_states = 2 is the same stack-up with on/off pixels only."""
     h = H_RO4350
     ports = (Port(0, SIDE_RIGHT, 10), Port(0, SIDE_LEFT, 10), Port(2, SIDE_LEFT, 10))
-    return Grid("stripline_20x20x3_via", 3, 20, 20, 0.45e-3, MEDIUM_STRIPLINE, (h, 2 * h, 3 * h), 4 * h,
-                3.66, 0.004, 3, ports)
+    name = "stripline_20x20x3_via" if n_states == 3 else "stripline_20x20x3"
+    return Grid(name, 3, 20, 20, 0.45e-3, MEDIUM_STRIPLINE, (h, 2 * h, 3 * h), 4 * h, 3.66, 0.004, n_states, ports)
 
 
 def grid_stripline_32x32x4() -> Grid:
@@ -198,6 +200,20 @@ def single_flip_batch(seed: np.ndarray, n_states: int = 2) -> np.ndarray:
                     c[l, y, x] = s
                     out.append(c)
     return np.ascontiguousarray(np.stack(out).astype(np.uint8))
+
+
+def depth_flips(seed: np.ndarray, depth: int, count: int, n_states: int, rng_seed: int) -> np.ndarray:
+    """`count` candidates that each change `depth` distinct pixels of `seed` to another state
+    (pixels and new states drawn uniformly).  Shape [count][layers][ny][nx], uint8."""
+    g = rng(rng_seed)
+    out = np.repeat(seed[None], count, axis=0).astype(np.uint8)
+    flat = out.reshape(count, -1)
+    for c in range(count):
+        pix = g.choice(flat.shape[1], size=depth, replace=False)
+        for j in pix:
+            s = int(g.integers(n_states - 1))
+            flat[c, j] = s if s < flat[c, j] else s + 1
+    return np.ascontiguousarray(out)
 
 
 def random_maps(grid: Grid, count: int, fill: float, seed: int) -> np.ndarray:

@@ -1,0 +1,111 @@
+"""GPU parity for support sets beyond the default shared-memory layout (N of one to several
+thousand): the narrow-panel layout with the solve vectors in global memory, against the oracle.
+
+The grid is the 3-layer 20 x 20 stripline of the batching workload with on/off pixels; candidates
+are depth-1..3 changes of seeded maps of different fill, so one launch mixes support sets from
+about 1000 to 2400 (uneven work in one persistent queue).  Two frequencies of the 0.5-8 GHz sweep.
+"""
+import numpy as np
+import pytest
+
+import pmom_inputs as PI
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FREQS = [2.0e9, 6.2e9]
+
+
+@pytest.fixture(scope="module")
+def large_case():
+    from paper_2412_17617_gb300 import build as B
+    B.build()
+    from paper_2412_17617_gb300 import pmom
+    g = PI.grid_stripline_20x20x3(n_states=2)
+    OG = O.Grid(g)
+    Z, _ = O.fill(OG, FREQS)
+    Z64 = Z.astype(np.complex64)
+    del Z
+    maps = []
+    for k, fill in enumerate((0.35, 0.55, 0.75)):
+        seed = PI.seed_map(g, fill, 40 + k)
+        maps.append(PI.depth_flips(seed, 1 + k, 2, 2, 90 + k))
+    maps = np.ascontiguousarray(np.concatenate(maps))
+    N = np.array([len(O.active_set(OG, m)) for m in maps])
+    S_ref, st = O.eval_batch(OG, Z64, maps)
+    assert (st == 0).all()
+    band = O.bands(FREQS, PI.UNII_BANDS)
+    fom_ref = O.fom_batch(S_ref, band)
+    ev = pmom.Evaluator(g)
+    ev.load_Z(FREQS, torch.from_numpy(Z64).cuda())
+    ev.set_fom(pmom.band_codes(FREQS, PI.UNII_BANDS))
+    yield ev, maps, N, S_ref, fom_ref
+    ev.close()
+
+
+def _check(S, fom, S_ref, fom_ref, prec):
+    err = np.abs(S - S_ref)
+    if prec == "fp64":
+        assert (err <= 1e-10 * np.maximum(1.0, np.abs(S_ref))).all(), float(err.max())
+        tf = 1e-10
+    else:
+        assert err.max() <= 1e-6, float(err.max())
+        tf = 1e-6
+    rel = np.abs(fom - fom_ref) / np.abs(fom_ref)
+    assert rel.max() <= tf, float(rel.max())
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_large_support_sets_match_oracle(large_case, prec):
+    ev, maps, N, S_ref, fom_ref = large_case
+    n_default, n_max = ev.capacity(prec)
+    # the batch needs the large layout, and every candidate fits it
+    assert N.max() > n_default, (N.max(), n_default)
+    assert N.max() <= n_max, (N.max(), n_max)
+    S, fom, status = ev.eval(torch.from_numpy(maps).cuda(), prec)
+    torch.cuda.synchronize()
+    codes = status.cpu().numpy()
+    assert np.isin(codes, [0, 3]).all(), codes
+    if prec == "fp64":
+        assert (codes == 0).all()
+    _check(S.cpu().numpy(), fom.cpu().numpy(), S_ref, fom_ref, prec)
+    assert int(np.argmin(fom.cpu().numpy())) == int(np.argmin(fom_ref))
+
+
+def test_large_support_sets_graph_replay(large_case):
+    """The benchmark's launch configuration: autotune, then one CUDA graph per batch, replayed."""
+    ev, maps, N, S_ref, fom_ref = large_case
+    dm = torch.from_numpy(maps).cuda()
+    B = dm.shape[0]
+    ev.autotune(dm, "mixed")
+    S = torch.empty((B, len(FREQS), 3, 3), dtype=torch.complex128, device="cuda")
+    fom = torch.empty((B,), dtype=torch.float64, device="cuda")
+    status = torch.empty((B,), dtype=torch.int32, device="cuda")
+    ev.graph_capture(dm, "mixed", out=(S, fom, status), ncap=int(N.max()))
+    for _ in range(2):
+        ev.graph_launch()
+    torch.cuda.synchronize()
+    assert np.isin(status.cpu().numpy(), [0, 3]).all()
+    _check(S.cpu().numpy(), fom.cpu().numpy(), S_ref, fom_ref, "mixed")
+
+
+def test_capacity_flags_oversized_candidates(large_case):
+    """A graph captured for a smaller capacity flags the larger candidates instead of solving
+    them; the others are still solved."""
+    ev, maps, N, S_ref, fom_ref = large_case
+    order = np.argsort(N)
+    cap = int(N[order[2]])   # the three smallest fit
+    dm = torch.from_numpy(maps).cuda()
+    B = dm.shape[0]
+    S = torch.empty((B, len(FREQS), 3, 3), dtype=torch.complex128, device="cuda")
+    fom = torch.empty((B,), dtype=torch.float64, device="cuda")
+    status = torch.empty((B,), dtype=torch.int32, device="cuda")
+    ev.graph_capture(dm, "mixed", out=(S, fom, status), ncap=cap)
+    ev.graph_launch()
+    torch.cuda.synchronize()
+    codes = status.cpu().numpy()
+    fits = N <= cap
+    assert (codes[~fits] == 6).all(), codes
+    assert np.isin(codes[fits], [0, 3]).all(), codes
+    _check(S.cpu().numpy()[fits], fom.cpu().numpy()[fits], S_ref[fits], fom_ref[fits], "mixed")
