@@ -153,3 +153,25 @@ def test_brute_force_every_3x3_map():
     off = S[0] * (1 - np.eye(3))
     assert np.abs(off).max() < 1e-2
     assert np.abs(np.diagonal(S[0], axis1=1, axis2=2)).min() > 0.99
+
+
+def test_lapack_solve_route_matches_c_oracle(c1):
+    """The LAPACK-backed evaluation (used for support sets of thousands of BFs) follows the same
+    definition as the plain C path: agreement to 1e-12 on the 8x8 microstrip and a 4x4x2
+    stripline, both storage precisions; port edges are one pixel side (R2 stub geometry)."""
+    w, OG, Z = c1
+    g = w.grid
+    maps = PI.random_maps(g, 3, 0.5, 11)
+    assert np.allclose(O.port_lengths(OG), g.pitch_m, rtol=1e-14)
+    for m in maps:
+        S_c, st = O.eval_map(OG, Z, m)
+        assert st == 0
+        assert np.abs(O.eval_map_lapack(OG, Z, m) - S_c).max() <= 1e-12
+    gs = PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2)
+    OGs = O.Grid(gs)
+    Zs, _ = O.fill(OGs, [2.0e9, 6.5e9])
+    Zs64 = Zs.astype(np.complex64)
+    for m in PI.random_maps(gs, 3, 0.6, 12):
+        S_c, st = O.eval_map(OGs, Zs64, m)
+        assert st == 0
+        assert np.abs(O.eval_map_lapack(OGs, Zs64, m) - S_c).max() <= 1e-12
