@@ -60,7 +60,9 @@ enum {
   PMOM_CAND_REPAIRED = 3,        /* mixed path did not converge at some frequency; that frequency
                                     was re-solved on the FP64 path (results are valid) */
   PMOM_CAND_BAD_STATE = 5,       /* a pixel state >= n_states; S/FoM not computed */
-  PMOM_CAND_CAPACITY = 6         /* support set larger than a captured graph's capacity; not computed */
+  PMOM_CAND_CAPACITY = 6,        /* support set larger than a captured graph's capacity; not computed */
+  PMOM_CAND_FAR = 7              /* bordered evaluation: more than PMOM_BORDER_K basis functions removed
+                                    or added relative to the reference map; not computed */
 };
 
 typedef struct {
@@ -196,6 +198,26 @@ pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev,
  * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning. */
 pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
 
+/* Bordered low-rank evaluation of candidates close to a reference map (the single-pixel changes
+ * of a search step).  A change removes a set R and adds a set A of basis functions relative to the
+ * reference support set S (Eq. 3; a flip touches the pixel's inner BF, its inter-pixel BFs and a
+ * pixel-port BF, Section II-C).  Per frequency the call factors the reference Z_sub = Z(f)[S, S]
+ * in FP64 and forms its inverse G; each candidate's port solutions then follow exactly (up to
+ * rounding) from the block-inverse identities
+ *     (Z_TT)^-1 = G_TT - G_TR G_RR^-1 G_RT   (T = S \ R)
+ * and the Schur complement C = Z_AA - Z_AT (Z_TT)^-1 Z_TA of the bordered system, in
+ * O(|S|^2 |A| + |S| k (k + P)) work instead of a new O(N^3) factorization; Y and S follow Eq. 6-7
+ * and the FoM Eq. 8-9 as in pmom_eval_candidates.  All arithmetic is FP64.
+ *   reference_map_dev : device uint8 [layers][ny][nx]
+ *   maps_dev, S_out_dev, fom_out_dev, status_dev : as pmom_eval_candidates
+ * Candidates with |R| or |A| above PMOM_BORDER_K report PMOM_CAND_FAR (evaluate them with
+ * pmom_eval_candidates).  The call reads the reference's support-set size back (one stream
+ * synchronization) and allocates F * |S|^2 * 32 bytes of reference factors on first use.
+ * Errors: INVALID_ARG, NOT_READY, BAD_STATE_VALUE (reference map), OOM, CUDA. */
+#define PMOM_BORDER_K 8
+pmom_status pmom_eval_bordered(pmom_ctx* ctx, const uint8_t* reference_map_dev, const uint8_t* maps_dev, int32_t B,
+                               double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
+
 /* Support-set capacity of one task on this GPU for `precision` (PMOM_FP64 or
  * PMOM_MIXED_REFINED): *n_default = the largest N the default shared-memory layout holds (wide
  * panels, solve vectors in shared memory, up to two tasks per SM); *n_max = the largest N any
@@ -233,7 +255,9 @@ pmom_status pmom_stats(pmom_ctx* ctx, int64_t* out8);
 
 /* Kernel timing of later eval calls: on != 0 makes each eval record CUDA events on its stream
  * around its kernels; pmom_kernel_times then returns the last call's milliseconds for
- * [0] activation, [1] evaluation, [2] FP64 repair, [3] FoM (host double [4]; synchronizes). */
+ * [0] activation, [1] evaluation, [2] FP64 repair, [3] Y -> S and FoM (host double [4];
+ * synchronizes).  After pmom_eval_bordered the four are [0] reference gather + FP64 LU,
+ * [1] reference inverse, [2] candidate activation + bordered update, [3] Y -> S and FoM. */
 pmom_status pmom_set_timing(pmom_ctx* ctx, int32_t on);
 pmom_status pmom_kernel_times(pmom_ctx* ctx, double* ms4_host);
 

@@ -52,6 +52,15 @@ struct pmom_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;   // capture stream (the legacy default stream cannot be captured)
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // bordered evaluation: reference support set, FP64 factors and inverses, per-slot scratch
+  int32_t* d_ref_idx = nullptr;    // [M] then n (one int) and the reference's bad-state flag
+  uint32_t* d_ref_flags = nullptr;  // [F]
+  double2* d_ref_lu = nullptr;
+  double2* d_ref_g = nullptr;
+  int* d_ref_piv = nullptr;
+  size_t ref_cap = 0;               // elements of d_ref_lu / d_ref_g
+  double2* d_bwork = nullptr;
+  size_t bwork_elems = 0;
   std::string err;
 };
 
@@ -223,6 +232,12 @@ pmom_status pmom_destroy(pmom_ctx* c) {
   free_dev(c->d_small);
   free_dev(c->d_work);
   free_dev(c->d_order);
+  free_dev(c->d_ref_idx);
+  free_dev(c->d_ref_flags);
+  free_dev(c->d_ref_lu);
+  free_dev(c->d_ref_g);
+  free_dev(c->d_ref_piv);
+  free_dev(c->d_bwork);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -403,6 +418,88 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
   return enqueue_eval(c, maps, B, precision, S_out, fom_out, status, s, 0);
+}
+
+pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_t* maps, int32_t B, double* S_out,
+                               double* fom_out, int32_t* status, void* stream) {
+  if (!c || !ref_map || !maps || !fom_out || !status || B < 1)
+    return fail(c, PMOM_ERR_INVALID_ARG, "eval_bordered: bad argument");
+  if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval_bordered: load Z and set the FoM bands first");
+  pmom_status st = ensure_batch(c, B);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  const int M = c->M, F = c->F, P = c->grid.n_ports;
+  if (!c->d_ref_idx) PMOM_CUDA(c, cudaMalloc(&c->d_ref_idx, sizeof(int32_t) * (M + 2)));
+  if (!c->d_ref_flags) PMOM_CUDA(c, cudaMalloc(&c->d_ref_flags, sizeof(uint32_t) * F));
+  int32_t* d_ref_n = c->d_ref_idx + M;
+  uint32_t* d_ref_bad = reinterpret_cast<uint32_t*>(c->d_ref_idx + M + 1);
+  int* small = static_cast<int*>(c->d_small);
+  // reference support set (a1), its size read back to size the factors
+  pmom::EvalArgs r{};
+  r.rules = c->d_rules; r.M = M; r.P = P; r.F = F; r.B = 1; r.npix = c->grid.pixels();
+  r.n_states = c->grid.n_states; r.maps = ref_map; r.idx = c->d_ref_idx; r.n_act = d_ref_n; r.flags = d_ref_bad;
+  r.n_max = small + 2;
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_small, 0, 256, s));
+  PMOM_CUDA(c, cudaMemsetAsync(d_ref_bad, 0, sizeof(uint32_t), s));
+  PMOM_CUDA(c, pmom::launch_activate(r, s));
+  int n = 0;
+  PMOM_CUDA(c, cudaMemcpyAsync(&n, d_ref_n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaStreamSynchronize(s));
+  if (n <= 0) return fail(c, PMOM_ERR_BAD_STATE_VALUE, "eval_bordered: reference map has a pixel state out of range");
+  const int ldn = (n + 3) & ~3;
+  const size_t ref_elems = static_cast<size_t>(F) * n * ldn;
+  if (ref_elems > c->ref_cap) {
+    free_dev(c->d_ref_lu);
+    free_dev(c->d_ref_g);
+    free_dev(c->d_ref_piv);
+    c->ref_cap = 0;
+    PMOM_CUDA(c, cudaMalloc(&c->d_ref_lu, sizeof(double2) * ref_elems));
+    PMOM_CUDA(c, cudaMalloc(&c->d_ref_g, sizeof(double2) * ref_elems));
+    PMOM_CUDA(c, cudaMalloc(&c->d_ref_piv, sizeof(int) * static_cast<size_t>(F) * M));
+    c->ref_cap = ref_elems;
+  }
+  // per frequency: FP64 LU of the reference (a4) and its inverse (a5, n right-hand sides)
+  const bool tm = c->timing;
+  c->timed = tm;
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
+  PMOM_CUDA(c, pmom::launch_ref_factor(c->d_Z, c->dtype == PMOM_C128, M, c->d_ref_idx, d_ref_n, n, F, c->d_ref_lu,
+                                       ldn, c->d_ref_piv, c->d_ref_flags, s));
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
+  PMOM_CUDA(c, pmom::launch_ref_inverse(c->d_ref_lu, ldn, c->d_ref_piv, d_ref_n, n, F, c->d_ref_g, s));
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[2], s));
+  // candidates: support sets, then the bordered update per (candidate, frequency) task
+  pmom::EvalArgs a{};
+  a.rules = c->d_rules; a.M = M; a.P = P; a.F = F; a.B = B; a.npix = c->grid.pixels();
+  a.n_states = c->grid.n_states; a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.flags = c->d_flags;
+  a.n_max = small + 2;
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
+  PMOM_CUDA(c, pmom::launch_activate(a, s));
+  int nslots = pmom::border_slots(c->num_sms, n);
+  if (nslots > B * F) nslots = B * F;
+  const size_t se = pmom::border_slot_elems(n);
+  if (se * nslots > c->bwork_elems) {
+    free_dev(c->d_bwork);
+    c->bwork_elems = 0;
+    PMOM_CUDA(c, cudaMalloc(&c->d_bwork, sizeof(double2) * se * nslots));
+    c->bwork_elems = se * nslots;
+  }
+  pmom::BorderArgs ba{};
+  ba.Z = c->d_Z; ba.z_c128 = c->dtype == PMOM_C128; ba.M = M; ba.P = P; ba.F = F; ba.B = B;
+  ba.ref_idx = c->d_ref_idx; ba.ref_n = d_ref_n; ba.ref_flags = c->d_ref_flags; ba.G = c->d_ref_g; ba.ldn = ldn;
+  ba.idx = c->d_idx; ba.n_act = c->d_nact;
+  double2* Sd = S_out ? reinterpret_cast<double2*>(S_out) : c->d_S;
+  ba.S = Sd; ba.flags = c->d_flags;
+  for (int p = 0; p < pmom::kMaxPorts; ++p) ba.port_len[p] = c->grid.pitch;
+  ba.task_counter = small;
+  ba.work = c->d_bwork; ba.slot_elems = se;
+  PMOM_CUDA(c, pmom::launch_border(ba, nslots, n, s));
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[3], s));
+  PMOM_CUDA(c, pmom::launch_ys(Sd, B, F, P, c->Z0, c->d_flags, s));
+  PMOM_CUDA(c, pmom::launch_fom(Sd, c->d_bands, F, P, B, c->d_flags, c->d_nact, fom_out, status, s));
+  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
+  c->launches = 7;
+  return PMOM_OK;
 }
 
 pmom_status pmom_graph_capture(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,

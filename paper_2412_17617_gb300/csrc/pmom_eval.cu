@@ -4,16 +4,6 @@
 #include "pmom_eval_kernels.cuh"
 
 namespace pmom {
-namespace {
-
-// The large-support-set layout is used when the default layout's single task group does not fit
-// the opt-in shared memory of one CTA.
-template <typename CT>
-bool needs_large(int ncap, bool tc) {
-  return group_smem_bytes<CT>(ncap, tc, false) + kStaticSmemSlack > static_cast<size_t>(optin_smem());
-}
-
-}  // namespace
 
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
   activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.idx, a.n_act, a.flags,
@@ -22,7 +12,7 @@ cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
 }
 
 bool eval_is_large(int precision, int ncap, int use_tc) {
-  return precision == PMOM_FP64 ? needs_large<double2>(ncap, false) : needs_large<float2>(ncap, use_tc != 0);
+  return precision == PMOM_FP64 ? needs_large_layout<double2>(ncap, false) : needs_large_layout<float2>(ncap, use_tc != 0);
 }
 
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {

@@ -1232,6 +1232,9 @@ __global__ void fom_kernel(const double2* __restrict__ S, const uint8_t* __restr
   } else if (fl & kFlagCapacity) {
     st = PMOM_CAND_CAPACITY;
     sum = __longlong_as_double(0x7ff8000000000000ll);
+  } else if (fl & kFlagFar) {
+    st = PMOM_CAND_FAR;
+    sum = __longlong_as_double(0x7ff8000000000000ll);
   } else if ((fl & kFlagNonfinite) || !isfinite(sum)) st = PMOM_CAND_NONFINITE;
   else if (fl & kFlagSingular) st = PMOM_CAND_SINGULAR;
   else if (fl & kFlagRepaired) st = PMOM_CAND_REPAIRED;
@@ -1275,6 +1278,13 @@ int optin_smem() {
   return optin;
 }
 constexpr size_t kStaticSmemSlack = 2048;   // static shared memory and the runtime's reservation
+
+// The large-support-set layout is used when the default layout's single task group does not fit
+// the opt-in shared memory of one CTA.
+template <typename CT>
+bool needs_large_layout(int ncap, bool tc) {
+  return group_smem_bytes<CT>(ncap, tc, false) + kStaticSmemSlack > static_cast<size_t>(optin_smem());
+}
 
 // Task groups per CTA: two when both groups' shared memory fits one CTA, else one.
 template <typename CT>

@@ -60,8 +60,37 @@ struct EvalArgs {
 };
 
 enum CandFlag : uint32_t {
-  kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u, kFlagCapacity = 16u
+  kFlagSingular = 1u, kFlagNonfinite = 2u, kFlagRepaired = 4u, kFlagBadState = 8u, kFlagCapacity = 16u,
+  kFlagFar = 32u
 };
+
+// Bordered evaluation against a reference map (pmom_border.cu).
+constexpr int kBorderK = 8;   // BFs a candidate may remove from / add to the reference support set
+struct BorderArgs {
+  const void* Z;              // [F][M][M] resident database
+  int z_c128;
+  int M, P, F, B;
+  const int32_t* ref_idx;     // [n] reference support set (ascending)
+  const int32_t* ref_n;       // n (device)
+  const uint32_t* ref_flags;  // [F] 1: the reference matrix is singular at f
+  const double2* G;           // [F][n][ldn] reference inverses (FP64)
+  int ldn;
+  const int32_t* idx;         // [B][M] candidates' support sets
+  const int32_t* n_act;       // [B]
+  double2* S;                 // [B][F][P][P]: Y written here, converted by launch_ys
+  uint32_t* flags;            // [B]
+  double port_len[kMaxPorts];
+  int* task_counter;
+  double2* work;              // per-slot scratch
+  size_t slot_elems;
+};
+cudaError_t launch_ref_factor(const void* Z, int z_c128, int M, const int32_t* ref_idx, const int32_t* ref_n, int n,
+                              int F, double2* LU, int ldn, int* piv, uint32_t* ref_flags, cudaStream_t s);
+cudaError_t launch_ref_inverse(const double2* LU, int ldn, const int* piv, const int32_t* ref_n, int n, int F,
+                               double2* G, cudaStream_t s);
+size_t border_slot_elems(int n);
+int border_slots(int num_sms, int n);
+cudaError_t launch_border(const BorderArgs& a, int nslots, int n, cudaStream_t s);
 
 // Launchers (pmom_eval.cu).
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);

@@ -19,7 +19,8 @@ PMOM_OK = 0
 PMOM_C64, PMOM_C128 = 0, 1
 PMOM_MEM_HOST, PMOM_MEM_DEVICE = 0, 1
 PMOM_FP64, PMOM_MIXED_REFINED = 0, 1
-CAND_OK, CAND_SINGULAR, CAND_NONFINITE, CAND_REPAIRED, CAND_BAD_STATE, CAND_CAPACITY = 0, 1, 2, 3, 5, 6
+CAND_OK, CAND_SINGULAR, CAND_NONFINITE, CAND_REPAIRED, CAND_BAD_STATE, CAND_CAPACITY, CAND_FAR = 0, 1, 2, 3, 5, 6, 7
+BORDER_K = 8   # basis functions a candidate may remove from / add to the reference (pmom_eval_bordered)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z_SHAPE_MISMATCH", 5: "CUDA",
                 6: "NOT_READY", 7: "UNSUPPORTED"}
 # names exported by libpmom.so, one per declaration in include/pmom.h
@@ -27,7 +28,7 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
            "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_capacity", "pmom_graph_capture", "pmom_graph_launch",
-           "pmom_autotune", "pmom_search")
+           "pmom_autotune", "pmom_search", "pmom_eval_bordered")
 
 
 class PmomError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
         "pmom_set_tensor_cores": [V, I32],
         "pmom_capacity": [V, I32, P, P],
+        "pmom_eval_bordered": [V, P, P, I32, P, P, P, V],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
@@ -130,6 +132,7 @@ class Evaluator:
     def __init__(self, grid):
         self.L = load_library()
         self.grid = grid
+        self._last_kind = "eval"
         self._z = (ctypes.c_double * grid.layers)(*grid.layer_z_m)
         self._ports = (_Port * len(grid.ports))(*[_Port(p.layer, p.side, p.pos) for p in grid.ports])
         desc = _GridDesc(grid.layers, grid.nx, grid.ny, grid.pitch_m, grid.medium, self._z, grid.h_total_m,
@@ -233,9 +236,29 @@ class Evaluator:
             status = torch.empty((B,), dtype=torch.int32, device="cuda")
         else:
             S, fom, status = out
+        self._last_kind = "eval"
         self._check(self.L.pmom_eval_candidates(
             self.h, ctypes.c_void_p(maps.data_ptr()), B, prec, ctypes.c_void_p(S.data_ptr() if S is not None else 0),
             ctypes.c_void_p(fom.data_ptr()), ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return S, fom, status
+
+    def eval_bordered(self, reference_map, maps, want_S: bool = True, out=None, stream=None):
+        """Bordered low-rank evaluation of `maps` (torch CUDA uint8 [B][layers][ny][nx]) against the
+        torch CUDA uint8 `reference_map` [layers][ny][nx]; same outputs as eval().  Candidates that
+        remove or add more than BORDER_K basis functions report CAND_FAR."""
+        import torch
+        B = maps.shape[0]
+        if out is None:
+            S = torch.empty((B, self.F, self.P, self.P), dtype=torch.complex128, device="cuda") if want_S else None
+            fom = torch.empty((B,), dtype=torch.float64, device="cuda")
+            status = torch.empty((B,), dtype=torch.int32, device="cuda")
+        else:
+            S, fom, status = out
+        self._last_kind = "bordered"
+        self._check(self.L.pmom_eval_bordered(
+            self.h, ctypes.c_void_p(reference_map.data_ptr()), ctypes.c_void_p(maps.data_ptr()), B,
+            ctypes.c_void_p(S.data_ptr() if S is not None else 0), ctypes.c_void_p(fom.data_ptr()),
+            ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
 
     def eval_host(self, maps: np.ndarray, precision: str = "mixed", S: Optional[np.ndarray] = None,
@@ -339,6 +362,8 @@ class Evaluator:
         """Milliseconds of the last eval call's kernels (CUDA events on its stream)."""
         out = np.zeros(4, dtype=np.float64)
         self._check(self.L.pmom_kernel_times(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        if self._last_kind == "bordered":
+            return {"ref_lu": out[0], "ref_inverse": out[1], "border": out[2], "fom": out[3]}
         return {"activate": out[0], "eval": out[1], "repair": out[2], "fom": out[3]}
 
     def sync(self, stream=None):

@@ -1,0 +1,126 @@
+"""GPU parity of the bordered low-rank evaluation (single-pixel changes of a reference map):
+against the oracle's direct solve of every candidate, and against the library's own full FP64
+path on the same batch.
+
+The bordered path is FP64 throughout; its results follow from the reference inverse by exact
+block-inverse identities, so it is held to 1e-8 per S entry here (the mixed path's 1e-6 target
+with margin) and its decisions must equal the oracle's.
+"""
+import numpy as np
+import pytest
+
+import pmom_inputs as PI
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_S, TOL_F = 1e-8, 1e-8
+
+
+@pytest.fixture(scope="module")
+def pm():
+    from paper_2412_17617_gb300 import build as B
+    B.build()
+    from paper_2412_17617_gb300 import pmom
+    return pmom
+
+
+def _check(S, fom, S_ref, fom_ref):
+    err = np.abs(S - S_ref)
+    assert err.max() <= TOL_S * max(1.0, np.abs(S_ref).max()), float(err.max())
+    rel = np.abs(fom - fom_ref) / np.abs(fom_ref)
+    assert rel.max() <= TOL_F, float(rel.max())
+
+
+def test_plain_all_flips(pm):
+    """8x8 microstrip, complex128 database, all 64 single flips of the seed (removals and
+    additions of up to five BFs)."""
+    w = PI.workload_plain()
+    OG = O.Grid(w.grid)
+    Z, _ = O.fill(OG, w.freqs())
+    seed = PI.seed_map(w.grid, w.fill, 0)
+    maps = PI.workload_maps(w, seed=0)
+    S_ref, st = O.eval_batch(OG, Z, maps)
+    assert (st == 0).all()
+    fom_ref = O.fom_batch(S_ref, O.bands(w.freqs(), w.bands))
+    ev = pm.Evaluator(w.grid)
+    ev.load_Z(w.freqs(), torch.from_numpy(Z).cuda())
+    ev.set_fom(pm.band_codes(w.freqs(), w.bands))
+    S, fom, status = ev.eval_bordered(torch.from_numpy(seed).cuda(), torch.from_numpy(maps).cuda())
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    _check(S.cpu().numpy(), fom.cpu().numpy(), S_ref, fom_ref)
+    assert int(np.argmin(fom.cpu().numpy())) == int(np.argmin(fom_ref))
+    # the reference itself (no change) and a two-pixel change come out right too
+    two = seed.copy()
+    two[0, 0, 0] ^= 1
+    two[0, 5, 6] ^= 1
+    extra = np.ascontiguousarray(np.stack([seed, two]))
+    S2, f2, s2 = ev.eval_bordered(torch.from_numpy(seed).cuda(), torch.from_numpy(extra).cuda())
+    S2_ref, _ = O.eval_batch(OG, Z, extra)
+    assert (s2.cpu().numpy() == 0).all()
+    _check(S2.cpu().numpy(), f2.cpu().numpy(), S2_ref, O.fom_batch(S2_ref, O.bands(w.freqs(), w.bands)))
+    ev.close()
+
+
+@pytest.fixture(scope="module")
+def precision_case(pm):
+    w = PI.workload_precision()
+    OG = O.Grid(w.grid)
+    Z, _ = O.fill(OG, w.freqs())
+    Z64 = Z.astype(np.complex64)
+    del Z
+    seed = PI.seed_map(w.grid, w.fill, 0)
+    maps = PI.workload_maps(w, seed=0)
+    ev = pm.Evaluator(w.grid)
+    ev.load_Z(w.freqs(), torch.from_numpy(Z64).cuda())
+    ev.set_fom(pm.band_codes(w.freqs(), w.bands))
+    sample = np.array([0, 3, 97, 200, 255, 256, 300, 411, 480, 511])
+    S_ref, st = O.eval_batch(OG, Z64, maps[sample])
+    assert (st == 0).all()
+    fom_ref = O.fom_batch(S_ref, O.bands(w.freqs(), w.bands))
+    yield w, seed, maps, ev, sample, S_ref, fom_ref
+    ev.close()
+
+
+def test_precision_workload_full_batch(precision_case):
+    """16x16x2 stripline, complex64 database, 41 frequencies, all 512 single-bit flips in one call
+    (the benchmark's configuration); sampled candidates against the oracle, every candidate
+    against the library's full FP64 path."""
+    w, seed, maps, ev, sample, S_ref, fom_ref = precision_case
+    dm = torch.from_numpy(maps).cuda()
+    S, fom, status = ev.eval_bordered(torch.from_numpy(seed).cuda(), dm)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    Sn, fn = S.cpu().numpy(), fom.cpu().numpy()
+    _check(Sn[sample], fn[sample], S_ref, fom_ref)
+    assert int(np.argmin(fn[sample])) == int(np.argmin(fom_ref))
+    S64, f64, s64 = ev.eval(dm[:128], "fp64")
+    torch.cuda.synchronize()
+    assert (s64.cpu().numpy() == 0).all()
+    _check(Sn[:128], fn[:128], S64.cpu().numpy(), f64.cpu().numpy())
+
+
+def test_far_and_bad_state(precision_case):
+    """Candidates that change too many BFs report FAR; a bad pixel state reports BAD_STATE; both
+    leave the other candidates of the batch untouched.  A bad reference is a call error."""
+    w, seed, maps, ev, sample, S_ref, fom_ref = precision_case
+    far = PI.random_maps(w.grid, 1, 0.5, 3)
+    bad = maps[:1].copy()
+    bad[0, 1, 2, 3] = 7
+    batch = np.ascontiguousarray(np.concatenate([maps[:2], far, bad, maps[2:3]]))
+    S, fom, status = ev.eval_bordered(torch.from_numpy(seed).cuda(), torch.from_numpy(batch).cuda())
+    torch.cuda.synchronize()
+    codes = status.cpu().numpy()
+    assert codes.tolist() == [0, 0, 7, 5, 0], codes
+    keep = [0, 1, 4]
+    Sn = S.cpu().numpy()
+    # same numbers as the clean batch
+    S0, f0, _ = ev.eval_bordered(torch.from_numpy(seed).cuda(), torch.from_numpy(np.ascontiguousarray(maps[:3])).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(Sn[keep], S0.cpu().numpy())
+    badref = seed.copy()
+    badref[0, 0, 0] = 9
+    with pytest.raises(Exception):
+        ev.eval_bordered(torch.from_numpy(badref).cuda(), torch.from_numpy(batch).cuda())
