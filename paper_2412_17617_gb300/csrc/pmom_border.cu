@@ -121,7 +121,9 @@ __device__ bool small_solve(double2* Am, int k, double2* Bm, int nr, int ldb) {
   return true;
 }
 
-template <typename ZT>
+// SMEM_B: the added columns B = Z(f)[S, Ad] are staged in shared memory (q-major, so the lanes of
+// a warp read consecutive rows); otherwise they stay in the slot's global scratch.
+template <typename ZT, bool SMEM_B>
 __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task, s_kr, s_ka, s_bad;
@@ -132,12 +134,13 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
   __shared__ double2 s_C[kBK * kBK], s_D[kBK * kBK];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = a.M, P = a.P, n = *a.ref_n, ldn = a.ldn;
-  int32_t* s_ref = reinterpret_cast<int32_t*>(smem);
+  double2* s_B = reinterpret_cast<double2*>(smem);   // kBK x n (SMEM_B)
+  int32_t* s_ref = reinterpret_cast<int32_t*>(smem + (SMEM_B ? static_cast<size_t>(kBK) * n * sizeof(double2) : 0));
   for (int i = tid; i < n; i += kThreads) s_ref[i] = a.ref_idx[i];
   const int NQ = kMaxPorts + kBK;
   double2* ws = a.work + a.slot_elems * blockIdx.x;
-  double2* Bm = ws;                                   // n x kBK : Z(f)[S, Ad]
-  double2* Wm = Bm + static_cast<size_t>(n) * kBK;     // n x kBK : G B
+  double2* Bm = SMEM_B ? s_B : ws;                    // kBK x n : Z(f)[S, Ad], column q of B is row q
+  double2* Wm = ws + static_cast<size_t>(n) * kBK;     // n x kBK : G B
   double2* Em = Wm + static_cast<size_t>(n) * kBK;     // kBK x n : Z(f)[Ad, S]
   double2* Qm = Em + static_cast<size_t>(kBK) * n;     // n x NQ  : [H V_T | H B_T] rows over T (0 on R)
   double lp[kMaxPorts];
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
     // additions: B = Z(f)[S, Ad], E = Z(f)[Ad, S], D = Z(f)[Ad, Ad]
     for (int e = tid; e < n * ka; e += kThreads) {
       const int j = e / ka, q = e % ka;
-      Bm[static_cast<size_t>(j) * kBK + q] = zload<ZT, double2>(Zf + static_cast<size_t>(s_ref[j]) * M + s_A[q]);
+      Bm[static_cast<size_t>(q) * n + j] = zload<ZT, double2>(Zf + static_cast<size_t>(s_ref[j]) * M + s_A[q]);
     }
     for (int e = tid; e < ka * n; e += kThreads) {
       const int q = e / n, j = e % n;
@@ -215,19 +218,28 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
       s_D[q * kBK + r] = zload<ZT, double2>(Zf + static_cast<size_t>(s_A[q]) * M + s_A[r]);
     }
     __syncthreads();
-    // W = G B: one warp per row of G, lanes over the columns
+    // W = G B: one warp per row of G, lanes over the columns, two column steps in flight
     if (ka > 0) {
       for (int i = warp; i < n; i += kWarps) {
         double2 acc[kBK];
 #pragma unroll
         for (int q = 0; q < kBK; ++q) acc[q] = make_double2(0.0, 0.0);
         const double2* grow = Gf + static_cast<size_t>(i) * ldn;
-        for (int j = lane; j < n; j += 32) {
-          const double2 g = grow[j];
-          const double2* brow = Bm + static_cast<size_t>(j) * kBK;
+        int j = lane;
+        for (; j + 32 < n; j += 64) {
+          const double2 g0 = grow[j], g1 = grow[j + 32];
 #pragma unroll
           for (int q = 0; q < kBK; ++q)
-            if (q < ka) acc[q] = cfma(g, brow[q], acc[q]);
+            if (q < ka) {
+              acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
+              acc[q] = cfma(g1, Bm[static_cast<size_t>(q) * n + j + 32], acc[q]);
+            }
+        }
+        if (j < n) {
+          const double2 g0 = grow[j];
+#pragma unroll
+          for (int q = 0; q < kBK; ++q)
+            if (q < ka) acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < kBK; ++q) {
@@ -374,30 +386,42 @@ size_t border_slot_elems(int n) {
   return static_cast<size_t>(n) * (3 * kBK + kMaxPorts + kBK) + 64;
 }
 
-int border_slots(int num_sms, int n) {
-  const size_t smem = static_cast<size_t>(n) * sizeof(int32_t);
+namespace {
+size_t border_smem(int n, bool smem_b) {
+  return static_cast<size_t>(n) * sizeof(int32_t) + (smem_b ? static_cast<size_t>(kBK) * n * sizeof(double2) : 0);
+}
+bool border_smem_b(int n) { return border_smem(n, true) + 16384 <= static_cast<size_t>(optin_smem()); }
+
+template <typename ZT, bool SMEM_B>
+int border_slots_t(int num_sms, int n) {
+  const size_t smem = border_smem(n, SMEM_B);
+  auto k = border_kernel<ZT, SMEM_B>;
   int per_sm = 0;
-  cudaFuncSetAttribute(border_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, border_kernel<float2>, kThreads, smem) != cudaSuccess ||
-      per_sm < 1)
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   return per_sm * num_sms;
 }
 
-cudaError_t launch_border(const BorderArgs& a, int nslots, int n, cudaStream_t s) {
-  const size_t smem = static_cast<size_t>(n) * sizeof(int32_t);
-  if (a.z_c128) {
-    cudaError_t e = cudaFuncSetAttribute(border_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    border_kernel<double2><<<nslots, kThreads, smem, s>>>(a);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(border_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    border_kernel<float2><<<nslots, kThreads, smem, s>>>(a);
-  }
+template <typename ZT, bool SMEM_B>
+cudaError_t launch_border_t(const BorderArgs& a, int nslots, int n, cudaStream_t s) {
+  const size_t smem = border_smem(n, SMEM_B);
+  auto k = border_kernel<ZT, SMEM_B>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k<<<nslots, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+int border_slots(int num_sms, int n) {
+  return border_smem_b(n) ? border_slots_t<float2, true>(num_sms, n) : border_slots_t<float2, false>(num_sms, n);
+}
+
+cudaError_t launch_border(const BorderArgs& a, int nslots, int n, cudaStream_t s) {
+  const bool sb = border_smem_b(n);
+  if (a.z_c128) return sb ? launch_border_t<double2, true>(a, nslots, n, s) : launch_border_t<double2, false>(a, nslots, n, s);
+  return sb ? launch_border_t<float2, true>(a, nslots, n, s) : launch_border_t<float2, false>(a, nslots, n, s);
 }
 
 }  // namespace pmom
