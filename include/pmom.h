@@ -207,7 +207,13 @@ pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
  *     (Z_TT)^-1 = G_TT - G_TR G_RR^-1 G_RT   (T = S \ R)
  * and the Schur complement C = Z_AA - Z_AT (Z_TT)^-1 Z_TA of the bordered system, in
  * O(|S|^2 |A| + |S| k (k + P)) work instead of a new O(N^3) factorization; Y and S follow Eq. 6-7
- * and the FoM Eq. 8-9 as in pmom_eval_candidates.  All arithmetic is FP64.
+ * and the FoM Eq. 8-9 as in pmom_eval_candidates.
+ *   precision : PMOM_FP64 -- the reference LU, its inverse and the products G * Z(f)[S, A] in FP64;
+ *               PMOM_MIXED_REFINED (complex64 databases) -- the reference LU in single precision on
+ *               the tensor cores, the inverse refined column block by column block with
+ *               float-float residuals to a normwise backward error of 1e-12 (frequencies that
+ *               do not get there are redone in FP64), the products in float-float arithmetic;
+ *               complex128 databases always take the FP64 route
  *   reference_map_dev : device uint8 [layers][ny][nx]
  *   maps_dev, S_out_dev, fom_out_dev, status_dev : as pmom_eval_candidates
  * Candidates with |R| or |A| above PMOM_BORDER_K report PMOM_CAND_FAR (evaluate them with
@@ -216,7 +222,8 @@ pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
  * Errors: INVALID_ARG, NOT_READY, BAD_STATE_VALUE (reference map), OOM, CUDA. */
 #define PMOM_BORDER_K 8
 pmom_status pmom_eval_bordered(pmom_ctx* ctx, const uint8_t* reference_map_dev, const uint8_t* maps_dev, int32_t B,
-                               double* S_out_dev, double* fom_out_dev, int32_t* status_dev, void* stream);
+                               int32_t precision, double* S_out_dev, double* fom_out_dev, int32_t* status_dev,
+                               void* stream);
 
 /* Support-set capacity of one task on this GPU for `precision` (PMOM_FP64 or
  * PMOM_MIXED_REFINED): *n_default = the largest N the default shared-memory layout holds (wide

@@ -61,6 +61,8 @@ struct pmom_ctx {
   size_t ref_cap = 0;               // elements of d_ref_lu / d_ref_g
   double2* d_bwork = nullptr;
   size_t bwork_elems = 0;
+  void* d_ref_work = nullptr;       // single-precision reference factors, one evaluation slot per frequency
+  size_t ref_work_bytes = 0;
   std::string err;
 };
 
@@ -238,6 +240,7 @@ pmom_status pmom_destroy(pmom_ctx* c) {
   free_dev(c->d_ref_g);
   free_dev(c->d_ref_piv);
   free_dev(c->d_bwork);
+  free_dev(c->d_ref_work);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -420,9 +423,10 @@ pmom_status pmom_eval_candidates(pmom_ctx* c, const uint8_t* maps, int32_t B, in
   return enqueue_eval(c, maps, B, precision, S_out, fom_out, status, s, 0);
 }
 
-pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_t* maps, int32_t B, double* S_out,
-                               double* fom_out, int32_t* status, void* stream) {
-  if (!c || !ref_map || !maps || !fom_out || !status || B < 1)
+pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_t* maps, int32_t B, int32_t precision,
+                               double* S_out, double* fom_out, int32_t* status, void* stream) {
+  if (!c || !ref_map || !maps || !fom_out || !status || B < 1 ||
+      (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
     return fail(c, PMOM_ERR_INVALID_ARG, "eval_bordered: bad argument");
   if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval_bordered: load Z and set the FoM bands first");
   pmom_status st = ensure_batch(c, B);
@@ -459,14 +463,54 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
     PMOM_CUDA(c, cudaMalloc(&c->d_ref_piv, sizeof(int) * static_cast<size_t>(F) * M));
     c->ref_cap = ref_elems;
   }
-  // per frequency: FP64 LU of the reference (a4) and its inverse (a5, n right-hand sides)
+  const bool mixed = precision == PMOM_MIXED_REFINED && c->dtype == PMOM_C64 && pmom::ref_inverse_mixed_fits(n);
   const bool tm = c->timing;
   c->timed = tm;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[0], s));
-  PMOM_CUDA(c, pmom::launch_ref_factor(c->d_Z, c->dtype == PMOM_C128, M, c->d_ref_idx, d_ref_n, n, F, c->d_ref_lu,
-                                       ldn, c->d_ref_piv, c->d_ref_flags, s));
-  if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
-  PMOM_CUDA(c, pmom::launch_ref_inverse(c->d_ref_lu, ldn, c->d_ref_piv, d_ref_n, n, F, c->d_ref_g, s));
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_ref_flags, 0, sizeof(uint32_t) * F, s));
+  if (mixed) {
+    // per frequency: single-precision LU of the reference (tensor cores), kept in slot f ...
+    int lda = 0;
+    const size_t sb = pmom::eval_slot_bytes(PMOM_MIXED_REFINED, n, P, &lda);
+    if (sb * F > c->ref_work_bytes) {
+      free_dev(c->d_ref_work);
+      c->ref_work_bytes = 0;
+      PMOM_CUDA(c, cudaMalloc(&c->d_ref_work, sb * F));
+      c->ref_work_bytes = sb * F;
+    }
+    pmom::EvalArgs fa{};
+    fa.rules = c->d_rules; fa.M = M; fa.P = P; fa.F = F; fa.B = 1; fa.npix = c->grid.pixels();
+    fa.n_states = c->grid.n_states; fa.maps = ref_map; fa.idx = c->d_ref_idx; fa.n_act = d_ref_n;
+    fa.Z = c->d_Z; fa.z_c128 = 0;
+    for (int p = 0; p < pmom::kMaxPorts; ++p) fa.port_len[p] = c->grid.pitch;
+    fa.Z0 = c->Z0; fa.flags = c->d_ref_flags; fa.task_counter = small;
+    fa.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
+    fa.work = c->d_ref_work; fa.slot_bytes = sb; fa.lda = lda; fa.ncap = n; fa.use_tc = c->use_tc;
+    fa.factor_only = 1;
+    PMOM_CUDA(c, pmom::launch_eval(fa, PMOM_MIXED_REFINED, slots_for(c, PMOM_MIXED_REFINED, F, n), s));
+    if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
+    // ... its inverse, refined to FP64 accuracy column block by column block ...
+    PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
+    pmom::RefInvArgs ri{};
+    ri.F = F; ri.P = P; ri.ncap = n; ri.lda = lda; ri.ldn = ldn; ri.ref_n = d_ref_n; ri.work = c->d_ref_work;
+    ri.slot_bytes = sb; ri.G = c->d_ref_g; ri.ref_flags = c->d_ref_flags; ri.task_counter = small;
+    const int nblk = (n + 3) / 4;
+    int rs = pmom::ref_inverse_mixed_slots(c->num_sms, n);
+    if (rs > F * nblk) rs = F * nblk;
+    PMOM_CUDA(c, pmom::launch_ref_inverse_mixed(ri, rs, n, s));
+    // ... and the FP64 path for any frequency whose factorization or refinement failed
+    PMOM_CUDA(c, pmom::launch_ref_factor(c->d_Z, 0, M, c->d_ref_idx, d_ref_n, n, F, c->d_ref_lu, ldn, c->d_ref_piv,
+                                         c->d_ref_flags, 1, s));
+    PMOM_CUDA(c, pmom::launch_ref_inverse(c->d_ref_lu, ldn, c->d_ref_piv, d_ref_n, n, F, c->d_ref_g, c->d_ref_flags,
+                                          1, s));
+  } else {
+    // per frequency: FP64 LU of the reference (a4) and its inverse (a5, n right-hand sides)
+    PMOM_CUDA(c, pmom::launch_ref_factor(c->d_Z, c->dtype == PMOM_C128, M, c->d_ref_idx, d_ref_n, n, F, c->d_ref_lu,
+                                         ldn, c->d_ref_piv, c->d_ref_flags, 0, s));
+    if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
+    PMOM_CUDA(c, pmom::launch_ref_inverse(c->d_ref_lu, ldn, c->d_ref_piv, d_ref_n, n, F, c->d_ref_g, c->d_ref_flags,
+                                          0, s));
+  }
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[2], s));
   // candidates: support sets, then the bordered update per (candidate, frequency) task
   pmom::EvalArgs a{};
@@ -475,7 +519,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   a.n_max = small + 2;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, pmom::launch_activate(a, s));
-  int nslots = pmom::border_slots(c->num_sms, n);
+  int nslots = pmom::border_slots(c->num_sms, n, c->dtype == PMOM_C128, mixed);
   if (nslots > B * F) nslots = B * F;
   const size_t se = pmom::border_slot_elems(n);
   if (se * nslots > c->bwork_elems) {
@@ -493,12 +537,13 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   for (int p = 0; p < pmom::kMaxPorts; ++p) ba.port_len[p] = c->grid.pitch;
   ba.task_counter = small;
   ba.work = c->d_bwork; ba.slot_elems = se;
-  PMOM_CUDA(c, pmom::launch_border(ba, nslots, n, s));
+  PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
+  PMOM_CUDA(c, pmom::launch_border(ba, nslots, n, mixed, s));
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[3], s));
   PMOM_CUDA(c, pmom::launch_ys(Sd, B, F, P, c->Z0, c->d_flags, s));
   PMOM_CUDA(c, pmom::launch_fom(Sd, c->d_bands, F, P, B, c->d_flags, c->d_nact, fom_out, status, s));
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
-  c->launches = 7;
+  c->launches = mixed ? 10 : 7;
   return PMOM_OK;
 }
 

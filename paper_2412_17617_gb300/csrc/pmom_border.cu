@@ -26,14 +26,21 @@ namespace {
 constexpr int kBK = kBorderK;   // BFs removed / added per candidate at most
 constexpr int kInvCols = 4;     // inverse columns per CTA (the solve's right-hand-side width)
 
+// Reference-state bits per frequency: kRefSingular (the reference matrix has a zero pivot),
+// kRefFailed (the single-precision reference could not be refined: redo it in FP64), kRefRedone
+// (set by the FP64 factorization of a failed frequency, read by the FP64 inverse).
+constexpr uint32_t kRefSingular = 1u, kRefFailed = 2u, kRefRedone = 4u;
+
+// gated: only the frequencies whose single-precision reference failed are factored (FP64 fallback)
 template <typename ZT, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
 ref_lu_kernel(const ZT* __restrict__ Z, int M, const int32_t* __restrict__ ref_idx, const int32_t* __restrict__ ref_n,
-              double2* __restrict__ LU, int ldn, int* __restrict__ piv, uint32_t* __restrict__ ref_flags) {
+              double2* __restrict__ LU, int ldn, int* __restrict__ piv, uint32_t* __restrict__ ref_flags, int gated) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_val[kWarps + 1];
   __shared__ int s_row[kWarps + 1];
   const int f = blockIdx.x, tid = threadIdx.x;
+  if (gated && !(ref_flags[f] & (kRefSingular | kRefFailed))) return;
   const int n = *ref_n;
   constexpr bool large = NB != Cfg<double2>::NB;
   size_t u_off, idx_off, tc_off;
@@ -51,16 +58,17 @@ ref_lu_kernel(const ZT* __restrict__ Z, int M, const int32_t* __restrict__ ref_i
   }
   gsync();
   const bool singular = lu_factor<double2, NB>(A, ldn, n, piv + static_cast<size_t>(f) * n, Pn, Ut, s_val, s_row, nullptr);
-  if (tid == 0) ref_flags[f] = singular ? 1u : 0u;
+  if (tid == 0) ref_flags[f] = (singular ? kRefSingular : 0u) | (gated ? kRefRedone : 0u);
 }
 
 __global__ void __launch_bounds__(kThreads)
 ref_inv_kernel(const double2* __restrict__ LU, int ldn, const int* __restrict__ piv, const int32_t* __restrict__ ref_n,
-               int nblk, double2* __restrict__ G) {
+               int nblk, double2* __restrict__ G, const uint32_t* __restrict__ ref_flags, int gated) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = *ref_n;
   const int f = blockIdx.x / nblk, j0 = (blockIdx.x % nblk) * kInvCols;
   if (j0 >= n) return;
+  if (gated && !(ref_flags[f] & kRefRedone)) return;
   const int tid = threadIdx.x;
   double2* W = reinterpret_cast<double2*>(smem);                                  // n x 4
   double2* D = reinterpret_cast<double2*>(smem + static_cast<size_t>(n) * kInvCols * sizeof(double2));   // 32 x 33
@@ -75,6 +83,105 @@ ref_inv_kernel(const double2* __restrict__ LU, int ldn, const int* __restrict__ 
   for (int e = tid; e < n * kInvCols; e += kThreads) {
     const int i = e / kInvCols, c = e % kInvCols;
     if (j0 + c < n) Gf[static_cast<size_t>(i) * ldn + j0 + c] = W[e];
+  }
+}
+
+// Reference inverse from the single-precision factors kept by the factor-only evaluation launch
+// (workspace slot f: LU, pivots and the exact complex64 copy of Z_sub), four columns per task:
+// X = LU^-1 e_j, then iterative refinement with the float-float residual e_j - Z_sub X until the
+// normwise backward error reaches kEtaTarget.  Columns whose refinement stalls mark their
+// frequency kRefFailed; the gated FP64 kernels then recompute that frequency.
+__global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_red[2 * kWarps], s_norm[2];
+  __shared__ int s_task, s_flag;
+  const int n = *r.ref_n, ldn = r.ldn, lda = r.lda;
+  const int nblk = (n + kInvCols - 1) / kInvCols, ntasks = r.F * nblk;
+  const int tid = gtid();
+  float2* W = reinterpret_cast<float2*>(smem);                                   // n x 4, aliases xf
+  float4* xf = reinterpret_cast<float4*>(smem);                                  // n x 4
+  double2* Rv = reinterpret_cast<double2*>(smem + static_cast<size_t>(n) * kInvCols * sizeof(float4));
+  float2* D = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(double2)));
+  const Slot sl = slot_layout(r.ncap, lda, r.P, sizeof(float2));
+  double lone[kMaxPorts] = {1.0, 1.0, 1.0, 1.0};
+  for (;;) {
+    if (tid == 0) {
+      const int tt = atomicAdd(r.task_counter, 1);
+      s_task = tt;
+      // a frequency whose factorization or another column block failed is left to the FP64
+      // fallback (read once: other CTAs may set the flag meanwhile)
+      s_flag = tt < ntasks ? static_cast<int>(r.ref_flags[tt / nblk] & (kRefSingular | kRefFailed)) : 0;
+    }
+    gsync();
+    const int t = s_task, skip = s_flag;
+    gsync();
+    if (t >= ntasks) break;
+    const int f = t / nblk, j0 = (t % nblk) * kInvCols;
+    if (skip) continue;
+    const unsigned char* ws = static_cast<const unsigned char*>(r.work) + r.slot_bytes * f;
+    const float2* A = reinterpret_cast<const float2*>(ws + sl.a_off);
+    const float2* Zs = reinterpret_cast<const float2*>(ws + sl.zs_off);
+    const int* piv = reinterpret_cast<const int*>(ws + sl.piv_off);
+    double2* X = r.G + static_cast<size_t>(f) * n * ldn;   // columns j0..j0+3 of G hold x (ldn >= j0 + 4)
+    for (int e = tid; e < n * kInvCols; e += kThreads) {
+      const int i = e / kInvCols, c = e % kInvCols;
+      W[e] = make_float2(i == j0 + c ? 1.f : 0.f, 0.f);
+    }
+    gsync();
+    lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
+    for (int e = tid; e < n * kInvCols; e += kThreads) {
+      const int i = e / kInvCols, c = e % kInvCols;
+      X[static_cast<size_t>(i) * ldn + j0 + c] = to_d2(W[e]);
+    }
+    gsync();
+    bool converged = false;
+    double rprev = 0.0;
+    for (int it = 0; it <= kMaxRefine; ++it) {
+      double xmax = 0.0;
+      for (int e = tid; e < n * kInvCols; e += kThreads) {
+        const int i = e / kInvCols, c = e % kInvCols;
+        const double2 v = X[static_cast<size_t>(i) * ldn + j0 + c];
+        const float hx = static_cast<float>(v.x), hy = static_cast<float>(v.y);
+        xf[e] = make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
+        xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
+      }
+      gsync();
+      residual_df<kInvCols>(Zs, lda, n, xf, kInvCols, lone, Rv, s_red, s_norm, j0);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
+      if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
+      gsync();
+      if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
+        const double rn = s_norm[0], zn = s_norm[1];
+        const double eta = rn / (zn * m + 1.0);
+        int flag = 0;
+        if (eta <= kEtaTarget) flag = 1;
+        else if (it > 0 && rn > 0.5 * rprev) flag = 2;
+        else if (it == kMaxRefine) flag = 2;
+        s_flag = flag;
+        s_norm[0] = rn;
+      }
+      gsync();
+      const int flag = s_flag;
+      rprev = s_norm[0];
+      if (flag != 0) {
+        converged = flag == 1;
+        break;
+      }
+      for (int e = tid; e < n * kInvCols; e += kThreads) W[e] = make_float2(static_cast<float>(Rv[e].x), static_cast<float>(Rv[e].y));
+      gsync();
+      lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
+      for (int e = tid; e < n * kInvCols; e += kThreads) {
+        const int i = e / kInvCols, c = e % kInvCols;
+        double2& x = X[static_cast<size_t>(i) * ldn + j0 + c];
+        const double2 d = to_d2(W[e]);
+        x = make_double2(x.x + d.x, x.y + d.y);
+      }
+      gsync();
+    }
+    if (!converged && tid == 0) atomicOr(&r.ref_flags[f], kRefFailed);
   }
 }
 
@@ -123,7 +230,10 @@ __device__ bool small_solve(double2* Am, int k, double2* Bm, int nr, int ldb) {
 
 // SMEM_B: the added columns B = Z(f)[S, Ad] are staged in shared memory (q-major, so the lanes of
 // a warp read consecutive rows); otherwise they stay in the slot's global scratch.
-template <typename ZT, bool SMEM_B>
+// DF (complex64 databases only): W = G B in float-float arithmetic on the FP32 pipe -- B's
+// entries are exact floats and each G entry is split into two floats -- instead of FP64 (the
+// FP64 pipe runs at 1/64 of the FP32 rate); partial sums carry about 2^-44 relative error.
+template <typename ZT, bool SMEM_B, bool DF>
 __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task, s_kr, s_ka, s_bad;
@@ -134,12 +244,14 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
   __shared__ double2 s_C[kBK * kBK], s_D[kBK * kBK];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = a.M, P = a.P, n = *a.ref_n, ldn = a.ldn;
-  double2* s_B = reinterpret_cast<double2*>(smem);   // kBK x n (SMEM_B)
-  int32_t* s_ref = reinterpret_cast<int32_t*>(smem + (SMEM_B ? static_cast<size_t>(kBK) * n * sizeof(double2) : 0));
+  static_assert(!DF || std::is_same<ZT, float2>::value, "float-float W needs exact float database entries");
+  using BT = typename std::conditional<DF, float2, double2>::type;
+  BT* s_B = reinterpret_cast<BT*>(smem);   // kBK x n (SMEM_B)
+  int32_t* s_ref = reinterpret_cast<int32_t*>(smem + (SMEM_B ? static_cast<size_t>(kBK) * n * sizeof(BT) : 0));
   for (int i = tid; i < n; i += kThreads) s_ref[i] = a.ref_idx[i];
   const int NQ = kMaxPorts + kBK;
   double2* ws = a.work + a.slot_elems * blockIdx.x;
-  double2* Bm = SMEM_B ? s_B : ws;                    // kBK x n : Z(f)[S, Ad], column q of B is row q
+  BT* Bm = SMEM_B ? s_B : reinterpret_cast<BT*>(ws);  // kBK x n : Z(f)[S, Ad], column q of B is row q
   double2* Wm = ws + static_cast<size_t>(n) * kBK;     // n x kBK : G B
   double2* Em = Wm + static_cast<size_t>(n) * kBK;     // kBK x n : Z(f)[Ad, S]
   double2* Qm = Em + static_cast<size_t>(kBK) * n;     // n x NQ  : [H V_T | H B_T] rows over T (0 on R)
@@ -156,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
     double2* Y = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
     const int N = a.n_act[b];
     const double2 nan2 = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
-    if (N <= 0 || a.ref_flags[f]) {   // bad pixel state (flagged by the activation) or singular reference
+    if (N <= 0 || (a.ref_flags[f] & kRefSingular)) {   // bad pixel state (flagged by the activation) or singular reference
       if (tid < P * P) Y[tid] = nan2;
       if (tid == 0 && N > 0) atomicOr(&a.flags[b], kFlagSingular);
       __syncthreads();
@@ -207,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
     // additions: B = Z(f)[S, Ad], E = Z(f)[Ad, S], D = Z(f)[Ad, Ad]
     for (int e = tid; e < n * ka; e += kThreads) {
       const int j = e / ka, q = e % ka;
-      Bm[static_cast<size_t>(q) * n + j] = zload<ZT, double2>(Zf + static_cast<size_t>(s_ref[j]) * M + s_A[q]);
+      Bm[static_cast<size_t>(q) * n + j] = zload<ZT, BT>(Zf + static_cast<size_t>(s_ref[j]) * M + s_A[q]);
     }
     for (int e = tid; e < ka * n; e += kThreads) {
       const int q = e / n, j = e % n;
@@ -218,39 +330,77 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
       s_D[q * kBK + r] = zload<ZT, double2>(Zf + static_cast<size_t>(s_A[q]) * M + s_A[r]);
     }
     __syncthreads();
-    // W = G B: one warp per row of G, lanes over the columns, two column steps in flight
+    // W = G B: one warp per row of G, lanes over the columns
     if (ka > 0) {
-      for (int i = warp; i < n; i += kWarps) {
-        double2 acc[kBK];
+      if constexpr (DF) {
+        for (int i = warp; i < n; i += kWarps) {
+          float rh[kBK], rl[kBK], ih[kBK], il[kBK];
 #pragma unroll
-        for (int q = 0; q < kBK; ++q) acc[q] = make_double2(0.0, 0.0);
-        const double2* grow = Gf + static_cast<size_t>(i) * ldn;
-        int j = lane;
-        for (; j + 32 < n; j += 64) {
-          const double2 g0 = grow[j], g1 = grow[j + 32];
+          for (int q = 0; q < kBK; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+          const double2* grow = Gf + static_cast<size_t>(i) * ldn;
+          for (int j = lane; j < n; j += 32) {
+            const double2 g = grow[j];
+            const float gxh = static_cast<float>(g.x), gyh = static_cast<float>(g.y);
+            const float gxl = static_cast<float>(g.x - gxh), gyl = static_cast<float>(g.y - gyh);
 #pragma unroll
-          for (int q = 0; q < kBK; ++q)
-            if (q < ka) {
-              acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
-              acc[q] = cfma(g1, Bm[static_cast<size_t>(q) * n + j + 32], acc[q]);
-            }
-        }
-        if (j < n) {
-          const double2 g0 = grow[j];
-#pragma unroll
-          for (int q = 0; q < kBK; ++q)
-            if (q < ka) acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < kBK; ++q) {
-          if (q >= ka) break;
-          double2 v = acc[q];
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            v.x += __shfl_down_sync(0xffffffffu, v.x, d);
-            v.y += __shfl_down_sync(0xffffffffu, v.y, d);
+            for (int q = 0; q < kBK; ++q)
+              if (q < ka) {
+                const float2 bq = Bm[static_cast<size_t>(q) * n + j];
+                df_mac(bq.x, gxh, gxl, rh[q], rl[q]);
+                df_mac(-bq.y, gyh, gyl, rh[q], rl[q]);
+                df_mac(bq.y, gxh, gxl, ih[q], il[q]);
+                df_mac(bq.x, gyh, gyl, ih[q], il[q]);
+              }
           }
-          if (lane == 0) Wm[static_cast<size_t>(i) * kBK + q] = v;
+#pragma unroll
+          for (int q = 0; q < kBK; ++q) {
+            if (q >= ka) break;
+            float xh = rh[q], xl = rl[q], yh = ih[q], yl = il[q];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+              const float oxh = __shfl_down_sync(0xffffffffu, xh, d), oxl = __shfl_down_sync(0xffffffffu, xl, d);
+              const float oyh = __shfl_down_sync(0xffffffffu, yh, d), oyl = __shfl_down_sync(0xffffffffu, yl, d);
+              dd_add(xh, xl, oxh, oxl);
+              dd_add(yh, yl, oyh, oyl);
+            }
+            if (lane == 0)
+              Wm[static_cast<size_t>(i) * kBK + q] =
+                  make_double2(static_cast<double>(xh) + static_cast<double>(xl), static_cast<double>(yh) + static_cast<double>(yl));
+          }
+        }
+      } else {
+        for (int i = warp; i < n; i += kWarps) {
+          double2 acc[kBK];
+#pragma unroll
+          for (int q = 0; q < kBK; ++q) acc[q] = make_double2(0.0, 0.0);
+          const double2* grow = Gf + static_cast<size_t>(i) * ldn;
+          int j = lane;
+          for (; j + 32 < n; j += 64) {   // two column steps in flight
+            const double2 g0 = grow[j], g1 = grow[j + 32];
+#pragma unroll
+            for (int q = 0; q < kBK; ++q)
+              if (q < ka) {
+                acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
+                acc[q] = cfma(g1, Bm[static_cast<size_t>(q) * n + j + 32], acc[q]);
+              }
+          }
+          if (j < n) {
+            const double2 g0 = grow[j];
+#pragma unroll
+            for (int q = 0; q < kBK; ++q)
+              if (q < ka) acc[q] = cfma(g0, Bm[static_cast<size_t>(q) * n + j], acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < kBK; ++q) {
+            if (q >= ka) break;
+            double2 v = acc[q];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+              v.x += __shfl_down_sync(0xffffffffu, v.x, d);
+              v.y += __shfl_down_sync(0xffffffffu, v.y, d);
+            }
+            if (lane == 0) Wm[static_cast<size_t>(i) * kBK + q] = v;
+          }
         }
       }
     }
@@ -350,35 +500,61 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
 
 template <typename ZT, int NB>
 cudaError_t launch_ref_lu_t(const void* Z, int M, const int32_t* ref_idx, const int32_t* ref_n, int n, int F,
-                            double2* LU, int ldn, int* piv, uint32_t* ref_flags, cudaStream_t s) {
+                            double2* LU, int ldn, int* piv, uint32_t* ref_flags, int gated, cudaStream_t s) {
   size_t u_off, idx_off, tc_off;
   const size_t smem = smem_layout<double2>(n, 0, NB != Cfg<double2>::NB, &u_off, &idx_off, &tc_off);
   auto k = ref_lu_kernel<ZT, NB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k<<<F, kThreads, smem, s>>>(static_cast<const ZT*>(Z), M, ref_idx, ref_n, LU, ldn, piv, ref_flags);
+  k<<<F, kThreads, smem, s>>>(static_cast<const ZT*>(Z), M, ref_idx, ref_n, LU, ldn, piv, ref_flags, gated);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_ref_factor(const void* Z, int z_c128, int M, const int32_t* ref_idx, const int32_t* ref_n, int n,
-                              int F, double2* LU, int ldn, int* piv, uint32_t* ref_flags, cudaStream_t s) {
+                              int F, double2* LU, int ldn, int* piv, uint32_t* ref_flags, int gated, cudaStream_t s) {
   const bool large = needs_large_layout<double2>(n, false);
   if (z_c128)
-    return large ? launch_ref_lu_t<double2, Cfg<double2>::NBL>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, s)
-                 : launch_ref_lu_t<double2, Cfg<double2>::NB>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, s);
-  return large ? launch_ref_lu_t<float2, Cfg<double2>::NBL>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, s)
-               : launch_ref_lu_t<float2, Cfg<double2>::NB>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, s);
+    return large ? launch_ref_lu_t<double2, Cfg<double2>::NBL>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, gated, s)
+                 : launch_ref_lu_t<double2, Cfg<double2>::NB>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, gated, s);
+  return large ? launch_ref_lu_t<float2, Cfg<double2>::NBL>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, gated, s)
+               : launch_ref_lu_t<float2, Cfg<double2>::NB>(Z, M, ref_idx, ref_n, n, F, LU, ldn, piv, ref_flags, gated, s);
 }
 
 cudaError_t launch_ref_inverse(const double2* LU, int ldn, const int* piv, const int32_t* ref_n, int n, int F,
-                               double2* G, cudaStream_t s) {
+                               double2* G, const uint32_t* ref_flags, int gated, cudaStream_t s) {
   const int nblk = (n + kInvCols - 1) / kInvCols;
   const size_t smem = static_cast<size_t>(n) * kInvCols * sizeof(double2) + 32 * 33 * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(ref_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  ref_inv_kernel<<<F * nblk, kThreads, smem, s>>>(LU, ldn, piv, ref_n, nblk, G);
+  ref_inv_kernel<<<F * nblk, kThreads, smem, s>>>(LU, ldn, piv, ref_n, nblk, G, ref_flags, gated);
+  return cudaGetLastError();
+}
+
+size_t ref_inverse_mixed_smem(int n) {
+  return static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(double2)) + 32 * 33 * sizeof(float2);
+}
+
+bool ref_inverse_mixed_fits(int n) { return ref_inverse_mixed_smem(n) + 4096 <= static_cast<size_t>(optin_smem()); }
+
+int ref_inverse_mixed_slots(int num_sms, int n) {
+  const size_t smem = ref_inverse_mixed_smem(n);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(ref_inv_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ref_inv_mixed_kernel, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * num_sms;
+}
+
+cudaError_t launch_ref_inverse_mixed(const RefInvArgs& r, int nslots, int n, cudaStream_t s) {
+  const size_t smem = ref_inverse_mixed_smem(n);
+  cudaError_t e = cudaFuncSetAttribute(ref_inv_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  ref_inv_mixed_kernel<<<nslots, kThreads, smem, s>>>(r);
   return cudaGetLastError();
 }
 
@@ -387,15 +563,16 @@ size_t border_slot_elems(int n) {
 }
 
 namespace {
-size_t border_smem(int n, bool smem_b) {
-  return static_cast<size_t>(n) * sizeof(int32_t) + (smem_b ? static_cast<size_t>(kBK) * n * sizeof(double2) : 0);
+size_t border_smem(int n, bool smem_b, bool df) {
+  return static_cast<size_t>(n) * sizeof(int32_t) +
+         (smem_b ? static_cast<size_t>(kBK) * n * (df ? sizeof(float2) : sizeof(double2)) : 0);
 }
-bool border_smem_b(int n) { return border_smem(n, true) + 16384 <= static_cast<size_t>(optin_smem()); }
+bool border_smem_b(int n, bool df) { return border_smem(n, true, df) + 16384 <= static_cast<size_t>(optin_smem()); }
 
-template <typename ZT, bool SMEM_B>
+template <typename ZT, bool SMEM_B, bool DF>
 int border_slots_t(int num_sms, int n) {
-  const size_t smem = border_smem(n, SMEM_B);
-  auto k = border_kernel<ZT, SMEM_B>;
+  const size_t smem = border_smem(n, SMEM_B, DF);
+  auto k = border_kernel<ZT, SMEM_B, DF>;
   int per_sm = 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
@@ -403,10 +580,10 @@ int border_slots_t(int num_sms, int n) {
   return per_sm * num_sms;
 }
 
-template <typename ZT, bool SMEM_B>
+template <typename ZT, bool SMEM_B, bool DF>
 cudaError_t launch_border_t(const BorderArgs& a, int nslots, int n, cudaStream_t s) {
-  const size_t smem = border_smem(n, SMEM_B);
-  auto k = border_kernel<ZT, SMEM_B>;
+  const size_t smem = border_smem(n, SMEM_B, DF);
+  auto k = border_kernel<ZT, SMEM_B, DF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k<<<nslots, kThreads, smem, s>>>(a);
@@ -414,14 +591,22 @@ cudaError_t launch_border_t(const BorderArgs& a, int nslots, int n, cudaStream_t
 }
 }  // namespace
 
-int border_slots(int num_sms, int n) {
-  return border_smem_b(n) ? border_slots_t<float2, true>(num_sms, n) : border_slots_t<float2, false>(num_sms, n);
+int border_slots(int num_sms, int n, int z_c128, int df) {
+  const bool d = df && !z_c128;
+  if (d) return border_smem_b(n, true) ? border_slots_t<float2, true, true>(num_sms, n) : border_slots_t<float2, false, true>(num_sms, n);
+  return border_smem_b(n, false) ? border_slots_t<float2, true, false>(num_sms, n) : border_slots_t<float2, false, false>(num_sms, n);
 }
 
-cudaError_t launch_border(const BorderArgs& a, int nslots, int n, cudaStream_t s) {
-  const bool sb = border_smem_b(n);
-  if (a.z_c128) return sb ? launch_border_t<double2, true>(a, nslots, n, s) : launch_border_t<double2, false>(a, nslots, n, s);
-  return sb ? launch_border_t<float2, true>(a, nslots, n, s) : launch_border_t<float2, false>(a, nslots, n, s);
+cudaError_t launch_border(const BorderArgs& a, int nslots, int n, int df, cudaStream_t s) {
+  if (a.z_c128) {
+    return border_smem_b(n, false) ? launch_border_t<double2, true, false>(a, nslots, n, s)
+                                   : launch_border_t<double2, false, false>(a, nslots, n, s);
+  }
+  if (df)
+    return border_smem_b(n, true) ? launch_border_t<float2, true, true>(a, nslots, n, s)
+                                  : launch_border_t<float2, false, true>(a, nslots, n, s);
+  return border_smem_b(n, false) ? launch_border_t<float2, true, false>(a, nslots, n, s)
+                                 : launch_border_t<float2, false, false>(a, nslots, n, s);
 }
 
 }  // namespace pmom

@@ -715,9 +715,11 @@ __device__ __forceinline__ void dd_add(float& ah, float& al, float bh, float bl)
 // partial sums), lane partials combined across the warp in float-float too, so the FP64 pipe
 // (1/64 of the FP32 rate) only sees one conversion per output.  xs: x split as
 // (re_hi, re_lo, im_hi, im_lo).  NP: compile-time bound on the port count P.
+// V: the port excitation V[3p+1][p] = l_p when e0 < 0, else the identity columns V[e0+p][p] = 1.
 template <int NP>
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
-                            const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
+                            const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
+                            int e0 = -1) {
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
@@ -777,7 +779,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
         if (lane == 0 && i < N) {
           const double vx = static_cast<double>(xh) + static_cast<double>(xl);
           const double vy = static_cast<double>(yh) + static_cast<double>(yl);
-          const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
+          const double vv = e0 < 0 ? ((i == 3 * p + 1) ? lport[p] : 0.0) : ((i == e0 + p) ? 1.0 : 0.0);
           const double2 ri = make_double2(vv - vx, -vy);
           r[i * P + p] = ri;
           rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
@@ -1031,15 +1033,6 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   const int P = a.P, M = a.M, lda = a.lda;
   const Slot sl = slot_layout(a.ncap, lda, P, sizeof(CT));
   const int slot = blockIdx.x * ngroups + g;
-  unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * slot;
-  CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
-  float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
-  int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
-  double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
-  double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
-  // right-hand sides / corrections (W), the x cache of the residual, the solve's diagonal block
-  unsigned char* vec = LARGE ? ws + sl.wx_off : smem;
-  CT* W = reinterpret_cast<CT*>(vec);
   CT* Dg = LARGE ? Pn : Ut;
   const ZT* Zall = static_cast<const ZT*>(a.Z);
   const int ntasks = a.ntasks_list ? *a.repair_count : a.B * a.F;
@@ -1057,14 +1050,27 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     const int t = a.ntasks_list ? a.repair_list[tq] : tq;
     const int f = t / a.B, b = a.order ? a.order[t % a.B] : t % a.B;
     const int N = a.n_act[b];
-    double2* Sout = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
+    // the task's workspace: the group's slot, or (factor-only launches) slot t, which keeps the
+    // factors for a later kernel
+    unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * (a.factor_only ? t : slot);
+    CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
+    float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
+    int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
+    double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
+    double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
+    // right-hand sides / corrections (W), the x cache of the residual
+    unsigned char* vec = LARGE ? ws + sl.wx_off : smem;
+    CT* W = reinterpret_cast<CT*>(vec);
+    uint32_t* flag_of = &a.flags[a.factor_only ? t : b];
     if (N <= 0 || N > a.ncap) {
       // bad pixel states, or a support set larger than the shared memory this launch was sized
       // for (a graph captured with a smaller capacity): no solve, NaN S, flagged candidate
-      if (tid < P * P) Sout[tid] = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
-      if (tid == 0 && N > a.ncap) atomicOr(&a.flags[b], kFlagCapacity);
+      if (!a.factor_only && tid < P * P)
+        a.S[(static_cast<size_t>(b) * a.F + f) * P * P + tid] = make_double2(__longlong_as_double(0x7ff8000000000000ll), 0.0);
+      if (tid == 0 && N > a.ncap) atomicOr(flag_of, kFlagCapacity);
       continue;
     }
+    double2* Sout = a.S + (static_cast<size_t>(b) * a.F + f) * P * P;
     const ZT* Zf = Zall + static_cast<size_t>(f) * M * M;
     const int32_t* gidx = a.idx + static_cast<size_t>(b) * M;
     for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
@@ -1083,6 +1089,12 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     }
     gsync();
     const bool singular = lu_factor<CT, NB>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
+    if (a.factor_only) {   // factors stay in slot t; a zero pivot or a failed tensor-core wait is flagged
+      if (tid == 0 && (singular || tcs.failed)) atomicOr(flag_of, kFlagSingular);
+      tcs.failed = false;
+      gsync();
+      continue;
+    }
     // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
     for (int e = tid; e < N * P; e += kThreads) {
       const int i = e / P, p = e % P;

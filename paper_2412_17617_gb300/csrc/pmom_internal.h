@@ -55,6 +55,7 @@ struct EvalArgs {
   int ncap;                // largest N of the batch (sizes the shared-memory panel); <= M
   int* n_max;              // activation writes max N here (atomicMax)
   int use_tc;              // single-precision LU: trailing updates on the tensor cores (tcgen05)
+  int factor_only;         // 1: task t factors into workspace slot t (kept) and ends after the LU
   const int* order;        // [B] candidates in task order (largest support set first), or null
   int nslots;              // workspace slots of this launch (set by the launcher)
 };
@@ -84,13 +85,29 @@ struct BorderArgs {
   double2* work;              // per-slot scratch
   size_t slot_elems;
 };
+// FP64 reference factorization and inverse; gated = 1: only the frequencies whose single-precision
+// reference failed (the fallback after launch_ref_inverse_mixed).
 cudaError_t launch_ref_factor(const void* Z, int z_c128, int M, const int32_t* ref_idx, const int32_t* ref_n, int n,
-                              int F, double2* LU, int ldn, int* piv, uint32_t* ref_flags, cudaStream_t s);
+                              int F, double2* LU, int ldn, int* piv, uint32_t* ref_flags, int gated, cudaStream_t s);
 cudaError_t launch_ref_inverse(const double2* LU, int ldn, const int* piv, const int32_t* ref_n, int n, int F,
-                               double2* G, cudaStream_t s);
+                               double2* G, const uint32_t* ref_flags, int gated, cudaStream_t s);
+// Refined reference inverse from single-precision factors kept in evaluation workspace slot f.
+struct RefInvArgs {
+  int F, P, ncap, lda, ldn;
+  const int32_t* ref_n;
+  const void* work;
+  size_t slot_bytes;
+  double2* G;
+  uint32_t* ref_flags;
+  int* task_counter;
+};
+bool ref_inverse_mixed_fits(int n);
+int ref_inverse_mixed_slots(int num_sms, int n);
+cudaError_t launch_ref_inverse_mixed(const RefInvArgs& r, int nslots, int n, cudaStream_t s);
 size_t border_slot_elems(int n);
-int border_slots(int num_sms, int n);
-cudaError_t launch_border(const BorderArgs& a, int nslots, int n, cudaStream_t s);
+// df = 1: W = G B in float-float arithmetic (complex64 databases; ignored for complex128)
+int border_slots(int num_sms, int n, int z_c128, int df);
+cudaError_t launch_border(const BorderArgs& a, int nslots, int n, int df, cudaStream_t s);
 
 // Launchers (pmom_eval.cu).
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);

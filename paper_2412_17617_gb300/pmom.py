@@ -83,7 +83,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
         "pmom_set_tensor_cores": [V, I32],
         "pmom_capacity": [V, I32, P, P],
-        "pmom_eval_bordered": [V, P, P, I32, P, P, P, V],
+        "pmom_eval_bordered": [V, P, P, I32, I32, P, P, P, V],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
@@ -242,7 +242,8 @@ class Evaluator:
             ctypes.c_void_p(fom.data_ptr()), ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
 
-    def eval_bordered(self, reference_map, maps, want_S: bool = True, out=None, stream=None):
+    def eval_bordered(self, reference_map, maps, precision: str = "mixed", want_S: bool = True, out=None,
+                      stream=None):
         """Bordered low-rank evaluation of `maps` (torch CUDA uint8 [B][layers][ny][nx]) against the
         torch CUDA uint8 `reference_map` [layers][ny][nx]; same outputs as eval().  Candidates that
         remove or add more than BORDER_K basis functions report CAND_FAR."""
@@ -255,8 +256,9 @@ class Evaluator:
         else:
             S, fom, status = out
         self._last_kind = "bordered"
+        prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED
         self._check(self.L.pmom_eval_bordered(
-            self.h, ctypes.c_void_p(reference_map.data_ptr()), ctypes.c_void_p(maps.data_ptr()), B,
+            self.h, ctypes.c_void_p(reference_map.data_ptr()), ctypes.c_void_p(maps.data_ptr()), B, prec,
             ctypes.c_void_p(S.data_ptr() if S is not None else 0), ctypes.c_void_p(fom.data_ptr()),
             ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return S, fom, status
