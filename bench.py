@@ -223,6 +223,7 @@ def run_ours(args):
     # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
     nfp = min(Bsz, 32)
     sub = maps[:nfp]
+    S_mixed, fom_mixed = S[:nfp].clone(), fom[:nfp].clone()
     sub_out = (S[:nfp], fom[:nfp], status[:nfp])
     ev.eval(sub, "fp64", out=sub_out)
     barrier()
@@ -232,6 +233,38 @@ def run_ours(args):
     barrier()
     fp64_ms = e0.elapsed_time(e1)
     fp64_value = world * nfp / (fp64_ms * 1e-3)
+    S_ref64, fom_ref64 = S[:nfp].clone(), fom[:nfp].clone()
+
+    def accuracy(Sx, fx):
+        return {"max_abs_dS_vs_fp64": float((Sx - S_ref64).abs().max().item()),
+                "max_rel_fom_vs_fp64": float(((fx - fom_ref64).abs() / fom_ref64.abs()).max().item()),
+                "candidates": nfp}
+    # ---- bordered update of the same batch (every candidate is one pixel change of the seed map):
+    #      reference factors and inverse per frequency, k x k updates per candidate, recomputed
+    #      every step
+    bordered = None
+    if args.bordered:
+        seed_d = torch.from_numpy(PI.seed_map(w.grid, w.fill, rank)).cuda()
+        Sb, fb, sb = torch.empty_like(S), torch.empty_like(fom), torch.empty_like(status)
+        for _ in range(args.warmup):
+            ev.eval_bordered(seed_d, maps, "mixed", out=(Sb, fb, sb))
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ev.eval_bordered(seed_d, maps, "mixed", out=(Sb, fb, sb))
+        e1.record(stream)
+        barrier()
+        b_ms = e0.elapsed_time(e1) / args.steps
+        ev.set_timing(True)
+        ev.eval_bordered(seed_d, maps, "mixed", out=(Sb, fb, sb))
+        phases = {k: float(v) for k, v in ev.kernel_times().items()}
+        ev.set_timing(False)
+        torch.cuda.synchronize()
+        bordered = {"value": world * Bsz / (b_ms * 1e-3), "unit": "candidate evals/s", "ms_per_step": b_ms,
+                    "precision": "mixed (tensor-core reference LU, float-float refined inverse)",
+                    "speedup_over_full_solve": (world * Bsz / (b_ms * 1e-3)) / value,
+                    "status_ok": int((sb == 0).sum().item()), "phases_ms": phases,
+                    "accuracy": accuracy(Sb[:nfp], fb[:nfp])}
     # ---- end to end through the host-buffer entry point (pinned host memory)
     maps_h = torch.from_numpy(maps_np).pin_memory()
     S_h = torch.empty((Bsz, w.n_freq, ev.P, ev.P), dtype=torch.complex128).pin_memory()
@@ -274,6 +307,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (Z database 0.72 GB)", "parallelism": f"replicas x{world}"},
         "fp64_path": {"value": fp64_value, "unit": "candidate evals/s", "candidates": nfp,
                       "speedup_mixed_over_fp64": value / fp64_value},
+        "accuracy": accuracy(S_mixed, fom_mixed),
+        "bordered_update": bordered,
         "refinement": {"iters_total": st["refine_iters"], "iters_max": st["refine_max"],
                        "repaired_tasks": st["repaired_tasks"], "tasks": st["tasks"],
                        "bad_status": int((status_np != 0).sum())},
@@ -305,6 +340,8 @@ def main():
                     help="profile: a smaller grid running the same kernels, for counter captures")
     ap.add_argument("--batch", type=int, default=0, help="evaluate only the first B candidates")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-bordered", dest="bordered", action="store_false",
+                    help="skip the bordered-update measurement of the same batch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -503,6 +503,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
                                          c->d_ref_flags, 1, s));
     PMOM_CUDA(c, pmom::launch_ref_inverse(c->d_ref_lu, ldn, c->d_ref_piv, d_ref_n, n, F, c->d_ref_g, c->d_ref_flags,
                                           1, s));
+    PMOM_CUDA(c, pmom::launch_ref_g_to_df(c->d_ref_g, d_ref_n, ldn, c->d_ref_flags, F, s));
   } else {
     // per frequency: FP64 LU of the reference (a4) and its inverse (a5, n right-hand sides)
     PMOM_CUDA(c, pmom::launch_ref_factor(c->d_Z, c->dtype == PMOM_C128, M, c->d_ref_idx, d_ref_n, n, F, c->d_ref_lu,
@@ -543,7 +544,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   PMOM_CUDA(c, pmom::launch_ys(Sd, B, F, P, c->Z0, c->d_flags, s));
   PMOM_CUDA(c, pmom::launch_fom(Sd, c->d_bands, F, P, B, c->d_flags, c->d_nact, fom_out, status, s));
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[4], s));
-  c->launches = mixed ? 10 : 7;
+  c->launches = mixed ? 11 : 7;
   return PMOM_OK;
 }
 

@@ -24,6 +24,12 @@ namespace pmom {
 namespace {
 
 constexpr int kBK = kBorderK;   // BFs removed / added per candidate at most
+// The reference inverse is refined further than a candidate's port solutions: the bordered
+// formulas subtract quantities of the reference's size to get a candidate's, so the inverse's
+// error reaches the candidate's S relative to the reference's (for a candidate with |S21| of
+// 1e-5 against a reference with 0.1, four orders of magnitude).  Refinement goes on until the
+// backward error reaches kEtaInverse or stops improving; it is accepted at kEtaTarget.
+constexpr double kEtaInverse = 1e-14;
 constexpr int kInvCols = 4;     // inverse columns per CTA (the solve's right-hand-side width)
 
 // Reference-state bits per frequency: kRefSingular (the reference matrix has a zero pivot),
@@ -84,6 +90,11 @@ ref_inv_kernel(const double2* __restrict__ LU, int ldn, const int* __restrict__ 
     const int i = e / kInvCols, c = e % kInvCols;
     if (j0 + c < n) Gf[static_cast<size_t>(i) * ldn + j0 + c] = W[e];
   }
+}
+
+__device__ __forceinline__ float4 split_df(double2 v) {
+  const float hx = static_cast<float>(v.x), hy = static_cast<float>(v.y);
+  return make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
 }
 
 // Reference inverse from the single-precision factors kept by the factor-only evaluation launch
@@ -157,9 +168,8 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
         const double rn = s_norm[0], zn = s_norm[1];
         const double eta = rn / (zn * m + 1.0);
         int flag = 0;
-        if (eta <= kEtaTarget) flag = 1;
-        else if (it > 0 && rn > 0.5 * rprev) flag = 2;
-        else if (it == kMaxRefine) flag = 2;
+        if (eta <= kEtaInverse) flag = 1;
+        else if ((it > 0 && rn > 0.5 * rprev) || it == kMaxRefine) flag = eta <= kEtaTarget ? 1 : 2;
         s_flag = flag;
         s_norm[0] = rn;
       }
@@ -181,8 +191,30 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
       }
       gsync();
     }
-    if (!converged && tid == 0) atomicOr(&r.ref_flags[f], kRefFailed);
+    if (!converged) {
+      if (tid == 0) atomicOr(&r.ref_flags[f], kRefFailed);
+    } else {   // the bordered update reads G as float-float pairs (no FP64 conversions in its loop)
+      for (int e = tid; e < n * kInvCols; e += kThreads) {
+        const int i = e / kInvCols, c = e % kInvCols;
+        double2* x = &X[static_cast<size_t>(i) * ldn + j0 + c];
+        *reinterpret_cast<float4*>(x) = split_df(*x);
+      }
+    }
   }
+}
+
+// The FP64 fallback writes G(f) as doubles; the float-float route converts the frequencies it
+// redid in place.
+__global__ void ref_g_to_df_kernel(double2* __restrict__ G, const int32_t* __restrict__ ref_n, int ldn,
+                                   const uint32_t* __restrict__ ref_flags) {
+  const int f = blockIdx.y;
+  if (!(ref_flags[f] & kRefRedone)) return;
+  const int n = *ref_n;
+  double2* Gf = G + static_cast<size_t>(f) * n * ldn;
+  const size_t total = static_cast<size_t>(n) * ldn;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x)
+    *reinterpret_cast<float4*>(&Gf[e]) = split_df(Gf[e]);
 }
 
 __device__ __forceinline__ bool in_sorted(const int32_t* a, int n, int v) {
@@ -305,16 +337,27 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
         for (int j = i; j > 0 && s_A[j - 1] > s_A[j]; --j) { const int x = s_A[j]; s_A[j] = s_A[j - 1]; s_A[j - 1] = x; }
     }
     __syncthreads();
-    const double2* Gf = a.G + static_cast<size_t>(f) * n * ldn;
+    // G(f): double2, or (DF) float-float pairs (re_hi, re_lo, im_hi, im_lo) read back as doubles
+    const double2* Gf = static_cast<const double2*>(a.G) + static_cast<size_t>(f) * n * ldn;
+    const float4* Gq = static_cast<const float4*>(a.G) + static_cast<size_t>(f) * n * ldn;
+    auto gv = [&](size_t off) -> double2 {
+      if constexpr (DF) {
+        const float4 v = Gq[off];
+        return make_double2(static_cast<double>(v.x) + static_cast<double>(v.y),
+                            static_cast<double>(v.z) + static_cast<double>(v.w));
+      } else {
+        return Gf[off];
+      }
+    };
     const ZT* Zf = static_cast<const ZT*>(a.Z) + static_cast<size_t>(f) * M * M;
     // small blocks of G: G_RR, G[ports, R], and the right-hand sides [Xs[R] | W[R]] come later
     for (int e = tid; e < kr * kr; e += kThreads) {
       const int r = e / kr, q = e % kr;
-      s_GRR[r * kBK + q] = Gf[static_cast<size_t>(s_R[r]) * ldn + s_R[q]];
+      s_GRR[r * kBK + q] = gv(static_cast<size_t>(s_R[r]) * ldn + s_R[q]);
     }
     for (int e = tid; e < P * kr; e += kThreads) {
       const int p = e / kr, r = e % kr;
-      s_GpR[p * kBK + r] = Gf[static_cast<size_t>(3 * p + 1) * ldn + s_R[r]];
+      s_GpR[p * kBK + r] = gv(static_cast<size_t>(3 * p + 1) * ldn + s_R[r]);
     }
     // additions: B = Z(f)[S, Ad], E = Z(f)[Ad, S], D = Z(f)[Ad, Ad]
     for (int e = tid; e < n * ka; e += kThreads) {
@@ -337,11 +380,10 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
           float rh[kBK], rl[kBK], ih[kBK], il[kBK];
 #pragma unroll
           for (int q = 0; q < kBK; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
-          const double2* grow = Gf + static_cast<size_t>(i) * ldn;
+          const float4* grow = Gq + static_cast<size_t>(i) * ldn;
           for (int j = lane; j < n; j += 32) {
-            const double2 g = grow[j];
-            const float gxh = static_cast<float>(g.x), gyh = static_cast<float>(g.y);
-            const float gxl = static_cast<float>(g.x - gxh), gyl = static_cast<float>(g.y - gyh);
+            const float4 g = grow[j];
+            const float gxh = g.x, gxl = g.y, gyh = g.z, gyl = g.w;
 #pragma unroll
             for (int q = 0; q < kBK; ++q)
               if (q < ka) {
@@ -411,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
       for (int r = 0; r < kr; ++r) {
         const size_t row = static_cast<size_t>(s_R[r]) * ldn;
         for (int p = 0; p < P; ++p) {
-          const double2 g = Gf[row + 3 * p + 1];
+          const double2 g = gv(row + 3 * p + 1);
           s_Z[r * NQ + p] = make_double2(g.x * lp[p], g.y * lp[p]);
         }
         for (int q = 0; q < ka; ++q) s_Z[r * NQ + kMaxPorts + q] = Wm[static_cast<size_t>(s_R[r]) * kBK + q];
@@ -421,7 +463,7 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
       for (int p = 0; p < P; ++p) {
         const size_t row = static_cast<size_t>(3 * p + 1) * ldn;
         for (int q = 0; q < P; ++q) {
-          const double2 g = Gf[row + 3 * q + 1];
+          const double2 g = gv(row + 3 * q + 1);
           double2 v = make_double2(g.x * lp[q], g.y * lp[q]);
           for (int r = 0; r < kr; ++r) v = cfms(s_GpR[p * kBK + r], s_Z[r * NQ + q], v);
           s_HVp[p * kMaxPorts + q] = v;
@@ -445,12 +487,12 @@ __global__ void __launch_bounds__(kThreads) border_kernel(BorderArgs a) {
         if (!inR) {
           const size_t row = static_cast<size_t>(i) * ldn;
           if (c < P) {
-            const double2 g = Gf[row + 3 * c + 1];
+            const double2 g = gv(row + 3 * c + 1);
             v = make_double2(g.x * lp[c], g.y * lp[c]);
           } else {
             v = Wm[static_cast<size_t>(i) * kBK + (c - P)];
           }
-          for (int r = 0; r < kr; ++r) v = cfms(Gf[row + s_R[r]], s_Z[r * NQ + q], v);
+          for (int r = 0; r < kr; ++r) v = cfms(gv(row + s_R[r]), s_Z[r * NQ + q], v);
         }
         Qm[static_cast<size_t>(i) * NQ + q] = v;
       }
@@ -529,6 +571,12 @@ cudaError_t launch_ref_inverse(const double2* LU, int ldn, const int* piv, const
   cudaError_t e = cudaFuncSetAttribute(ref_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   ref_inv_kernel<<<F * nblk, kThreads, smem, s>>>(LU, ldn, piv, ref_n, nblk, G, ref_flags, gated);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_g_to_df(double2* G, const int32_t* ref_n, int ldn, const uint32_t* ref_flags, int F,
+                               cudaStream_t s) {
+  ref_g_to_df_kernel<<<dim3(64, F), 256, 0, s>>>(G, ref_n, ldn, ref_flags);
   return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ struct BorderArgs {
   const int32_t* ref_idx;     // [n] reference support set (ascending)
   const int32_t* ref_n;       // n (device)
   const uint32_t* ref_flags;  // [F] 1: the reference matrix is singular at f
-  const double2* G;           // [F][n][ldn] reference inverses (FP64)
+  const void* G;              // [F][n][ldn] reference inverses: double2, or float-float float4 (df route)
   int ldn;
   const int32_t* idx;         // [B][M] candidates' support sets
   const int32_t* n_act;       // [B]
@@ -104,6 +104,9 @@ struct RefInvArgs {
 bool ref_inverse_mixed_fits(int n);
 int ref_inverse_mixed_slots(int num_sms, int n);
 cudaError_t launch_ref_inverse_mixed(const RefInvArgs& r, int nslots, int n, cudaStream_t s);
+// In place double2 -> float-float (float4) for the frequencies the FP64 fallback redid.
+cudaError_t launch_ref_g_to_df(double2* G, const int32_t* ref_n, int ldn, const uint32_t* ref_flags, int F,
+                               cudaStream_t s);
 size_t border_slot_elems(int n);
 // df = 1: W = G B in float-float arithmetic (complex64 databases; ignored for complex128)
 int border_slots(int num_sms, int n, int z_c128, int df);
