@@ -225,6 +225,48 @@ pmom_status pmom_eval_bordered(pmom_ctx* ctx, const uint8_t* reference_map_dev, 
                                int32_t precision, double* S_out_dev, double* fom_out_dev, int32_t* status_dev,
                                void* stream);
 
+/* ---- Learned pre-ranker (a multilayer perceptron trained on the evaluator's own outputs) ----
+ * The search step of Algorithm 1 evaluates every child of a node; the pre-ranker predicts each
+ * child's |S| in dB from its pixel map so that only the best-ranked children get an exact
+ * evaluation (the exact solver stays the arbiter of every accepted change).  The paper has no
+ * learned component; this follows the search's candidate structure (Section III-A).
+ * Network: layer l maps h_l (B x dims[l]) to h_l W_l^T + b_l (W_l: dims[l+1] x dims[l]),
+ * ReLU on all but the last layer; input = the map's pixel states as 0/1; BF16 weights and
+ * activations, FP32 accumulation (tensor cores, tcgen05 kind::f16), FP32 master weights, Adam.
+ * Parameters are one flat FP32 vector [W_0, b_0, W_1, b_1, ...] (W row-major). */
+typedef struct pmom_mlp pmom_mlp;
+/* dims: n_layers + 1 sizes (input first); initial weights He-uniform from SplitMix64(seed),
+ * biases 0.  Needs the GPU.  Errors: INVALID_ARG, OOM, CUDA. */
+pmom_status pmom_mlp_create(int32_t n_layers, const int32_t* dims, uint64_t seed, pmom_mlp** out);
+pmom_status pmom_mlp_destroy(pmom_mlp* net);
+const char* pmom_mlp_last_error(const pmom_mlp* net);
+pmom_status pmom_mlp_num_params(const pmom_mlp* net, int64_t* count);
+/* Copy the FP32 parameters and/or the last gradients to host float [count] (either may be NULL;
+ * synchronizes the device). */
+pmom_status pmom_mlp_get_params(pmom_mlp* net, float* params_host, float* grads_host);
+/* Replace the parameters (host float [count]); resets the Adam state. */
+pmom_status pmom_mlp_set_params(pmom_mlp* net, const float* params_host);
+/* y_dev (device float [B][dims[L]]) = network(x_dev), x_dev device uint8 [B][dims[0]]. */
+pmom_status pmom_mlp_forward(pmom_mlp* net, const uint8_t* x_dev, int32_t B, float* y_dev, void* stream);
+/* Gradients of the mean squared error against target_dev (device float [B][dims[L]]) into the
+ * network's gradient buffer; loss_host (optional) receives the loss (synchronizes). */
+pmom_status pmom_mlp_backward(pmom_mlp* net, const uint8_t* x_dev, const float* target_dev, int32_t B,
+                              double* loss_host, void* stream);
+/* One Adam step with the last gradients. */
+pmom_status pmom_mlp_adam(pmom_mlp* net, float lr, float beta1, float beta2, float eps, void* stream);
+/* Predicted FoM (Eq. 8-9) of each map: the network's outputs are read as dB of S11, S21, S31, S32
+ * (output q * F + f, times out_scale) and scored with band codes (device uint8 [F], as for
+ * pmom_set_fom); fom_dev device double [B].  Needs dims[L] == 4 F. */
+pmom_status pmom_mlp_predict_fom(pmom_mlp* net, const uint8_t* x_dev, int32_t B, const uint8_t* bands_dev,
+                                 int32_t F, float out_scale, double* fom_dev, void* stream);
+/* Training targets from evaluated S (device double [B][F][P][P][2], P = 3 or 4, as written by
+ * pmom_eval_candidates): target_dev[b][q * F + f] = out_scale * dB(S_q(f)) for q = S11, S21,
+ * S31, S32 (the entries the FoM of Eq. 8-9 reads), dB = 20 log10(max(|S|, 1e-15)). */
+pmom_status pmom_mlp_targets(const double* S_dev, int32_t B, int32_t F, int32_t P, float out_scale,
+                             float* target_dev, void* stream);
+/* Tensor-core completion waits that ran out since creation (their GEMM tiles were skipped). */
+pmom_status pmom_mlp_errors(pmom_mlp* net, int32_t* timeouts);
+
 /* Support-set capacity of one task on this GPU for `precision` (PMOM_FP64 or
  * PMOM_MIXED_REFINED): *n_default = the largest N the default shared-memory layout holds (wide
  * panels, solve vectors in shared memory, up to two tasks per SM); *n_max = the largest N any

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpmom.so")
-SOURCES = ["pmom_api.cu", "pmom_eval.cu", "pmom_eval_large.cu", "pmom_border.cu", "pmom_fill.cu", "pmom_mesh.cpp", "pmom_search.cpp"]
+SOURCES = ["pmom_api.cu", "pmom_eval.cu", "pmom_eval_large.cu", "pmom_border.cu", "pmom_mlp.cu", "pmom_fill.cu", "pmom_mesh.cpp", "pmom_search.cpp"]
 PUBLIC_HEADER = os.path.join(os.path.dirname(HERE), "include", "pmom.h")
 HEADERS = [os.path.join(CSRC, h) for h in ("pmom_internal.h", "pmom_eval_kernels.cuh", "pmom_tc.cuh")] + [PUBLIC_HEADER]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -28,7 +28,10 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
            "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_capacity", "pmom_graph_capture", "pmom_graph_launch",
-           "pmom_autotune", "pmom_search", "pmom_eval_bordered")
+           "pmom_autotune", "pmom_search", "pmom_eval_bordered",
+           "pmom_mlp_create", "pmom_mlp_destroy", "pmom_mlp_last_error", "pmom_mlp_num_params", "pmom_mlp_get_params",
+           "pmom_mlp_set_params", "pmom_mlp_forward", "pmom_mlp_backward", "pmom_mlp_adam", "pmom_mlp_predict_fom",
+           "pmom_mlp_targets", "pmom_mlp_errors")
 
 
 class PmomError(RuntimeError):
@@ -88,12 +91,25 @@ def load_library(path: str = LIB_PATH):
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
         "pmom_search": [V, P, P, P, P, P, P, I32, P, V],
+        "pmom_mlp_create": [I32, P, ctypes.c_uint64, P],
+        "pmom_mlp_destroy": [V],
+        "pmom_mlp_num_params": [V, P],
+        "pmom_mlp_get_params": [V, P, P],
+        "pmom_mlp_set_params": [V, P],
+        "pmom_mlp_forward": [V, P, I32, P, V],
+        "pmom_mlp_backward": [V, P, P, I32, P, V],
+        "pmom_mlp_adam": [V, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, V],
+        "pmom_mlp_predict_fom": [V, P, I32, P, I32, ctypes.c_float, P, V],
+        "pmom_mlp_targets": [P, I32, I32, I32, ctypes.c_float, P, V],
+        "pmom_mlp_errors": [V, P],
+        "pmom_mlp_last_error": [V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int32
     L.pmom_last_error.restype = ctypes.c_char_p
+    L.pmom_mlp_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
