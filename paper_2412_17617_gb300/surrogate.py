@@ -149,3 +149,48 @@ def preranked_step(ev, net: MLP, bands_dev, parent, children, k: int, precision:
     f = np.where(status.cpu().numpy() == 0, f, np.inf)
     j = int(np.argmin(f))
     return int(top[j]), float(f[j]), top
+
+
+def walk(ev, start: np.ndarray, budget: int, pick, tabu_len: int = 16, precision: str = "mixed"):
+    """Best-neighbour walk over single-pixel flips with a budget of exact evaluations.  Each step
+    `pick(parent_dev, children_dev, tabu)` returns the indices of the children to evaluate exactly
+    (all of them for the exhaustive walk, the top-k for the pre-ranked one); the walk moves to
+    the best evaluated child (bordered update against the parent's factors) and keeps the flipped
+    pixels of the last `tabu_len` moves out of reach, so that it does not undo them.  Returns the
+    best exact FoM seen and the number of exact evaluations used."""
+    import torch
+    cur = np.ascontiguousarray(start)
+    best, used, tabu = np.inf, 0, []
+    while used < budget:
+        kids = np.ascontiguousarray(_flips(cur))
+        dk = torch.from_numpy(kids).cuda()
+        parent = torch.from_numpy(cur).cuda()
+        sel = np.asarray(pick(parent, dk, tabu))
+        sub = dk[torch.from_numpy(sel).cuda()].contiguous()
+        _, fom, status = ev.eval_bordered(parent, sub, precision, want_S=False)
+        f = fom.cpu().numpy()
+        f = np.where(status.cpu().numpy() == 0, f, np.inf)
+        jj = int(np.argmin(f))
+        used += len(sel)
+        best = min(best, float(f[jj]))
+        cur = kids[int(sel[jj])]
+        tabu = (tabu + [int(sel[jj])])[-tabu_len:]
+    return best, used
+
+
+def _flips(m: np.ndarray) -> np.ndarray:
+    """Every single-pixel change of a two-state map, pixel-major (child i flips pixel i)."""
+    L, ny, nx = m.shape
+    flat = np.repeat(m.reshape(1, -1), L * ny * nx, axis=0)
+    idx = np.arange(L * ny * nx)
+    flat[idx, idx] ^= 1
+    return flat.reshape(-1, L, ny, nx)
+
+
+def pick_top(net: MLP, bands_dev, F: int, k: int):
+    """Selection rule of the pre-ranked walk: the k children with the lowest predicted FoM."""
+    def pick(parent, children, tabu):
+        pred = net.predict_fom(children.reshape(children.shape[0], -1), bands_dev, F).cpu().numpy()
+        pred[tabu] = np.inf
+        return np.argsort(pred, kind="stable")[:k]
+    return pick

@@ -120,32 +120,47 @@ def test_targets_are_db_of_the_fom_entries(S, search_case):
         assert np.abs(t[:, q * F:(q + 1) * F] - ref).max() <= 1e-5
 
 
-def test_preranking_beats_random_selection(S, search_case):
-    """Train on the first 11 steps' children, then for the next three steps rank the 512 children
-    and exact-evaluate only the top 32: the best FoM found must beat the expected best of 32
-    children drawn at random (computed exactly from the exhaustive evaluation), on average over
-    the three steps; the exact evaluation of the selected children is the arbiter."""
+def _spearman(a, b):
+    ra, rb = np.argsort(np.argsort(a)), np.argsort(np.argsort(b))
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+@pytest.fixture(scope="module")
+def trained(S, search_case):
+    """The network trained on the first 11 steps' children (5632 exact evaluations)."""
     w, ev, bands, xs, ts, steps = search_case
-    n_train, k = 11, 32
-    X = torch.cat(xs[:n_train]).contiguous()
-    T = torch.cat(ts[:n_train]).contiguous()
-    D = X.shape[1]
-    net = S.MLP([D, 512, 512, 4 * w.n_freq], seed=7)
-    hist = S.train(net, X, T, epochs=40, batch=256, lr=1e-3)
-    assert hist[-1] < 0.5 * hist[0], hist
-    ours, rand = [], []
-    for cur, kids, f in steps[n_train:]:
-        j, fj, top = S.preranked_step(ev, net, bands, torch.from_numpy(cur).cuda(), torch.from_numpy(kids).cuda(), k)
-        assert abs(fj - f[j]) <= 1e-6 * abs(f[j])        # the exact FoM of the chosen child
-        # expected minimum of k of the n children drawn without replacement
-        fs = np.sort(f)
-        n = fs.size
-        from math import comb
-        pr = np.array([comb(n - 1 - i, k - 1) / comb(n, k) for i in range(n)])
-        e_rand = float(np.sum(pr * fs))
-        best = float(fs[0])
-        ours.append((fj - best) / abs(best))
-        rand.append((e_rand - best) / abs(best))
-    print("relative regret: pre-ranked", ours, "random", rand)
-    assert np.mean(ours) < np.mean(rand), (ours, rand)
+    X = torch.cat(xs[:11]).contiguous()
+    T = torch.cat(ts[:11]).contiguous()
+    net = S.MLP([X.shape[1], 1024, 1024, 4 * w.n_freq], seed=7)
+    hist = S.train(net, X, T, epochs=300, batch=256, lr=5e-4)
+    assert hist[-1] < 0.05 * hist[0], hist
+    yield net
     net.close()
+
+
+def test_ranking_follows_exact_fom(S, search_case, trained):
+    """On the children of the three next (held-out) steps, the predicted FoM ranks the children
+    in the order of their exact FoM well above chance (Spearman rank correlation; 0 would be an
+    uninformed ranking)."""
+    w, ev, bands, xs, ts, steps = search_case
+    rho = []
+    for cur, kids, f in steps[11:14]:
+        pred = trained.predict_fom(torch.from_numpy(kids).cuda().reshape(512, -1), bands, w.n_freq).cpu().numpy()
+        rho.append(_spearman(pred, f))
+    print("Spearman rank correlation, predicted vs exact FoM:", rho)
+    assert np.mean(rho) > 0.2, rho
+
+
+def test_preranked_walk_beats_exhaustive_walk_at_equal_budget(S, search_case, trained):
+    """What the network gains over the method without it: from the state the training steps
+    reached, a best-neighbour walk that exact-evaluates only the network's top 32 of the 512
+    children reaches a lower FoM with 2048 exact evaluations than the walk that evaluates every
+    child (four steps).  The exact solver picks every move."""
+    w, ev, bands, xs, ts, steps = search_case
+    start = steps[11][0]
+    budget = 2048
+    f_ex, n_ex = S.walk(ev, start, budget, lambda p, c, tabu: np.setdiff1d(np.arange(c.shape[0]), tabu))
+    f_pr, n_pr = S.walk(ev, start, budget, S.pick_top(trained, bands, w.n_freq, 32))
+    print("best FoM with", budget, "exact evaluations: exhaustive", f_ex, "pre-ranked", f_pr)
+    assert n_ex >= budget and n_pr >= budget
+    assert f_pr < f_ex, (f_pr, f_ex)
