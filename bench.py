@@ -33,6 +33,13 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
+# DRAM bytes (read + write) of one launch of the tensor-core evaluation kernel on the full
+# 512-candidate x 41-frequency stripline batch, from one ncu capture of this build
+# (profiles/eval_kernel_stripline16x16x2_launches.md gives the command); reported only for that
+# kernel on that workload.
+TRAFFIC_PER_LAUNCH = {("stripline_16x16x2_f41_b512", "tc"): 1.17e12 + 550.42e9}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -290,7 +297,8 @@ def run_ours(args):
         bf16 = float(peaks.get("bf16_tflops") or 1900.0)
         peak = bf16 * 1.1 / 2.25
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "eval_kernel<float2,float2,mixed,tc>",
+                "traffic": TRAFFIC_PER_LAUNCH.get((w.name, "tc")) if Bsz == w.batch else None,
+                "kernel": "eval_kernel<float2,float2,mixed,tc>",
                 "peak_source": "measured bf16 %.1f TFLOP/s x 1.1/2.25 (TF32 dense); %s" % (
                     bf16, "of measured" if peaks.get("bf16_tflops") else "of fallback"),
                 "frac_of_3xtf32_peak": achieved / (peak / 3.0), "frac_of_fp32_alu": achieved / alu_peak}
