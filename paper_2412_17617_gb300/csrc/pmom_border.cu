@@ -100,19 +100,22 @@ __device__ __forceinline__ float4 split_df(double2 v) {
 // Reference inverse from the single-precision factors kept by the factor-only evaluation launch
 // (workspace slot f: LU, pivots and the exact complex64 copy of Z_sub), four columns per task:
 // X = LU^-1 e_j, then iterative refinement with the float-float residual e_j - Z_sub X until the
-// normwise backward error reaches kEtaTarget.  Columns whose refinement stalls mark their
-// frequency kRefFailed; the gated FP64 kernels then recompute that frequency.
+// normwise backward error reaches kEtaInverse (or stops improving; accepted at kEtaTarget).  X
+// stays in shared memory as float-float pairs (re_hi, re_lo, im_hi, im_lo): the residual reads it
+// as it is and each float correction is added in float-float, so the refinement does no FP64
+// work, and the converged columns go to G in the same form.  Columns whose refinement stalls mark
+// their frequency kRefFailed; the gated FP64 kernels then recompute that frequency.
 __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_red[2 * kWarps], s_norm[2];
+  __shared__ float s_xmax[kWarps];
   __shared__ int s_task, s_flag;
   const int n = *r.ref_n, ldn = r.ldn, lda = r.lda;
   const int nblk = (n + kInvCols - 1) / kInvCols, ntasks = r.F * nblk;
   const int tid = gtid();
-  float2* W = reinterpret_cast<float2*>(smem);                                   // n x 4, aliases xf
-  float4* xf = reinterpret_cast<float4*>(smem);                                  // n x 4
-  double2* Rv = reinterpret_cast<double2*>(smem + static_cast<size_t>(n) * kInvCols * sizeof(float4));
-  float2* D = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(double2)));
+  float4* X = reinterpret_cast<float4*>(smem);                                                    // n x 4
+  float2* W = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * sizeof(float4));   // n x 4
+  float2* D = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(float2)));
   const Slot sl = slot_layout(r.ncap, lda, r.P, sizeof(float2));
   double lone[kMaxPorts] = {1.0, 1.0, 1.0, 1.0};
   for (;;) {
@@ -133,40 +136,29 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
     const float2* A = reinterpret_cast<const float2*>(ws + sl.a_off);
     const float2* Zs = reinterpret_cast<const float2*>(ws + sl.zs_off);
     const int* piv = reinterpret_cast<const int*>(ws + sl.piv_off);
-    double2* X = r.G + static_cast<size_t>(f) * n * ldn;   // columns j0..j0+3 of G hold x (ldn >= j0 + 4)
     for (int e = tid; e < n * kInvCols; e += kThreads) {
       const int i = e / kInvCols, c = e % kInvCols;
       W[e] = make_float2(i == j0 + c ? 1.f : 0.f, 0.f);
     }
     gsync();
     lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
-    for (int e = tid; e < n * kInvCols; e += kThreads) {
-      const int i = e / kInvCols, c = e % kInvCols;
-      X[static_cast<size_t>(i) * ldn + j0 + c] = to_d2(W[e]);
-    }
+    for (int e = tid; e < n * kInvCols; e += kThreads) X[e] = make_float4(W[e].x, 0.f, W[e].y, 0.f);
     gsync();
     bool converged = false;
     double rprev = 0.0;
     for (int it = 0; it <= kMaxRefine; ++it) {
-      double xmax = 0.0;
-      for (int e = tid; e < n * kInvCols; e += kThreads) {
-        const int i = e / kInvCols, c = e % kInvCols;
-        const double2 v = X[static_cast<size_t>(i) * ldn + j0 + c];
-        const float hx = static_cast<float>(v.x), hy = static_cast<float>(v.y);
-        xf[e] = make_float4(hx, static_cast<float>(v.x - hx), hy, static_cast<float>(v.y - hy));
-        xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
-      }
-      gsync();
-      residual_df<kInvCols>(Zs, lda, n, xf, kInvCols, lone, Rv, s_red, s_norm, j0);
+      float xmax = 0.f;
+      for (int e = tid; e < n * kInvCols; e += kThreads) xmax = fmaxf(xmax, fabsf(X[e].x) + fabsf(X[e].z));
+      residual_df<kInvCols, true>(Zs, lda, n, X, kInvCols, lone, nullptr, s_red, s_norm, j0, W);
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
-      if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
+      for (int d = 16; d > 0; d >>= 1) xmax = fmaxf(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
+      if ((tid & 31) == 0) s_xmax[tid >> 5] = xmax;
       gsync();
       if (tid == 0) {
-        double m = 0.0;
-        for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
+        float m = 0.f;
+        for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_xmax[w]);
         const double rn = s_norm[0], zn = s_norm[1];
-        const double eta = rn / (zn * m + 1.0);
+        const double eta = rn / (zn * static_cast<double>(m) + 1.0);
         int flag = 0;
         if (eta <= kEtaInverse) flag = 1;
         else if ((it > 0 && rn > 0.5 * rprev) || it == kMaxRefine) flag = eta <= kEtaTarget ? 1 : 2;
@@ -180,26 +172,25 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
         converged = flag == 1;
         break;
       }
-      for (int e = tid; e < n * kInvCols; e += kThreads) W[e] = make_float2(static_cast<float>(Rv[e].x), static_cast<float>(Rv[e].y));
-      gsync();
       lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
-      for (int e = tid; e < n * kInvCols; e += kThreads) {
-        const int i = e / kInvCols, c = e % kInvCols;
-        double2& x = X[static_cast<size_t>(i) * ldn + j0 + c];
-        const double2 d = to_d2(W[e]);
-        x = make_double2(x.x + d.x, x.y + d.y);
+      for (int e = tid; e < n * kInvCols; e += kThreads) {   // X += correction, in float-float
+        float4 x = X[e];
+        dd_add(x.x, x.y, W[e].x, 0.f);
+        dd_add(x.z, x.w, W[e].y, 0.f);
+        X[e] = x;
       }
       gsync();
     }
     if (!converged) {
       if (tid == 0) atomicOr(&r.ref_flags[f], kRefFailed);
-    } else {   // the bordered update reads G as float-float pairs (no FP64 conversions in its loop)
+    } else {   // the bordered update reads G as float-float pairs
+      float4* Gq = reinterpret_cast<float4*>(r.G) + static_cast<size_t>(f) * n * ldn;
       for (int e = tid; e < n * kInvCols; e += kThreads) {
         const int i = e / kInvCols, c = e % kInvCols;
-        double2* x = &X[static_cast<size_t>(i) * ldn + j0 + c];
-        *reinterpret_cast<float4*>(x) = split_df(*x);
+        Gq[static_cast<size_t>(i) * ldn + j0 + c] = X[e];
       }
     }
+    gsync();
   }
 }
 
@@ -581,7 +572,7 @@ cudaError_t launch_ref_g_to_df(double2* G, const int32_t* ref_n, int ldn, const 
 }
 
 size_t ref_inverse_mixed_smem(int n) {
-  return static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(double2)) + 32 * 33 * sizeof(float2);
+  return static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(float2)) + 32 * 33 * sizeof(float2);
 }
 
 bool ref_inverse_mixed_fits(int n) { return ref_inverse_mixed_smem(n) + 4096 <= static_cast<size_t>(optin_smem()); }

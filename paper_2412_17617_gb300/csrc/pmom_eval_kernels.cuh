@@ -716,15 +716,18 @@ __device__ __forceinline__ void dd_add(float& ah, float& al, float bh, float bl)
 // (1/64 of the FP32 rate) only sees one conversion per output.  xs: x split as
 // (re_hi, re_lo, im_hi, im_lo).  NP: compile-time bound on the port count P.
 // V: the port excitation V[3p+1][p] = l_p when e0 < 0, else the identity columns V[e0+p][p] = 1.
-template <int NP>
+// F32OUT (identity columns only): the residual is formed in float-float and written rounded to
+// float into rw (the precision of the correction solve that consumes it), with no FP64 work.
+template <int NP, bool F32OUT = false>
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
                             const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
-                            int e0 = -1) {
+                            int e0 = -1, float2* __restrict__ rw = nullptr) {
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
+  float rmaxf = 0.f, zmaxf = 0.f;
   for (int i0 = warp; i0 < N; i0 += kWarps * R) {
     float rh[R][NP], rl[R][NP], ih[R][NP], il[R][NP], ra[R];
 #pragma unroll
@@ -777,16 +780,31 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
           dd_add(yh, yl, oyh, oyl);
         }
         if (lane == 0 && i < N) {
-          const double vx = static_cast<double>(xh) + static_cast<double>(xl);
-          const double vy = static_cast<double>(yh) + static_cast<double>(yl);
-          const double vv = e0 < 0 ? ((i == 3 * p + 1) ? lport[p] : 0.0) : ((i == e0 + p) ? 1.0 : 0.0);
-          const double2 ri = make_double2(vv - vx, -vy);
-          r[i * P + p] = ri;
-          rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
+          if constexpr (F32OUT) {
+            float a = -xh, b = -xl;
+            dd_add(a, b, i == e0 + p ? 1.f : 0.f, 0.f);
+            const float rx = a + b, ry = -(yh + yl);
+            rw[i * P + p] = make_float2(rx, ry);
+            rmaxf = fmaxf(rmaxf, fabsf(rx) + fabsf(ry));
+          } else {
+            const double vx = static_cast<double>(xh) + static_cast<double>(xl);
+            const double vy = static_cast<double>(yh) + static_cast<double>(yl);
+            const double vv = e0 < 0 ? ((i == 3 * p + 1) ? lport[p] : 0.0) : ((i == e0 + p) ? 1.0 : 0.0);
+            const double2 ri = make_double2(vv - vx, -vy);
+            r[i * P + p] = ri;
+            rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
+          }
         }
       }
-      if (lane == 0 && i < N) zmax = fmax(zmax, static_cast<double>(rs));
+      if (lane == 0 && i < N) {
+        if constexpr (F32OUT) zmaxf = fmaxf(zmaxf, rs);
+        else zmax = fmax(zmax, static_cast<double>(rs));
+      }
     }
+  }
+  if constexpr (F32OUT) {
+    rmax = static_cast<double>(rmaxf);
+    zmax = static_cast<double>(zmaxf);
   }
   if (lane == 0) {
     s_red[warp] = rmax;
