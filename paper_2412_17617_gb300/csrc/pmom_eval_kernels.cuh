@@ -41,6 +41,10 @@ constexpr int kMaxRefine = 10;
 // Refinement target on the normwise backward error: reachable by the float-float residual
 // (about 2^-44 per partial sum) and, with cond(Z_sub) ~ 1e4-1e5, far below |dS| = 1e-6.
 constexpr double kEtaTarget = 1e-12;
+// Stop without another residual once the predicted forward error of the corrected x -- this
+// correction times the contraction rate seen over the last two corrections -- is below this
+// fraction of ||x||_inf (the classic correction-norm test of iterative refinement).
+constexpr double kDxTarget = 1e-10;
 
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -1005,6 +1009,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   __shared__ double s_norm_g[kMaxGroups][2];
   __shared__ int s_task_g[kMaxGroups];
   __shared__ int s_flag_g[kMaxGroups];
+  __shared__ double s_dx_g[kMaxGroups][2];   // refinement: last correction norm, ||x||_inf
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups];
   constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
@@ -1016,6 +1021,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   double* s_norm = s_norm_g[g];
   int& s_task = s_task_g[g];
   int& s_flag = s_flag_g[g];
+  double* s_dx = s_dx_g[g];
   size_t u_off, idx_off, tc_off;
   constexpr int NB = LARGE ? Cfg<CT>::NBL : Cfg<CT>::NB;
   const size_t group_bytes = group_smem_bytes<CT>(a.ncap, use_tc, LARGE);
@@ -1157,6 +1163,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
         if (tid == 0) {
           double m = 0.0;
           for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w]);
+          s_dx[1] = m;
           const double rn = s_norm[0], zn = s_norm[1];
           const double eta = rn / (zn * m + vnorm);
           int flag = 0;   // 0 continue, 1 converged, 2 stop (stagnated or out of iterations)
@@ -1176,12 +1183,29 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
         gsync();
         lu_solve<CT>(A, lda, N, piv, W, P, Dg);
+        double dmax = 0.0;   // ||correction||_inf
         for (int e = tid; e < N * P; e += kThreads) {
           const double2 d = to_d2(W[e]);
           X[e] = make_double2(X[e].x + d.x, X[e].y + d.y);
+          dmax = fmax(dmax, fabs(d.x) + fabs(d.y));
         }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
+        if ((tid & 31) == 0) s_red[tid >> 5] = dmax;
         gsync();
         ++iters;
+        if (tid == 0) {
+          double dn = 0.0;
+          for (int w = 0; w < kWarps; ++w) dn = fmax(dn, s_red[w]);
+          const double dprev = s_dx[0];
+          s_flag = (it > 0 && dn < 0.5 * dprev && (dn / dprev) * dn <= kDxTarget * s_dx[1]) ? 1 : 0;
+          s_dx[0] = dn;
+        }
+        gsync();
+        if (s_flag) {
+          converged = true;
+          break;
+        }
       }
       if (!converged) repaired = true;
     }
