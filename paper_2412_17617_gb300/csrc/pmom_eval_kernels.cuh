@@ -28,7 +28,7 @@ constexpr int kWarps = kThreads / 32;
 // The evaluation kernel runs up to two independent task groups of kThreads threads per CTA: a
 // kernel that allocates tensor memory gets one CTA per SM, and two groups keep two tasks in flight
 // per SM (one overlapping the other's latency-bound phases).  Each group synchronises on its own
-// named barrier and owns a shared-memory region, a workspace slot and 128 TMEM columns.
+// named barrier and owns a shared-memory region, a workspace slot and 256 TMEM columns.
 constexpr int kMaxGroups = 2;
 __device__ __forceinline__ int gtid() { return threadIdx.x & (kThreads - 1); }
 __device__ __forceinline__ int group_id() { return threadIdx.x / kThreads; }
@@ -207,8 +207,9 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
 }
 
 // ------------------------------------------------------------------ tensor-core trailing update
-// State of the CTA's tensor-core pipeline: 64 KB operand staging (A_hi | A_lo | B_hi | B_lo, each
-// a 128 x 32 K-major fp32 tile), a 128-column TMEM accumulator and the MMA-completion barrier.
+// State of the task group's tensor-core pipeline: 96 KB operand staging (A_hi | A_lo, each a
+// 128 x 32 K-major fp32 tile, then B_hi | B_lo, each 256 x 32), a 256-column TMEM accumulator and
+// the MMA-completion barrier.
 struct TcState {
   unsigned char* stage;
   uint32_t tmem;
@@ -217,6 +218,8 @@ struct TcState {
   bool failed;
 };
 constexpr long long kTcWaitPolls = 1ll << 26;   // bounded wait; a stall flags the task instead of hanging
+constexpr int kTcCols = 128;                     // complex output columns per tile (MMA N = 256 real)
+constexpr uint32_t kTmemCols = 2 * kTcCols;      // TMEM columns per task group
 
 __device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float v) {
   const float h = tc::to_tf32(v);
@@ -226,12 +229,12 @@ __device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, 
 }
 
 // Outer-panel update A22 -= L21 U12 on the tensor cores, with K = jb <= 64 complex columns taken
-// in chunks of 16.  Per 128 x 64 complex output tile, each chunk is one real GEMM
-// [Lr | Li] (128 x 32) times B (32 x 128), B's first 64 columns being [Ur; -Ui] (real parts of the
-// product) and its last 64 [Ui; Ur] (imaginary parts).  Every fp32 operand is split into two TF32
-// terms (hi + lo) and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32 in
-// TMEM across all chunks, which keeps fp32-level accuracy; the tile is then subtracted from A22
-// once.  L21 = A[rb.., j0..j0+jb), U12 = A[j0..j0+jb, rb..), A22 = A[rb.., rb..], rb = j0 + jb.
+// in chunks of 16.  Per 128 x 128 complex output tile, each chunk is one real GEMM
+// [Lr | Li] (128 x 32) times B (32 x 256), B's first 128 columns being [Ur; -Ui] (real parts of
+// the product) and its last 128 [Ui; Ur] (imaginary parts), i.e. one M = 128, N = 256 MMA shape.
+// Every fp32 operand is split into two TF32 terms (hi + lo) and the three significant products
+// (lo*hi, hi*lo, hi*hi) accumulate in fp32 in TMEM across the chunks (3xTF32).  One thread
+// issues; the completion arrives on an mbarrier that the group waits on with an iteration limit.
 __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int jb, TcState& st) {
   const int tid = gtid(), warp = tid >> 5, lane = tid & 31;
   const int rb = j0 + jb, n2 = N - rb;
@@ -239,18 +242,18 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
   unsigned char* Ah = st.stage;
   unsigned char* Al = st.stage + 16384;
   unsigned char* Bh = st.stage + 32768;
-  unsigned char* Bl = st.stage + 49152;
-  const uint32_t idesc = tc::idesc_tf32(128, 128);
-  for (int c0 = rb; c0 < N; c0 += 64) {
+  unsigned char* Bl = st.stage + 65536;
+  const uint32_t idesc = tc::idesc_tf32(128, 2 * kTcCols);
+  for (int c0 = rb; c0 < N; c0 += kTcCols) {
     for (int r0 = 0; r0 < n2; r0 += 128) {
       for (int kc = 0; kc < nk; ++kc) {
         const int kbase = j0 + 16 * kc, kw = min(16, jb - 16 * kc);
         {
           // all loads first (independent, in flight together), then the split stores
-          float2 u[4], l[8];
+          float2 u[8], l[8];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
+          for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kThreads, t = e >> 7, c = e & 127;
             u[i] = (t < kw && c0 + c < N) ? A[static_cast<size_t>(kbase + t) * lda + c0 + c] : make_float2(0.f, 0.f);
           }
 #pragma unroll
@@ -259,12 +262,12 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
             l[i] = (t < kw && r0 + r < n2) ? A[static_cast<size_t>(rb + r0 + r) * lda + kbase + t] : make_float2(0.f, 0.f);
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * kThreads, t = e >> 6, c = e & 63;
+          for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kThreads, t = e >> 7, c = e & 127;
             put_split(Bh, Bl, c, t, u[i].x);
             put_split(Bh, Bl, c, 16 + t, -u[i].y);
-            put_split(Bh, Bl, 64 + c, t, u[i].y);
-            put_split(Bh, Bl, 64 + c, 16 + t, u[i].x);
+            put_split(Bh, Bl, kTcCols + c, t, u[i].y);
+            put_split(Bh, Bl, kTcCols + c, 16 + t, u[i].x);
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -300,38 +303,43 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
         gsync();
       }
       tc::fence_after_sync();
-      // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update
+      // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update,
+      // 64 complex columns at a time
       float2* T = reinterpret_cast<float2*>(st.stage);
       constexpr int LDT = 65;
-      {
-        const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
-        float re[32], im[32];
-        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * h, re);
-        tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 + 32 * h, im);
+      for (int hc = 0; hc < kTcCols; hc += 64) {
+        {
+          const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
+          float re[32], im[32];
+          tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + hc + 32 * h, re);
+          tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + kTcCols + hc + 32 * h, im);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
-      }
-      tc::fence_before_sync();
-      gsync();
-      // 32 elements per thread in two batches of 16 independent loads, then the stores
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float2 v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
-          v[i] = (r0 + r < n2 && c0 + c < N) ? A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] : make_float2(0.f, 0.f);
+          for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
         }
+        tc::fence_before_sync();
+        gsync();
+        // 32 elements per thread in two batches of 16 independent loads, then the stores
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = e & 63;
-          if (r0 + r < n2 && c0 + c < N) {
-            const float2 d = T[r * LDT + c];
-            A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] = make_float2(v[i].x - d.x, v[i].y - d.y);
+        for (int half = 0; half < 2; ++half) {
+          float2 v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = hc + (e & 63);
+            v[i] = (r0 + r < n2 && c0 + c < N) ? A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = hc + (e & 63);
+            if (r0 + r < n2 && c0 + c < N) {
+              const float2 d = T[r * LDT + (e & 63)];
+              A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] = make_float2(v[i].x - d.x, v[i].y - d.y);
+            }
           }
         }
+        tc::fence_before_sync();
+        gsync();
+        tc::fence_after_sync();
       }
-      gsync();
     }
   }
 }
@@ -959,12 +967,12 @@ __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_byt
 }
 
 // Dynamic shared memory: [union of the panel (M x (NB+1)), the x cache and, for the tensor-core
-// path, the operand staging (64 KB + 2 KB alignment slack) | U tile / diagonal block | idx (M ints)].
+// path, the operand staging (96 KB + 2 KB alignment slack) | U tile / diagonal block | idx (M ints)].
 // The staging is only live during the outer-panel steps, when the panel has been written back, so
 // the two share memory and the tensor-core variant still fits two task groups per SM.
 // Large-support-set variant (`large`): panel of NBL columns; the right-hand sides and the x cache
 // live in the slot's global workspace and the solve's diagonal block in the (then idle) panel.
-constexpr size_t kTcStageBytes = 65536 + 2048;   // 64 KB operands (or the 128 x 65 result tile) + alignment
+constexpr size_t kTcStageBytes = 98304 + 2048;   // 96 KB operands (or the 128 x 65 result tile) + alignment
 
 template <typename CT>
 __host__ __device__ inline size_t smem_layout(int M, int use_tc, bool large, size_t* u_off, size_t* idx_off,
@@ -1041,8 +1049,8 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     // 1024-byte aligned operand staging inside this group's tensor-core region
     const uint32_t base = tc::smem_u32(smem + tc_off);
     tcs.stage = smem + tc_off + ((1024u - (base & 1023u)) & 1023u);
-    if (threadIdx.x < 32) {   // one warp allocates 128 TMEM columns per group for the whole CTA
-      tc::tmem_alloc(&s_tmem, 128u * ngroups);
+    if (threadIdx.x < 32) {   // one warp allocates 256 TMEM columns per group for the whole CTA
+      tc::tmem_alloc(&s_tmem, kTmemCols * ngroups);
       tc::tmem_relinquish();
     }
     if (threadIdx.x == 0) {
@@ -1052,7 +1060,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    tcs.tmem = s_tmem + 128u * g;
+    tcs.tmem = s_tmem + kTmemCols * g;
   }
   const int P = a.P, M = a.M, lda = a.lda;
   const Slot sl = slot_layout(a.ncap, lda, P, sizeof(CT));
@@ -1240,7 +1248,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   if (use_tc) {   // both groups are done with the tensor memory
     tc::fence_before_sync();
     __syncthreads();
-    if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, 128u * ngroups);
+    if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, kTmemCols * ngroups);
   }
 }
 
