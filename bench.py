@@ -164,6 +164,30 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def rank_batch(w, rank: int, batch: int = 0) -> np.ndarray:
+    """The candidates one rank evaluates: every single flip of that rank's own seeded map, so ranks
+    share no data and need no collective on the data path (weak scaling)."""
+    maps = PI.workload_maps(w, seed=rank)
+    if batch > 0:
+        maps = np.ascontiguousarray(maps[:batch])
+    return maps
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time for a step: the slowest rank's (all-reduce MAX of one scalar)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, batch: int, ms: float) -> float:
+    """Whole-job candidate evaluations per second: every rank's batch over the slowest rank's time."""
+    return world * batch / (ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     rank, world, local = _dist()
@@ -180,9 +204,7 @@ def run_ours(args):
     ev.fill_Z(freqs, w.z_dtype)
     ev.set_fom(band_codes(freqs, w.bands), w.z0_ohm)
     # each rank evaluates its own batch (independent candidates): weak scaling, no collective
-    maps_np = PI.workload_maps(w, seed=rank)
-    if args.batch > 0:
-        maps_np = np.ascontiguousarray(maps_np[: args.batch])
+    maps_np = rank_batch(w, rank, args.batch)
     maps = torch.from_numpy(maps_np).cuda()
     Bsz = maps.shape[0]
     idx, n = ev.active_set(maps)
@@ -218,15 +240,11 @@ def run_ours(args):
             ev.graph_launch()
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     clocks = clk.summary()
     st = ev.stats()
     status_np = status.cpu().numpy()
-    value = world * Bsz / (ms * 1e-3)
+    value = aggregate_rate(world, Bsz, ms)
     # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
     nfp = min(Bsz, 32)
     sub = maps[:nfp]
