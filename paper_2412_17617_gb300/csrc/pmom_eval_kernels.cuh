@@ -549,9 +549,16 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
   }
   gsync();
-  // forward: L y = P b, unit diagonal, blocks of 32 rows
+  // forward: L y = P b, unit diagonal, blocks of 32 rows.  The whole group stages each 32 x 32
+  // diagonal block (independent loads, in flight with the off-diagonal products) for warp 0's
+  // triangular solve.
   for (int i0 = 0; i0 < N; i0 += 32) {
     const int bs = min(32, N - i0);
+    for (int e = tid; e < 32 * 32; e += kThreads) {
+      const int r = e >> 5, c = e & 31;
+      D[r * 33 + c] = (r < bs && c < bs) ? A[static_cast<size_t>(i0 + r) * lda + i0 + c] : czero(D[0]);
+    }
+    if (i0 == 0) gsync();
     if (i0 > 0) {
       for (int ii = warp; ii < bs; ii += kWarps) {
         const int i = i0 + ii;
@@ -598,9 +605,6 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (warp == 0) {
       const int i = i0 + lane;
-      for (int r = 0; r < bs; ++r)
-        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
-      __syncwarp();
       CT w[kMaxPorts];
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
@@ -621,6 +625,11 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
   // backward: U x = y, blocks of 32 rows from the bottom
   for (int i1 = N; i1 > 0; i1 -= 32) {
     const int i0 = max(0, i1 - 32), bs = i1 - i0;
+    for (int e = tid; e < 32 * 32; e += kThreads) {
+      const int r = e >> 5, c = e & 31;
+      D[r * 33 + c] = (r < bs && c < bs) ? A[static_cast<size_t>(i0 + r) * lda + i0 + c] : czero(D[0]);
+    }
+    if (i1 == N) gsync();
     if (i1 < N) {
       for (int ii = warp; ii < bs; ii += kWarps) {
         const int i = i0 + ii;
@@ -667,9 +676,6 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (warp == 0) {
       const int i = i0 + lane;
-      for (int r = 0; r < bs; ++r)
-        D[r * 33 + lane] = lane < bs ? A[static_cast<size_t>(i0 + r) * lda + i0 + lane] : czero(D[0]);
-      __syncwarp();
       CT w[kMaxPorts];
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
