@@ -533,6 +533,82 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 // ------------------------------------------------------------------ triangular solves
 // W (shared, N x P) holds the right-hand sides on entry and the solution on exit.
 // D: shared 32 x 33 staging of the current diagonal block (read once, coalesced).
+// W[i] -= sum over t in [tb, te) of A[i][t] W[t] for the rows i0 .. i0 + bs - 1 of a solve
+// block (all P right-hand sides).  Each warp takes RW rows at once, lanes over t, two column
+// steps per iteration: 2 RW independent loads in flight, and each W load serves RW rows.
+template <typename CT>
+__device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda, int i0, int bs, int tb, int te,
+                                               CT* __restrict__ W, int P) {
+  constexpr int RW = sizeof(CT) == sizeof(float2) ? 4 : 2;
+  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
+  for (int ii0 = warp; ii0 < bs; ii0 += kWarps * RW) {
+    CT acc[RW][kMaxPorts];
+    const CT* row[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int ii = ii0 + q * kWarps;
+      row[q] = A + static_cast<size_t>(i0 + (ii < bs ? ii : ii0)) * lda;   // rows past the block reread ii0
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) acc[q][p] = czero(acc[0][0]);
+    }
+    int t = tb + lane;
+    for (; t + 32 < te; t += 64) {
+      CT l0[RW], l1[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) {
+        l0[q] = row[q][t];
+        l1[q] = row[q][t + 32];
+      }
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) {
+        if (p < P) {
+          const CT w0 = W[t * P + p], w1 = W[(t + 32) * P + p];
+#pragma unroll
+          for (int q = 0; q < RW; ++q) {
+            acc[q][p] = cfms(l0[q], w0, acc[q][p]);
+            acc[q][p] = cfms(l1[q], w1, acc[q][p]);
+          }
+        }
+      }
+    }
+    if (t < te) {
+      CT l0[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) l0[q] = row[q][t];
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) {
+        if (p < P) {
+          const CT w0 = W[t * P + p];
+#pragma unroll
+          for (int q = 0; q < RW; ++q) acc[q][p] = cfms(l0[q], w0, acc[q][p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int ii = ii0 + q * kWarps;
+      if (ii >= bs) break;
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) {
+        if (p >= P) break;
+        CT v = acc[q][p];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          const CT o = shfl_c_down(v, d);
+          v.x += o.x;
+          v.y += o.y;
+        }
+        if (lane == 0) {
+          CT w = W[(i0 + ii) * P + p];
+          w.x += v.x;   // acc holds -sum, so adding applies the subtraction
+          w.y += v.y;
+          W[(i0 + ii) * P + p] = w;
+        }
+      }
+    }
+  }
+}
+
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
                          int P, CT* __restrict__ D) {
@@ -560,47 +636,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (i0 == 0) gsync();
     if (i0 > 0) {
-      for (int ii = warp; ii < bs; ii += kWarps) {
-        const int i = i0 + ii;
-        CT acc[kMaxPorts];
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
-        const CT* row = A + static_cast<size_t>(i) * lda;
-        int t = lane;
-        for (; t + 96 < i0; t += 128) {   // four independent loads in flight
-          CT l[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) l[u] = row[t + 32 * u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int p = 0; p < kMaxPorts; ++p)
-              if (p < P) acc[p] = cfms(l[u], W[(t + 32 * u) * P + p], acc[p]);
-        }
-        for (; t < i0; t += 32) {
-          const CT l = row[t];
-#pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p)
-            if (p < P) acc[p] = cfms(l, W[t * P + p], acc[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          if (p >= P) break;
-          CT v = acc[p];
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            const CT o = shfl_c_down(v, d);
-            v.x += o.x;
-            v.y += o.y;
-          }
-          if (lane == 0) {
-            CT w = W[i * P + p];
-            w.x += v.x;   // acc holds -sum, so adding applies the subtraction
-            w.y += v.y;
-            W[i * P + p] = w;
-          }
-        }
-      }
+      offdiag_update<CT>(A, lda, i0, bs, 0, i0, W, P);
       gsync();
     }
     if (warp == 0) {
@@ -631,47 +667,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (i1 == N) gsync();
     if (i1 < N) {
-      for (int ii = warp; ii < bs; ii += kWarps) {
-        const int i = i0 + ii;
-        CT acc[kMaxPorts];
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) acc[p] = czero(acc[0]);
-        const CT* row = A + static_cast<size_t>(i) * lda;
-        int t = i1 + lane;
-        for (; t + 96 < N; t += 128) {   // four independent loads in flight
-          CT uu[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) uu[u] = row[t + 32 * u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int p = 0; p < kMaxPorts; ++p)
-              if (p < P) acc[p] = cfms(uu[u], W[(t + 32 * u) * P + p], acc[p]);
-        }
-        for (; t < N; t += 32) {
-          const CT u = row[t];
-#pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p)
-            if (p < P) acc[p] = cfms(u, W[t * P + p], acc[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          if (p >= P) break;
-          CT v = acc[p];
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            const CT o = shfl_c_down(v, d);
-            v.x += o.x;
-            v.y += o.y;
-          }
-          if (lane == 0) {
-            CT w = W[i * P + p];
-            w.x += v.x;
-            w.y += v.y;
-            W[i * P + p] = w;
-          }
-        }
-      }
+      offdiag_update<CT>(A, lda, i0, bs, i1, N, W, P);
       gsync();
     }
     if (warp == 0) {
