@@ -422,10 +422,17 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       const bool zero = cabs2(d) == R(0);
       if (zero) singular = true;
       const CT inv = zero ? czero(d) : cinv(d);
+      // pivot row in registers; the column loop unrolled over the panel width so that the
+      // shared-memory loads of one row are in flight together
+      CT prow[NB];
+#pragma unroll
+      for (int c = 1; c < NB; ++c) prow[c] = (j + c < kb) ? Pn[j * LDP + j + c] : czero(d);
       for (int r = j + 1 + tid; r < nr; r += kThreads) {
         const CT l = cmul(Pn[r * LDP + j], inv);
         Pn[r * LDP + j] = l;
-        for (int c = j + 1; c < kb; ++c) Pn[r * LDP + c] = cfms(l, Pn[j * LDP + c], Pn[r * LDP + c]);
+#pragma unroll
+        for (int c = 1; c < NB; ++c)
+          if (j + c < kb) Pn[r * LDP + j + c] = cfms(l, prow[c], Pn[r * LDP + j + c]);
       }
       gsync();
     }
