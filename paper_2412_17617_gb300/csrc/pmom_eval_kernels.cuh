@@ -396,10 +396,19 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
     const int kb = min(NB, N - k0);
     const int nr = N - k0;
     if (tcs != nullptr && k0 % kOuter == 0) cend = min(N, k0 + kOuter);
-    // 1. panel -> shared memory
-    for (int e = tid; e < nr * NB; e += kThreads) {
-      const int r = e / NB, c = e % NB;
-      if (c < kb) Pn[r * LDP + c] = A[static_cast<size_t>(k0 + r) * lda + k0 + c];
+    // 1. panel -> shared memory (eight independent loads in flight per thread)
+    for (int e0 = tid; e0 < nr * NB; e0 += 8 * kThreads) {
+      CT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kThreads, r = e / NB, c = e % NB;
+        v[u] = (e < nr * NB && c < kb) ? A[static_cast<size_t>(k0 + r) * lda + k0 + c] : czero(v[0]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kThreads, r = e / NB, c = e % NB;
+        if (e < nr * NB && c < kb) Pn[r * LDP + c] = v[u];
+      }
     }
     gsync();
     // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row)
@@ -1117,15 +1126,23 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
     gsync();
     // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
+    // (eight independent loads in flight per thread, then the stores)
     constexpr bool kZsCopy = MIXED && std::is_same<ZT, float2>::value;
-    for (int i = 0; i < N; ++i) {
-      const ZT* zrow = Zf + static_cast<size_t>(s_idx[i]) * M;
-      CT* arow = A + static_cast<size_t>(i) * lda;
-      float2* zsrow = Zs + static_cast<size_t>(i) * lda;
-      for (int j = tid; j < N; j += kThreads) {
-        const CT v = zload<ZT, CT>(zrow + s_idx[j]);
-        arow[j] = v;
-        if constexpr (kZsCopy) zsrow[j] = v;
+    const int NN = N * N;
+    for (int e0 = tid; e0 < NN; e0 += 8 * kThreads) {
+      CT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
+        v[u] = e < NN ? zload<ZT, CT>(Zf + static_cast<size_t>(s_idx[i]) * M + s_idx[j]) : czero(v[0]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
+        if (e < NN) {
+          A[static_cast<size_t>(i) * lda + j] = v[u];
+          if constexpr (kZsCopy) Zs[static_cast<size_t>(i) * lda + j] = make_float2(static_cast<float>(v[u].x), static_cast<float>(v[u].y));
+        }
       }
     }
     gsync();
