@@ -194,16 +194,17 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
   }
   if (lane == 0) { s_val[warp] = v; s_row[warp] = row; }
   gsync();
-  if (gtid() == 0) {
-    R bv = s_val[0];
-    int br = s_row[0];
-    for (int w = 1; w < kWarps; ++w) {
-      if (s_val[w] > bv || (s_val[w] == bv && s_row[w] >= 0 && (br < 0 || s_row[w] < br))) { bv = s_val[w]; br = s_row[w]; }
-    }
-    s_row[kWarps] = br;
+  // every warp reduces the per-warp results itself (butterfly over groups of kWarps lanes): one
+  // barrier per argmax; the callers' next barrier precedes any reuse of s_val / s_row
+  R bv = s_val[lane & (kWarps - 1)];
+  int br = s_row[lane & (kWarps - 1)];
+#pragma unroll
+  for (int d = kWarps / 2; d > 0; d >>= 1) {
+    const R ov = __shfl_xor_sync(0xffffffffu, bv, d);
+    const int orow = __shfl_xor_sync(0xffffffffu, br, d);
+    if (ov > bv || (ov == bv && orow >= 0 && (br < 0 || orow < br))) { bv = ov; br = orow; }
   }
-  gsync();
-  return s_row[kWarps];
+  return br;
 }
 
 // ------------------------------------------------------------------ tensor-core trailing update
