@@ -250,21 +250,26 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
       for (int kc = 0; kc < nk; ++kc) {
         const int kbase = j0 + 16 * kc, kw = min(16, jb - 16 * kc);
         {
-          // all loads first (independent, in flight together), then the split stores
+          // all loads first (independent, in flight together), then the split stores.  Each warp
+          // covers whole core matrices (8 operand rows x 4 K values): lane = 4 (row % 8) + k % 4,
+          // so its shared-memory stores are conflict-free and its loads still use full sectors.
           float2 u[8], l[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, t = e >> 7, c = e & 127;
+            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
+            const int t = (w >> 4) * 4 + (ln & 3), c = (w & 15) * 8 + (ln >> 2);
             u[i] = (t < kw && c0 + c < N) ? A[static_cast<size_t>(kbase + t) * lda + c0 + c] : make_float2(0.f, 0.f);
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
+            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
+            const int t = (w & 3) * 4 + (ln & 3), r = (w >> 2) * 8 + (ln >> 2);
             l[i] = (t < kw && r0 + r < n2) ? A[static_cast<size_t>(rb + r0 + r) * lda + kbase + t] : make_float2(0.f, 0.f);
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, t = e >> 7, c = e & 127;
+            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
+            const int t = (w >> 4) * 4 + (ln & 3), c = (w & 15) * 8 + (ln >> 2);
             put_split(Bh, Bl, c, t, u[i].x);
             put_split(Bh, Bl, c, 16 + t, -u[i].y);
             put_split(Bh, Bl, kTcCols + c, t, u[i].y);
@@ -272,7 +277,8 @@ __device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int 
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, r = e >> 4, t = e & 15;
+            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
+            const int t = (w & 3) * 4 + (ln & 3), r = (w >> 2) * 8 + (ln >> 2);
             put_split(Ah, Al, r, t, l[i].x);
             put_split(Ah, Al, r, 16 + t, l[i].y);
           }
