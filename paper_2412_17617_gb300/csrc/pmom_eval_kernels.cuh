@@ -779,10 +779,17 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
       const int i = i0 + q * kWarps;
       zrow[q] = Zs + static_cast<size_t>(i < N ? i : 0) * lda;
     }
+    // the next column step's entries are loaded while this one's are used (one step of prefetch)
+    float2 zn[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) zn[q] = (i0 + q * kWarps < N && lane < N) ? zrow[q][lane] : make_float2(0.f, 0.f);
     for (int t = lane; t < N; t += 32) {
       float2 z[R];
 #pragma unroll
-      for (int q = 0; q < R; ++q) z[q] = (i0 + q * kWarps < N) ? zrow[q][t] : make_float2(0.f, 0.f);
+      for (int q = 0; q < R; ++q) {
+        z[q] = zn[q];
+        zn[q] = (i0 + q * kWarps < N && t + 32 < N) ? zrow[q][t + 32] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (p < P) {
