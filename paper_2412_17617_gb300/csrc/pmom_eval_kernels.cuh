@@ -367,10 +367,14 @@ __device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int j
       float2 u[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) u[i] = i < rw ? A[static_cast<size_t>(j0 + 16 * ch + i) * lda + c] : make_float2(0.f, 0.f);
-      for (int t = 0; t < 16 * ch; ++t) {   // contributions of the rows already solved
-        const float2 y = A[static_cast<size_t>(j0 + t) * lda + c];
+      for (int t = 0; t < 16 * ch; t += 4) {   // contributions of the rows already solved, four at a time
+        float2 y[4];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) u[i] = cfms(Ls[(16 * ch + i) * LDL + t], y, u[i]);
+        for (int k = 0; k < 4; ++k) y[k] = A[static_cast<size_t>(j0 + t + k) * lda + c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) u[i] = cfms(Ls[(16 * ch + i) * LDL + t + k], y[k], u[i]);
       }
 #pragma unroll
       for (int i = 1; i < 16; ++i)
