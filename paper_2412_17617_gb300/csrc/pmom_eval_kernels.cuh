@@ -461,21 +461,35 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       const int r = e / NB, c = e % NB;
       if (c < kb) A[static_cast<size_t>(k0 + r) * lda + k0 + c] = Pn[r * LDP + c];
     }
-    // 4. the panel's row interchanges on the columns outside it
+    // 4. the panel's row interchanges on the columns outside it (a barrier only after an actual
+    //    interchange: the pivot is usually the diagonal row); four columns per thread in flight
     for (int j = 0; j < kb; ++j) {
       const int p = piv[k0 + j];
       if (p != k0 + j) {
         CT* ra = A + static_cast<size_t>(k0 + j) * lda;
         CT* rb = A + static_cast<size_t>(p) * lda;
-        for (int c = tid; c < N; c += kThreads) {
-          if (c >= k0 && c < k0 + kb) continue;
-          const CT t = ra[c];
-          ra[c] = rb[c];
-          rb[c] = t;
+        for (int c0 = tid; c0 < N; c0 += 4 * kThreads) {
+          CT va[4], vb[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * kThreads;
+            const bool mv = c < N && (c < k0 || c >= k0 + kb);
+            va[u] = mv ? ra[c] : czero(va[0]);
+            vb[u] = mv ? rb[c] : czero(vb[0]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * kThreads;
+            if (c < N && (c < k0 || c >= k0 + kb)) {
+              ra[c] = vb[u];
+              rb[c] = va[u];
+            }
+          }
         }
+        gsync();
       }
-      gsync();
     }
+    gsync();
     // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory), columns up
     //    to the end of the current outer panel
     for (int c = k0 + kb + tid; c < cend; c += kThreads) {
@@ -500,9 +514,11 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       const int ntile_c = (cend - r_begin + kTile - 1) / kTile;
       for (int tc = 0; tc < ntile_c; ++tc) {
         const int c0 = r_begin + tc * kTile;
-        for (int e = tid; e < NB * kTile; e += kThreads) {
-          const int t = e / kTile, cc = e % kTile;
-          Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
+#pragma unroll
+        for (int e0 = 0; e0 < NB * kTile; e0 += kThreads) {   // compile-time trip count: loads in flight together
+          const int e = e0 + tid, t = e / kTile, cc = e % kTile;
+          if (e < NB * kTile)
+            Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
         }
         gsync();
         for (int tr = 0; tr < ntile; ++tr) {
