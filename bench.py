@@ -37,7 +37,7 @@ SM_MAX_MHZ = 2070.0
 # 512-candidate x 41-frequency stripline batch, from one ncu capture of this build
 # (profiles/eval_kernel_stripline16x16x2_launches.md gives the command); reported only for that
 # kernel on that workload.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {("stripline_16x16x2_f41_b512", "tc"): 1.05e12 + 551.98e9}
 
 
 def _peaks():
