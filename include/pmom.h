@@ -35,7 +35,8 @@ enum {
   PMOM_OK = 0,
   PMOM_ERR_INVALID_ARG = 1,      /* null pointer, size out of range, inconsistent grid */
   PMOM_ERR_OOM = 2,              /* a device allocation failed */
-  PMOM_ERR_BAD_STATE_VALUE = 3,  /* a pixel state >= n_states (reported per candidate as well) */
+  PMOM_ERR_BAD_STATE_VALUE = 3,  /* a pixel state >= n_states, or a via on the last layer (reported per
+                                    candidate as well) */
   PMOM_ERR_Z_SHAPE_MISMATCH = 4, /* Z / frequency / band shapes disagree with the grid */
   PMOM_ERR_CUDA = 5,             /* a CUDA runtime call failed; see pmom_last_error */
   PMOM_ERR_NOT_READY = 6,        /* call order: Z or the FoM bands not loaded yet */
@@ -59,7 +60,7 @@ enum {
   PMOM_CAND_NONFINITE = 2,       /* NaN/Inf in S or FoM */
   PMOM_CAND_REPAIRED = 3,        /* mixed path did not converge at some frequency; that frequency
                                     was re-solved on the FP64 path (results are valid) */
-  PMOM_CAND_BAD_STATE = 5,       /* a pixel state >= n_states; S/FoM not computed */
+  PMOM_CAND_BAD_STATE = 5,       /* a pixel state >= n_states or a via on the last layer; S/FoM not computed */
   PMOM_CAND_CAPACITY = 6,        /* support set larger than a captured graph's capacity; not computed */
   PMOM_CAND_FAR = 7              /* bordered evaluation: more than PMOM_BORDER_K basis functions removed
                                     or added relative to the reference map; not computed */
@@ -79,7 +80,8 @@ typedef struct {
   const double* layer_z_m;     /* [layers], host; heights of the metal layers */
   double h_total_m;            /* stripline plate spacing */
   double eps_r, tan_d;         /* homogenised substrate */
-  int32_t n_states;            /* 2 (void / metal) in this build */
+  int32_t n_states;            /* 2: void / metal; 3: void / metal / metal with a via up to the next
+                                  layer (layers >= 2; the last layer rejects state 2) */
   int32_t n_ports;             /* 1..4 */
   const pmom_port* ports;      /* [n_ports], host */
 } pmom_grid_desc;
@@ -97,11 +99,16 @@ const char* pmom_last_error(const pmom_ctx* ctx);
 pmom_status pmom_num_bfs(const pmom_ctx* ctx, int32_t* M, int32_t* P);
 
 /* BF table, host int32 [M][8]: class (0 always-present, 1 inner-pixel, 2 inter-pixel,
- * 3 pixel-port), pixel A, pixel B, port, key(T+), key(T-), free vertex in T+, free vertex in T-.
- * pixel = (layer*ny + y)*nx + x; key = (((layer*128 + y+4)*128 + x+4)*2 + half), half 0 being the
- * triangle that holds the pixel's lower (-y) side.  Canonical BF order: port stubs (per port: inner
- * stub diagonal, delta-gap edge, outer stub diagonal), then per layer and pixel (row-major):
- * diagonal, +x side, +y side, then one pixel-port BF per port. */
+ * 3 pixel-port, 4 via strip, 5 via junction with its own pixel, 6 via junction with the pixel
+ * above), pixel A, pixel B, port, key(T+), key(T-), free vertex in T+, free vertex in T-.
+ * pixel = (layer*ny + y)*nx + x; key = (((layer*128 + y+4)*128 + x+4)*4 + half), half 0 being the
+ * triangle that holds the pixel's lower (-y) side and halves 2, 3 the two triangles of the via
+ * strip standing on the pixel diagonal (D0, D1 its ends): (D0@l, D1@l, D1@l+1), (D0@l, D1@l+1,
+ * D0@l+1).  Canonical BF order: port stubs (per port: inner stub diagonal, delta-gap edge, outer
+ * stub diagonal), then per layer and pixel (row-major): diagonal, +x side, +y side, then one
+ * pixel-port BF per port, then (three-state grids) per via layer 0..L-2 and pixel: strip, own
+ * junction, upper junction.  A via BF is active when its pixel has state 2 (the upper junction also
+ * needs metal on the pixel above). */
 pmom_status pmom_bf_table(const pmom_ctx* ctx, int32_t* table_host);
 
 /* Load the parent database Z[F][M][M] (row-major; complex interleaved re,im) for F frequencies

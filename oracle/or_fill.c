@@ -2,23 +2,27 @@
  * or_fill.c -- oracle EFIE (MPIE) fill of the parent interaction matrix Z(f).  TEST INFRASTRUCTURE ONLY.
  *
  * Eq. (1)-(2) with RWG functions (Section II-B), Galerkin testing, e^{+jwt} convention:
- *   Z_mn = jw mu  <f_m, G f_n>  +  1/(jw eps) <div f_m, G div' f_n>
+ *   Z_mn = jw mu  <f_m, G_A f_n>  +  1/(jw eps) <div f_m, G_phi div' f_n>
  * with f = s (l / 2A) (r - v_free) and div f = s l / A on T+ (s = +1) and T- (s = -1).
  *
  * Green's function (the paper uses FEKO's layered-media MPIE, Section II-D; that code is not
- * available, so the stack-up is read as a homogeneous dielectric eps_r (1 - j tan d)):
+ * available, so the stack-up is read as a homogeneous dielectric eps_r (1 - j tan d)).  PEC planes
+ * image a horizontal current and a charge with the opposite sign and a vertical current with the
+ * same sign, so G_phi and the horizontal components of the dyadic G_A are the Dirichlet function
+ * G_D of the stack-up and its vertical component is the Neumann function G_N (for a homogeneous
+ * medium between PEC planes this mixed-potential form is exact: dG_N/dz = -dG_D/dz'):
  *   microstrip: one PEC ground at z = 0, homogeneous medium of Hammerstad-Jensen eps_eff at
- *               w = pitch, one negative image:  G = g(R) - g(R_image)
- *   stripline : PEC planes at z = 0 and z = H, dielectric between them.  Horizontal currents and
- *               charges both see the Dirichlet Green's function of the slab, which we evaluate in
- *               two exact representations:
- *                 image series  G = sum_n g(rho, z - z' + 2nH) - g(rho, z + z' + 2nH)
- *                 mode series   G = 1/(pi H) sum_{m>=1} sin(m pi z/H) sin(m pi z'/H) K0(gamma_m rho),
- *                               gamma_m = sqrt((m pi/H)^2 - k^2)
+ *               w = pitch, one image:  G_D = g(R) - g(R_image),  G_N = g(R) + g(R_image)
+ *   stripline : PEC planes at z = 0 and z = H, dielectric between them, in two exact representations:
+ *                 image series  G = sum_n g(rho, z - z' + 2nH) -/+ g(rho, z + z' + 2nH)
+ *                 mode series   G_D = 1/(pi H) sum_{m>=1} sin(m pi z/H) sin(m pi z'/H) K0(gamma_m rho)
+ *                               G_N = 1/(2 pi H) sum_{m>=0} e_m cos(m pi z/H) cos(m pi z'/H) K0(gamma_m rho)
+ *                               gamma_m = sqrt((m pi/H)^2 - k^2), e_0 = 1, e_m = 2
  *               For rho >= H/2 the mode series is summed to round-off.  For rho < H/2 the image
  *               terms |n| <= K are summed explicitly and the remaining images, which are smooth
  *               and even in rho, are represented by c0 + c1 rho^2 + c2 rho^4 matched to the mode
- *               series at rho = H/2, 3H/4, H.
+ *               series at rho = H/2, 3H/4, H, separately for every pair of heights (z, z') that
+ *               the quadrature visits (metal layers, and the points of vertical via triangles).
  *   g(R) = exp(-jkR) / (4 pi R),  k = w sqrt(mu0 eps0 eps_r (1 - j tan d)).
  *
  * Quadrature: Radon's 7-point degree-5 rule on both triangles of a well-separated pair;
@@ -37,7 +41,6 @@
 #define C0 299792458.0
 #define MU0 (4.0e-7 * OR_PI)
 #define EPS0 (1.0 / (MU0 * C0 * C0))
-#define MAXL 8
 #define IMG_K 16
 
 /* ---------------------------------------------------------------- quadrature rules */
@@ -153,11 +156,60 @@ double or_eps_eff(const or_grid* g) {
   return 0.5 * (er + 1.0) + 0.5 * (er - 1.0) * pow(1.0 + 10.0 / u, -a * b);
 }
 
+/* K0(w) for any Re w >= 0, in particular near the imaginary axis (the TEM term of the Neumann mode
+ * series, where the fixed-step trapezoidal rule above is inaccurate):
+ *   |w| > 17                 Hankel's asymptotic expansion (Abramowitz & Stegun 9.7.2);
+ *   Re w <= |w| / 10         the ascending series -(ln(w/2) + gamma_E) I0(w) + sum_k (w^2/4)^k / (k!)^2 H_k
+ *                            (A&S 9.6.13), whose cancellation stays below e^{1.1 |w|};
+ *   otherwise                the trapezoidal rule on int_0^inf exp(-w cosh t) dt with a step
+ *                            h = 2 pi d / 40, d = pi/2 - |arg w| the half-width of the strip in
+ *                            which the integrand stays bounded (error ~ e^{-2 pi d / h}). */
+double complex or_bessel_k0_any(double complex w) {
+  double aw = cabs(w);
+  if (aw > 17.0) {
+    double complex a = 1.0, sum = 1.0;
+    for (int k = 1; k < 60; ++k) {
+      double complex na = a * (-(2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k * w);
+      if (cabs(na) >= cabs(a)) break;
+      a = na;
+      sum += a;
+      if (cabs(a) < 1e-17) break;
+    }
+    return csqrt(OR_PI / (2.0 * w)) * cexp(-w) * sum;
+  }
+  if (creal(w) <= 0.1 * aw) {
+    double complex q = w * w / 4.0, t = 1.0, I0 = 1.0, S = 0.0;
+    double Hk = 0.0;
+    for (int k = 1; k < 400; ++k) {
+      t *= q / ((double)k * (double)k);
+      Hk += 1.0 / k;
+      I0 += t;
+      S += t * Hk;
+      if (k > aw && cabs(t) * (Hk + 1.0) < 1e-18) break;
+    }
+    return -(clog(w / 2.0) + 0.57721566490153286061) * I0 + S;
+  }
+  double d = 0.5 * OR_PI - fabs(carg(w));
+  double h = 2.0 * OR_PI * d / 40.0;
+  if (h > 0.2) h = 0.2;
+  if (h > 0.6 / sqrt(aw)) h = 0.6 / sqrt(aw);
+  double complex s = 0.5 * cexp(-w);
+  for (int j = 1; j < 200000; ++j) {
+    double c = cosh(j * h);
+    if (creal(w) * (c - 1.0) > 40.0) break;
+    s += cexp(-w * c);
+  }
+  return h * s;
+}
+
+/* Kernel kinds: 0 = Dirichlet G_D (horizontal currents, charges), 1 = Neumann G_N (vertical currents). */
 typedef struct {
   const or_grid* g;
   double omega, H, rho_s;
   double complex k, eps;
-  double complex fit[MAXL][MAXL][3];
+  int nz;                 /* distinct heights: the metal layers first (id = layer), then via points */
+  const double* z;
+  double complex* fit;    /* stripline: [kind][nz][nz][3] tail coefficients */
 } medium_t;
 
 static double complex gfree(double complex k, double R) { return cexp(-I * k * R) / (4.0 * OR_PI * R); }
@@ -169,8 +221,8 @@ static double complex gfree_reg(double complex k, double R) {
   return (cexp(x) - 1.0) / (4.0 * OR_PI * R);
 }
 
-static double complex strip_images(const medium_t* md, double zp, double zq, double rho, int K, int reg) {
-  double H = md->H, r2 = rho * rho;
+static double complex strip_images(const medium_t* md, int kind, double zp, double zq, double rho, int K, int reg) {
+  double H = md->H, r2 = rho * rho, sg2 = kind == 0 ? -1.0 : 1.0;
   double complex s = 0.0;
   for (int a = 0; a <= K; ++a) {
     for (int sg = (a == 0 ? 1 : -1); sg <= 1; sg += 2) {
@@ -179,25 +231,27 @@ static double complex strip_images(const medium_t* md, double zp, double zq, dou
       double Rp = sqrt(r2 + zp_ * zp_), Rm = sqrt(r2 + zm_ * zm_);
       if (n == 0 && reg) s += gfree_reg(md->k, Rp);
       else s += gfree(md->k, Rp);
-      s -= gfree(md->k, Rm);
+      s += sg2 * gfree(md->k, Rm);
     }
   }
   return s;
 }
 
-static double complex strip_modal(const medium_t* md, double zp, double zq, double rho) {
+static double complex strip_modal(const medium_t* md, int kind, double zp, double zq, double rho) {
   double H = md->H;
   double complex s = 0.0;
+  if (kind == 1) s = 0.5 * or_bessel_k0_any(csqrt(-md->k * md->k) * rho);   /* m = 0 (TEM), e_0 / 2 */
   for (int m = 1; m < 4000; ++m) {
     double km = m * OR_PI / H;
     double complex gam = csqrt(km * km - md->k * md->k);
     if (creal(gam) * rho > 40.0) break;
-    s += sin(km * zp) * sin(km * zq) * or_bessel_k0(gam * rho);
+    double w = kind == 0 ? sin(km * zp) * sin(km * zq) : cos(km * zp) * cos(km * zq);
+    s += w * or_bessel_k0(gam * rho);
   }
   return s / (OR_PI * H);
 }
 
-static void medium_init(medium_t* md, const or_grid* g, double freq) {
+static void medium_init(medium_t* md, const or_grid* g, double freq, int nz, const double* z) {
   md->g = g;
   md->omega = 2.0 * OR_PI * freq;
   double er = or_eps_eff(g);
@@ -205,72 +259,107 @@ static void medium_init(medium_t* md, const or_grid* g, double freq) {
   md->k = md->omega * csqrt(MU0 * md->eps);
   md->H = g->h_total;
   md->rho_s = 0.5 * g->h_total;
+  md->nz = nz;
+  md->z = z;
+  md->fit = NULL;
   if (g->medium == 1) {
-    for (int p = 0; p < g->layers; ++p) {
-      for (int q = 0; q < g->layers; ++q) {
-        double zp = g->layer_z[p], zq = g->layer_z[q];
-        double x[3];
-        double complex y[3];
-        for (int i = 0; i < 3; ++i) {
-          double rho = md->rho_s * (1.0 + 0.5 * i);
-          x[i] = rho * rho;
-          y[i] = strip_modal(md, zp, zq, rho) - strip_images(md, zp, zq, rho, IMG_K, 0);
+    md->fit = (double complex*)malloc(sizeof(double complex) * 2 * nz * nz * 3);
+    for (int kind = 0; kind < 2; ++kind) {
+      for (int p = 0; p < nz; ++p) {
+        for (int q = 0; q < nz; ++q) {
+          double complex* c = md->fit + ((size_t)(kind * nz + p) * nz + q) * 3;
+          if (q < p) {   /* both kernels are symmetric in (z, z') */
+            const double complex* t = md->fit + ((size_t)(kind * nz + q) * nz + p) * 3;
+            c[0] = t[0]; c[1] = t[1]; c[2] = t[2];
+            continue;
+          }
+          double x[3];
+          double complex y[3];
+          for (int i = 0; i < 3; ++i) {
+            double rho = md->rho_s * (1.0 + 0.5 * i);
+            x[i] = rho * rho;
+            y[i] = strip_modal(md, kind, z[p], z[q], rho) - strip_images(md, kind, z[p], z[q], rho, IMG_K, 0);
+          }
+          /* quadratic in x = rho^2 through the three points (Newton divided differences) */
+          double complex d01 = (y[1] - y[0]) / (x[1] - x[0]);
+          double complex d12 = (y[2] - y[1]) / (x[2] - x[1]);
+          double complex d012 = (d12 - d01) / (x[2] - x[0]);
+          c[2] = d012;
+          c[1] = d01 - d012 * (x[0] + x[1]);
+          c[0] = y[0] - d01 * x[0] + d012 * x[0] * x[1];
         }
-        /* quadratic in x = rho^2 through the three points (Newton divided differences) */
-        double complex d01 = (y[1] - y[0]) / (x[1] - x[0]);
-        double complex d12 = (y[2] - y[1]) / (x[2] - x[1]);
-        double complex d012 = (d12 - d01) / (x[2] - x[0]);
-        double complex c2 = d012;
-        double complex c1 = d01 - d012 * (x[0] + x[1]);
-        double complex c0 = y[0] - d01 * x[0] + d012 * x[0] * x[1];
-        md->fit[p][q][0] = c0; md->fit[p][q][1] = c1; md->fit[p][q][2] = c2;
       }
     }
   }
 }
 
-/* G (reg = 0) or G - 1/(4 pi R_direct) (reg = 1) between layers lp, lq at lateral distance rho. */
-static double complex green_eval(const medium_t* md, int lp, int lq, double rho, int reg) {
+static void medium_free(medium_t* md) { free(md->fit); md->fit = NULL; }
+
+/* G (reg = 0) or G - 1/(4 pi R_direct) (reg = 1) of kernel `kind` between heights z[ip], z[iq] at
+ * lateral distance rho. */
+static double complex green_eval(const medium_t* md, int kind, int ip, int iq, double rho, int reg) {
   const or_grid* g = md->g;
-  double zp = g->layer_z[lp], zq = g->layer_z[lq];
+  double zp = md->z[ip], zq = md->z[iq];
   if (g->medium == 0) {
     double Rd = sqrt(rho * rho + (zp - zq) * (zp - zq)), Ri = sqrt(rho * rho + (zp + zq) * (zp + zq));
-    return (reg ? gfree_reg(md->k, Rd) : gfree(md->k, Rd)) - gfree(md->k, Ri);
+    double complex gi = gfree(md->k, Ri);
+    return (reg ? gfree_reg(md->k, Rd) : gfree(md->k, Rd)) + (kind == 0 ? -gi : gi);
   }
   if (rho >= md->rho_s) {
-    double complex G = strip_modal(md, zp, zq, rho);
+    double complex G = strip_modal(md, kind, zp, zq, rho);
     if (reg) G -= 1.0 / (4.0 * OR_PI * sqrt(rho * rho + (zp - zq) * (zp - zq)));
     return G;
   }
-  const double complex* c = md->fit[lp][lq];
+  const double complex* c = md->fit + ((size_t)(kind * md->nz + ip) * md->nz + iq) * 3;
   double x = rho * rho;
-  return strip_images(md, zp, zq, rho, IMG_K, reg) + c[0] + x * (c[1] + x * c[2]);
+  return strip_images(md, kind, zp, zq, rho, IMG_K, reg) + c[0] + x * (c[1] + x * c[2]);
 }
 
 double complex or_green(const or_grid* g, double freq, int lp, int lq, double rho) {
   medium_t md;
-  medium_init(&md, g, freq);
-  return green_eval(&md, lp, lq, rho, 0);
+  medium_init(&md, g, freq, g->layers, g->layer_z);
+  double complex G = green_eval(&md, 0, lp, lq, rho, 0);
+  medium_free(&md);
+  return G;
 }
 
 double complex or_green_images(const or_grid* g, double freq, int lp, int lq, double rho, int K) {
   medium_t md;
-  medium_init(&md, g, freq);
-  return strip_images(&md, g->layer_z[lp], g->layer_z[lq], rho, K, 0);
+  medium_init(&md, g, freq, 0, NULL);
+  double complex G = strip_images(&md, 0, g->layer_z[lp], g->layer_z[lq], rho, K, 0);
+  medium_free(&md);
+  return G;
 }
 
 double complex or_green_modal(const or_grid* g, double freq, int lp, int lq, double rho) {
   medium_t md;
-  medium_init(&md, g, freq);
-  return strip_modal(&md, g->layer_z[lp], g->layer_z[lq], rho);
+  medium_init(&md, g, freq, 0, NULL);
+  double complex G = strip_modal(&md, 0, g->layer_z[lp], g->layer_z[lq], rho);
+  medium_free(&md);
+  return G;
+}
+
+double complex or_green_heights(const or_grid* g, double freq, int kind, double zp, double zq, double rho,
+                                int route, int K) {
+  double z[2] = {zp, zq};
+  medium_t md;
+  medium_init(&md, g, freq, route == 0 ? 2 : 0, z);
+  double complex G;
+  if (route == 1) G = strip_images(&md, kind, zp, zq, rho, K, 0);
+  else if (route == 2) G = strip_modal(&md, kind, zp, zq, rho);
+  else G = green_eval(&md, kind, 0, 1, rho, 0);
+  medium_free(&md);
+  return G;
 }
 
 /* ---------------------------------------------------------------- triangle-pair integrals */
 typedef struct {
   double v[3][3];
   double c[3];
+  double n[3];            /* unit normal */
   double area, lmax;
-  int layer;
+  int layer, vert;        /* vert: a vertical (via) triangle */
+  int zid[2][13];         /* height id of every point of the 7-point (0) and 13-point (1) rule */
 } tri_t;
 
 static void tri_setup(tri_t* t, const double v[3][3], int layer) {
@@ -279,7 +368,9 @@ static void tri_setup(tri_t* t, const double v[3][3], int layer) {
   sub3(v[1], v[0], e1);
   sub3(v[2], v[0], e2);
   cross3(e1, e2, n);
-  t->area = 0.5 * norm3(n);
+  double nn = norm3(n);
+  t->area = 0.5 * nn;
+  for (int i = 0; i < 3; ++i) t->n[i] = n[i] / nn;
   t->lmax = 0.0;
   for (int i = 0; i < 3; ++i) {
     double e[3];
@@ -289,13 +380,44 @@ static void tri_setup(tri_t* t, const double v[3][3], int layer) {
     t->c[i] = (v[0][i] + v[1][i] + v[2][i]) / 3.0;
   }
   t->layer = layer;
+  t->vert = !(v[0][2] == v[1][2] && v[0][2] == v[2][2]);
+  for (int r = 0; r < 2; ++r)
+    for (int i = 0; i < 13; ++i) t->zid[r][i] = layer;
+}
+
+/* Height of a quadrature point: exactly the layer height on a horizontal triangle. */
+static double point_z(const tri_t* t, const double* b) {
+  if (!t->vert) return t->v[0][2];
+  return t->v[0][2] + b[1] * (t->v[1][2] - t->v[0][2]) + b[2] * (t->v[2][2] - t->v[0][2]);
 }
 
 static void tri_point(const tri_t* t, const double* b, double* r) {
-  for (int k = 0; k < 3; ++k) r[k] = b[0] * t->v[0][k] + b[1] * t->v[1][k] + b[2] * t->v[2][k];
+  for (int k = 0; k < 2; ++k) r[k] = b[0] * t->v[0][k] + b[1] * t->v[1][k] + b[2] * t->v[2][k];
+  r[2] = point_z(t, b);
 }
 
-/* out[0] = int int G ; out[1 + 3a + b] = int int (r - v_a).(r' - v_b) G  over T_p x T_q */
+/* Height ids of the quadrature points of vertical triangles: appended to `z` (which starts with the
+ * layer heights) as they are met; returns the new count. */
+static int assign_heights(tri_t* tris, int T, double* z, int nz) {
+  for (int t = 0; t < T; ++t) {
+    if (!tris[t].vert) continue;
+    for (int r = 0; r < 2; ++r) {
+      const double *b, *w;
+      int n = or_tri_rule(r == 0 ? 7 : 13, &b, &w);
+      for (int i = 0; i < n; ++i) {
+        double zz = point_z(&tris[t], b + 3 * i);
+        int id = -1;
+        for (int j = 0; j < nz; ++j) if (z[j] == zz) { id = j; break; }
+        if (id < 0) { id = nz; z[nz++] = zz; }
+        tris[t].zid[r][i] = id;
+      }
+    }
+  }
+  return nz;
+}
+
+/* out[0] = int int G_D ; out[1 + 3a + b] = int int (r - v_a) . G_A (r' - v_b), where G_A acts with
+ * G_D on the horizontal and G_N on the vertical components, over T_p x T_q */
 static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, double complex out[10]) {
   for (int i = 0; i < 10; ++i) out[i] = 0.0;
   double dc[3];
@@ -303,6 +425,7 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
   double lm = p->lmax > q->lmax ? p->lmax : q->lmax;
   /* lattice geometry puts many pairs exactly on the threshold: resolve ties as "near" */
   int near = norm3(dc) < 2.0 * lm * (1.0 + 1e-9);
+  int both_vert = p->vert && q->vert;
   const double *bo, *wo, *bi, *wi;
   int no = or_tri_rule(near ? 13 : 7, &bo, &wo);
   int ni = or_tri_rule(near ? 13 : 7, &bi, &wi);
@@ -311,11 +434,13 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
     tri_point(p, bo + 3 * i, r);
     for (int a = 0; a < 3; ++a) sub3(r, p->v[a], ra[a]);
     double wpo = wo[i] * p->area;
+    int izp = p->zid[near][i];
     if (near) {
-      double I1, Iv[3];
+      double I1, Iv[3], rv[3];
       or_tri_potentials(q->v, r, &I1, Iv);
-      double d = r[2] - q->v[0][2];
-      double r0[3] = {r[0], r[1], r[2] - d};    /* projection on the (horizontal) plane of T_q */
+      sub3(r, q->v[0], rv);
+      double d = dot3(q->n, rv);
+      double r0[3] = {r[0] - d * q->n[0], r[1] - d * q->n[1], r[2] - d * q->n[2]};   /* projection on T_q's plane */
       out[0] += wpo * I1 / (4.0 * OR_PI);
       for (int b = 0; b < 3; ++b) {
         double vb[3], t[3];
@@ -327,14 +452,19 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
     for (int j = 0; j < ni; ++j) {
       double rq[3];
       tri_point(q, bi + 3 * j, rq);
+      int izq = q->zid[near][j];
       double rho = hypot(r[0] - rq[0], r[1] - rq[1]);
-      double complex G = green_eval(md, p->layer, q->layer, rho, near);
-      double complex wG = wpo * wi[j] * q->area * G;
-      out[0] += wG;
+      double complex GD = green_eval(md, 0, izp, izq, rho, near);
+      double complex GN = both_vert ? green_eval(md, 1, izp, izq, rho, near) : 0.0;
+      double complex w = wpo * wi[j] * q->area;
+      out[0] += w * GD;
       double rb[3][3];
       for (int b = 0; b < 3; ++b) sub3(rq, q->v[b], rb[b]);
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) out[1 + 3 * a + b] += wG * dot3(ra[a], rb[b]);
+        for (int b = 0; b < 3; ++b) {
+          double dh = ra[a][0] * rb[b][0] + ra[a][1] * rb[b][1], dz = ra[a][2] * rb[b][2];
+          out[1 + 3 * a + b] += w * (dh * GD + (both_vert ? dz * GN : 0.0));
+        }
     }
   }
 }
@@ -349,11 +479,14 @@ typedef struct {
   int T;
   const int32_t* tri_keys;     /* [T] */
   int32_t* key_to_tri;         /* key -> triangle index */
+  const tri_t* tris;           /* [T], with height ids */
+  int nz;
+  const double* z;             /* [nz] heights */
 } fill_job;
 
 static void key_parts(int32_t key, int* layer, int* x, int* y, int* half) {
-  *half = key & 1;
-  key >>= 1;
+  *half = key & 3;
+  key >>= 2;
   *x = key % 128 - 4;
   key /= 128;
   *y = key % 128 - 4;
@@ -364,18 +497,11 @@ static void* fill_worker(void* arg) {
   fill_job* J = (fill_job*)arg;
   const or_grid* g = J->g;
   int T = J->T, M = J->M;
-  tri_t* tris = (tri_t*)malloc(sizeof(tri_t) * T);
-  for (int t = 0; t < T; ++t) {
-    double v[3][3];
-    int layer, x, y, half;
-    or_triangle(g, J->tri_keys[t], v);
-    key_parts(J->tri_keys[t], &layer, &x, &y, &half);
-    tri_setup(&tris[t], v, layer);
-  }
+  const tri_t* tris = J->tris;
   /* pair-integral storage: direct mode keeps all T x T pairs; table mode keeps one entry per
-   * (layer pair, orientation/half pair, lattice offset) */
+   * (layer pair, orientation/triangle pair, lattice offset) */
   int W = (g->nx > g->ny ? g->nx : g->ny) + 5, NW = 2 * W + 1;
-  size_t nslots = J->mode == 0 ? (size_t)T * T : (size_t)g->layers * g->layers * 16 * NW * NW;
+  size_t nslots = J->mode == 0 ? (size_t)T * T : (size_t)g->layers * g->layers * 64 * NW * NW;
   double complex* slot = (double complex*)malloc(sizeof(double complex) * 10 * nslots);
   unsigned char* have = (unsigned char*)malloc(nslots);
   int32_t* pair_slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * T);
@@ -389,7 +515,7 @@ static void* fill_worker(void* arg) {
       if (J->mode == 0) s = (size_t)p * T + q;
       else {
         int op = (xp + yp) & 1, oq = (xq + yq) & 1;
-        s = ((((((size_t)lp * g->layers + lq) * 2 + op) * 2 + hp) * 2 + oq) * 2 + hq) * NW * NW +
+        s = ((((((size_t)lp * g->layers + lq) * 2 + op) * 4 + hp) * 2 + oq) * 4 + hq) * NW * NW +
             (size_t)(xq - xp + W) * NW + (yq - yp + W);
       }
       pair_slot[(size_t)p * T + q] = (int32_t)s;
@@ -397,7 +523,7 @@ static void* fill_worker(void* arg) {
   }
   for (int f = J->tid; f < J->F; f += J->nthreads) {
     medium_t md;
-    medium_init(&md, g, J->freqs[f]);
+    medium_init(&md, g, J->freqs[f], J->nz, J->z);
     memset(have, 0, nslots);
     for (int p = 0; p < T; ++p) {
       for (int q = 0; q < T; ++q) {
@@ -439,12 +565,38 @@ static void* fill_worker(void* arg) {
         Zf[(size_t)m * M + n] = z;
       }
     }
+    medium_free(&md);
   }
-  free(tris);
   free(slot);
   free(have);
   free(pair_slot);
   return NULL;
+}
+
+/* Distinct triangles of the grid's BFs with their geometry and height ids; returns T. */
+static int collect_triangles(const or_grid* g, const int32_t* table, int M, int32_t* key_to_tri, int32_t* keys,
+                             tri_t** tris_out, double** z_out, int* nz_out) {
+  int T = 0;
+  for (int m = 0; m < M; ++m) {
+    for (int s = 0; s < 2; ++s) {
+      int32_t k = table[OR_BF_COLS * m + 4 + s];
+      if (key_to_tri[k] < 0) { key_to_tri[k] = T; keys[T++] = k; }
+    }
+  }
+  tri_t* tris = (tri_t*)malloc(sizeof(tri_t) * T);
+  for (int t = 0; t < T; ++t) {
+    double v[3][3];
+    int layer, x, y, half;
+    or_triangle(g, keys[t], v);
+    key_parts(keys[t], &layer, &x, &y, &half);
+    tri_setup(&tris[t], v, layer);
+  }
+  double* z = (double*)malloc(sizeof(double) * (g->layers + 40 * T + 1));
+  for (int l = 0; l < g->layers; ++l) z[l] = g->layer_z[l];
+  *nz_out = assign_heights(tris, T, z, g->layers);
+  *tris_out = tris;
+  *z_out = z;
+  return T;
 }
 
 double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threads, double complex* Z) {
@@ -455,18 +607,15 @@ double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threa
   int32_t* key_to_tri = (int32_t*)malloc(sizeof(int32_t) * (1 << 21));
   for (int i = 0; i < (1 << 21); ++i) key_to_tri[i] = -1;
   int32_t* keys = (int32_t*)malloc(sizeof(int32_t) * 2 * M);
-  int T = 0;
-  for (int m = 0; m < M; ++m) {
-    for (int s = 0; s < 2; ++s) {
-      int32_t k = table[OR_BF_COLS * m + 4 + s];
-      if (key_to_tri[k] < 0) { key_to_tri[k] = T; keys[T++] = k; }
-    }
-  }
+  tri_t* tris;
+  double* z;
+  int nz;
+  int T = collect_triangles(g, table, M, key_to_tri, keys, &tris, &z, &nz);
   if (threads < 1) threads = 1;
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * threads);
   fill_job* jobs = (fill_job*)malloc(sizeof(fill_job) * threads);
   for (int i = 0; i < threads; ++i) {
-    fill_job j = {g, table, M, F, mode, threads, i, freqs, Z, T, keys, key_to_tri};
+    fill_job j = {g, table, M, F, mode, threads, i, freqs, Z, T, keys, key_to_tri, tris, nz, z};
     jobs[i] = j;
     pthread_create(&th[i], NULL, fill_worker, &jobs[i]);
   }
@@ -494,21 +643,28 @@ double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threa
   free(keys);
   free(key_to_tri);
   free(table);
+  free(tris);
+  free(z);
   return amax > 0.0 ? dmax / amax : 0.0;
 }
 
 /* Test hook: the ten integrals of one triangle pair (keys of the grid's lattice). */
 void or_pair_integrals(const or_grid* g, double freq, int32_t kp, int32_t kq, double complex out[10]) {
+  int32_t keys[2] = {kp, kq};
+  tri_t tr[2];
+  for (int i = 0; i < 2; ++i) {
+    double v[3][3];
+    int layer, x, y, half;
+    or_triangle(g, keys[i], v);
+    key_parts(keys[i], &layer, &x, &y, &half);
+    tri_setup(&tr[i], v, layer);
+  }
+  double* z = (double*)malloc(sizeof(double) * (g->layers + 80));
+  for (int l = 0; l < g->layers; ++l) z[l] = g->layer_z[l];
+  int nz = assign_heights(tr, 2, z, g->layers);
   medium_t md;
-  medium_init(&md, g, freq);
-  double v[3][3];
-  int layer, x, y, half;
-  tri_t P, Q;
-  or_triangle(g, kp, v);
-  key_parts(kp, &layer, &x, &y, &half);
-  tri_setup(&P, v, layer);
-  or_triangle(g, kq, v);
-  key_parts(kq, &layer, &x, &y, &half);
-  tri_setup(&Q, v, layer);
-  pair_integrals(&md, &P, &Q, out);
+  medium_init(&md, g, freq, nz, z);
+  pair_integrals(&md, &tr[0], &tr[1], out);
+  medium_free(&md);
+  free(z);
 }

@@ -16,19 +16,29 @@
  * pixel is metal).
  * Canonical BF order: port stubs (port-major: inner stub diagonal, port edge, outer stub
  * diagonal) -> per layer, per pixel row-major (y outer, x inner): diagonal, +x side, +y side
- * -> pixel-port BFs (port-major).
+ * -> pixel-port BFs (port-major) -> via BFs.
+ *
+ * Via state (n_states = 3; the paper names vias only as an extension, Section VII): state 2 on
+ * layer l is metal on layer l plus a vertical strip standing on the pixel diagonal, from layer l
+ * up to layer l+1.  The strip is a rectangle A = D0@z_l, B = D1@z_l, C = D1@z_{l+1}, D = D0@z_{l+1}
+ * (D0, D1 = the diagonal's end corners) cut along A-C into Ta = (A, B, C) and Tb = (A, C, D).
+ * Three BFs per via site (layers 0 .. L-2, per pixel row-major): the strip's own diagonal A-C
+ * (Ta -> Tb); the junction A-B with the lower-indexed triangle (half 0) of pixel (l, x, y)
+ * (half 0 -> Ta), active with the via; the junction D-C with half 0 of pixel (l+1, x, y)
+ * (Tb -> that half), active only when that pixel has metal.  The last layer has no via state.
  */
 #include <string.h>
 
 #include "pmom_oracle.h"
 
+/* half 0, 1: the pixel's horizontal triangles; 2, 3: Ta, Tb of the via strip above it */
 static int32_t tri_key(int layer, int x, int y, int half) {
-  return ((layer * 128 + (y + 4)) * 128 + (x + 4)) * 2 + half;
+  return ((layer * 128 + (y + 4)) * 128 + (x + 4)) * 4 + half;
 }
 
 static void key_decode(int32_t key, int* layer, int* x, int* y, int* half) {
-  *half = key & 1;
-  key >>= 1;
+  *half = key & 3;
+  key >>= 2;
   *x = key % 128 - 4;
   key /= 128;
   *y = key % 128 - 4;
@@ -49,9 +59,30 @@ static void tri_corners(int x, int y, int half, int c[3][2]) {
   for (int i = 0; i < 3; ++i) { c[i][0] = v[i][0]; c[i][1] = v[i][1]; }
 }
 
+/* End corners D0, D1 of the pixel diagonal (the corners that both halves share, in the order
+ * they appear in half 0). */
+static void diag_ends(int x, int y, int d0[2], int d1[2]) {
+  if (((x + y) & 1) == 0) { d0[0] = x; d0[1] = y + 1; d1[0] = x + 1; d1[1] = y; }
+  else                    { d0[0] = x; d0[1] = y;     d1[0] = x + 1; d1[1] = y + 1; }
+}
+
 void or_triangle(const or_grid* g, int32_t key, double v[3][3]) {
   int layer, x, y, half, c[3][2];
   key_decode(key, &layer, &x, &y, &half);
+  if (half >= 2) {
+    int d0[2], d1[2];
+    diag_ends(x, y, d0, d1);
+    double zl = g->layer_z[layer], zu = g->layer_z[layer + 1];
+    /* Ta = (A, B, C), Tb = (A, C, D) */
+    const int* xy[3] = {d0, d1, half == 2 ? d1 : d0};
+    double z[3] = {zl, half == 2 ? zl : zu, zu};
+    for (int i = 0; i < 3; ++i) {
+      v[i][0] = xy[i][0] * g->pitch;
+      v[i][1] = xy[i][1] * g->pitch;
+      v[i][2] = z[i];
+    }
+    return;
+  }
   tri_corners(x, y, half, c);
   for (int i = 0; i < 3; ++i) {
     v[i][0] = c[i][0] * g->pitch;
@@ -128,9 +159,12 @@ static void port_pixels(const or_grid* g, const int32_t* port, int s1[2], int s2
 
 static int pix_index(const or_grid* g, int layer, int x, int y) { return (layer * g->ny + y) * g->nx + x; }
 
+static int has_vias(const or_grid* g) { return g->n_states >= 3 && g->layers >= 2; }
+
 int or_count_bfs(const or_grid* g) {
   int per_layer = g->nx * g->ny + (g->nx - 1) * g->ny + g->nx * (g->ny - 1);
-  return 4 * g->n_ports + g->layers * per_layer;
+  int vias = has_vias(g) ? 3 * (g->layers - 1) * g->nx * g->ny : 0;
+  return 4 * g->n_ports + g->layers * per_layer + vias;
 }
 
 int or_bf_table(const or_grid* g, int32_t* t) {
@@ -172,12 +206,42 @@ int or_bf_table(const or_grid* g, int32_t* t) {
     r[0] = OR_BF_PIXPORT; r[1] = pix_index(g, layer, gp[0], gp[1]); r[2] = -1; r[3] = p;
     emit_side(r, layer, s1[0], s1[1], gp[0], gp[1]);
   }
+  if (has_vias(g)) {
+    for (int l = 0; l + 1 < g->layers; ++l) {
+      for (int y = 0; y < g->ny; ++y) {
+        for (int x = 0; x < g->nx; ++x) {
+          int f0 = -1, c[3][2];
+          int32_t* r = t + OR_BF_COLS * m++;
+          /* strip diagonal A-C: free vertices B (index 1 of Ta) and D (index 2 of Tb) */
+          r[0] = OR_BF_VIA_STRIP; r[1] = pix_index(g, l, x, y); r[2] = -1; r[3] = -1;
+          r[4] = tri_key(l, x, y, 2); r[5] = tri_key(l, x, y, 3); r[6] = 1; r[7] = 2;
+          /* free vertex of half 0 with respect to the pixel diagonal */
+          int d0[2], d1[2];
+          diag_ends(x, y, d0, d1);
+          tri_corners(x, y, 0, c);
+          for (int i = 0; i < 3; ++i) {
+            int on0 = c[i][0] == d0[0] && c[i][1] == d0[1], on1 = c[i][0] == d1[0] && c[i][1] == d1[1];
+            if (!on0 && !on1) f0 = i;
+          }
+          /* junction A-B: half 0 of (l, x, y) -> Ta; free vertex of Ta is C (index 2) */
+          r = t + OR_BF_COLS * m++;
+          r[0] = OR_BF_VIA_JOIN; r[1] = pix_index(g, l, x, y); r[2] = -1; r[3] = -1;
+          r[4] = tri_key(l, x, y, 0); r[5] = tri_key(l, x, y, 2); r[6] = f0; r[7] = 2;
+          /* junction D-C: Tb -> half 0 of (l+1, x, y); free vertex of Tb is A (index 0) */
+          r = t + OR_BF_COLS * m++;
+          r[0] = OR_BF_VIA_LAND; r[1] = pix_index(g, l, x, y); r[2] = pix_index(g, l + 1, x, y); r[3] = -1;
+          r[4] = tri_key(l, x, y, 3); r[5] = tri_key(l + 1, x, y, 0); r[6] = 0; r[7] = f0;
+        }
+      }
+    }
+  }
   return m;
 }
 
 int or_active_set(const or_grid* g, const int32_t* t, int M, const uint8_t* map, int32_t* idx) {
-  int np = g->layers * g->ny * g->nx;
+  int np = g->layers * g->ny * g->nx, last = (g->layers - 1) * g->ny * g->nx;
   for (int i = 0; i < np; ++i) if (map[i] >= g->n_states) return -1;
+  for (int i = last; i < np; ++i) if (map[i] == 2) return -1;   /* no via above the last layer */
   int n = 0;
   for (int m = 0; m < M; ++m) {
     const int32_t* r = t + OR_BF_COLS * m;
@@ -187,6 +251,9 @@ int or_active_set(const or_grid* g, const int32_t* t, int M, const uint8_t* map,
       case OR_BF_INNER: on = map[r[1]] >= 1; break;
       case OR_BF_INTER: on = map[r[1]] >= 1 && map[r[2]] >= 1; break;
       case OR_BF_PIXPORT: on = map[r[1]] >= 1; break;
+      case OR_BF_VIA_STRIP: on = map[r[1]] == 2; break;
+      case OR_BF_VIA_JOIN: on = map[r[1]] == 2; break;
+      case OR_BF_VIA_LAND: on = map[r[1]] == 2 && map[r[2]] >= 1; break;
       default: on = 0;
     }
     if (on) idx[n++] = m;

@@ -65,8 +65,12 @@ def lib():
                 getattr(L, fn).restype = _C128
             L.or_green_images.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.or_green_images.restype = _C128
-            L.or_bessel_k0.argtypes = [_C128]
-            L.or_bessel_k0.restype = _C128
+            for fn in ("or_bessel_k0", "or_bessel_k0_any"):
+                getattr(L, fn).argtypes = [_C128]
+                getattr(L, fn).restype = _C128
+            L.or_green_heights.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            L.or_green_heights.restype = _C128
             L.or_tri_potentials.argtypes = [P, P, P, P]
             L.or_tri_rule.argtypes = [ctypes.c_int, P, P]
             L.or_eps_eff.argtypes = [P]
@@ -144,8 +148,17 @@ def green(grid: Grid, freq: float, lp: int, lq: int, rho: float, route: str = "d
     return _c(L.or_green(grid.ref, freq, lp, lq, rho))
 
 
-def bessel_k0(w: complex) -> complex:
-    return _c(lib().or_bessel_k0(_C128(w.real, w.imag)))
+def bessel_k0(w: complex, any_arg: bool = False) -> complex:
+    f = lib().or_bessel_k0_any if any_arg else lib().or_bessel_k0
+    return _c(f(_C128(w.real, w.imag)))
+
+
+def green_heights(grid: Grid, freq: float, kind: int, zp: float, zq: float, rho: float, route: str = "default",
+                  K: int = 64) -> complex:
+    """Kernel `kind` (0 Dirichlet: horizontal currents and charges; 1 Neumann: vertical currents)
+    between arbitrary heights."""
+    r = {"default": 0, "images": 1, "modal": 2}[route]
+    return _c(lib().or_green_heights(grid.ref, freq, kind, zp, zq, rho, r, K))
 
 
 def tri_potentials(tri: np.ndarray, r: np.ndarray):

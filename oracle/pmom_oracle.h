@@ -34,18 +34,21 @@ typedef struct {
   const double* layer_z;   /* [layers] metal heights [m] */
   double h_total;          /* stripline plate spacing [m] (microstrip: unused) */
   double eps_r, tan_d;
-  int n_states;            /* 2: void/metal */
+  int n_states;            /* 2: void/metal; 3: void/metal/metal with a via to the next layer */
   int n_ports;
   const int32_t* ports;    /* [n_ports][3] = layer, side (0 right, 1 top, 2 left, 3 bottom), pos */
 } or_grid;
 
-/* Basis-function classes (Section II-C). */
-enum { OR_BF_ALWAYS = 0, OR_BF_INNER = 1, OR_BF_INTER = 2, OR_BF_PIXPORT = 3 };
+/* Basis-function classes (Section II-C), plus the three BFs of a via site (state 2). */
+enum { OR_BF_ALWAYS = 0, OR_BF_INNER = 1, OR_BF_INTER = 2, OR_BF_PIXPORT = 3,
+       OR_BF_VIA_STRIP = 4, OR_BF_VIA_JOIN = 5, OR_BF_VIA_LAND = 6 };
 
 /* One BF-table row = 8 int32:
  *   [0] class  [1] pixel A  [2] pixel B  [3] port (or -1)
  *   [4] key of T+  [5] key of T-  [6] free-vertex index in T+  [7] free-vertex index in T-
- * pixel index = (layer*ny + y)*nx + x; triangle key = (((layer*128 + y+4)*128 + x+4)*2 + half). */
+ * pixel index = (layer*ny + y)*nx + x; triangle key = (((layer*128 + y+4)*128 + x+4)*4 + half),
+ * half 0/1 = the pixel's triangles, 2/3 = the triangles Ta/Tb of the via strip from the pixel up
+ * to layer+1.  Via rows: [1] = the via pixel (l, x, y); [2] = (l+1, x, y) for the landing junction. */
 #define OR_BF_COLS 8
 
 int or_count_bfs(const or_grid* g);
@@ -68,6 +71,12 @@ double complex or_green(const or_grid* g, double freq, int lp, int lq, double rh
 double complex or_green_images(const or_grid* g, double freq, int lp, int lq, double rho, int K);
 double complex or_green_modal(const or_grid* g, double freq, int lp, int lq, double rho);
 double complex or_bessel_k0(double complex w);
+/* K0 for any Re w >= 0 (series / asymptotic; used for the TEM term of the Neumann mode series). */
+double complex or_bessel_k0_any(double complex w);
+/* Kernel `kind` (0: Dirichlet G_D, 1: Neumann G_N) between arbitrary heights zp, zq [m];
+ * route 0: the fill's evaluation, 1: image series with K images, 2: mode series. */
+double complex or_green_heights(const or_grid* g, double freq, int kind, double zp, double zq, double rho,
+                                int route, int K);
 /* Analytic potential integrals over a planar triangle (used by the singular part of the fill). */
 void or_tri_potentials(const double tri[3][3], const double r[3], double* I1, double Iv[3]);
 /* Quadrature rules on the reference triangle: n = 7 or 13; returns barycentric rows and weights. */

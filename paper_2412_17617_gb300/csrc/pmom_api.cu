@@ -200,7 +200,8 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   if (g->layers < 1 || g->layers > 8 || g->nx < 1 || g->ny < 1 || g->nx > 100 || g->ny > 100 || g->pitch_m <= 0 ||
       g->n_ports < 1 || g->n_ports > pmom::kMaxPorts || !g->ports || !g->layer_z_m || (g->medium != 0 && g->medium != 1))
     return PMOM_ERR_INVALID_ARG;
-  if (g->n_states != 2) return PMOM_ERR_UNSUPPORTED;
+  if (g->n_states != 2 && g->n_states != 3) return PMOM_ERR_UNSUPPORTED;
+  if (g->n_states == 3 && g->layers < 2) return PMOM_ERR_INVALID_ARG;   // a via needs a layer above
   for (int p = 0; p < g->n_ports; ++p) {
     const pmom_port& q = g->ports[p];
     const int lim = (q.side == 0 || q.side == 2) ? g->ny : g->nx;
@@ -328,7 +329,7 @@ pmom_status pmom_active_set(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   pmom::EvalArgs a{};
-  a.rules = c->d_rules; a.M = c->M; a.B = B; a.npix = c->grid.pixels(); a.n_states = c->grid.n_states;
+  a.rules = c->d_rules; a.M = c->M; a.B = B; a.npix = c->grid.pixels(); a.n_states = c->grid.n_states; a.via_top = c->grid.via_top();
   a.maps = maps; a.idx = idx_out; a.n_act = n_out; a.flags = c->d_flags;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, pmom::launch_activate(a, s));
@@ -352,7 +353,7 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
   const int P = c->grid.n_ports;
   pmom::EvalArgs a{};
   a.rules = c->d_rules; a.M = c->M; a.P = P; a.F = c->F; a.B = B; a.npix = c->grid.pixels();
-  a.n_states = c->grid.n_states; a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.Z = c->d_Z;
+  a.n_states = c->grid.n_states; a.via_top = c->grid.via_top(); a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.Z = c->d_Z;
   a.z_c128 = c->dtype == PMOM_C128;
   for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch;   // delta-gap edges are pixel sides
   a.Z0 = c->Z0;
@@ -442,7 +443,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   // reference support set (a1), its size read back to size the factors
   pmom::EvalArgs r{};
   r.rules = c->d_rules; r.M = M; r.P = P; r.F = F; r.B = 1; r.npix = c->grid.pixels();
-  r.n_states = c->grid.n_states; r.maps = ref_map; r.idx = c->d_ref_idx; r.n_act = d_ref_n; r.flags = d_ref_bad;
+  r.n_states = c->grid.n_states; r.via_top = c->grid.via_top(); r.maps = ref_map; r.idx = c->d_ref_idx; r.n_act = d_ref_n; r.flags = d_ref_bad;
   r.n_max = small + 2;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_small, 0, 256, s));
   PMOM_CUDA(c, cudaMemsetAsync(d_ref_bad, 0, sizeof(uint32_t), s));
@@ -480,7 +481,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
     }
     pmom::EvalArgs fa{};
     fa.rules = c->d_rules; fa.M = M; fa.P = P; fa.F = F; fa.B = 1; fa.npix = c->grid.pixels();
-    fa.n_states = c->grid.n_states; fa.maps = ref_map; fa.idx = c->d_ref_idx; fa.n_act = d_ref_n;
+    fa.n_states = c->grid.n_states; fa.via_top = c->grid.via_top(); fa.maps = ref_map; fa.idx = c->d_ref_idx; fa.n_act = d_ref_n;
     fa.Z = c->d_Z; fa.z_c128 = 0;
     for (int p = 0; p < pmom::kMaxPorts; ++p) fa.port_len[p] = c->grid.pitch;
     fa.Z0 = c->Z0; fa.flags = c->d_ref_flags; fa.task_counter = small;
@@ -516,7 +517,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   // candidates: support sets, then the bordered update per (candidate, frequency) task
   pmom::EvalArgs a{};
   a.rules = c->d_rules; a.M = M; a.P = P; a.F = F; a.B = B; a.npix = c->grid.pixels();
-  a.n_states = c->grid.n_states; a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.flags = c->d_flags;
+  a.n_states = c->grid.n_states; a.via_top = c->grid.via_top(); a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.flags = c->d_flags;
   a.n_max = small + 2;
   PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, pmom::launch_activate(a, s));
@@ -813,7 +814,7 @@ extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* 
   int* small = reinterpret_cast<int*>(base + o_small);
   pmom::EvalArgs a{};
   a.rules = c->d_rules; a.M = M; a.P = P; a.F = F; a.B = B; a.npix = c->grid.pixels();
-  a.n_states = c->grid.n_states; a.maps = maps;
+  a.n_states = c->grid.n_states; a.via_top = c->grid.via_top(); a.maps = maps;
   a.idx = reinterpret_cast<int32_t*>(base + o_idx);
   a.n_act = reinterpret_cast<int32_t*>(base + o_nact);
   a.flags = reinterpret_cast<uint32_t*>(base + o_flags);

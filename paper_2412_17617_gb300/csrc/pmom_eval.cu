@@ -6,7 +6,7 @@
 namespace pmom {
 
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s) {
-  activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.idx, a.n_act, a.flags,
+  activate_kernel<<<a.B, kThreads, 0, s>>>(a.rules, a.M, a.maps, a.npix, a.n_states, a.via_top, a.idx, a.n_act, a.flags,
                                             a.n_max);
   return cudaGetLastError();
 }

@@ -127,7 +127,7 @@ template <> struct Cfg<double2> { static constexpr int NB = 8; static constexpr 
 
 // ------------------------------------------------------------------ activation (Eq. 3)
 __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restrict__ rules, int M,
-                                                           const uint8_t* __restrict__ maps, int npix, int n_states,
+                                                           const uint8_t* __restrict__ maps, int npix, int n_states, int via_top,
                                                            int32_t* __restrict__ idx, int32_t* __restrict__ n_act,
                                                            uint32_t* __restrict__ flags, int* __restrict__ n_max) {
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restri
   if (tid == 0) s_bad = 0;
   __syncthreads();
   for (int i = tid; i < npix; i += kThreads)
-    if (map[i] >= n_states) s_bad = 1;
+    if (map[i] >= n_states || (map[i] == 2 && i >= via_top)) s_bad = 1;
   __syncthreads();
   if (s_bad) {
     if (tid == 0) {
@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(kThreads) activate_kernel(const int4* __restri
         case kInner: on = map[r.y] >= 1; break;
         case kInter: on = map[r.y] >= 1 && map[r.z] >= 1; break;
         case kPixPort: on = map[r.y] >= 1; break;
+        case kViaStrip:
+        case kViaJoin: on = map[r.y] == 2; break;
+        case kViaLand: on = map[r.y] == 2 && map[r.z] >= 1; break;
         default: on = false;
       }
     }

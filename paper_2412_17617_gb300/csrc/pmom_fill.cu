@@ -2,12 +2,18 @@
 //
 // Galerkin MPIE, e^{+jwt}:  Z_mn = jw mu0 <f_m, G f_n> + <div f_m, G div f_n> / (jw eps),
 // eps = eps0 eps_r (1 - j tan d) (microstrip: Hammerstad-Jensen eps_eff of a strip w = pitch).
-// Green's function of the homogeneous stack-up:
-//   microstrip  G = g(R) - g(R'), R' to the image below the ground plane z = 0
-//   stripline   Dirichlet function of the plates z = 0, H: for lateral distance rho >= H/2 the
-//               waveguide-mode sum (1/(pi H)) sum_m sin(m pi z/H) sin(m pi z'/H) K0(gamma_m rho);
+// Green's functions of the homogeneous stack-up.  The ground planes mirror horizontal currents and
+// charges with a sign change and vertical (via) currents without one, so the scalar potential and
+// the horizontal part of the vector potential use the Dirichlet function G_D and the vertical part
+// the Neumann function G_N (exact mixed-potential form for a homogeneous medium between PEC planes):
+//   microstrip  G_D = g(R) - g(R'), G_N = g(R) + g(R'), R' to the image below the ground z = 0
+//   stripline   plates z = 0, H: for lateral distance rho >= H/2 the waveguide-mode sums
+//               G_D = (1/(pi H)) sum_{m>=1} sin(m pi z/H) sin(m pi z'/H) K0(gamma_m rho),
+//               G_N = (1/(2 pi H)) [K0(gamma_0 rho) + 2 sum_{m>=1} cos(m pi z/H) cos(m pi z'/H) K0(gamma_m rho)];
 //               below H/2 the images with |n| <= 16 plus a quadratic in rho^2 matched to the mode
-//               sum at rho = H/2, 3H/4, H (the remaining images are smooth and even in rho).
+//               sum at rho = H/2, 3H/4, H (the remaining images are smooth and even in rho), one
+//               quadratic per kernel and pair of heights: the metal layers and the heights of the
+//               quadrature points on vertical via triangles.
 // Triangle pairs related by a lattice translation (same layers, orientations, halves and
 // offset) share one integration: one thread integrates one such class at one frequency
 // (7-point rule x 7-point rule when the centroids are at least two longest edges apart; else
@@ -34,8 +40,10 @@ constexpr int kMaxLayers = 8;
 struct FillTri {
   double v[3][3];
   double c[3];
+  double n[3];          // unit normal
   double area, lmax;
-  int layer;
+  int layer, vert;      // vert: a vertical via triangle
+  int16_t zid[2][13];   // height id of each point of the 7-point (0) and 13-point (1) rule
 };
 
 struct Medium {
@@ -43,8 +51,7 @@ struct Medium {
   double2 k;       // complex wavenumber
   double2 eps;     // complex permittivity
   int stripline;
-  double z[kMaxLayers];
-  int layers;
+  int nz;          // distinct heights (metal layers first, id = layer)
 };
 
 // ------------------------------------------------------------------ complex double helpers
@@ -110,47 +117,98 @@ __device__ double2 bessel_k0(double2 w) {
   return cscale(sum, h);
 }
 
-__device__ double2 strip_modes(const Medium& md, double zp, double zq, double rho) {
+// K0(w) for any Re w >= 0 (the TEM term of G_N lies near the imaginary axis, where the fixed-step
+// rule of bessel_k0 fails): Hankel's asymptotic expansion sqrt(pi/2w) e^-w sum_k a_k for |w| > 17
+// (Abramowitz & Stegun 9.7.2); the ascending series -(ln(w/2) + gamma_E) I0(w) + sum_k
+// (w^2/4)^k H_k / (k!)^2 (A&S 9.6.13) when Re w <= |w|/10; else the trapezoidal rule with its step
+// scaled to the width pi/2 - |arg w| of the strip where exp(-w cosh t) stays bounded.
+__device__ double2 bessel_k0_tem(double2 w) {
+  const double aw = hypot(w.x, w.y);
+  if (aw > 17.0) {
+    double2 a = make_double2(1.0, 0.0), acc = a;
+    const double2 inv8w = cdiv(make_double2(0.125, 0.0), w);
+    for (int k = 1; k < 60; ++k) {
+      const double2 na = cscale(cm(a, inv8w), -(2.0 * k - 1.0) * (2.0 * k - 1.0) / k);
+      if (hypot(na.x, na.y) >= hypot(a.x, a.y)) break;
+      a = na;
+      acc = ca(acc, a);
+      if (hypot(a.x, a.y) < 1e-17) break;
+    }
+    const double2 pre = csqrt_(cdiv(make_double2(0.5 * kPi, 0.0), w));
+    return cm(cm(pre, cexp_(make_double2(-w.x, -w.y))), acc);
+  }
+  if (w.x <= 0.1 * aw) {
+    const double2 q = cscale(cm(w, w), 0.25);
+    double2 t = make_double2(1.0, 0.0), i0 = t, sum = make_double2(0.0, 0.0);
+    double hk = 0.0;
+    for (int k = 1; k < 400; ++k) {
+      t = cscale(cm(t, q), 1.0 / (static_cast<double>(k) * k));
+      hk += 1.0 / k;
+      i0 = ca(i0, t);
+      sum = ca(sum, cscale(t, hk));
+      if (k > aw && hypot(t.x, t.y) * (hk + 1.0) < 1e-18) break;
+    }
+    const double2 lg = make_double2(log(0.5 * aw) + 0.57721566490153286061, atan2(w.y, w.x));
+    return cs(sum, cm(lg, i0));
+  }
+  const double d = 0.5 * kPi - fabs(atan2(w.y, w.x));
+  const double h = fmin(fmin(2.0 * kPi * d / 40.0, 0.2), 0.6 / sqrt(aw));
+  double2 acc = cscale(cexp_(make_double2(-w.x, -w.y)), 0.5);
+  for (int j = 1; j < 200000; ++j) {
+    const double ch = cosh(j * h);
+    if (w.x * (ch - 1.0) > 40.0) break;
+    acc = ca(acc, cexp_(make_double2(-w.x * ch, -w.y * ch)));
+  }
+  return cscale(acc, h);
+}
+
+// kind 0: G_D mode sum; kind 1: G_N mode sum (with the TEM term m = 0)
+__device__ double2 strip_modes(const Medium& md, int kind, double zp, double zq, double rho) {
   double2 s = make_double2(0.0, 0.0);
   const double2 k2 = cm(md.k, md.k);
+  if (kind == 1) s = cscale(bessel_k0_tem(cscale(csqrt_(make_double2(-k2.x, -k2.y)), rho)), 0.5);
   for (int m = 1; m < 4000; ++m) {
     const double km = m * kPi / md.H;
     const double2 gam = csqrt_(make_double2(km * km - k2.x, -k2.y));
     if (gam.x * rho > 40.0) break;
-    const double w = sin(km * zp) * sin(km * zq);
+    const double w = kind == 0 ? sin(km * zp) * sin(km * zq) : cos(km * zp) * cos(km * zq);
     s = ca(s, cscale(bessel_k0(cscale(gam, rho)), w));
   }
   return cscale(s, 1.0 / (kPi * md.H));
 }
 
-// image sum |n| <= kImages; `smooth` replaces the direct term by its R -> 0 regular part
-__device__ double2 strip_images(const Medium& md, double zp, double zq, double rho, bool smooth) {
+// image sum |n| <= kImages (second family subtracted for G_D, added for G_N); `smooth` replaces
+// the direct term by its R -> 0 regular part
+__device__ double2 strip_images(const Medium& md, int kind, double zp, double zq, double rho, bool smooth) {
   double2 s = make_double2(0.0, 0.0);
   const double r2 = rho * rho;
   for (int n = -kImages; n <= kImages; ++n) {
     const double a = zp - zq + 2.0 * n * md.H, b = zp + zq + 2.0 * n * md.H;
     const double Ra = sqrt(r2 + a * a), Rb = sqrt(r2 + b * b);
     s = ca(s, (n == 0 && smooth) ? g_free_smooth(md.k, Ra) : g_free(md.k, Ra));
-    s = cs(s, g_free(md.k, Rb));
+    s = kind == 0 ? cs(s, g_free(md.k, Rb)) : ca(s, g_free(md.k, Rb));
   }
   return s;
 }
 
-// G(rho) between layers lp, lq; smooth = true returns G - 1/(4 pi R_direct).
-__device__ double2 green(const Medium& md, const double2* fit, int lp, int lq, double rho, bool smooth) {
-  const double zp = md.z[lp], zq = md.z[lq];
+// Kernel `kind` between heights z[ip], z[iq] at lateral distance rho; smooth = true returns
+// G - 1/(4 pi R_direct).
+__device__ double2 green(const Medium& md, const double* z, const double2* fit, int kind, int ip, int iq, double rho,
+                         bool smooth) {
+  const double zp = z[ip], zq = z[iq];
   if (!md.stripline) {
     const double Rd = sqrt(rho * rho + (zp - zq) * (zp - zq)), Ri = sqrt(rho * rho + (zp + zq) * (zp + zq));
-    return cs(smooth ? g_free_smooth(md.k, Rd) : g_free(md.k, Rd), g_free(md.k, Ri));
+    const double2 gd = smooth ? g_free_smooth(md.k, Rd) : g_free(md.k, Rd), gi = g_free(md.k, Ri);
+    return kind == 0 ? cs(gd, gi) : ca(gd, gi);
   }
   if (rho >= md.rho_s) {
-    double2 G = strip_modes(md, zp, zq, rho);
+    double2 G = strip_modes(md, kind, zp, zq, rho);
     if (smooth) G.x -= 1.0 / (4.0 * kPi * sqrt(rho * rho + (zp - zq) * (zp - zq)));
     return G;
   }
-  const double2* c = fit + 3 * (lp * md.layers + lq);
+  const double2* c = fit + 3 * ((static_cast<size_t>(kind) * md.nz + ip) * md.nz + iq);
   const double x = rho * rho;
-  return ca(strip_images(md, zp, zq, rho, smooth), ca(c[0], cscale(ca(c[1], cscale(c[2], x)), x)));
+  return ca(strip_images(md, kind, zp, zq, rho, smooth), ca(c[0], cscale(ca(c[1], cscale(c[2], x)), x)));
 }
 
 // ------------------------------------------------------------------ quadrature (barycentric)
@@ -220,58 +278,66 @@ __device__ void potentials(const FillTri& t, const double r[3], double* I1, doub
   Iv[0] = sv[0]; Iv[1] = sv[1]; Iv[2] = sv[2];
 }
 
-__global__ void fit_kernel(const Medium* __restrict__ media, double2* __restrict__ fits, int L) {
-  const int f = blockIdx.x, pq = threadIdx.x;
-  if (pq >= L * L) return;
+// Tail quadratics of both kernels for every pair of heights at frequency blockIdx.x:
+// fits[f][kind][ip][iq][3].
+__global__ void fit_kernel(const Medium* __restrict__ media, const double* __restrict__ z, double2* __restrict__ fits) {
+  const int f = blockIdx.x;
   const Medium md = media[f];
-  double2* c = fits + (static_cast<size_t>(f) * L * L + pq) * 3;
-  if (!md.stripline) {
-    c[0] = c[1] = c[2] = make_double2(0.0, 0.0);
-    return;
+  const int nz = md.nz, pairs = 2 * nz * nz;
+  for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+    double2* c = fits + (static_cast<size_t>(f) * pairs + t) * 3;
+    if (!md.stripline) {
+      c[0] = c[1] = c[2] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const int kind = t / (nz * nz), ip = (t / nz) % nz, iq = t % nz;
+    double x[3];
+    double2 y[3];
+    for (int i = 0; i < 3; ++i) {
+      const double rho = md.rho_s * (1.0 + 0.5 * i);
+      x[i] = rho * rho;
+      y[i] = cs(strip_modes(md, kind, z[ip], z[iq], rho), strip_images(md, kind, z[ip], z[iq], rho, false));
+    }
+    // Lagrange form of the quadratic in x through the three points, expanded to c0 + c1 x + c2 x^2
+    double2 c0 = make_double2(0, 0), c1 = c0, c2 = c0;
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      const double den = (x[i] - x[j]) * (x[i] - x[k]);
+      c2 = ca(c2, cscale(y[i], 1.0 / den));
+      c1 = ca(c1, cscale(y[i], -(x[j] + x[k]) / den));
+      c0 = ca(c0, cscale(y[i], x[j] * x[k] / den));
+    }
+    c[0] = c0; c[1] = c1; c[2] = c2;
   }
-  const int lp = pq / L, lq = pq % L;
-  double x[3];
-  double2 y[3];
-  for (int i = 0; i < 3; ++i) {
-    const double rho = md.rho_s * (1.0 + 0.5 * i);
-    x[i] = rho * rho;
-    y[i] = cs(strip_modes(md, md.z[lp], md.z[lq], rho), strip_images(md, md.z[lp], md.z[lq], rho, false));
-  }
-  // Lagrange form of the quadratic in x through the three points, expanded to c0 + c1 x + c2 x^2
-  double2 c0 = make_double2(0, 0), c1 = c0, c2 = c0;
-  for (int i = 0; i < 3; ++i) {
-    const int j = (i + 1) % 3, k = (i + 2) % 3;
-    const double den = (x[i] - x[j]) * (x[i] - x[k]);
-    c2 = ca(c2, cscale(y[i], 1.0 / den));
-    c1 = ca(c1, cscale(y[i], -(x[j] + x[k]) / den));
-    c0 = ca(c0, cscale(y[i], x[j] * x[k] / den));
-  }
-  c[0] = c0; c[1] = c1; c[2] = c2;
 }
 
 // One thread: integrals of one translation class at one frequency.
-// out[0] = int int G, out[1 + 3a + b] = int int (r - v_a).(r' - v_b) G.
+// out[0] = int int G_D, out[1 + 3a + b] = int int (r - v_a) . G_A (r' - v_b) with G_A = G_D on the
+// horizontal and G_N on the vertical components.
 __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ tris, const int2* __restrict__ rep, int U,
-                                                     const Medium* __restrict__ media, const double2* __restrict__ fits,
-                                                     int L, int F, double2* __restrict__ out) {
+                                                     const Medium* __restrict__ media, const double* __restrict__ z,
+                                                     const double2* __restrict__ fits, int F, double2* __restrict__ out) {
   const long gid = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= static_cast<long>(U) * F) return;
   const int f = static_cast<int>(gid / U), u = static_cast<int>(gid % U);
   const Medium md = media[f];
-  const double2* fit = fits + static_cast<size_t>(f) * L * L * 3;
-  const FillTri p = tris[rep[u].x];
-  const FillTri q = tris[rep[u].y];
+  const double2* fit = fits + static_cast<size_t>(f) * 2 * md.nz * md.nz * 3;
+  const FillTri& p = tris[rep[u].x];
+  const FillTri& q = tris[rep[u].y];
   double2 acc[10];
   for (int i = 0; i < 10; ++i) acc[i] = make_double2(0.0, 0.0);
   const double dc = sqrt((p.c[0] - q.c[0]) * (p.c[0] - q.c[0]) + (p.c[1] - q.c[1]) * (p.c[1] - q.c[1]) +
                          (p.c[2] - q.c[2]) * (p.c[2] - q.c[2]));
   const double lmax = fmax(p.lmax, q.lmax);
   const bool near = dc < 2.0 * lmax * (1.0 + 1e-9);
-  const int nq = near ? 13 : 7;
+  const bool both_vert = p.vert && q.vert;
+  const int nq = near ? 13 : 7, rs = near ? 1 : 0;
   const double(*Q)[4] = near ? kQ13 : kQ7;
   for (int i = 0; i < nq; ++i) {
+    const int ip = p.zid[rs][i];
     double r[3];
-    for (int k = 0; k < 3; ++k) r[k] = Q[i][0] * p.v[0][k] + Q[i][1] * p.v[1][k] + Q[i][2] * p.v[2][k];
+    for (int k = 0; k < 2; ++k) r[k] = Q[i][0] * p.v[0][k] + Q[i][1] * p.v[1][k] + Q[i][2] * p.v[2][k];
+    r[2] = z[ip];
     const double wo = Q[i][3] * p.area;
     double ra[3][3];
     for (int a = 0; a < 3; ++a)
@@ -281,7 +347,9 @@ __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ 
       potentials(q, r, &I1, Iv);
       const double s = wo / (4.0 * kPi);
       acc[0].x += s * I1;
-      const double r0[3] = {r[0], r[1], q.v[0][2]};
+      // projection of r on the plane of q
+      const double d = q.n[0] * (r[0] - q.v[0][0]) + q.n[1] * (r[1] - q.v[0][1]) + q.n[2] * (r[2] - q.v[0][2]);
+      const double r0[3] = {r[0] - d * q.n[0], r[1] - d * q.n[1], r[2] - d * q.n[2]};
       for (int b = 0; b < 3; ++b) {
         double tv[3];
         for (int k = 0; k < 3; ++k) tv[k] = Iv[k] + (r0[k] - q.v[b][k]) * I1;
@@ -289,15 +357,20 @@ __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ 
       }
     }
     for (int j = 0; j < nq; ++j) {
+      const int iq = q.zid[rs][j];
       double rq[3];
-      for (int k = 0; k < 3; ++k) rq[k] = Q[j][0] * q.v[0][k] + Q[j][1] * q.v[1][k] + Q[j][2] * q.v[2][k];
+      for (int k = 0; k < 2; ++k) rq[k] = Q[j][0] * q.v[0][k] + Q[j][1] * q.v[1][k] + Q[j][2] * q.v[2][k];
+      rq[2] = z[iq];
       const double rho = hypot(r[0] - rq[0], r[1] - rq[1]);
-      const double2 G = cscale(green(md, fit, p.layer, q.layer, rho, near), wo * Q[j][3] * q.area);
-      acc[0] = ca(acc[0], G);
+      const double w = wo * Q[j][3] * q.area;
+      const double2 GD = cscale(green(md, z, fit, 0, ip, iq, rho, near), w);
+      const double2 GN = both_vert ? cscale(green(md, z, fit, 1, ip, iq, rho, near), w) : make_double2(0.0, 0.0);
+      acc[0] = ca(acc[0], GD);
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-          const double dd = ra[a][0] * (rq[0] - q.v[b][0]) + ra[a][1] * (rq[1] - q.v[b][1]) + ra[a][2] * (rq[2] - q.v[b][2]);
-          acc[1 + 3 * a + b] = ca(acc[1 + 3 * a + b], cscale(G, dd));
+          const double dh = ra[a][0] * (rq[0] - q.v[b][0]) + ra[a][1] * (rq[1] - q.v[b][1]);
+          const double dz = ra[a][2] * (rq[2] - q.v[b][2]);
+          acc[1 + 3 * a + b] = ca(acc[1 + 3 * a + b], ca(cscale(GD, dh), cscale(GN, dz)));
         }
     }
   }
@@ -360,31 +433,54 @@ double hj_eps_eff(const Grid& g) {
   return 0.5 * (er + 1.0) + 0.5 * (er - 1.0) * std::pow(1.0 + 10.0 / u, -a * b);
 }
 
+// Geometry of a triangle key (half 0, 1: the pixel's triangles; 2, 3: the via strip's Ta, Tb).
 void key_triangle(const Grid& g, int32_t key, FillTri* t) {
-  const int half = key & 1;
-  int k = key >> 1;
+  const int half = key & 3;
+  int k = key >> 2;
   const int x = k % 128 - 4;
   k /= 128;
   const int y = k % 128 - 4;
   const int layer = k / 128;
   static const int corner[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
   static const int tri[2][2][3] = {{{0, 1, 2}, {1, 3, 2}}, {{0, 1, 3}, {0, 3, 2}}};
+  static const int dend[2][2] = {{2, 1}, {0, 3}};   // diagonal end corners D0, D1 per orientation
   const int o = (x + y) & 1;
+  if (half < 2) {
+    for (int i = 0; i < 3; ++i) {
+      const int cc = tri[o][half][i];
+      t->v[i][0] = (x + corner[cc][0]) * g.pitch;
+      t->v[i][1] = (y + corner[cc][1]) * g.pitch;
+      t->v[i][2] = g.layer_z[layer];
+    }
+  } else {
+    // Ta = (D0@l, D1@l, D1@l+1), Tb = (D0@l, D1@l+1, D0@l+1)
+    const int cs3[2][3] = {{dend[o][0], dend[o][1], dend[o][1]}, {dend[o][0], dend[o][1], dend[o][0]}};
+    const int up[2][3] = {{0, 0, 1}, {0, 1, 1}};
+    for (int i = 0; i < 3; ++i) {
+      const int cc = cs3[half - 2][i];
+      t->v[i][0] = (x + corner[cc][0]) * g.pitch;
+      t->v[i][1] = (y + corner[cc][1]) * g.pitch;
+      t->v[i][2] = g.layer_z[layer + up[half - 2][i]];
+    }
+  }
+  double e1[3], e2[3];
+  for (int i = 0; i < 3; ++i) { e1[i] = t->v[1][i] - t->v[0][i]; e2[i] = t->v[2][i] - t->v[0][i]; }
+  const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   double lmax = 0.0;
   for (int i = 0; i < 3; ++i) {
-    const int cc = tri[o][half][i];
-    t->v[i][0] = (x + corner[cc][0]) * g.pitch;
-    t->v[i][1] = (y + corner[cc][1]) * g.pitch;
-    t->v[i][2] = g.layer_z[layer];
-  }
-  for (int i = 0; i < 3; ++i) {
+    t->n[i] = n[i] / nn;
     t->c[i] = (t->v[0][i] + t->v[1][i] + t->v[2][i]) / 3.0;
-    const double dx = t->v[(i + 1) % 3][0] - t->v[i][0], dy = t->v[(i + 1) % 3][1] - t->v[i][1];
-    lmax = std::max(lmax, std::sqrt(dx * dx + dy * dy));
+    const int j = (i + 1) % 3;
+    const double dx = t->v[j][0] - t->v[i][0], dy = t->v[j][1] - t->v[i][1], dz = t->v[j][2] - t->v[i][2];
+    lmax = std::max(lmax, std::sqrt(dx * dx + dy * dy + dz * dz));
   }
-  t->area = 0.5 * g.pitch * g.pitch;
+  t->area = 0.5 * nn;
   t->lmax = lmax;
   t->layer = layer;
+  t->vert = half >= 2;
+  for (int r = 0; r < 2; ++r)
+    for (int i = 0; i < 13; ++i) t->zid[r][i] = static_cast<int16_t>(layer);
 }
 
 }  // namespace
@@ -411,17 +507,36 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
       }
     }
   const int T = static_cast<int>(tris.size());
+  double q7[7][4], q13[13][4];
+  host_rules(q7, q13);
+  // heights visited by the quadrature: the layers, then the points of vertical triangles
+  std::vector<double> heights(g.layer_z.begin(), g.layer_z.end());
+  for (FillTri& t : tris) {
+    if (!t.vert) continue;
+    for (int r = 0; r < 2; ++r) {
+      const int n = r ? 13 : 7;
+      for (int i = 0; i < n; ++i) {
+        const double* b = r ? q13[i] : q7[i];
+        const double zz = t.v[0][2] + b[1] * (t.v[1][2] - t.v[0][2]) + b[2] * (t.v[2][2] - t.v[0][2]);
+        size_t id = 0;
+        while (id < heights.size() && heights[id] != zz) ++id;
+        if (id == heights.size()) heights.push_back(zz);
+        t.zid[r][i] = static_cast<int16_t>(id);
+      }
+    }
+  }
+  const int nz = static_cast<int>(heights.size());
   // translation classes
   std::unordered_map<long long, int> cls_of;
   std::vector<int2> rep;
   std::vector<int> pair_class(static_cast<size_t>(T) * T);
   for (int p = 0; p < T; ++p) {
     const int32_t kp = keys[p];
-    const int hp = kp & 1, xp = (kp >> 1) % 128, yp = ((kp >> 1) / 128) % 128, lp = (kp >> 1) / (128 * 128);
+    const int hp = kp & 3, xp = (kp >> 2) % 128, yp = ((kp >> 2) / 128) % 128, lp = (kp >> 2) / (128 * 128);
     for (int q = 0; q < T; ++q) {
       const int32_t kq = keys[q];
-      const int hq = kq & 1, xq = (kq >> 1) % 128, yq = ((kq >> 1) / 128) % 128, lq = (kq >> 1) / (128 * 128);
-      const long long key = ((((((static_cast<long long>(lp) * 8 + lq) * 2 + ((xp + yp) & 1)) * 2 + hp) * 2 + hq) * 512 +
+      const int hq = kq & 3, xq = (kq >> 2) % 128, yq = ((kq >> 2) / 128) % 128, lq = (kq >> 2) / (128 * 128);
+      const long long key = ((((((static_cast<long long>(lp) * 8 + lq) * 2 + ((xp + yp) & 1)) * 4 + hp) * 4 + hq) * 512 +
                               (xq - xp + 256)) * 512) + (yq - yp + 256);
       auto it = cls_of.find(key);
       int c;
@@ -463,12 +578,10 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
     md.stripline = g.medium == 1;
     md.H = g.h_total;
     md.rho_s = 0.5 * g.h_total;
-    md.layers = g.layers;
-    for (int l = 0; l < kMaxLayers; ++l) md.z[l] = l < g.layers ? g.layer_z[l] : 0.0;
+    md.nz = nz;
   }
-  double q7[7][4], q13[13][4];
-  host_rules(q7, q13);
   FillTri* d_tris = nullptr;
+  double* d_z = nullptr;
   int2* d_rep = nullptr;
   int* d_pc = nullptr;
   BfGeom* d_bfs = nullptr;
@@ -486,7 +599,8 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   chk(cudaMalloc(&d_pc, sizeof(int) * pair_class.size()));
   chk(cudaMalloc(&d_bfs, sizeof(BfGeom) * M));
   chk(cudaMalloc(&d_media, sizeof(Medium) * F));
-  chk(cudaMalloc(&d_fit, sizeof(double2) * 3 * g.layers * g.layers * F));
+  chk(cudaMalloc(&d_z, sizeof(double) * nz));
+  chk(cudaMalloc(&d_fit, sizeof(double2) * 3 * 2 * static_cast<size_t>(nz) * nz * F));
   chk(cudaMalloc(&d_cls, sizeof(double2) * 10 * static_cast<size_t>(U) * F));
   chk(cudaMalloc(&d_Z, zel * static_cast<size_t>(F) * M * M));
   if (e == cudaSuccess) {
@@ -495,12 +609,13 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
     chk(cudaMemcpyAsync(d_pc, pair_class.data(), sizeof(int) * pair_class.size(), cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(d_bfs, bfs.data(), sizeof(BfGeom) * M, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(d_media, media.data(), sizeof(Medium) * F, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(d_z, heights.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
   }
   if (e == cudaSuccess) {
-    fit_kernel<<<F, 64, 0, s>>>(d_media, d_fit, g.layers);
+    fit_kernel<<<F, 128, 0, s>>>(d_media, d_z, d_fit);
     chk(cudaGetLastError());
     const long work = static_cast<long>(U) * F;
-    class_kernel<<<static_cast<unsigned>((work + 127) / 128), 128, 0, s>>>(d_tris, d_rep, U, d_media, d_fit, g.layers, F, d_cls);
+    class_kernel<<<static_cast<unsigned>((work + 127) / 128), 128, 0, s>>>(d_tris, d_rep, U, d_media, d_z, d_fit, F, d_cls);
     chk(cudaGetLastError());
     const dim3 grid(static_cast<unsigned>((static_cast<long>(M) * M + 255) / 256), F);
     if (dtype == PMOM_C128)
@@ -516,6 +631,7 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   cudaFree(d_bfs);
   cudaFree(d_media);
   cudaFree(d_fit);
+  cudaFree(d_z);
   cudaFree(d_cls);
   if (e != cudaSuccess) {
     if (d_Z) cudaFree(d_Z);

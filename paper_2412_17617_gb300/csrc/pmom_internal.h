@@ -14,8 +14,10 @@ namespace pmom {
 constexpr int kMaxPorts = 4;
 constexpr int kTableCols = 8;
 
-// Activation rule of one basis function, as the kernels read it.
-enum RuleKind : int32_t { kAlways = 0, kInner = 1, kInter = 2, kPixPort = 3 };
+// Activation rule of one basis function, as the kernels read it.  kVia*: the three BFs of a via
+// site (state 2: metal plus a vertical strip up to the next layer): the strip's own diagonal, its
+// junction with the via pixel, and its junction with the pixel above (active when that one is metal).
+enum RuleKind : int32_t { kAlways = 0, kInner = 1, kInter = 2, kPixPort = 3, kViaStrip = 4, kViaJoin = 5, kViaLand = 6 };
 
 struct Grid {
   int layers = 0, nx = 0, ny = 0, medium = 0, n_states = 2, n_ports = 0;
@@ -23,6 +25,9 @@ struct Grid {
   std::vector<double> layer_z;
   std::vector<pmom_port> ports;
   int pixels() const { return layers * nx * ny; }
+  bool vias() const { return n_states >= 3 && layers >= 2; }
+  // first pixel index that cannot hold the via state (the last layer has no layer above it)
+  int via_top() const { return vias() ? (layers - 1) * nx * ny : pixels(); }
 };
 
 // Grid of a context (pmom_api.cu).
@@ -35,6 +40,7 @@ int build_bf_table(const Grid& g, std::vector<int32_t>& table);
 struct EvalArgs {
   const int4* rules;       // [M] {kind, pixA, pixB, 0}
   int M, P, F, B, npix, n_states;
+  int via_top;             // pixels at index >= via_top reject state 2 (Grid::via_top)
   const uint8_t* maps;     // [B][npix]
   int32_t* idx;            // [B][M]
   int32_t* n_act;          // [B]

@@ -2,6 +2,13 @@
 // Section V-A; corner-only contact is no connection, Section VI-A).  Table-driven: the two
 // halves of a pixel, which half owns each pixel side, and which triangle corner is the free RWG
 // vertex are fixed per diagonal orientation and looked up instead of searched.
+//
+// Via state (grids with three pixel states; the paper leaves vias to future work, Section VII):
+// a vertical strip stands on the pixel diagonal D0-D1 from layer l to layer l+1, cut along
+// D0@l - D1@l+1 into the triangles Ta = (D0@l, D1@l, D1@l+1) and Tb = (D0@l, D1@l+1, D0@l+1)
+// (triangle keys with half 2 and 3).  Its three BFs follow the pixel-port BFs, per via layer and
+// pixel row-major: strip diagonal (Ta -> Tb), junction with half 0 of the via pixel (half 0 -> Ta)
+// and junction with half 0 of the pixel above (Tb -> that half).
 #include "pmom_internal.h"
 
 namespace pmom {
@@ -24,7 +31,8 @@ constexpr HalfFree kSideOwner[2][4] = {
 // Free vertex of each half for the pixel's own diagonal.
 constexpr int8_t kDiagFree[2][2] = {{0, 1}, {1, 2}};
 
-int32_t tri_key(int layer, int x, int y, int half) { return ((layer * 128 + (y + 4)) * 128 + (x + 4)) * 2 + half; }
+// half 0, 1: the pixel's own triangles; 2, 3: Ta, Tb of the via strip standing on it
+int32_t tri_key(int layer, int x, int y, int half) { return ((layer * 128 + (y + 4)) * 128 + (x + 4)) * 4 + half; }
 
 void put_diag(int32_t* r, int layer, int x, int y) {
   const int o = (x + y) & 1;
@@ -67,7 +75,8 @@ void stub(const Grid& g, const pmom_port& p, int s1[2], int s2[2], int gp[2]) {
 }  // namespace
 
 int build_bf_table(const Grid& g, std::vector<int32_t>& t) {
-  const int M = 4 * g.n_ports + g.layers * (g.nx * g.ny + (g.nx - 1) * g.ny + g.nx * (g.ny - 1));
+  const int M = 4 * g.n_ports + g.layers * (g.nx * g.ny + (g.nx - 1) * g.ny + g.nx * (g.ny - 1)) +
+                (g.vias() ? 3 * (g.layers - 1) * g.nx * g.ny : 0);
   t.assign(static_cast<size_t>(M) * kTableCols, -1);
   int m = 0;
   auto row = [&](int kind, int pa, int pb, int port) {
@@ -97,6 +106,18 @@ int build_bf_table(const Grid& g, std::vector<int32_t>& t) {
     stub(g, g.ports[p], s1, s2, gp);
     put_side(row(kPixPort, pix(l, gp[0], gp[1]), -1, p), l, s1[0], s1[1], gp[0], gp[1]);
   }
+  if (g.vias())
+    for (int l = 0; l + 1 < g.layers; ++l)
+      for (int y = 0; y < g.ny; ++y)
+        for (int x = 0; x < g.nx; ++x) {
+          const int8_t f0 = kDiagFree[(x + y) & 1][0];   // corner of half 0 off the diagonal
+          int32_t* r = row(kViaStrip, pix(l, x, y), -1, -1);
+          r[4] = tri_key(l, x, y, 2); r[5] = tri_key(l, x, y, 3); r[6] = 1; r[7] = 2;
+          r = row(kViaJoin, pix(l, x, y), -1, -1);
+          r[4] = tri_key(l, x, y, 0); r[5] = tri_key(l, x, y, 2); r[6] = f0; r[7] = 2;
+          r = row(kViaLand, pix(l, x, y), pix(l + 1, x, y), -1);
+          r[4] = tri_key(l, x, y, 3); r[5] = tri_key(l + 1, x, y, 0); r[6] = 0; r[7] = f0;
+        }
   return M;
 }
 

@@ -237,3 +237,31 @@ def all_maps(grid: Grid) -> np.ndarray:
     codes = np.arange(1 << n, dtype=np.int64)
     bits = ((codes[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
     return np.ascontiguousarray(bits.reshape(-1, grid.layers, grid.ny, grid.nx))
+
+
+def seed_map_vias(grid: Grid, fill: float, via_frac: float, seed: int) -> np.ndarray:
+    """uint8 [layers][ny][nx] with three states: each pixel metal with probability `fill`; a
+    metal pixel below the last layer is a via (state 2) with probability `via_frac`."""
+    g = rng(seed)
+    shape = (grid.layers, grid.ny, grid.nx)
+    m = (g.random(shape) < fill).astype(np.uint8)
+    v = (g.random(shape) < via_frac) & (m == 1)
+    v[-1] = False
+    m[v] = 2
+    return m
+
+
+def state_changes(seed: np.ndarray, depth: int, count: int, rng_seed: int) -> np.ndarray:
+    """`count` candidates that each change `depth` distinct pixels of a three-state map to another
+    state, drawn uniformly among the pixel's valid states (the last layer has no via state).
+    Shape [count][layers][ny][nx], uint8."""
+    g = rng(rng_seed)
+    L, ny, nx = seed.shape
+    out = np.repeat(seed[None], count, axis=0).astype(np.uint8)
+    flat = out.reshape(count, -1)
+    for c in range(count):
+        for j in g.choice(flat.shape[1], size=depth, replace=False):
+            k = 2 if j >= (L - 1) * ny * nx else 3
+            s = int(g.integers(k - 1))
+            flat[c, j] = s if s < flat[c, j] else s + 1
+    return np.ascontiguousarray(out)

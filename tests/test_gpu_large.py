@@ -1,9 +1,11 @@
 """GPU parity for support sets beyond the default shared-memory layout (N of one to several
 thousand): the narrow-panel layout with the solve vectors in global memory, against the oracle.
 
-The grid is the 3-layer 20 x 20 stripline of the batching workload with on/off pixels; candidates
-are depth-1..3 changes of seeded maps of different fill, so one launch mixes support sets from
-about 1000 to 2400 (uneven work in one persistent queue).  Two frequencies of the 0.5-8 GHz sweep.
+The grid is the 3-layer 20 x 20 stripline of the batching workload with three pixel states
+(void / metal / via to the next layer, M = 5892); candidates are depth-1..3 changes of seeded
+three-state maps of different fill, so one launch mixes support sets from about 950 to 2500
+(uneven work in one persistent queue).  Two frequencies of the 0.5-8 GHz sweep.  The oracle's
+reference is its LAPACK-backed route (same definition, pinned against its plain LU).
 """
 import numpy as np
 import pytest
@@ -22,19 +24,20 @@ def large_case():
     from paper_2412_17617_gb300 import build as B
     B.build()
     from paper_2412_17617_gb300 import pmom
-    g = PI.grid_stripline_20x20x3(n_states=2)
+    g = PI.grid_stripline_20x20x3(n_states=3)
     OG = O.Grid(g)
+    assert OG.M == 5892
     Z, _ = O.fill(OG, FREQS)
     Z64 = Z.astype(np.complex64)
     del Z
     maps = []
     for k, fill in enumerate((0.35, 0.55, 0.75)):
-        seed = PI.seed_map(g, fill, 40 + k)
-        maps.append(PI.depth_flips(seed, 1 + k, 2, 2, 90 + k))
+        seed = PI.seed_map_vias(g, fill, 0.2, 40 + k)
+        maps.append(PI.state_changes(seed, 1 + k, 2, 90 + k))
     maps = np.ascontiguousarray(np.concatenate(maps))
+    assert (maps == 2).any(axis=(1, 2, 3)).all()
     N = np.array([len(O.active_set(OG, m)) for m in maps])
-    S_ref, st = O.eval_batch(OG, Z64, maps)
-    assert (st == 0).all()
+    S_ref = np.stack([O.eval_map_lapack(OG, Z64, m) for m in maps])
     band = O.bands(FREQS, PI.UNII_BANDS)
     fom_ref = O.fom_batch(S_ref, band)
     ev = pmom.Evaluator(g)

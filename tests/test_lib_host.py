@@ -33,6 +33,10 @@ def _grids():
     ports = (PI.Port(0, 0, 0), PI.Port(0, 1, 4), PI.Port(1, 2, 2), PI.Port(1, 3, 0))
     gs.append(PI.Grid("sides_5x3x2", 2, 5, 3, 1e-3, PI.MEDIUM_STRIPLINE, (0.5e-3, 1.0e-3), 1.5e-3, 3.66, 0.004, 2,
                       ports))
+    # three-state grids (via BFs after the pixel-port BFs)
+    gs.append(PI.Grid("sides_5x3x2_via", 2, 5, 3, 1e-3, PI.MEDIUM_STRIPLINE, (0.5e-3, 1.0e-3), 1.5e-3, 3.66, 0.004, 3,
+                      ports))
+    gs.append(PI.grid_stripline_20x20x3(n_states=3))
     return gs
 
 
@@ -57,9 +61,14 @@ def test_argument_validation(lib):
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(bad)
     assert e.value.status == 1
+    # a via needs a layer above it
     three = PI.Grid("via", 1, 3, 3, 1e-3, 0, (0.5e-3,), 0.5e-3, 3.5, 0.0, 3, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(three)
+    assert e.value.status == 1
+    four = PI.Grid("four", 2, 3, 3, 1e-3, 0, (0.5e-3, 1e-3), 1e-3, 3.5, 0.0, 4, (PI.Port(0, 0, 1),))
+    with pytest.raises(pmom.PmomError) as e:
+        pmom.Evaluator(four)
     assert e.value.status == 7
     ev = pmom.Evaluator(g)
     with pytest.raises(pmom.PmomError) as e:
