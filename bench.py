@@ -103,7 +103,8 @@ class Clocks:
 
 
 def workload(name: str):
-    return {"precision": PI.workload_precision, "plain": PI.workload_plain, "profile": PI.workload_profile}[name]()
+    return {"precision": PI.workload_precision, "plain": PI.workload_plain, "profile": PI.workload_profile,
+            "batching": PI.workload_batching}[name]()
 
 
 def lu_flops(N: np.ndarray, F: int, P: int) -> float:
@@ -246,7 +247,8 @@ def run_ours(args):
     status_np = status.cpu().numpy()
     value = aggregate_rate(world, Bsz, ms)
     # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
-    nfp = min(Bsz, 32)
+    three_state = w.grid.n_states == 3
+    nfp = min(Bsz, 8 if three_state else 32)
     sub = maps[:nfp]
     S_mixed, fom_mixed = S[:nfp].clone(), fom[:nfp].clone()
     sub_out = (S[:nfp], fom[:nfp], status[:nfp])
@@ -268,7 +270,7 @@ def run_ours(args):
     #      reference factors and inverse per frequency, k x k updates per candidate, recomputed
     #      every step
     bordered = None
-    if args.bordered:
+    if args.bordered and not three_state:   # the three-state batch changes several seeds, not one reference
         seed_d = torch.from_numpy(PI.seed_map(w.grid, w.fill, rank)).cuda()
         Sb, fb, sb = torch.empty_like(S), torch.empty_like(fom), torch.empty_like(status)
         for _ in range(args.warmup):
@@ -307,6 +309,7 @@ def run_ours(args):
     peaks = _peaks()
     eval_ms = float(np.median(kern_ms)) if kern_ms else ms
     flops = lu_flops(N, w.n_freq, ev.P)
+    large = int(N.max()) > ev.capacity("mixed")[0]
     achieved = flops / (eval_ms * 1e-3) / 1e12
     alu_peak = FP32_LANES_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
     if tc_choice:
@@ -316,7 +319,7 @@ def run_ours(args):
         peak = bf16 * 1.1 / 2.25
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_LAUNCH.get((w.name, "tc")) if Bsz == w.batch else None,
-                "kernel": "eval_kernel<float2,float2,mixed,tc>",
+                "kernel": "eval_kernel<float2,float2,mixed,tc%s>" % (",large" if large else ""),
                 "peak_source": "measured bf16 %.1f TFLOP/s x 1.1/2.25 (TF32 dense); %s" % (
                     bf16, "of measured" if peaks.get("bf16_tflops") else "of fallback"),
                 "frac_of_3xtf32_peak": achieved / (peak / 3.0), "frac_of_fp32_alu": achieved / alu_peak}
@@ -330,7 +333,10 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "c64 LU + f64 refinement", "data": "synthetic",
         "config": {"workload": w.name, "global_batch": Bsz * world, "freqs": w.n_freq, "M": ev.M,
                    "N_mean": float(N.mean()), "N_min": int(N.min()), "N_max": int(N.max()),
-                   "l2": "inputs larger than L2 (Z database 0.72 GB)", "parallelism": f"replicas x{world}"},
+                   "N_hist": [[int(e) for e in np.histogram(N, bins=6)[1]], [int(c) for c in np.histogram(N, bins=6)[0]]],
+                   "l2": "inputs larger than L2 (Z database %.2f GB)" % (
+                       w.n_freq * ev.M * ev.M * (8 if w.z_dtype == "c64" else 16) / 1e9),
+                   "parallelism": f"replicas x{world}"},
         "fp64_path": {"value": fp64_value, "unit": "candidate evals/s", "candidates": nfp,
                       "speedup_mixed_over_fp64": value / fp64_value},
         "accuracy": accuracy(S_mixed, fom_mixed),
@@ -362,8 +368,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="precision", choices=["precision", "plain", "profile"],
-                    help="profile: a smaller grid running the same kernels, for counter captures")
+    ap.add_argument("--workload", default="precision", choices=["precision", "plain", "profile", "batching"],
+                    help="profile: a smaller grid running the same kernels, for counter captures; batching: "
+                         "the 3-layer 20x20 three-state stripline, 101 frequencies, uneven support sets "
+                         "(use --batch to bound it)")
     ap.add_argument("--batch", type=int, default=0, help="evaluate only the first B candidates")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-bordered", dest="bordered", action="store_false",

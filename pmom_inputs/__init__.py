@@ -222,7 +222,10 @@ def random_maps(grid: Grid, count: int, fill: float, seed: int) -> np.ndarray:
 
 
 def workload_maps(w: Workload, seed: int = 0) -> np.ndarray:
-    """The candidate batch of a workload: all single flips of a seeded map, trimmed/tiled to w.batch."""
+    """The candidate batch of a workload: all single flips of a seeded map, trimmed/tiled to w.batch
+    (three-state grids: `batching_maps`)."""
+    if w.grid.n_states == 3:
+        return batching_maps(w, seed)
     base = seed_map(w.grid, w.fill, seed)
     flips = single_flip_batch(base, 2)
     if flips.shape[0] >= w.batch:
@@ -264,4 +267,20 @@ def state_changes(seed: np.ndarray, depth: int, count: int, rng_seed: int) -> np
             k = 2 if j >= (L - 1) * ny * nx else 3
             s = int(g.integers(k - 1))
             flat[c, j] = s if s < flat[c, j] else s + 1
+    return np.ascontiguousarray(out)
+
+
+BATCHING_FILLS = tuple(float(f) for f in np.linspace(0.35, 0.75, 8))
+
+
+def batching_maps(w: Workload, seed: int = 0, count: int = 0) -> np.ndarray:
+    """Candidates of the three-state batching workload: eight seed maps of per-layer fill 0.35 ..
+    0.75 (20 % of the metal pixels below the top layer are vias), candidate i changing 1 + (i // 8) % 3
+    random pixels of seed i % 8, so every prefix of the batch spans the support-set sizes of all
+    seeds (about 950 to 2500 on the 20 x 20 x 3 grid).  Shape [count][layers][ny][nx], uint8."""
+    count = count or w.batch
+    seeds = [seed_map_vias(w.grid, f, 0.2, 1000 * seed + k) for k, f in enumerate(BATCHING_FILLS)]
+    out = np.empty((count, w.grid.layers, w.grid.ny, w.grid.nx), np.uint8)
+    for i in range(count):
+        out[i] = state_changes(seeds[i % len(seeds)], 1 + (i // len(seeds)) % 3, 1, 7919 * seed + i)[0]
     return np.ascontiguousarray(out)
