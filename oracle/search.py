@@ -4,15 +4,18 @@ TEST INFRASTRUCTURE ONLY (oracle side): it evaluates candidates with the CPU ora
 library's native search (pmom_search) is checked against it decision by decision.
 
 Readings where Algorithm 1 leaves a choice open:
-  * a pixel is one (x, y) column; its state is the bit pattern of its layers (K = 2**layers
-    states), so a node has K - 1 children, one per other state of the chosen column;
+  * a pixel is one (x, y) column; its state is the pattern of its layers' states, a mixed-radix
+    number with layer 0 as the lowest digit (radix 2 per layer; radix 3 for the layers below the
+    last one on a grid with the via state), so K = 2**layers states on an on/off grid; a node has
+    K - 1 children, one per other state of the chosen column;
   * the column j of node (d, k) is drawn uniformly from the columns not yet on the node's path,
     with the counter-based SplitMix64 generator keyed by (seed, restart, iteration, d, k);
   * every child at every depth is evaluated; the best leaf is the argmin over depth-D leaves
     only (ties: lowest leaf index); it is accepted if strictly better than the current F;
   * after M(D) consecutive non-improving iterations the depth grows; when it would exceed Dmax
-    the search restarts from a random map (each layer pixel metal with probability 1/2, drawn by
-    the same generator) at depth 1, keeping the global best;
+    the search restarts from a random map (each layer pixel metal with probability 1/2 from the top
+    bit of the same generator; on a grid with vias a metal pixel below the last layer is a via when
+    the next bit is set) at depth 1, keeping the global best;
   * the search stops once the evaluation budget is used up (a started tree is finished);
   * a candidate whose evaluation failed (non-finite FoM) counts as +infinity.
 """
@@ -39,34 +42,48 @@ def key(*parts: int) -> int:
     return h
 
 
-def random_map(seed: int, restart: int, shape) -> np.ndarray:
+def radices(L: int, n_states: int = 2):
+    """Number of states of each layer's pixel in a column (the last layer holds no via)."""
+    return [3 if (n_states >= 3 and l < L - 1) else 2 for l in range(L)]
+
+
+def random_map(seed: int, restart: int, shape, n_states: int = 2) -> np.ndarray:
     L, ny, nx = shape
     out = np.zeros(shape, np.uint8)
     for i in range(L * ny * nx):
-        out.flat[i] = key(seed, 0xA5A5, restart, i) >> 63
+        u = key(seed, 0xA5A5, restart, i)
+        s = u >> 63
+        if s and n_states >= 3 and i < (L - 1) * ny * nx:
+            s = 1 + ((u >> 62) & 1)
+        out.flat[i] = s
     return out
 
 
-def column_state(m: np.ndarray, j: int) -> int:
+def column_state(m: np.ndarray, j: int, n_states: int = 2) -> int:
     L, ny, nx = m.shape
     y, x = divmod(j, nx)
-    return sum(int(m[l, y, x]) << l for l in range(L))
+    v, w = 0, 1
+    for l, r in enumerate(radices(L, n_states)):
+        v += int(m[l, y, x]) * w
+        w *= r
+    return v
 
 
-def set_column(m: np.ndarray, j: int, s: int) -> np.ndarray:
+def set_column(m: np.ndarray, j: int, s: int, n_states: int = 2) -> np.ndarray:
     L, ny, nx = m.shape
     y, x = divmod(j, nx)
     c = m.copy()
-    for l in range(L):
-        c[l, y, x] = (s >> l) & 1
+    for l, r in enumerate(radices(L, n_states)):
+        c[l, y, x] = s % r
+        s //= r
     return c
 
 
-def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, max_evals: int):
+def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, max_evals: int, n_states: int = 2):
     """evaluate(maps[B][L][ny][nx]) -> FoM[B].  Returns (best_map, best_F, evals, trace) where
     trace[i] is the current F after iteration i."""
     L, ny, nx = init_map.shape
-    ncol, K = ny * nx, 1 << L
+    ncol, K = ny * nx, int(np.prod(radices(L, n_states)))
 
     def F_of(maps):
         f = np.asarray(evaluate(np.ascontiguousarray(maps)), dtype=np.float64)
@@ -86,10 +103,10 @@ def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, m
             for k, (S, Pn) in enumerate(nodes):
                 free = [c for c in range(ncol) if c not in S]
                 j = free[key(seed, restart, it, d, k) % len(free)]
-                cur = column_state(Pn, j)
+                cur = column_state(Pn, j, n_states)
                 for s in range(K):
                     if s != cur:
-                        children.append((S | {j}, set_column(Pn, j, s)))
+                        children.append((S | {j}, set_column(Pn, j, s, n_states)))
             Fs = F_of(np.stack([c[1] for c in children]))
             evals += len(children)
             nodes = children
@@ -106,7 +123,7 @@ def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, m
             counter = 0
         if D > d_max:
             restart += 1
-            P = random_map(seed, restart, (L, ny, nx))
+            P = random_map(seed, restart, (L, ny, nx), n_states)
             F = float(F_of(P[None])[0])
             evals += 1
             D, counter = 1, 0

@@ -1,14 +1,17 @@
 // Depth-increasing all-way tree search (paper Algorithm 1, Section III-A) over the GPU evaluator.
 //
 // Each level of a tree is evaluated as one batch through the evaluator.  Readings where the
-// algorithm leaves a choice open: a pixel is an (x, y) column whose state is the bit pattern of
-// its layers (K = 2^layers), so every node branches into the K - 1 other states of its chosen
-// column; the column is drawn uniformly among those not yet on the node's path with a
-// counter-based SplitMix64 generator keyed by (seed, restart, iteration, depth, node); the best
-// depth-D leaf (lowest index on ties) is accepted only if strictly better; after M(D) failures
-// the depth grows, and past Dmax the search restarts from a random half-filled map at depth 1,
-// keeping the global best; it stops once the evaluation budget is spent (a started tree is
-// finished).  A candidate whose evaluation failed counts as +infinity.
+// algorithm leaves a choice open: a pixel is an (x, y) column whose state is the pattern of its
+// layers' states, a mixed-radix number with layer 0 as the lowest digit (radix 2, or 3 for the
+// layers below the last one on a grid with the via state; K = 2^layers on an on/off grid), so
+// every node branches into the K - 1 other states of its chosen column; the column is drawn
+// uniformly among those not yet on the node's path with a counter-based SplitMix64 generator
+// keyed by (seed, restart, iteration, depth, node); the best depth-D leaf (lowest index on ties)
+// is accepted only if strictly better; after M(D) failures the depth grows, and past Dmax the
+// search restarts from a random half-filled map at depth 1 (a metal pixel below the last layer
+// of a via grid is a via when the generator's next bit is set), keeping the global best; it
+// stops once the evaluation budget is spent (a started tree is finished).  A candidate whose
+// evaluation failed counts as +infinity.
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -33,18 +36,31 @@ uint64_t chain(std::initializer_list<uint64_t> parts) {
 
 struct Shape {
   int L, ny, nx;
+  bool vias;
   int cols() const { return ny * nx; }
   size_t pix() const { return static_cast<size_t>(L) * ny * nx; }
+  int radix(int l) const { return (vias && l < L - 1) ? 3 : 2; }
+  int states() const {
+    int k = 1;
+    for (int l = 0; l < L; ++l) k *= radix(l);
+    return k;
+  }
 };
 
 int col_state(const uint8_t* m, const Shape& s, int j) {
-  int v = 0;
-  for (int l = 0; l < s.L; ++l) v |= (m[static_cast<size_t>(l) * s.cols() + j] & 1) << l;
+  int v = 0, w = 1;
+  for (int l = 0; l < s.L; ++l) {
+    v += m[static_cast<size_t>(l) * s.cols() + j] * w;
+    w *= s.radix(l);
+  }
   return v;
 }
 
 void set_col(uint8_t* m, const Shape& s, int j, int v) {
-  for (int l = 0; l < s.L; ++l) m[static_cast<size_t>(l) * s.cols() + j] = static_cast<uint8_t>((v >> l) & 1);
+  for (int l = 0; l < s.L; ++l) {
+    m[static_cast<size_t>(l) * s.cols() + j] = static_cast<uint8_t>(v % s.radix(l));
+    v /= s.radix(l);
+  }
 }
 
 }  // namespace
@@ -57,9 +73,9 @@ extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, c
   int32_t M = 0, P = 0;
   pmom_num_bfs(c, &M, &P);
   const pmom::Grid& g = pmom::grid_of(c);
-  const Shape sh{g.layers, g.ny, g.nx};
+  const Shape sh{g.layers, g.ny, g.nx, g.vias()};
   const size_t npix = sh.pix();
-  const int K = 1 << sh.L;
+  const int K = sh.states();
   std::vector<uint8_t> batch;
   std::vector<double> fom;
   std::vector<int32_t> status;
@@ -129,7 +145,13 @@ extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, c
     if (counter >= prm->m_of_d[D - 1]) { ++D; counter = 0; }
     if (D > prm->d_max) {
       ++restart;
-      for (size_t i = 0; i < npix; ++i) cur[i] = static_cast<uint8_t>(chain({prm->seed, 0xA5A5ull, restart, i}) >> 63);
+      const size_t below_top = static_cast<size_t>(sh.L - 1) * sh.cols();
+      for (size_t i = 0; i < npix; ++i) {
+        const uint64_t u = chain({prm->seed, 0xA5A5ull, restart, i});
+        int v = static_cast<int>(u >> 63);
+        if (v && sh.vias && i < below_top) v = 1 + static_cast<int>((u >> 62) & 1);
+        cur[i] = static_cast<uint8_t>(v);
+      }
       st = evaluate(cur, 1, f1);
       if (st) return st;
       F = f1[0];

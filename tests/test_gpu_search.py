@@ -29,22 +29,27 @@ def _problem(g, freqs, bands):
     return Z, band, evaluate
 
 
-@pytest.mark.parametrize("case", ["tiny_3x3", "plain_8x8", "stripline_4x4x2"])
+@pytest.mark.parametrize("case", ["tiny_3x3", "plain_8x8", "stripline_4x4x2", "via_3x3x2"])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_search_decisions_match_oracle(built, case, prec):
     if case == "tiny_3x3":
         g, freqs, bands, budget = PI.grid_tiny(3), np.array([2.0e9, 2.5e9, 3.5e9, 5.0e9]), PI.PLAIN_BANDS, 300
     elif case == "plain_8x8":
         g, freqs, bands, budget = PI.grid_plain_8x8(), np.array([2.0e9, 3.0e9, 5.0e9]), PI.PLAIN_BANDS, 120
-    else:
+    elif case == "stripline_4x4x2":
         g = PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5625e-3)
         freqs, bands, budget = np.array([5.5e9, 6.2e9, 6.8e9, 8.0e9]), PI.UNII_BANDS, 150
+    else:   # three pixel states: columns of 3 x 2 mixed-radix states, vias placed by the search
+        import dataclasses
+        g = dataclasses.replace(PI.grid_tiny(3, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5625e-3), name="via_3x3x2", n_states=3)
+        freqs, bands, budget = np.array([5.5e9, 6.2e9, 6.8e9, 8.0e9]), PI.UNII_BANDS, 200
     Z, band, evaluate = _problem(g, freqs, bands)
     ev = built.Evaluator(g)
     ev.load_Z(freqs, torch.from_numpy(Z).cuda())
     ev.set_fom(band)
     init = PI.seed_map(g, 0.5, 5)
-    m_ref, f_ref, e_ref, t_ref = OS.tree_search(evaluate, init, seed=42, d_max=2, m_of_d=(10, 3), max_evals=budget)
+    m_ref, f_ref, e_ref, t_ref = OS.tree_search(evaluate, init, seed=42, d_max=2, m_of_d=(10, 3), max_evals=budget,
+                                                n_states=g.n_states)
     m_gpu, f_gpu, e_gpu, t_gpu = ev.search(init, seed=42, d_max=2, m_of_d=(10, 3), max_evals=budget, precision=prec)
     ev.close()
     tol = 1e-6 if prec == "mixed" else 1e-10

@@ -53,3 +53,51 @@ def test_search_bookkeeping_small_budget():
     assert evals >= 20
     # a 1-layer grid has two states per column: one child per node, D children per tree
     assert len(trace) >= 5
+
+
+def _via_problem():
+    import dataclasses
+    g = dataclasses.replace(PI.grid_tiny(2, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5625e-3), name="via_2x2x2", n_states=3)
+    OG = O.Grid(g)
+    freqs = np.array([5.5e9, 6.2e9, 6.8e9, 8.0e9])
+    Z, _ = O.fill(OG, freqs)
+    band = O.bands(freqs, PI.UNII_BANDS)
+
+    def evaluate(maps):
+        S, _ = O.eval_batch(OG, Z, maps)
+        return O.fom_batch(S, band)
+    return g, evaluate
+
+
+def test_three_state_column_states():
+    """Mixed-radix column states of a three-layer grid with vias: 3 x 3 x 2 = 18 states, each
+    set/read back exactly, together exactly the valid layer patterns (no via on the last layer);
+    the restart map keeps about half the pixels metal and puts vias only below the last layer."""
+    m = np.zeros((3, 2, 2), np.uint8)
+    assert OS.radices(3, 3) == [3, 3, 2] and OS.radices(3, 2) == [2, 2, 2]
+    seen = set()
+    for s in range(18):
+        c = OS.set_column(m, 3, s, 3)
+        assert OS.column_state(c, 3, 3) == s
+        seen.add(tuple(int(v) for v in c[:, 1, 1]))
+        assert np.array_equal(np.delete(c.reshape(3, -1), 3, axis=1), np.zeros((3, 3), np.uint8))
+    assert seen == {(a, b, t) for a in range(3) for b in range(3) for t in range(2)}
+    r = OS.random_map(5, 1, (3, 20, 20), 3)
+    assert (r[2] <= 1).all() and (r[:2] == 2).any()
+    assert abs((r >= 1).mean() - 0.5) < 0.05
+    assert np.array_equal(OS.random_map(5, 1, (2, 4, 4), 2), OS.random_map(5, 1, (2, 4, 4)))
+
+
+@pytest.mark.slow
+def test_search_with_vias_reaches_brute_force_optimum():
+    g, evaluate = _via_problem()
+    allm = np.stack([np.array([lo, hi], np.uint8).reshape(2, 2, 2)
+                     for lo in __import__("itertools").product(range(3), repeat=4)
+                     for hi in __import__("itertools").product(range(2), repeat=4)])
+    allf = evaluate(allm)
+    gmin = float(allf.min())
+    init = PI.seed_map(g, 0.5, 11)
+    best_map, best_F, evals, trace = OS.tree_search(evaluate, init, seed=7, d_max=2, m_of_d=(6, 2), max_evals=900,
+                                                    n_states=3)
+    assert best_F == pytest.approx(gmin, rel=1e-12)
+    assert (best_map == 2).any() == (allm[int(np.argmin(allf))] == 2).any()
