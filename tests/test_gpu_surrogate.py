@@ -164,3 +164,36 @@ def test_preranked_walk_beats_exhaustive_walk_at_equal_budget(S, search_case, tr
     print("best FoM with", budget, "exact evaluations: exhaustive", f_ex, "pre-ranked", f_pr)
     assert n_ex >= budget and n_pr >= budget
     assert f_pr < f_ex, (f_pr, f_ex)
+
+
+def _expected_min_random_subset(f, k):
+    """E[min f over a uniformly random k-subset of the n values]: the i-th smallest value (1-based)
+    is the minimum with probability C(n - i, k - 1) / C(n, k)."""
+    from math import comb
+    s = np.sort(f)
+    n = len(s)
+    p = np.array([comb(n - i, k - 1) for i in range(1, n + 1)], dtype=float) / comb(n, k)
+    return float(np.dot(p, s))
+
+
+def test_topk_regret_vs_exhaustive_and_random_subsets(S, search_case, trained):
+    """FoM regret of exact-evaluating only the predicted top k of a step's 512 children, against
+    exhaustive exact evaluation (regret = best FoM among the top k minus the best FoM of all
+    children, relative to the latter), on the three held-out steps, beside the exact expected
+    regret of k children drawn uniformly at random (no network)."""
+    w, ev, bands, xs, ts, steps = search_case
+    rows = []
+    for cur, kids, f in steps[11:14]:
+        pred = trained.predict_fom(torch.from_numpy(kids).cuda().reshape(512, -1), bands, w.n_freq).cpu().numpy()
+        order = np.argsort(pred, kind="stable")
+        best = float(f.min())
+        for k in (8, 32, 64):
+            reg = (float(f[order[:k]].min()) - best) / abs(best)
+            rnd = (_expected_min_random_subset(f, k) - best) / abs(best)
+            rows.append((k, reg, rnd, int(np.argmin(f)) in set(order[:k].tolist())))
+    for k in (8, 32, 64):
+        r = [x for x in rows if x[0] == k]
+        print("top-%d: regret per step" % k, [round(x[1], 4) for x in r], "random-subset expectation",
+              [round(x[2], 4) for x in r], "exact best in top-k", [x[3] for x in r])
+    r32 = [x for x in rows if x[0] == 32]
+    assert np.mean([x[1] for x in r32]) <= np.mean([x[2] for x in r32])
