@@ -104,7 +104,7 @@ class Clocks:
 
 def workload(name: str):
     return {"precision": PI.workload_precision, "plain": PI.workload_plain, "profile": PI.workload_profile,
-            "batching": PI.workload_batching}[name]()
+            "batching": PI.workload_batching, "scale": PI.workload_scale}[name]()
 
 
 def lu_flops(N: np.ndarray, F: int, P: int) -> float:
@@ -248,7 +248,8 @@ def run_ours(args):
     value = aggregate_rate(world, Bsz, ms)
     # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
     three_state = w.grid.n_states == 3
-    nfp = min(Bsz, 8 if three_state else 32)
+    huge = int(N.max()) > 3000          # FP64 LU of N ~ 4000 at 101 frequencies: ~20 s per candidate
+    nfp = min(Bsz, 2 if huge else 8 if three_state else 32)
     sub = maps[:nfp]
     S_mixed, fom_mixed = S[:nfp].clone(), fom[:nfp].clone()
     sub_out = (S[:nfp], fom[:nfp], status[:nfp])
@@ -270,7 +271,9 @@ def run_ours(args):
     #      reference factors and inverse per frequency, k x k updates per candidate, recomputed
     #      every step
     bordered = None
-    if args.bordered and not three_state:   # the three-state batch changes several seeds, not one reference
+    # the three-state batch changes several seeds, not one reference; at N ~ 4000 the reference
+    # inverse leaves the shared-memory route
+    if args.bordered and not three_state and not huge:
         seed_d = torch.from_numpy(PI.seed_map(w.grid, w.fill, rank)).cuda()
         Sb, fb, sb = torch.empty_like(S), torch.empty_like(fom), torch.empty_like(status)
         for _ in range(args.warmup):
@@ -368,10 +371,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="precision", choices=["precision", "plain", "profile", "batching"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "plain", "profile", "batching", "scale"],
                     help="profile: a smaller grid running the same kernels, for counter captures; batching: "
-                         "the 3-layer 20x20 three-state stripline, 101 frequencies, uneven support sets "
-                         "(use --batch to bound it)")
+                         "the 3-layer 20x20 three-state stripline, 101 frequencies, uneven support sets; scale: "
+                         "the 4-layer 32x32 stripline (M = 12048, N about 4000, 117 GB database); bound both "
+                         "with --batch")
     ap.add_argument("--batch", type=int, default=0, help="evaluate only the first B candidates")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-bordered", dest="bordered", action="store_false",
