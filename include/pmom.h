@@ -283,7 +283,7 @@ pmom_status pmom_mlp_errors(pmom_mlp* net, int32_t* timeouts);
 pmom_status pmom_capacity(pmom_ctx* ctx, int32_t precision, int32_t* n_default, int32_t* n_max);
 
 /* Depth-increasing all-way tree search (paper Algorithm 1, Section III-A; hyper-parameters of
- * Section III-D: Dmax = 2 with M(1) = 10, M(2) = 3 for the 8-state case).  A pixel is an (x, y)
+ * Section III-C: Dmax = 2 with M(1) = 10, M(2) = 3 for the 8-state case).  A pixel is an (x, y)
  * column whose state is the bit pattern of its layers; every tree node branches into all other
  * states of one column drawn uniformly (counter-based SplitMix64 keyed by seed, restart,
  * iteration, depth and node) among the columns not yet on its path; each tree level is one

@@ -18,7 +18,7 @@
  * diagonal) -> per layer, per pixel row-major (y outer, x inner): diagonal, +x side, +y side
  * -> pixel-port BFs (port-major) -> via BFs.
  *
- * Via state (n_states = 3; the paper names vias only as an extension, Section VII): state 2 on
+ * Via state (n_states = 3; additional states with vias are future work in Section VIII): state 2 on
  * layer l is metal on layer l plus a vertical strip standing on the pixel diagonal, from layer l
  * up to layer l+1.  The strip is a rectangle A = D0@z_l, B = D1@z_l, C = D1@z_{l+1}, D = D0@z_{l+1}
  * (D0, D1 = the diagonal's end corners) cut along A-C into Ta = (A, B, C) and Tb = (A, C, D).

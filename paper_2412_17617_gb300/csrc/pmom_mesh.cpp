@@ -3,10 +3,10 @@
 // halves of a pixel, which half owns each pixel side, and which triangle corner is the free RWG
 // vertex are fixed per diagonal orientation and looked up instead of searched.
 //
-// Via state (grids with three pixel states; the paper leaves vias to future work, Section VII):
-// a vertical strip stands on the pixel diagonal D0-D1 from layer l to layer l+1, cut along
-// D0@l - D1@l+1 into the triangles Ta = (D0@l, D1@l, D1@l+1) and Tb = (D0@l, D1@l+1, D0@l+1)
-// (triangle keys with half 2 and 3).  Its three BFs follow the pixel-port BFs, per via layer and
+// Via state (grids with three pixel states; the paper names additional states with vias as future
+// work, Section VIII): a vertical strip stands on the pixel diagonal D0-D1 from layer l to layer
+// l+1, cut along D0@l - D1@l+1 into the triangles Ta = (D0@l, D1@l, D1@l+1) and
+// Tb = (D0@l, D1@l+1, D0@l+1) (triangle keys with half 2 and 3).  Its three BFs follow the pixel-port BFs, per via layer and
 // pixel row-major: strip diagonal (Ta -> Tb), junction with half 0 of the via pixel (half 0 -> Ta)
 // and junction with half 0 of the pixel above (Tb -> that half).
 #include "pmom_internal.h"

@@ -8,7 +8,7 @@ any of the computation they are compared on.
 
 Geometry sources (paper): pixel pitch / map size / stack-up from Table I; eps_r = 3.66 and
 tan(delta) = 0.004 for Rogers 4350B from Section IV; the channel bands 5.15-5.925 GHz and
-6.425-7.125 GHz and the 3-9 GHz scoring range from Section III-C (Eq. 8-9).
+6.425-7.125 GHz and the 3-9 GHz scoring range from Section III-B (Eq. 8-9).
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
 """Oracle pins for the via state (three pixel states: void / metal / metal with a vertical strip up
-to the next layer; the paper leaves vias to future work, Section VII).
+to the next layer; the paper names additional states with vias as future work, Section VIII).
 
 Mesh: closed-form BF count, the geometry of the strip triangles and of the three via BFs, and the
 support set of every map of a small two-layer grid against a hand count.  Fill: K0 of complex
