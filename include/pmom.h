@@ -84,6 +84,12 @@ typedef struct {
                                   layer (layers >= 2; the last layer rejects state 2) */
   int32_t n_ports;             /* 1..4 */
   const pmom_port* ports;      /* [n_ports], host */
+  int32_t diag_pattern;        /* pixel diagonals (Section V-A, Fig. mesh_orientation a-c), the same on
+                                  every layer and on the port stubs: 0 alternating (diagonal
+                                  (x, y+1)-(x+1, y) when x+y is even, else (x, y)-(x+1, y+1)),
+                                  1 uniform (always the first), 2 random (the first when the top bit
+                                  of SplitMix64 chained over diag_seed and (y+4)*128 + x+4 is 0) */
+  uint64_t diag_seed;          /* pattern 2 only */
 } pmom_grid_desc;
 
 typedef struct pmom_ctx pmom_ctx;

@@ -514,7 +514,7 @@ static void* fill_worker(void* arg) {
       size_t s;
       if (J->mode == 0) s = (size_t)p * T + q;
       else {
-        int op = (xp + yp) & 1, oq = (xq + yq) & 1;
+        int op = or_orient(g, xp, yp), oq = or_orient(g, xq, yq);
         s = ((((((size_t)lp * g->layers + lq) * 2 + op) * 4 + hp) * 2 + oq) * 4 + hq) * NW * NW +
             (size_t)(xq - xp + W) * NW + (yq - yp + W);
       }

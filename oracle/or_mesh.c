@@ -1,9 +1,11 @@
 /*
  * or_mesh.c -- oracle mesher, basis-function classes and support set.  TEST INFRASTRUCTURE ONLY.
  *
- * Mesh (Section V-A, "alternating" orientation): every pixel is a square of side a split by one
- * diagonal into two right triangles.  The diagonal runs from (x, y+1) to (x+1, y) when x+y is
- * even and from (x, y) to (x+1, y+1) when x+y is odd, on every layer.  One RWG basis function
+ * Mesh (Section V-A): every pixel is a square of side a split by one diagonal into two right
+ * triangles.  With the "alternating" orientation (the default) the diagonal runs from (x, y+1) to
+ * (x+1, y) when x+y is even and from (x, y) to (x+1, y+1) when x+y is odd; the "uniform" one
+ * always takes the first, the "random" one draws it per lattice position from a seeded generator
+ * (Fig. mesh_orientation a-c); the pattern is the same on every layer.  One RWG basis function
  * (Section II-B) sits on every edge shared by two triangles:
  *   inner-pixel BF  : the diagonal of a pixel        -> active when the pixel is metal
  *   inter-pixel BF  : the side shared by two pixels  -> active when both pixels are metal
@@ -45,11 +47,29 @@ static void key_decode(int32_t key, int* layer, int* x, int* y, int* half) {
   *layer = key / 128;
 }
 
+/* SplitMix64 (Steele, Lea and Flood 2014): state advanced by the golden gamma, then mixed. */
+static uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int or_orient(const or_grid* g, int x, int y) {
+  if (g->diag_pattern == 1) return 0;
+  if (g->diag_pattern == 2) {
+    uint64_t h = splitmix64(0 ^ g->diag_seed);
+    h = splitmix64(h ^ (uint64_t)((y + 4) * 128 + (x + 4)));
+    return (int)(h >> 63);
+  }
+  return (x + y) & 1;
+}
+
 /* Lattice corners of triangle `half` of pixel (x, y), in canonical vertex order. */
-static void tri_corners(int x, int y, int half, int c[3][2]) {
+static void tri_corners(const or_grid* g, int x, int y, int half, int c[3][2]) {
   const int c00[2] = {x, y}, c10[2] = {x + 1, y}, c01[2] = {x, y + 1}, c11[2] = {x + 1, y + 1};
   const int* v[3];
-  if (((x + y) & 1) == 0) {          /* diagonal c01 - c10 */
+  if (or_orient(g, x, y) == 0) {     /* diagonal c01 - c10 */
     if (half == 0) { v[0] = c00; v[1] = c10; v[2] = c01; }
     else           { v[0] = c10; v[1] = c11; v[2] = c01; }
   } else {                           /* diagonal c00 - c11 */
@@ -61,8 +81,8 @@ static void tri_corners(int x, int y, int half, int c[3][2]) {
 
 /* End corners D0, D1 of the pixel diagonal (the corners that both halves share, in the order
  * they appear in half 0). */
-static void diag_ends(int x, int y, int d0[2], int d1[2]) {
-  if (((x + y) & 1) == 0) { d0[0] = x; d0[1] = y + 1; d1[0] = x + 1; d1[1] = y; }
+static void diag_ends(const or_grid* g, int x, int y, int d0[2], int d1[2]) {
+  if (or_orient(g, x, y) == 0) { d0[0] = x; d0[1] = y + 1; d1[0] = x + 1; d1[1] = y; }
   else                    { d0[0] = x; d0[1] = y;     d1[0] = x + 1; d1[1] = y + 1; }
 }
 
@@ -71,7 +91,7 @@ void or_triangle(const or_grid* g, int32_t key, double v[3][3]) {
   key_decode(key, &layer, &x, &y, &half);
   if (half >= 2) {
     int d0[2], d1[2];
-    diag_ends(x, y, d0, d1);
+    diag_ends(g, x, y, d0, d1);
     double zl = g->layer_z[layer], zu = g->layer_z[layer + 1];
     /* Ta = (A, B, C), Tb = (A, C, D) */
     const int* xy[3] = {d0, d1, half == 2 ? d1 : d0};
@@ -83,7 +103,7 @@ void or_triangle(const or_grid* g, int32_t key, double v[3][3]) {
     }
     return;
   }
-  tri_corners(x, y, half, c);
+  tri_corners(g, x, y, half, c);
   for (int i = 0; i < 3; ++i) {
     v[i][0] = c[i][0] * g->pitch;
     v[i][1] = c[i][1] * g->pitch;
@@ -92,10 +112,10 @@ void or_triangle(const or_grid* g, int32_t key, double v[3][3]) {
 }
 
 /* Which half of pixel (x, y) holds the lattice edge p-q, and the index of its free vertex. */
-static int find_half(int x, int y, const int p[2], const int q[2], int* free_idx) {
+static int find_half(const or_grid* g, int x, int y, const int p[2], const int q[2], int* free_idx) {
   for (int half = 0; half < 2; ++half) {
     int c[3][2], hit[3] = {0, 0, 0}, nhit = 0;
-    tri_corners(x, y, half, c);
+    tri_corners(g, x, y, half, c);
     for (int i = 0; i < 3; ++i) {
       if ((c[i][0] == p[0] && c[i][1] == p[1]) || (c[i][0] == q[0] && c[i][1] == q[1])) { hit[i] = 1; ++nhit; }
     }
@@ -109,25 +129,25 @@ static int find_half(int x, int y, const int p[2], const int q[2], int* free_idx
 
 /* Emit the BF on the edge shared by pixel P (positive side) and pixel Q (negative side);
  * the two pixels are lattice neighbours on `layer`. */
-static void emit_side(int32_t* row, int layer, int px, int py, int qx, int qy) {
+static void emit_side(const or_grid* g, int32_t* row, int layer, int px, int py, int qx, int qy) {
   int e0[2], e1[2];
   if (qx == px + 1)      { e0[0] = px + 1; e0[1] = py;     e1[0] = px + 1; e1[1] = py + 1; }
   else if (qx == px - 1) { e0[0] = px;     e0[1] = py;     e1[0] = px;     e1[1] = py + 1; }
   else if (qy == py + 1) { e0[0] = px;     e0[1] = py + 1; e1[0] = px + 1; e1[1] = py + 1; }
   else                   { e0[0] = px;     e0[1] = py;     e1[0] = px + 1; e1[1] = py; }
   int fp = -1, fq = -1;
-  int hp = find_half(px, py, e0, e1, &fp);
-  int hq = find_half(qx, qy, e0, e1, &fq);
+  int hp = find_half(g, px, py, e0, e1, &fp);
+  int hq = find_half(g, qx, qy, e0, e1, &fq);
   row[4] = tri_key(layer, px, py, hp);
   row[5] = tri_key(layer, qx, qy, hq);
   row[6] = fp;
   row[7] = fq;
 }
 
-static void emit_diag(int32_t* row, int layer, int x, int y) {
+static void emit_diag(const or_grid* g, int32_t* row, int layer, int x, int y) {
   int c0[3][2], c1[3][2];
-  tri_corners(x, y, 0, c0);
-  tri_corners(x, y, 1, c1);
+  tri_corners(g, x, y, 0, c0);
+  tri_corners(g, x, y, 1, c1);
   /* free vertex of each half = the corner not on the other half */
   int f0 = -1, f1 = -1;
   for (int i = 0; i < 3; ++i) {
@@ -174,26 +194,26 @@ int or_bf_table(const or_grid* g, int32_t* t) {
     int s1[2], s2[2], gp[2], layer = port[0];
     port_pixels(g, port, s1, s2, gp);
     int32_t* r;
-    r = t + OR_BF_COLS * m++; r[0] = OR_BF_ALWAYS; r[1] = -1; r[2] = -1; r[3] = p; emit_diag(r, layer, s1[0], s1[1]);
+    r = t + OR_BF_COLS * m++; r[0] = OR_BF_ALWAYS; r[1] = -1; r[2] = -1; r[3] = p; emit_diag(g, r, layer, s1[0], s1[1]);
     r = t + OR_BF_COLS * m++; r[0] = OR_BF_ALWAYS; r[1] = -1; r[2] = -1; r[3] = p;
-    emit_side(r, layer, s2[0], s2[1], s1[0], s1[1]);          /* positive triangle outside */
-    r = t + OR_BF_COLS * m++; r[0] = OR_BF_ALWAYS; r[1] = -1; r[2] = -1; r[3] = p; emit_diag(r, layer, s2[0], s2[1]);
+    emit_side(g, r, layer, s2[0], s2[1], s1[0], s1[1]);          /* positive triangle outside */
+    r = t + OR_BF_COLS * m++; r[0] = OR_BF_ALWAYS; r[1] = -1; r[2] = -1; r[3] = p; emit_diag(g, r, layer, s2[0], s2[1]);
   }
   for (int l = 0; l < g->layers; ++l) {
     for (int y = 0; y < g->ny; ++y) {
       for (int x = 0; x < g->nx; ++x) {
         int32_t* r = t + OR_BF_COLS * m++;
         r[0] = OR_BF_INNER; r[1] = pix_index(g, l, x, y); r[2] = -1; r[3] = -1;
-        emit_diag(r, l, x, y);
+        emit_diag(g, r, l, x, y);
         if (x + 1 < g->nx) {
           r = t + OR_BF_COLS * m++;
           r[0] = OR_BF_INTER; r[1] = pix_index(g, l, x, y); r[2] = pix_index(g, l, x + 1, y); r[3] = -1;
-          emit_side(r, l, x, y, x + 1, y);
+          emit_side(g, r, l, x, y, x + 1, y);
         }
         if (y + 1 < g->ny) {
           r = t + OR_BF_COLS * m++;
           r[0] = OR_BF_INTER; r[1] = pix_index(g, l, x, y); r[2] = pix_index(g, l, x, y + 1); r[3] = -1;
-          emit_side(r, l, x, y, x, y + 1);
+          emit_side(g, r, l, x, y, x, y + 1);
         }
       }
     }
@@ -204,7 +224,7 @@ int or_bf_table(const or_grid* g, int32_t* t) {
     port_pixels(g, port, s1, s2, gp);
     int32_t* r = t + OR_BF_COLS * m++;
     r[0] = OR_BF_PIXPORT; r[1] = pix_index(g, layer, gp[0], gp[1]); r[2] = -1; r[3] = p;
-    emit_side(r, layer, s1[0], s1[1], gp[0], gp[1]);
+    emit_side(g, r, layer, s1[0], s1[1], gp[0], gp[1]);
   }
   if (has_vias(g)) {
     for (int l = 0; l + 1 < g->layers; ++l) {
@@ -217,8 +237,8 @@ int or_bf_table(const or_grid* g, int32_t* t) {
           r[4] = tri_key(l, x, y, 2); r[5] = tri_key(l, x, y, 3); r[6] = 1; r[7] = 2;
           /* free vertex of half 0 with respect to the pixel diagonal */
           int d0[2], d1[2];
-          diag_ends(x, y, d0, d1);
-          tri_corners(x, y, 0, c);
+          diag_ends(g, x, y, d0, d1);
+          tri_corners(g, x, y, 0, c);
           for (int i = 0; i < 3; ++i) {
             int on0 = c[i][0] == d0[0] && c[i][1] == d0[1], on1 = c[i][0] == d1[0] && c[i][1] == d1[1];
             if (!on0 && !on1) f0 = i;

@@ -46,7 +46,8 @@ class _Grid(ctypes.Structure):
                 ("pitch", ctypes.c_double), ("medium", ctypes.c_int),
                 ("layer_z", ctypes.POINTER(ctypes.c_double)), ("h_total", ctypes.c_double),
                 ("eps_r", ctypes.c_double), ("tan_d", ctypes.c_double), ("n_states", ctypes.c_int),
-                ("n_ports", ctypes.c_int), ("ports", ctypes.POINTER(ctypes.c_int32))]
+                ("n_ports", ctypes.c_int), ("ports", ctypes.POINTER(ctypes.c_int32)),
+                ("diag_pattern", ctypes.c_int), ("diag_seed", ctypes.c_uint64)]
 
 
 def lib():
@@ -85,6 +86,7 @@ def lib():
             L.or_fom.restype = ctypes.c_double
             L.or_bands.argtypes = [P, ctypes.c_int, P, P]
             L.or_triangle.argtypes = [P, ctypes.c_int32, P]
+            L.or_orient.argtypes = [P, ctypes.c_int, ctypes.c_int]
             L.or_pair_integrals.argtypes = [P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, P]
             _lib = L
     return _lib
@@ -103,7 +105,8 @@ class Grid:
         self._ports = np.ascontiguousarray(np.array([[p.layer, p.side, p.pos] for p in g.ports], dtype=np.int32))
         self.c = _Grid(g.layers, g.nx, g.ny, g.pitch_m, g.medium,
                        self._z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), g.h_total_m, g.eps_r, g.tan_d,
-                       g.n_states, len(g.ports), self._ports.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+                       g.n_states, len(g.ports), self._ports.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                       getattr(g, "diag_pattern", 0), getattr(g, "diag_seed", 0))
         self.ref = ctypes.byref(self.c)
         self.M = lib().or_count_bfs(self.ref)
         self.P = len(g.ports)
@@ -175,6 +178,10 @@ def tri_rule(n: int):
     w = ctypes.POINTER(ctypes.c_double)()
     k = lib().or_tri_rule(n, ctypes.byref(b), ctypes.byref(w))
     return (np.ctypeslib.as_array(b, shape=(k, 3)).copy(), np.ctypeslib.as_array(w, shape=(k,)).copy())
+
+
+def orient(grid: Grid, x: int, y: int) -> int:
+    return lib().or_orient(grid.ref, x, y)
 
 
 def triangle(grid: Grid, key: int) -> np.ndarray:

@@ -37,6 +37,8 @@ typedef struct {
   int n_states;            /* 2: void/metal; 3: void/metal/metal with a via to the next layer */
   int n_ports;
   const int32_t* ports;    /* [n_ports][3] = layer, side (0 right, 1 top, 2 left, 3 bottom), pos */
+  int diag_pattern;        /* pixel diagonals (Section V-A, Fig. mesh_orientation a-c): 0 alternating, 1 uniform, 2 random */
+  uint64_t diag_seed;      /* pattern 2: seed of the per-position orientation draw */
 } or_grid;
 
 /* Basis-function classes (Section II-C), plus the three BFs of a via site (state 2). */
@@ -56,6 +58,11 @@ int or_bf_table(const or_grid* g, int32_t* table);
 /* Eq. (3): ascending indices of the BFs active under `map` ([layers][ny][nx] states).
  * Returns N >= 0, or -1 if a state is out of range. */
 int or_active_set(const or_grid* g, const int32_t* table, int M, const uint8_t* map, int32_t* idx);
+
+/* Diagonal orientation of lattice pixel (x, y) (stub pixels included; the same on every layer):
+ * 0 -> diagonal (x, y+1)-(x+1, y), 1 -> (x, y)-(x+1, y+1).  Alternating: (x + y) mod 2; uniform: 0;
+ * random: the top bit of SplitMix64 chained over (diag_seed, (y+4)*128 + x+4). */
+int or_orient(const or_grid* g, int x, int y);
 
 /* Triangle geometry of a key (3 vertices, metres). */
 void or_triangle(const or_grid* g, int32_t key, double v[3][3]);

@@ -202,6 +202,7 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
     return PMOM_ERR_INVALID_ARG;
   if (g->n_states != 2 && g->n_states != 3) return PMOM_ERR_UNSUPPORTED;
   if (g->n_states == 3 && g->layers < 2) return PMOM_ERR_INVALID_ARG;   // a via needs a layer above
+  if (g->diag_pattern < 0 || g->diag_pattern > 2) return PMOM_ERR_INVALID_ARG;
   for (int p = 0; p < g->n_ports; ++p) {
     const pmom_port& q = g->ports[p];
     const int lim = (q.side == 0 || q.side == 2) ? g->ny : g->nx;
@@ -211,6 +212,7 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   pmom_ctx* c = new pmom_ctx();
   pmom::Grid& gr = c->grid;
   gr.layers = g->layers; gr.nx = g->nx; gr.ny = g->ny; gr.medium = g->medium; gr.n_states = g->n_states;
+  gr.diag_pattern = g->diag_pattern; gr.diag_seed = g->diag_seed;
   gr.n_ports = g->n_ports; gr.pitch = g->pitch_m; gr.h_total = g->h_total_m; gr.eps_r = g->eps_r; gr.tan_d = g->tan_d;
   gr.layer_z.assign(g->layer_z_m, g->layer_z_m + g->layers);
   gr.ports.assign(g->ports, g->ports + g->n_ports);

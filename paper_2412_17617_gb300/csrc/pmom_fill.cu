@@ -444,7 +444,7 @@ void key_triangle(const Grid& g, int32_t key, FillTri* t) {
   static const int corner[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
   static const int tri[2][2][3] = {{{0, 1, 2}, {1, 3, 2}}, {{0, 1, 3}, {0, 3, 2}}};
   static const int dend[2][2] = {{2, 1}, {0, 3}};   // diagonal end corners D0, D1 per orientation
-  const int o = (x + y) & 1;
+  const int o = orient(g, x, y);
   if (half < 2) {
     for (int i = 0; i < 3; ++i) {
       const int cc = tri[o][half][i];
@@ -530,14 +530,20 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   std::unordered_map<long long, int> cls_of;
   std::vector<int2> rep;
   std::vector<int> pair_class(static_cast<size_t>(T) * T);
+  // diagonal orientation of each triangle's pixel: with the alternating pattern the second
+  // triangle's follows from the first's and the offset, with the uniform and random ones it does
+  // not, so both enter the class
+  std::vector<int> ori(T);
+  for (int t = 0; t < T; ++t) ori[t] = orient(g, (keys[t] >> 2) % 128 - 4, ((keys[t] >> 2) / 128) % 128 - 4);
   for (int p = 0; p < T; ++p) {
     const int32_t kp = keys[p];
     const int hp = kp & 3, xp = (kp >> 2) % 128, yp = ((kp >> 2) / 128) % 128, lp = (kp >> 2) / (128 * 128);
     for (int q = 0; q < T; ++q) {
       const int32_t kq = keys[q];
       const int hq = kq & 3, xq = (kq >> 2) % 128, yq = ((kq >> 2) / 128) % 128, lq = (kq >> 2) / (128 * 128);
-      const long long key = ((((((static_cast<long long>(lp) * 8 + lq) * 2 + ((xp + yp) & 1)) * 4 + hp) * 4 + hq) * 512 +
-                              (xq - xp + 256)) * 512) + (yq - yp + 256);
+      const long long key =
+          ((((((((static_cast<long long>(lp) * 8 + lq) * 2 + ori[p]) * 2 + ori[q]) * 4 + hp) * 4 + hq) * 512 +
+             (xq - xp + 256)) * 512) + (yq - yp + 256));
       auto it = cls_of.find(key);
       int c;
       if (it == cls_of.end()) {

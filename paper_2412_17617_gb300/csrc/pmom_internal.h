@@ -21,6 +21,8 @@ enum RuleKind : int32_t { kAlways = 0, kInner = 1, kInter = 2, kPixPort = 3, kVi
 
 struct Grid {
   int layers = 0, nx = 0, ny = 0, medium = 0, n_states = 2, n_ports = 0;
+  int diag_pattern = 0;    // 0 alternating, 1 uniform, 2 random (pmom_grid_desc)
+  uint64_t diag_seed = 0;
   double pitch = 0, h_total = 0, eps_r = 1, tan_d = 0;
   std::vector<double> layer_z;
   std::vector<pmom_port> ports;
@@ -29,6 +31,10 @@ struct Grid {
   // first pixel index that cannot hold the via state (the last layer has no layer above it)
   int via_top() const { return vias() ? (layers - 1) * nx * ny : pixels(); }
 };
+
+// Diagonal orientation of lattice pixel (x, y): 0 -> (x, y+1)-(x+1, y), 1 -> (x, y)-(x+1, y+1)
+// (pmom_mesh.cpp).
+int orient(const Grid& g, int x, int y);
 
 // Grid of a context (pmom_api.cu).
 const Grid& grid_of(const pmom_ctx* c);

@@ -46,6 +46,8 @@ class Grid:
     tan_d: float
     n_states: int
     ports: Tuple[Port, ...]
+    diag_pattern: int = 0     # pixel diagonals: 0 alternating, 1 uniform, 2 random (seeded by diag_seed)
+    diag_seed: int = 0
 
     @property
     def n_pixels(self) -> int:

@@ -200,3 +200,31 @@ def test_gpu_fill_matches_oracle_fill(built):
         for f in range(len(freqs)):
             assert np.abs(Zg[f] - Zr[f]).max() <= 1e-9 * np.abs(Zr[f]).max()
         ev.close()
+
+
+@pytest.mark.parametrize("pattern", [1, 2])
+def test_other_orientations_fill_and_eval(built, pattern):
+    """Uniform and random pixel diagonals (Fig. mesh_orientation a, c) on a 4 x 4 two-layer
+    stripline with vias: the GPU fill against the oracle's, then both precisions against the
+    oracle's solve."""
+    import dataclasses
+    g = dataclasses.replace(PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5625e-3), name=f"diag{pattern}",
+                            n_states=3, diag_pattern=pattern, diag_seed=11)
+    freqs = np.array([5.5e9, 7.0e9])
+    OG = O.Grid(g)
+    Zr, _ = O.fill(OG, freqs)
+    ev = built.Evaluator(g)
+    ev.fill_Z(freqs, "c128")
+    Zg = ev.copy_Z().cpu().numpy()
+    for f in range(len(freqs)):
+        assert np.abs(Zg[f] - Zr[f]).max() <= 1e-9 * np.abs(Zr[f]).max()
+    maps = PI.state_changes(PI.seed_map_vias(g, 0.6, 0.4, 1), 2, 6, 2)
+    S_ref, st = O.eval_batch(OG, Zr, maps)
+    assert (st == 0).all()
+    ev.set_fom(built.band_codes(freqs, PI.UNII_BANDS))
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-6)):
+        S, fom, status = ev.eval(torch.from_numpy(maps).cuda(), prec)
+        torch.cuda.synchronize()
+        assert np.isin(status.cpu().numpy(), [0, 3]).all()
+        assert np.abs(S.cpu().numpy() - S_ref).max() <= tol * max(1.0, np.abs(S_ref).max())
+    ev.close()

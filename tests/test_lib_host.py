@@ -37,6 +37,10 @@ def _grids():
     gs.append(PI.Grid("sides_5x3x2_via", 2, 5, 3, 1e-3, PI.MEDIUM_STRIPLINE, (0.5e-3, 1.0e-3), 1.5e-3, 3.66, 0.004, 3,
                       ports))
     gs.append(PI.grid_stripline_20x20x3(n_states=3))
+    # uniform and random diagonal orientations
+    import dataclasses
+    gs.append(dataclasses.replace(PI.grid_stripline_16x16x2(), name="stripline_16x16x2_uniform", diag_pattern=1))
+    gs.append(dataclasses.replace(gs[-3], name="sides_5x3x2_via_random", diag_pattern=2, diag_seed=77))
     return gs
 
 
@@ -65,6 +69,10 @@ def test_argument_validation(lib):
     three = PI.Grid("via", 1, 3, 3, 1e-3, 0, (0.5e-3,), 0.5e-3, 3.5, 0.0, 3, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(three)
+    assert e.value.status == 1
+    pat = PI.Grid("pattern", 1, 3, 3, 1e-3, 0, (0.5e-3,), 0.5e-3, 3.5, 0.0, 2, (PI.Port(0, 0, 1),), diag_pattern=3)
+    with pytest.raises(pmom.PmomError) as e:
+        pmom.Evaluator(pat)
     assert e.value.status == 1
     four = PI.Grid("four", 2, 3, 3, 1e-3, 0, (0.5e-3, 1e-3), 1e-3, 3.5, 0.0, 4, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:

@@ -133,3 +133,21 @@ def test_half_wave_strip_dipole():
     i = int(np.argmin(np.abs(zin.imag)))
     assert abs(zin[i].imag) < 15 and 60 < zin[i].real < 85
     assert 0.46 < (69 + 2 * i) * a / (C0 / f) < 0.49
+
+
+@pytest.mark.parametrize("pattern", [1, 2])
+def test_other_orientations_fill(pattern):
+    """Uniform and random diagonals (Fig. mesh_orientation a, c): the lattice-table fill, whose
+    classes carry both triangles' orientations, equals the direct fill; reciprocity and passivity
+    hold as for the alternating mesh."""
+    import dataclasses
+    g = dataclasses.replace(PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2), diag_pattern=pattern, diag_seed=3)
+    G = O.Grid(g)
+    f = [1.3e9, 6.1e9]
+    Zd, _ = O.fill(G, f, mode=0)
+    Zt, asym = O.fill(G, f, mode=1)
+    assert np.abs(Zd - Zt).max() <= 1e-12 * np.abs(Zd).max()
+    assert asym < 1e-4
+    for Zf in Zt:
+        herm = 0.5 * (Zf + Zf.conj().T)
+        assert np.linalg.eigvalsh(herm).min() >= -1e-10 * np.abs(Zf).max()

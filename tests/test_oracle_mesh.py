@@ -114,3 +114,41 @@ def test_bad_state_rejected():
     m[0, 1, 1] = 2
     with pytest.raises(ValueError):
         O.active_set(G, m)
+
+
+def _patterned(g, pattern, seed=0):
+    import dataclasses
+    return dataclasses.replace(g, name=f"{g.name}_diag{pattern}", diag_pattern=pattern, diag_seed=seed)
+
+
+def test_diagonal_orientation_patterns():
+    """Section V-A / Fig. mesh_orientation (a)-(c): alternating = (x + y) mod 2, uniform = 0,
+    random = the top bit of SplitMix64 chained over (seed, position), checked against the search
+    module's own SplitMix64; about half of the random diagonals take each orientation and two
+    seeds give different patterns."""
+    from oracle import search as OS
+    g = PI.grid_tiny(8)
+    G0, G1 = O.Grid(g), O.Grid(_patterned(g, 1))
+    G2, G2b = O.Grid(_patterned(g, 2, 17)), O.Grid(_patterned(g, 2, 18))
+    pos = [(x, y) for y in range(-2, 10) for x in range(-2, 10)]
+    assert all(O.orient(G0, x, y) == (x + y) % 2 for x, y in pos)
+    assert all(O.orient(G1, x, y) == 0 for x, y in pos)
+    r = [O.orient(G2, x, y) for x, y in pos]
+    assert r == [OS.key(17, (y + 4) * 128 + x + 4) >> 63 for x, y in pos]
+    assert 0.35 < np.mean(r) < 0.65
+    assert r != [O.orient(G2b, x, y) for x, y in pos]
+
+
+@pytest.mark.parametrize("pattern", [1, 2])
+def test_rwg_geometry_other_orientations(pattern):
+    g = _patterned(PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2), pattern, 5)
+    test_rwg_geometry_and_edge_census(g)
+
+
+@pytest.mark.parametrize("pattern", [1, 2])
+def test_activation_does_not_depend_on_orientation(pattern):
+    g = PI.grid_tiny(3)
+    G0, G = O.Grid(g), O.Grid(_patterned(g, pattern, 9))
+    assert G.M == G0.M and np.array_equal(G.table[:, :4], G0.table[:, :4])
+    for m in PI.all_maps(g)[::7]:
+        assert np.array_equal(O.active_set(G, m), O.active_set(G0, m))
