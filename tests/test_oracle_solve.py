@@ -175,3 +175,29 @@ def test_lapack_solve_route_matches_c_oracle(c1):
         S_c, st = O.eval_map(OGs, Zs64, m)
         assert st == 0
         assert np.abs(O.eval_map_lapack(OGs, Zs64, m) - S_c).max() <= 1e-12
+
+
+def test_condition_numbers_support_the_precision_policy():
+    """cond_2(Z_sub) of sampled candidates at five frequencies of the plain and precision
+    workloads (complex64 storage promoted exactly).  Mixed-precision refinement converges when
+    u_32 cond < 1 with a contraction of about u_32 cond per correction, and the forward error of
+    the refined solution is about cond times its backward error (1e-12), so cond <= 1e5 keeps
+    |dS| far inside 1e-6.  A report with a loose bound, not a tight pin."""
+    import pmom_inputs as PI
+    for w, bound in ((PI.workload_plain(), 1e5), (PI.workload_precision(), 2e5)):
+        OG = O.Grid(w.grid)
+        fr = w.freqs()
+        fs = fr[np.linspace(0, len(fr) - 1, 5).round().astype(int)]
+        Z, _ = O.fill(OG, fs)
+        maps = PI.workload_maps(w)[[0, 7, w.batch - 1]]
+        cs = []
+        for m in maps:
+            idx = O.active_set(OG, m)
+            for f in range(len(fs)):
+                A = Z[f][np.ix_(idx, idx)]
+                if w.z_dtype == "c64":
+                    A = A.astype(np.complex64).astype(np.complex128)
+                cs.append(np.linalg.cond(A))
+        print(w.name, "cond_2(Z_sub) min / median / max: %.3g / %.3g / %.3g" % (min(cs), np.median(cs), max(cs)))
+        assert max(cs) <= bound
+        assert max(cs) * 2.0 ** -24 < 1e-2
