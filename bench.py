@@ -8,7 +8,12 @@ each).  One step = one evaluation of the whole batch through the C ABI (activati
 LU + solves + refinement, S-parameters, FoM).  The database (0.72 GB) is larger than L2, so no
 L2 flush is needed between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload precision|plain]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload precision|plain|profile|batching|scale] [--batch B] [--no-cpu] [--no-bordered]
+
+The batching (3-layer 20x20 stripline with vias, 101 frequencies, support sets of about 800 to 2500)
+and scale (4-layer 32x32 stripline, 117 GB database, support sets of about 4100) workloads are
+opt-in legs; bound them with --batch.
 """
 from __future__ import annotations
 
