@@ -326,6 +326,15 @@ pmom_status pmom_kernel_times(pmom_ctx* ctx, double* ms4_host);
 /* Wait for all work the context issued on `stream`. */
 pmom_status pmom_sync(pmom_ctx* ctx, void* stream);
 
+/* Failure-detection self-test of the bounded completion wait that every tensor-core path uses
+ * (a stalled wait flags the task, PMOM_CAND_NONFINITE, instead of hanging the GPU): one warp waits
+ * on an mbarrier expecting one arrival, polling at most `polls` times (1 .. 2^30); with
+ * arrive != 0 it arrives first, otherwise nothing ever arrives.  *timed_out_host = 1 when the wait
+ * gave up, 0 when it saw the phase complete; *elapsed_ms_host = the kernel's CUDA-event time.  No
+ * context; synchronizes `stream`; the device stays usable.  Errors: INVALID_ARG, CUDA. */
+pmom_status pmom_selftest_wait(int64_t polls, int32_t arrive, int32_t* timed_out_host, double* elapsed_ms_host,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

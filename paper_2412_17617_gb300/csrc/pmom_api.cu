@@ -194,6 +194,31 @@ pmom_status ensure_device(pmom_ctx* c) {
 
 extern "C" {
 
+pmom_status pmom_selftest_wait(int64_t polls, int32_t arrive, int32_t* timed_out, double* elapsed_ms, void* stream) {
+  if (polls < 1 || polls > (1ll << 30) || !timed_out || !elapsed_ms) return PMOM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = pmom::launch_wait_selftest(polls, arrive != 0, d_out, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_out, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess) return PMOM_ERR_CUDA;
+  *timed_out = h;
+  *elapsed_ms = ms;
+  return PMOM_OK;
+}
+
 pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   if (!g || !out) return PMOM_ERR_INVALID_ARG;
   *out = nullptr;

@@ -15,6 +15,33 @@ bool eval_is_large(int precision, int ncap, int use_tc) {
   return precision == PMOM_FP64 ? needs_large_layout<double2>(ncap, false) : needs_large_layout<float2>(ncap, use_tc != 0);
 }
 
+// Failure-detection self-test of the bounded completion wait used by the tensor-core paths: one
+// warp initialises an mbarrier that expects one arrival; with `arrive` thread 0 arrives before
+// waiting, otherwise nothing ever arrives (a flag that nothing sets).  The wait polls at most
+// `polls` times and out[0] reports whether it gave up (1) or saw the phase complete (0).
+__global__ void wait_selftest_kernel(long long polls, int arrive, int* out) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) {
+      uint64_t state;
+      asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(tc::smem_u32(&mbar)) : "memory");
+      (void)state;
+    }
+    out[0] = tc::mbar_wait(&mbar, 0, polls) ? 0 : 1;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(&mbar)) : "memory");
+  }
+}
+
+cudaError_t launch_wait_selftest(long long polls, int arrive, int* d_out, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(polls, arrive, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {
   if (eval_is_large(precision, a.ncap, a.use_tc)) return launch_eval_large(a, precision, nslots, s);
   if (precision == PMOM_FP64) {

@@ -221,7 +221,9 @@ struct TcState {
   uint32_t phase;
   bool failed;
 };
-constexpr long long kTcWaitPolls = 1ll << 26;   // bounded wait; a stall flags the task instead of hanging
+// bounded wait: 2^18 polls of mbarrier.try_wait (about 1 s at the measured 3.8 us per unanswered
+// poll); a stall flags the task instead of hanging, a healthy completion answers in microseconds
+constexpr long long kTcWaitPolls = 1ll << 18;
 constexpr int kTcCols = 128;                     // complex output columns per tile (MMA N = 256 real)
 constexpr uint32_t kTmemCols = 2 * kTcCols;      // TMEM columns per task group
 

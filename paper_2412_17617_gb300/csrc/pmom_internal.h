@@ -126,6 +126,8 @@ cudaError_t launch_border(const BorderArgs& a, int nslots, int n, int df, cudaSt
 
 // Launchers (pmom_eval.cu).
 cudaError_t launch_activate(const EvalArgs& a, cudaStream_t s);
+// Self-test of the bounded mbarrier wait (pmom_eval.cu): d_out[0] = 1 when the wait gave up.
+cudaError_t launch_wait_selftest(long long polls, int arrive, int* d_out, cudaStream_t s);
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
 // Candidates sorted by support-set size, largest first (longest-processing-time order for the
 // persistent queue); one block, B <= 65536.

@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(kGT, 1) gemm_bf16_kernel(GemmArgs g) {
     }
     if (warp == 0) {   // the operands are overwritten by the next chunk: wait for the MMAs
       int ok = 1;
-      if (lane == 0) ok = tc::mbar_wait(&s_mbar, phase, 1ll << 24) ? 1 : 0;
+      // at most 2^18 polls (about 1 s at 3.8 us per unanswered try_wait), then the error flag
+      if (lane == 0) ok = tc::mbar_wait(&s_mbar, phase, 1ll << 18) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok && lane == 0) s_fail = 1;
     }

@@ -31,7 +31,7 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_autotune", "pmom_search", "pmom_eval_bordered",
            "pmom_mlp_create", "pmom_mlp_destroy", "pmom_mlp_last_error", "pmom_mlp_num_params", "pmom_mlp_get_params",
            "pmom_mlp_set_params", "pmom_mlp_forward", "pmom_mlp_backward", "pmom_mlp_adam", "pmom_mlp_predict_fom",
-           "pmom_mlp_targets", "pmom_mlp_errors")
+           "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait")
 
 
 class PmomError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_eval_candidates_noalloc": [V, P, I32, I32, P, P, P, V],
         "pmom_set_tensor_cores": [V, I32],
         "pmom_capacity": [V, I32, P, P],
+        "pmom_selftest_wait": [ctypes.c_int64, I32, P, P, V],
         "pmom_eval_bordered": [V, P, P, I32, I32, P, P, P, V],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
@@ -141,6 +142,18 @@ def band_codes(freqs, bands) -> np.ndarray:
 class _SearchParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("d_max", ctypes.c_int32), ("m_of_d", ctypes.c_int32 * 8),
                 ("max_evals", ctypes.c_int64), ("precision", ctypes.c_int32)]
+
+
+def selftest_wait(polls: int, arrive: bool, stream=None):
+    """Failure-detection self-test of the bounded completion wait (pmom_selftest_wait): returns
+    (timed_out, kernel milliseconds)."""
+    L = load_library()
+    to, ms = ctypes.c_int32(-1), ctypes.c_double(0.0)
+    st = L.pmom_selftest_wait(int(polls), 1 if arrive else 0, ctypes.byref(to), ctypes.byref(ms),
+                              ctypes.c_void_p(_stream_ptr(stream)))
+    if st != PMOM_OK:
+        raise PmomError(st, "pmom_selftest_wait")
+    return bool(to.value), ms.value
 
 
 class Evaluator:
