@@ -40,7 +40,9 @@ enum {
   PMOM_ERR_Z_SHAPE_MISMATCH = 4, /* Z / frequency / band shapes disagree with the grid */
   PMOM_ERR_CUDA = 5,             /* a CUDA runtime call failed; see pmom_last_error */
   PMOM_ERR_NOT_READY = 6,        /* call order: Z or the FoM bands not loaded yet */
-  PMOM_ERR_UNSUPPORTED = 7       /* feature outside this build (e.g. via states) */
+  PMOM_ERR_UNSUPPORTED = 7,      /* feature outside this build (e.g. more than three pixel states) */
+  PMOM_ERR_IO = 8                /* database file: open / read / write failed, not a database file,
+                                    truncated, or its checksum disagrees */
 };
 
 /* Storage of the parent matrix database. */
@@ -308,6 +310,19 @@ typedef struct {
 pmom_status pmom_search(pmom_ctx* ctx, const pmom_search_params* params, const uint8_t* init_map_host,
                         uint8_t* best_map_host, double* best_fom, int64_t* evals_used, double* trace_host,
                         int32_t trace_cap, int32_t* trace_len, void* stream);
+
+/* Database files (the paper's Phase 2 result, pre-computed once and reused).  Layout, little
+ * endian: "PMOMZDB1", uint32 version 1, uint32 dtype (PMOM_C64 / PMOM_C128), int32 M, int32 F,
+ * uint64 hash of the BF table (FNV-1a 64 over its M x 8 int32 in memory order), double freqs[F],
+ * the database [F][M][M] (interleaved re, im), uint64 checksum of the database (FNV-1a 64 over its
+ * 64-bit words).  pmom_save_Z writes the context's database (to path + ".tmp", then renamed);
+ * pmom_load_Z_file checks the header, the BF-table hash and the file size before any device work,
+ * then streams the data to the device (replacing the current database, as pmom_load_Z) and
+ * checks the checksum, dropping the database on a mismatch.  Both synchronize `stream`.
+ * Errors: INVALID_ARG, NOT_READY (save without a database), Z_SHAPE_MISMATCH (another grid: M or
+ * BF table differ), IO, OOM, CUDA. */
+pmom_status pmom_save_Z(pmom_ctx* ctx, const char* path, void* stream);
+pmom_status pmom_load_Z_file(pmom_ctx* ctx, const char* path, void* stream);
 
 /* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
  * max iterations of one task, tasks re-solved in FP64, tensor-core waits that ran out (the

@@ -1,5 +1,6 @@
 // C ABI of the evaluator: context, parent-database residency, FoM bands, and the evaluation
 // pipeline (activation -> persistent evaluation -> FP64 repair of unconverged tasks -> FoM).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -322,6 +323,166 @@ pmom_status pmom_load_Z(pmom_ctx* c, const double* freqs, int32_t F, const void*
   c->F = F;
   c->dtype = dtype;
   c->freqs.assign(freqs, freqs + F);
+  return PMOM_OK;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ database files
+constexpr char kZMagic[8] = {'P', 'M', 'O', 'M', 'Z', 'D', 'B', '1'};
+constexpr uint32_t kZVersion = 1;
+constexpr size_t kZChunk = size_t(64) << 20;   // bytes per host <-> device transfer
+
+uint64_t fnv1a_bytes(const void* p, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+  return h;
+}
+// FNV-1a over 64-bit words (n a multiple of 8)
+uint64_t fnv1a_words(const void* p, size_t n, uint64_t h) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b + i, 8);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  return h;
+}
+
+struct ZHeader {
+  char magic[8];
+  uint32_t version, dtype;
+  int32_t M, F;
+  uint64_t table_hash;
+};
+static_assert(sizeof(ZHeader) == 32, "database header layout");
+
+uint64_t table_hash(const pmom_ctx* c) {
+  return fnv1a_bytes(c->table.data(), c->table.size() * sizeof(int32_t));
+}
+
+}  // namespace
+
+pmom_status pmom_save_Z(pmom_ctx* c, const char* path, void* stream) {
+  if (!c || !path) return PMOM_ERR_INVALID_ARG;
+  if (!c->d_Z) return fail(c, PMOM_ERR_NOT_READY, "save_Z: no database");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* fp = std::fopen(tmp.c_str(), "wb");
+  if (!fp) return fail(c, PMOM_ERR_IO, "save_Z: cannot open " + tmp);
+  ZHeader h;
+  std::memcpy(h.magic, kZMagic, 8);
+  h.version = kZVersion;
+  h.dtype = static_cast<uint32_t>(c->dtype);
+  h.M = c->M;
+  h.F = c->F;
+  h.table_hash = table_hash(c);
+  bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 &&
+            std::fwrite(c->freqs.data(), sizeof(double), c->freqs.size(), fp) == c->freqs.size();
+  void* host = nullptr;
+  if (ok && cudaMallocHost(&host, kZChunk) != cudaSuccess) {
+    std::fclose(fp);
+    std::remove(tmp.c_str());
+    return fail(c, PMOM_ERR_OOM, "save_Z: pinned staging buffer");
+  }
+  uint64_t sum = 0xcbf29ce484222325ull;
+  cudaError_t e = cudaSuccess;
+  for (size_t off = 0; ok && off < c->z_bytes; off += kZChunk) {
+    const size_t n = std::min(kZChunk, c->z_bytes - off);
+    e = cudaMemcpyAsync(host, static_cast<const char*>(c->d_Z) + off, n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    sum = fnv1a_words(host, n, sum);
+    ok = std::fwrite(host, 1, n, fp) == n;
+  }
+  if (host) cudaFreeHost(host);
+  if (ok && e == cudaSuccess) ok = std::fwrite(&sum, sizeof(sum), 1, fp) == 1;
+  ok = (std::fclose(fp) == 0) && ok;
+  if (e != cudaSuccess) {
+    std::remove(tmp.c_str());
+    return fail(c, PMOM_ERR_CUDA, std::string("save_Z: ") + cudaGetErrorString(e));
+  }
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(c, PMOM_ERR_IO, std::string("save_Z: write failed for ") + path);
+  }
+  return PMOM_OK;
+}
+
+pmom_status pmom_load_Z_file(pmom_ctx* c, const char* path, void* stream) {
+  if (!c || !path) return PMOM_ERR_INVALID_ARG;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(c, PMOM_ERR_IO, std::string("load_Z_file: cannot open ") + path);
+  auto bail = [&](pmom_status st, const std::string& msg) {
+    std::fclose(fp);
+    return fail(c, st, "load_Z_file: " + msg);
+  };
+  ZHeader h;
+  if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kZMagic, 8) != 0 || h.version != kZVersion)
+    return bail(PMOM_ERR_IO, "not a database file (magic or version)");
+  if (h.dtype != PMOM_C64 && h.dtype != PMOM_C128) return bail(PMOM_ERR_IO, "unknown storage type");
+  if (h.M != c->M || h.table_hash != table_hash(c)) return bail(PMOM_ERR_Z_SHAPE_MISMATCH, "written for another grid");
+  if (h.F < 1) return bail(PMOM_ERR_Z_SHAPE_MISMATCH, "F < 1");
+  const size_t bytes = static_cast<size_t>(h.F) * h.M * h.M * z_elem(static_cast<int>(h.dtype));
+  const uint64_t expect = sizeof(h) + sizeof(double) * static_cast<uint64_t>(h.F) + bytes + sizeof(uint64_t);
+  if (std::fseek(fp, 0, SEEK_END) != 0) return bail(PMOM_ERR_IO, "seek");
+  const long long size = std::ftell(fp);
+  if (size < 0 || static_cast<uint64_t>(size) != expect) return bail(PMOM_ERR_IO, "truncated or oversized file");
+  std::vector<double> freqs(h.F);
+  if (std::fseek(fp, sizeof(h), SEEK_SET) != 0 ||
+      std::fread(freqs.data(), sizeof(double), freqs.size(), fp) != freqs.size())
+    return bail(PMOM_ERR_IO, "read frequencies");
+  // validated: now the device
+  const pmom_status dv = ensure_device(c);
+  if (dv) {
+    std::fclose(fp);
+    return dv;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (bytes != c->z_bytes) {
+    free_dev(c->d_Z);
+    c->z_bytes = 0;
+    if (cudaMalloc(&c->d_Z, bytes) != cudaSuccess) {
+      c->d_Z = nullptr;
+      return bail(PMOM_ERR_OOM, "database allocation");
+    }
+    c->z_bytes = bytes;
+  }
+  void* host = nullptr;
+  if (cudaMallocHost(&host, kZChunk) != cudaSuccess) return bail(PMOM_ERR_OOM, "pinned staging buffer");
+  uint64_t sum = 0xcbf29ce484222325ull, stored = 0;
+  bool ok = true;
+  cudaError_t e = cudaSuccess;
+  for (size_t off = 0; ok && off < bytes; off += kZChunk) {
+    const size_t n = std::min(kZChunk, bytes - off);
+    ok = std::fread(host, 1, n, fp) == n;
+    if (!ok) break;
+    sum = fnv1a_words(host, n, sum);
+    e = cudaMemcpyAsync(static_cast<char*>(c->d_Z) + off, host, n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+  }
+  cudaFreeHost(host);
+  if (ok && e == cudaSuccess) ok = std::fread(&stored, sizeof(stored), 1, fp) == 1;
+  std::fclose(fp);
+  if (e != cudaSuccess || !ok || stored != sum) {
+    free_dev(c->d_Z);
+    c->z_bytes = 0;
+    c->F = 0;
+    c->fom_ready = false;
+    if (e != cudaSuccess) return fail(c, PMOM_ERR_CUDA, std::string("load_Z_file: ") + cudaGetErrorString(e));
+    return fail(c, PMOM_ERR_IO, !ok ? "load_Z_file: read failed" : "load_Z_file: checksum mismatch");
+  }
+  if (h.F != c->F) {
+    c->fom_ready = false;
+    free_dev(c->d_S);
+    free_dev(c->d_repair);
+    c->b_cap = 0;
+    free_dev(c->d_idx);
+  }
+  c->F = h.F;
+  c->dtype = static_cast<int>(h.dtype);
+  c->freqs = freqs;
   return PMOM_OK;
 }
 

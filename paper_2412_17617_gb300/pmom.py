@@ -7,6 +7,7 @@ library is missing this module raises: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import struct
 import os
 from typing import Optional
 
@@ -22,7 +23,7 @@ PMOM_FP64, PMOM_MIXED_REFINED = 0, 1
 CAND_OK, CAND_SINGULAR, CAND_NONFINITE, CAND_REPAIRED, CAND_BAD_STATE, CAND_CAPACITY, CAND_FAR = 0, 1, 2, 3, 5, 6, 7
 BORDER_K = 8   # basis functions a candidate may remove from / add to the reference (pmom_eval_bordered)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z_SHAPE_MISMATCH", 5: "CUDA",
-                6: "NOT_READY", 7: "UNSUPPORTED"}
+                6: "NOT_READY", 7: "UNSUPPORTED", 8: "IO"}
 # names exported by libpmom.so, one per declaration in include/pmom.h
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
            "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
@@ -31,7 +32,7 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_autotune", "pmom_search", "pmom_eval_bordered",
            "pmom_mlp_create", "pmom_mlp_destroy", "pmom_mlp_last_error", "pmom_mlp_num_params", "pmom_mlp_get_params",
            "pmom_mlp_set_params", "pmom_mlp_forward", "pmom_mlp_backward", "pmom_mlp_adam", "pmom_mlp_predict_fom",
-           "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait")
+           "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait", "pmom_save_Z", "pmom_load_Z_file")
 
 
 class PmomError(RuntimeError):
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         "pmom_set_tensor_cores": [V, I32],
         "pmom_capacity": [V, I32, P, P],
         "pmom_selftest_wait": [ctypes.c_int64, I32, P, P, V],
+        "pmom_save_Z": [V, ctypes.c_char_p, V],
+        "pmom_load_Z_file": [V, ctypes.c_char_p, V],
         "pmom_eval_bordered": [V, P, P, I32, I32, P, P, P, V],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
@@ -119,6 +122,8 @@ def load_library(path: str = LIB_PATH):
 def _stream_ptr(stream) -> Optional[int]:
     if stream is None:
         import torch
+        if not torch.cuda.is_available():   # host-only calls (argument and file checks) on a machine without a GPU
+            return 0
         return torch.cuda.current_stream().cuda_stream
     return getattr(stream, "cuda_stream", stream)
 
@@ -224,6 +229,17 @@ class Evaluator:
         self._check(self.L.pmom_fill_Z(self.h, f.ctypes.data_as(ctypes.c_void_p), len(f), code,
                                        ctypes.c_void_p(_stream_ptr(stream))))
         self.F, self.dtype = len(f), code
+
+    def save_Z(self, path: str, stream=None):
+        """Write the database to a file (pmom_save_Z)."""
+        self._check(self.L.pmom_save_Z(self.h, os.fsencode(path), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def load_Z_file(self, path: str, stream=None):
+        """Load a database file written by save_Z for this grid (pmom_load_Z_file)."""
+        self._check(self.L.pmom_load_Z_file(self.h, os.fsencode(path), ctypes.c_void_p(_stream_ptr(stream))))
+        with open(path, "rb") as fh:
+            _, _, dtype, _, F = struct.unpack("<8sIIii", fh.read(24))
+        self.F, self.dtype = F, dtype
 
     def copy_Z(self):
         import torch
