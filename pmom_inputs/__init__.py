@@ -128,6 +128,15 @@ def grid_stripline_32x32x4() -> Grid:
                 5 * h, 3.66, 0.004, 2, ports)
 
 
+def grid_microstrip_24x24x3() -> Grid:
+    """3-layer 24x24 microstrip of 0.4 mm pixels (the 8-state pixel = three on/off layers, Section
+    IV-B), Rogers 4350B layers of 0.4866 mm over one ground plane; ports 1 right, 2 top, 3 left on
+    the top layer."""
+    h = H_RO4350
+    return Grid("microstrip_24x24x3", 3, 24, 24, 0.4e-3, MEDIUM_MICROSTRIP, (h, 2 * h, 3 * h), 3 * h, 3.66, 0.004,
+                2, _three_side_ports(24, layer=2))
+
+
 def grid_tiny(n: int = 3, medium: int = MEDIUM_MICROSTRIP, layers: int = 1, pitch_m: float = 2.0e-3) -> Grid:
     """Small grids for brute force and oracle pins."""
     if medium == MEDIUM_MICROSTRIP:
@@ -163,6 +172,13 @@ def workload_profile() -> Workload:
 
 def workload_batching() -> Workload:
     return Workload("stripline_20x20x3_f101_b4096", grid_stripline_20x20x3(), 0.5e9, 8e9, 101, 0.5, 4096, "c64",
+                    UNII_BANDS)
+
+
+def workload_learned() -> Workload:
+    """The pre-ranker's configuration: 3-layer 24x24 microstrip, 64 frequencies 3-9 GHz, complex64,
+    candidate pools of 10k changes per search step."""
+    return Workload("microstrip_24x24x3_f64_b10000", grid_microstrip_24x24x3(), 3e9, 9e9, 64, 0.5, 10000, "c64",
                     UNII_BANDS)
 
 

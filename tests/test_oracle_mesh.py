@@ -14,10 +14,12 @@ def _m_closed_form(g):
 
 
 @pytest.mark.parametrize("g", [PI.grid_plain_8x8(), PI.grid_stripline_16x16x2(), PI.grid_tiny(3),
-                               PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2)])
+                               PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2), PI.grid_microstrip_24x24x3()])
 def test_bf_count_closed_form(g):
     G = O.Grid(g)
     assert G.M == _m_closed_form(g)
+    if g.name == "microstrip_24x24x3":
+        assert G.M == 5052
     if g.name == "plain_8x8_microstrip":
         assert G.M == 188
     if g.name == "stripline_16x16x2":
