@@ -484,14 +484,6 @@ typedef struct {
   const double* z;             /* [nz] heights */
 } fill_job;
 
-static void key_parts(int32_t key, int* layer, int* x, int* y, int* half) {
-  *half = key & 3;
-  key >>= 2;
-  *x = key % 128 - 4;
-  key /= 128;
-  *y = key % 128 - 4;
-  *layer = key / 128;
-}
 
 static void* fill_worker(void* arg) {
   fill_job* J = (fill_job*)arg;
@@ -500,17 +492,18 @@ static void* fill_worker(void* arg) {
   const tri_t* tris = J->tris;
   /* pair-integral storage: direct mode keeps all T x T pairs; table mode keeps one entry per
    * (layer pair, orientation/triangle pair, lattice offset) */
-  int W = (g->nx > g->ny ? g->nx : g->ny) + 5, NW = 2 * W + 1;
+  int sub = g->sub > 1 ? g->sub : 1;
+  int W = ((g->nx > g->ny ? g->nx : g->ny) + 5) * sub, NW = 2 * W + 1;
   size_t nslots = J->mode == 0 ? (size_t)T * T : (size_t)g->layers * g->layers * 64 * NW * NW;
   double complex* slot = (double complex*)malloc(sizeof(double complex) * 10 * nslots);
   unsigned char* have = (unsigned char*)malloc(nslots);
   int32_t* pair_slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * T);
   for (int p = 0; p < T; ++p) {
     int lp, xp, yp, hp;
-    key_parts(J->tri_keys[p], &lp, &xp, &yp, &hp);
+    or_key_parts(g, J->tri_keys[p], &lp, &xp, &yp, &hp);
     for (int q = 0; q < T; ++q) {
       int lq, xq, yq, hq;
-      key_parts(J->tri_keys[q], &lq, &xq, &yq, &hq);
+      or_key_parts(g, J->tri_keys[q], &lq, &xq, &yq, &hq);
       size_t s;
       if (J->mode == 0) s = (size_t)p * T + q;
       else {
@@ -588,7 +581,7 @@ static int collect_triangles(const or_grid* g, const int32_t* table, int M, int3
     double v[3][3];
     int layer, x, y, half;
     or_triangle(g, keys[t], v);
-    key_parts(keys[t], &layer, &x, &y, &half);
+    or_key_parts(g, keys[t], &layer, &x, &y, &half);
     tri_setup(&tris[t], v, layer);
   }
   double* z = (double*)malloc(sizeof(double) * (g->layers + 40 * T + 1));
@@ -604,8 +597,11 @@ double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threa
   int32_t* table = (int32_t*)malloc(sizeof(int32_t) * OR_BF_COLS * M);
   or_bf_table(g, table);
   /* distinct triangles referenced by the BFs */
-  int32_t* key_to_tri = (int32_t*)malloc(sizeof(int32_t) * (1 << 21));
-  for (int i = 0; i < (1 << 21); ++i) key_to_tri[i] = -1;
+  int32_t kmax = 0;
+  for (int m = 0; m < M; ++m)
+    for (int s = 0; s < 2; ++s) if (table[OR_BF_COLS * m + 4 + s] > kmax) kmax = table[OR_BF_COLS * m + 4 + s];
+  int32_t* key_to_tri = (int32_t*)malloc(sizeof(int32_t) * ((size_t)kmax + 1));
+  for (int32_t i = 0; i <= kmax; ++i) key_to_tri[i] = -1;
   int32_t* keys = (int32_t*)malloc(sizeof(int32_t) * 2 * M);
   tri_t* tris;
   double* z;
@@ -656,7 +652,7 @@ void or_pair_integrals(const or_grid* g, double freq, int32_t kp, int32_t kq, do
     double v[3][3];
     int layer, x, y, half;
     or_triangle(g, keys[i], v);
-    key_parts(keys[i], &layer, &x, &y, &half);
+    or_key_parts(g, keys[i], &layer, &x, &y, &half);
     tri_setup(&tr[i], v, layer);
   }
   double* z = (double*)malloc(sizeof(double) * (g->layers + 80));

@@ -4,10 +4,13 @@
  * For one pixel map and one frequency (Section II-C and II-E):
  *   support set I (Eq. 3, ascending) -> Z_sub = S^T Z_parent S (Eq. 4-5, i.e. rows and columns I)
  *   -> solve Z_sub X = V for every port excitation (Eq. 2) -> port currents I_i = l_i x_i (Eq. 7)
- *   -> S-parameters.  Two equivalent forms are provided:
- *      form 0: unloaded delta-gap solve, V = l_j at the port-j BF; Y_ij = l_i x_i^(j);
- *              S = (1 + Z0 Y)^-1 (1 - Z0 Y)
- *      form 1: every port BF carries its Z0 load (Z_pp += Z0 l_p^2) and an EMF of 1 V drives
+ *   -> S-parameters.  A port's delta gap is its gap BFs (one with the two-triangle mesh, s with
+ *   s x s sub-squares per pixel); a unit gap voltage drives each of them with V_k = l_k, and the
+ *   port current is the sum over them.  Two equivalent forms are provided:
+ *      form 0: unloaded delta-gap solve, V = l_k at the gap BFs of port j;
+ *              Y_ij = sum over the gap of port i of l_k x_k^(j);  S = (1 + Z0 Y)^-1 (1 - Z0 Y)
+ *      form 1: every port carries its Z0 load across its gap (Z_kk' += Z0 l_k l_k' for gap BFs
+ *              k, k' of one port; Z_pp += Z0 l_p^2 with one gap BF) and an EMF of 1 V drives
  *              port j; S_ij = delta_ij - 2 Z0 I_i / V_j (Eq. 6)
  * FoM of Eq. (8)-(9) with S in dB = 20 log10(max(|S|, 1e-15)); lower is better.
  */
@@ -91,42 +94,53 @@ static int eval_one(const or_grid* g, const int32_t* table, int M, const void* Z
         A[(size_t)a * N + b] = ((const double complex*)Zf)[off];
       }
     }
-  /* position of each port BF (canonical index 3p + 1) in the support set */
-  int* pos = (int*)malloc(sizeof(int) * P);
-  double* lp = (double*)malloc(sizeof(double) * P);
+  /* the gap BFs of each port: canonical indices, which are also their positions in the support
+   * set (the always-present stub BFs come first), and their edge lengths */
+  int32_t gap[4][3];
+  double lg[4][3];
+  int ng = 0;
   for (int p = 0; p < P; ++p) {
-    pos[p] = -1;
-    for (int a = 0; a < N; ++a) if (idx[a] == 3 * p + 1) pos[p] = a;
-    lp[p] = port_edge_length(g, table, 3 * p + 1);
+    ng = or_port_gap(g, p, gap[p]);
+    for (int k = 0; k < ng; ++k) {
+      if (gap[p][k] >= N || idx[gap[p][k]] != gap[p][k]) { free(A); return 1; }
+      lg[p][k] = port_edge_length(g, table, gap[p][k]);
+    }
   }
   if (form == 1)
-    for (int p = 0; p < P; ++p) A[(size_t)pos[p] * N + pos[p]] += Z0 * lp[p] * lp[p];
+    for (int p = 0; p < P; ++p)
+      for (int k = 0; k < ng; ++k)
+        for (int q = 0; q < ng; ++q) A[(size_t)gap[p][k] * N + gap[p][q]] += Z0 * lg[p][k] * lg[p][q];
   double complex* X = (double complex*)calloc((size_t)N * P, sizeof(double complex));
-  for (int j = 0; j < P; ++j) X[(size_t)pos[j] * P + j] = lp[j] * 1.0;
+  for (int j = 0; j < P; ++j)
+    for (int k = 0; k < ng; ++k) X[(size_t)gap[j][k] * P + j] = lg[j][k] * 1.0;
   int32_t* piv = (int32_t*)malloc(sizeof(int32_t) * N);
   int sing = or_lu(A, N, piv);
   or_lu_solve(A, piv, N, X, P);
+  /* port currents: I_ij = sum over the gap of port i of l_k x_k^(j) */
+  double complex Ip[16];
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      double complex c = 0.0;
+      for (int k = 0; k < ng; ++k) c += lg[i][k] * X[(size_t)gap[i][k] * P + j];
+      Ip[i * P + j] = c;
+    }
   if (form == 0) {
-    /* Y_ij = l_i x_i^(j); S = (1 + Z0 Y)^-1 (1 - Z0 Y) */
+    /* Y = I (unit gap voltages); S = (1 + Z0 Y)^-1 (1 - Z0 Y) */
     double complex Ap[16], Bp[16];
     int32_t pv[4];
     for (int i = 0; i < P; ++i)
       for (int j = 0; j < P; ++j) {
-        double complex y = lp[i] * X[(size_t)pos[i] * P + j];
-        Ap[i * P + j] = (i == j ? 1.0 : 0.0) + Z0 * y;
-        Bp[i * P + j] = (i == j ? 1.0 : 0.0) - Z0 * y;
+        Ap[i * P + j] = (i == j ? 1.0 : 0.0) + Z0 * Ip[i * P + j];
+        Bp[i * P + j] = (i == j ? 1.0 : 0.0) - Z0 * Ip[i * P + j];
       }
     or_lu(Ap, P, pv);
     or_lu_solve(Ap, pv, P, Bp, P);
     memcpy(S, Bp, sizeof(double complex) * P * P);
   } else {
     for (int i = 0; i < P; ++i)
-      for (int j = 0; j < P; ++j) {
-        double complex Ii = lp[i] * X[(size_t)pos[i] * P + j];
-        S[i * P + j] = (i == j ? 1.0 : 0.0) - 2.0 * Z0 * Ii / 1.0;
-      }
+      for (int j = 0; j < P; ++j) S[i * P + j] = (i == j ? 1.0 : 0.0) - 2.0 * Z0 * Ip[i * P + j] / 1.0;
   }
-  free(A); free(pos); free(lp); free(X); free(piv);
+  free(A); free(X); free(piv);
   return sing;
 }
 

@@ -47,7 +47,7 @@ class _Grid(ctypes.Structure):
                 ("layer_z", ctypes.POINTER(ctypes.c_double)), ("h_total", ctypes.c_double),
                 ("eps_r", ctypes.c_double), ("tan_d", ctypes.c_double), ("n_states", ctypes.c_int),
                 ("n_ports", ctypes.c_int), ("ports", ctypes.POINTER(ctypes.c_int32)),
-                ("diag_pattern", ctypes.c_int), ("diag_seed", ctypes.c_uint64)]
+                ("diag_pattern", ctypes.c_int), ("diag_seed", ctypes.c_uint64), ("sub", ctypes.c_int)]
 
 
 def lib():
@@ -87,6 +87,8 @@ def lib():
             L.or_bands.argtypes = [P, ctypes.c_int, P, P]
             L.or_triangle.argtypes = [P, ctypes.c_int32, P]
             L.or_orient.argtypes = [P, ctypes.c_int, ctypes.c_int]
+            L.or_stub_bfs.argtypes = [P]
+            L.or_port_gap.argtypes = [P, ctypes.c_int, P]
             L.or_pair_integrals.argtypes = [P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, P]
             _lib = L
     return _lib
@@ -106,7 +108,9 @@ class Grid:
         self.c = _Grid(g.layers, g.nx, g.ny, g.pitch_m, g.medium,
                        self._z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), g.h_total_m, g.eps_r, g.tan_d,
                        g.n_states, len(g.ports), self._ports.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                       getattr(g, "diag_pattern", 0), getattr(g, "diag_seed", 0))
+                       getattr(g, "diag_pattern", 0), getattr(g, "diag_seed", 0), getattr(g, "sub", 1))
+        if getattr(g, "sub", 1) not in (1, 2, 3) or (getattr(g, "sub", 1) > 1 and g.n_states > 2):
+            raise ValueError("sub-squares per pixel side: 1, 2 or 3; the via state needs 1")
         self.ref = ctypes.byref(self.c)
         self.M = lib().or_count_bfs(self.ref)
         self.P = len(g.ports)
@@ -232,16 +236,27 @@ def eval_map(grid: Grid, Z: np.ndarray, pixel_map: np.ndarray, Z0: float = 50.0,
     return S, st
 
 
-def port_lengths(grid: Grid) -> np.ndarray:
-    """Length of each port's delta-gap edge: the edge of BF 3p + 1 opposite the free vertex of its
-    positive triangle (RWG edge length, Section II-C)."""
-    out = np.zeros(grid.P)
+def port_gaps(grid: Grid):
+    """Per port: the canonical indices of its delta-gap BFs (3p + 1 alone with the two-triangle
+    mesh) and their edge lengths (the edge opposite the free vertex of the positive triangle,
+    Section II-C)."""
+    out = []
     for p in range(grid.P):
-        r = grid.table[3 * p + 1]
-        v = triangle(grid, int(r[4]))
-        f = int(r[6])
-        out[p] = float(np.linalg.norm(v[(f + 1) % 3] - v[(f + 2) % 3]))
+        bf = np.zeros(3, np.int32)
+        n = lib().or_port_gap(grid.ref, p, _ptr(bf))
+        lens = []
+        for m in bf[:n]:
+            r = grid.table[int(m)]
+            v = triangle(grid, int(r[4]))
+            f = int(r[6])
+            lens.append(float(np.linalg.norm(v[(f + 1) % 3] - v[(f + 2) % 3])))
+        out.append((bf[:n].copy(), np.array(lens)))
     return out
+
+
+def port_lengths(grid: Grid) -> np.ndarray:
+    """Length of each port's delta-gap edge (two-triangle mesh: one gap BF per port)."""
+    return np.array([lens[0] for _, lens in port_gaps(grid)])
 
 
 def eval_map_lapack(grid: Grid, Z: np.ndarray, pixel_map: np.ndarray, Z0: float = 50.0) -> np.ndarray:
@@ -252,16 +267,17 @@ def eval_map_lapack(grid: Grid, Z: np.ndarray, pixel_map: np.ndarray, Z0: float 
     where the plain C LU takes minutes."""
     idx = active_set(grid, pixel_map)
     P = grid.P
-    pos = np.array([int(np.nonzero(idx == 3 * p + 1)[0][0]) for p in range(P)])
-    lp = port_lengths(grid)
+    gaps = port_gaps(grid)
     V = np.zeros((len(idx), P), np.complex128)
-    V[pos, np.arange(P)] = lp
+    for p, (bf, lens) in enumerate(gaps):
+        pos = np.array([int(np.nonzero(idx == m)[0][0]) for m in bf])
+        V[pos, p] = lens
     S = np.zeros((Z.shape[0], P, P), np.complex128)
     eye = np.eye(P)
     for f in range(Z.shape[0]):
         A = Z[f][np.ix_(idx, idx)].astype(np.complex128)
         X = np.linalg.solve(A, V)
-        Y = lp[:, None] * X[pos, :]
+        Y = np.stack([V[:, p] @ X for p in range(P)])       # sum over port p's gap of l_k x_k
         S[f] = np.linalg.solve(eye + Z0 * Y, eye - Z0 * Y)
     return S
 

@@ -39,6 +39,8 @@ typedef struct {
   const int32_t* ports;    /* [n_ports][3] = layer, side (0 right, 1 top, 2 left, 3 bottom), pos */
   int diag_pattern;        /* pixel diagonals (Section V-A, Fig. mesh_orientation a-c): 0 alternating, 1 uniform, 2 random */
   uint64_t diag_seed;      /* pattern 2: seed of the per-position orientation draw */
+  int sub;                 /* sub-squares per pixel side: 1, 2 or 3 (2, 8 or 18 triangles per pixel,
+                              Section V-A); 0 reads as 1; vias need 1 */
 } or_grid;
 
 /* Basis-function classes (Section II-C), plus the three BFs of a via site (state 2). */
@@ -48,12 +50,20 @@ enum { OR_BF_ALWAYS = 0, OR_BF_INNER = 1, OR_BF_INTER = 2, OR_BF_PIXPORT = 3,
 /* One BF-table row = 8 int32:
  *   [0] class  [1] pixel A  [2] pixel B  [3] port (or -1)
  *   [4] key of T+  [5] key of T-  [6] free-vertex index in T+  [7] free-vertex index in T-
- * pixel index = (layer*ny + y)*nx + x; triangle key = (((layer*128 + y+4)*128 + x+4)*4 + half),
- * half 0/1 = the pixel's triangles, 2/3 = the triangles Ta/Tb of the via strip from the pixel up
- * to layer+1.  Via rows: [1] = the via pixel (l, x, y); [2] = (l+1, x, y) for the landing junction. */
+ * pixel index = (layer*ny + y)*nx + x; triangle key = (((layer*W + Y+4s)*W + X+4s)*4 + half) with
+ * W = 128 s and (X, Y) the sub-square on the fine lattice (the pixel itself when s = 1); half 0/1 =
+ * the sub-square's triangles, 2/3 = the triangles Ta/Tb of the via strip from the pixel up to
+ * layer+1.  Via rows: [1] = the via pixel (l, x, y); [2] = (l+1, x, y) for the landing junction. */
 #define OR_BF_COLS 8
 
 int or_count_bfs(const or_grid* g);
+/* Always-present BFs per port stub (3 when s = 1), and the delta-gap BFs of port p: their
+ * canonical indices (s of them; 3p+1 when s = 1), which are also their positions in every
+ * support set (the stub BFs come first).  Returns s. */
+int or_stub_bfs(const or_grid* g);
+int or_port_gap(const or_grid* g, int p, int32_t* bf);
+/* Fine-lattice parts of a triangle key. */
+void or_key_parts(const or_grid* g, int32_t key, int* layer, int* X, int* Y, int* half);
 int or_bf_table(const or_grid* g, int32_t* table);
 /* Eq. (3): ascending indices of the BFs active under `map` ([layers][ny][nx] states).
  * Returns N >= 0, or -1 if a state is out of range. */

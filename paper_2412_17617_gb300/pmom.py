@@ -167,6 +167,8 @@ class Evaluator:
     def __init__(self, grid):
         self.L = load_library()
         self.grid = grid
+        if getattr(grid, "sub", 1) != 1:
+            raise PmomError(7, "pmom_create: 8- and 18-triangle pixel meshes are not in this build")
         self._last_kind = "eval"
         self._z = (ctypes.c_double * grid.layers)(*grid.layer_z_m)
         self._ports = (_Port * len(grid.ports))(*[_Port(p.layer, p.side, p.pos) for p in grid.ports])

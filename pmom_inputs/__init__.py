@@ -48,6 +48,7 @@ class Grid:
     ports: Tuple[Port, ...]
     diag_pattern: int = 0     # pixel diagonals: 0 alternating, 1 uniform, 2 random (seeded by diag_seed)
     diag_seed: int = 0
+    sub: int = 1              # sub-squares per pixel side: 1, 2, 3 = 2, 8, 18 triangles per pixel
 
     @property
     def n_pixels(self) -> int:

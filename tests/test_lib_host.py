@@ -74,6 +74,11 @@ def test_argument_validation(lib):
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(pat)
     assert e.value.status == 1
+    # the 8- and 18-triangle pixel meshes are in the oracle only: the library refuses them loudly
+    import dataclasses
+    with pytest.raises(pmom.PmomError) as e:
+        pmom.Evaluator(dataclasses.replace(g, sub=2))
+    assert e.value.status == 7
     four = PI.Grid("four", 2, 3, 3, 1e-3, 0, (0.5e-3, 1e-3), 1e-3, 3.5, 0.0, 4, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(four)
