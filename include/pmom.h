@@ -92,6 +92,11 @@ typedef struct {
                                   1 uniform (always the first), 2 random (the first when the top bit
                                   of SplitMix64 chained over diag_seed and (y+4)*128 + x+4 is 0) */
   uint64_t diag_seed;          /* pattern 2 only */
+  int32_t sub;                 /* sub-squares per pixel side, on the same fine lattice pattern: 1, 2 or 3
+                                  (2, 8 or 18 triangles per pixel, Section V-A; 0 reads as 1).  With
+                                  s > 1 a port's delta gap is the s edges between its stub pixels,
+                                  driven together (V_k = l_k) with the port current summed over them;
+                                  the via state and the bordered update need s = 1 */
 } pmom_grid_desc;
 
 typedef struct pmom_ctx pmom_ctx;

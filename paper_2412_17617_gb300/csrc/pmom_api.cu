@@ -229,6 +229,8 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   if (g->n_states != 2 && g->n_states != 3) return PMOM_ERR_UNSUPPORTED;
   if (g->n_states == 3 && g->layers < 2) return PMOM_ERR_INVALID_ARG;   // a via needs a layer above
   if (g->diag_pattern < 0 || g->diag_pattern > 2) return PMOM_ERR_INVALID_ARG;
+  if (g->sub < 0 || g->sub > 3) return PMOM_ERR_INVALID_ARG;
+  if (g->sub > 1 && g->n_states == 3) return PMOM_ERR_INVALID_ARG;   // the via stands on a pixel diagonal
   for (int p = 0; p < g->n_ports; ++p) {
     const pmom_port& q = g->ports[p];
     const int lim = (q.side == 0 || q.side == 2) ? g->ny : g->nx;
@@ -238,7 +240,7 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   pmom_ctx* c = new pmom_ctx();
   pmom::Grid& gr = c->grid;
   gr.layers = g->layers; gr.nx = g->nx; gr.ny = g->ny; gr.medium = g->medium; gr.n_states = g->n_states;
-  gr.diag_pattern = g->diag_pattern; gr.diag_seed = g->diag_seed;
+  gr.diag_pattern = g->diag_pattern; gr.diag_seed = g->diag_seed; gr.sub = g->sub > 1 ? g->sub : 1;
   gr.n_ports = g->n_ports; gr.pitch = g->pitch_m; gr.h_total = g->h_total_m; gr.eps_r = g->eps_r; gr.tan_d = g->tan_d;
   gr.layer_z.assign(g->layer_z_m, g->layer_z_m + g->layers);
   gr.ports.assign(g->ports, g->ports + g->n_ports);
@@ -543,7 +545,8 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
   a.rules = c->d_rules; a.M = c->M; a.P = P; a.F = c->F; a.B = B; a.npix = c->grid.pixels();
   a.n_states = c->grid.n_states; a.via_top = c->grid.via_top(); a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.Z = c->d_Z;
   a.z_c128 = c->dtype == PMOM_C128;
-  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch;   // delta-gap edges are pixel sides
+  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch / c->grid.subs();   // gap edges: sub-square sides
+  a.gap_stride = c->grid.stub_bfs(); a.gap_off = c->grid.inner_bfs(); a.gap_n = c->grid.subs();
   a.Z0 = c->Z0;
   a.S = S_out ? reinterpret_cast<double2*>(S_out) : c->d_S;
   a.flags = c->d_flags;
@@ -618,6 +621,8 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
       (precision != PMOM_FP64 && precision != PMOM_MIXED_REFINED))
     return fail(c, PMOM_ERR_INVALID_ARG, "eval_bordered: bad argument");
   if (!c->d_Z || !c->fom_ready) return fail(c, PMOM_ERR_NOT_READY, "eval_bordered: load Z and set the FoM bands first");
+  if (c->grid.subs() > 1)   // its port rows assume one gap BF per port (position 3p+1)
+    return fail(c, PMOM_ERR_UNSUPPORTED, "eval_bordered: pixels of more than two triangles");
   pmom_status st = ensure_batch(c, B);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -671,7 +676,8 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
     fa.rules = c->d_rules; fa.M = M; fa.P = P; fa.F = F; fa.B = 1; fa.npix = c->grid.pixels();
     fa.n_states = c->grid.n_states; fa.via_top = c->grid.via_top(); fa.maps = ref_map; fa.idx = c->d_ref_idx; fa.n_act = d_ref_n;
     fa.Z = c->d_Z; fa.z_c128 = 0;
-    for (int p = 0; p < pmom::kMaxPorts; ++p) fa.port_len[p] = c->grid.pitch;
+    for (int p = 0; p < pmom::kMaxPorts; ++p) fa.port_len[p] = c->grid.pitch / c->grid.subs();   // gap edges: sub-square sides
+    fa.gap_stride = c->grid.stub_bfs(); fa.gap_off = c->grid.inner_bfs(); fa.gap_n = c->grid.subs();
     fa.Z0 = c->Z0; fa.flags = c->d_ref_flags; fa.task_counter = small;
     fa.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
     fa.work = c->d_ref_work; fa.slot_bytes = sb; fa.lda = lda; fa.ncap = n; fa.use_tc = c->use_tc;
@@ -724,7 +730,7 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
   ba.idx = c->d_idx; ba.n_act = c->d_nact;
   double2* Sd = S_out ? reinterpret_cast<double2*>(S_out) : c->d_S;
   ba.S = Sd; ba.flags = c->d_flags;
-  for (int p = 0; p < pmom::kMaxPorts; ++p) ba.port_len[p] = c->grid.pitch;
+  for (int p = 0; p < pmom::kMaxPorts; ++p) ba.port_len[p] = c->grid.pitch;   // one gap edge (s = 1)
   ba.task_counter = small;
   ba.work = c->d_bwork; ba.slot_elems = se;
   PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
@@ -1008,7 +1014,8 @@ extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* 
   a.flags = reinterpret_cast<uint32_t*>(base + o_flags);
   a.Z = c->d_Z;
   a.z_c128 = c->dtype == PMOM_C128;
-  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch;
+  for (int p = 0; p < pmom::kMaxPorts; ++p) a.port_len[p] = c->grid.pitch / c->grid.subs();   // gap edges: sub-square sides
+  a.gap_stride = c->grid.stub_bfs(); a.gap_off = c->grid.inner_bfs(); a.gap_n = c->grid.subs();
   a.Z0 = c->Z0;
   a.S = S_out ? reinterpret_cast<double2*>(S_out) : reinterpret_cast<double2*>(base + o_S);
   a.task_counter = small;

@@ -777,13 +777,16 @@ __device__ __forceinline__ void dd_add(float& ah, float& al, float bh, float bl)
 // partial sums), lane partials combined across the warp in float-float too, so the FP64 pipe
 // (1/64 of the FP32 rate) only sees one conversion per output.  xs: x split as
 // (re_hi, re_lo, im_hi, im_lo).  NP: compile-time bound on the port count P.
-// V: the port excitation V[3p+1][p] = l_p when e0 < 0, else the identity columns V[e0+p][p] = 1.
+// V: the port excitation V[k][p] = l_p on port p's gap BFs k = p * gap_stride + gap_off + j,
+// j < gap_n (one BF, 3p+1, with two-triangle pixels) when e0 < 0, else the identity columns
+// V[e0+p][p] = 1.
 // F32OUT (identity columns only): the residual is formed in float-float and written rounded to
 // float into rw (the precision of the correction solve that consumes it), with no FP64 work.
 template <int NP, bool F32OUT = false>
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
                             const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
-                            int e0 = -1, float2* __restrict__ rw = nullptr) {
+                            int e0 = -1, float2* __restrict__ rw = nullptr, int gap_stride = 3, int gap_off = 1,
+                            int gap_n = 1) {
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
@@ -858,7 +861,9 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
           } else {
             const double vx = static_cast<double>(xh) + static_cast<double>(xl);
             const double vy = static_cast<double>(yh) + static_cast<double>(yl);
-            const double vv = e0 < 0 ? ((i == 3 * p + 1) ? lport[p] : 0.0) : ((i == e0 + p) ? 1.0 : 0.0);
+            const double vv = e0 < 0 ? (static_cast<unsigned>(i - (p * gap_stride + gap_off)) < static_cast<unsigned>(gap_n)
+                                             ? lport[p] : 0.0)
+                                      : ((i == e0 + p) ? 1.0 : 0.0);
             const double2 ri = make_double2(vv - vx, -vy);
             r[i * P + p] = ri;
             rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
@@ -897,7 +902,8 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
 // ||Z_sub||_inf in s_out[0..1].  x_s: shared copy of x (N x P double2).
 template <typename ZT>
 __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict__ s_idx, int N, const double2* x_s,
-                         int P, const double* lport, double2* __restrict__ r, double* s_red, double* s_out) {
+                         int P, const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
+                         int gap_stride, int gap_off, int gap_n) {
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
   for (int i = warp; i < N; i += kWarps) {
@@ -925,7 +931,8 @@ __device__ void residual(const ZT* __restrict__ Zf, int M, const int* __restrict
         v.y += __shfl_down_sync(0xffffffffu, v.y, d);
       }
       if (lane == 0) {
-        const double vv = (i == 3 * p + 1) ? lport[p] : 0.0;
+        const double vv =
+            static_cast<unsigned>(i - (p * gap_stride + gap_off)) < static_cast<unsigned>(gap_n) ? lport[p] : 0.0;
         const double2 ri = make_double2(vv - v.x, -v.y);
         r[i * P + p] = ri;
         rmax = fmax(rmax, fabs(ri.x) + fabs(ri.y));
@@ -1192,10 +1199,12 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       gsync();
       continue;
     }
-    // right-hand sides: V[3p+1][p] = l_p (delta gap of 1 V on port p's edge)
+    // right-hand sides: V[k][p] = l_p on port p's gap BFs (a delta gap of 1 V; one BF, 3p+1,
+    // with two-triangle pixels)
     for (int e = tid; e < N * P; e += kThreads) {
       const int i = e / P, p = e % P;
-      W[e] = from_d2<CT>(make_double2(i == 3 * p + 1 ? lport[p] : 0.0, 0.0));
+      const bool gap = static_cast<unsigned>(i - (p * a.gap_stride + a.gap_off)) < static_cast<unsigned>(a.gap_n);
+      W[e] = from_d2<CT>(make_double2(gap ? lport[p] : 0.0, 0.0));
     }
     gsync();
     lu_solve<CT>(A, lda, N, piv, W, P, Dg);
@@ -1219,15 +1228,18 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
             xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
           }
           gsync();
-          if (P <= 3) residual_df<3>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm);
-          else residual_df<kMaxPorts>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm);
+          if (P <= 3)
+            residual_df<3>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off, a.gap_n);
+          else
+            residual_df<kMaxPorts>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off,
+                                   a.gap_n);
         } else {
           for (int e = tid; e < N * P; e += kThreads) {
             xs[e] = X[e];
             xmax = fmax(xmax, fabs(X[e].x) + fabs(X[e].y));
           }
           gsync();
-          residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm);
+          residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm, a.gap_stride, a.gap_off, a.gap_n);
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
@@ -1302,11 +1314,17 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       }
     }
     tcs.failed = false;
-    // port admittances Y_ij = l_i x_i^(j) (Eq. 7) into the S slot; ys_kernel converts them
+    // port admittances Y_ij = sum over port i's gap BFs k of l_i x_k^(j) (Eq. 7; one BF, 3i+1, with
+    // two-triangle pixels) into the S slot; ys_kernel converts them
     if (!repaired && tid < P * P) {
       const int i = tid / P, j = tid % P;
-      const double2 xv = X[(3 * i + 1) * P + j];
-      Sout[tid] = make_double2(lport[i] * xv.x, lport[i] * xv.y);
+      double2 y = make_double2(0.0, 0.0);
+      for (int k = 0; k < a.gap_n; ++k) {
+        const double2 xv = X[(i * a.gap_stride + a.gap_off + k) * P + j];
+        y.x += lport[i] * xv.x;
+        y.y += lport[i] * xv.y;
+      }
+      Sout[tid] = y;
     }
     gsync();
   }

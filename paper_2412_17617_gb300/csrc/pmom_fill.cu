@@ -434,13 +434,21 @@ double hj_eps_eff(const Grid& g) {
 }
 
 // Geometry of a triangle key (half 0, 1: the pixel's triangles; 2, 3: the via strip's Ta, Tb).
-void key_triangle(const Grid& g, int32_t key, FillTri* t) {
-  const int half = key & 3;
+// Fine-lattice parts of a triangle key (the mesher's encoding: W = 128 s, offset 4 s).
+void key_parts(const Grid& g, int32_t key, int* layer, int* x, int* y, int* half) {
+  const int W = 128 * g.subs(), off = 4 * g.subs();
+  *half = key & 3;
   int k = key >> 2;
-  const int x = k % 128 - 4;
-  k /= 128;
-  const int y = k % 128 - 4;
-  const int layer = k / 128;
+  *x = k % W - off;
+  k /= W;
+  *y = k % W - off;
+  *layer = k / W;
+}
+
+void key_triangle(const Grid& g, int32_t key, FillTri* t) {
+  int half, x, y, layer;
+  key_parts(g, key, &layer, &x, &y, &half);
+  const double h = g.pitch / g.subs();   // sub-square side
   static const int corner[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
   static const int tri[2][2][3] = {{{0, 1, 2}, {1, 3, 2}}, {{0, 1, 3}, {0, 3, 2}}};
   static const int dend[2][2] = {{2, 1}, {0, 3}};   // diagonal end corners D0, D1 per orientation
@@ -448,8 +456,8 @@ void key_triangle(const Grid& g, int32_t key, FillTri* t) {
   if (half < 2) {
     for (int i = 0; i < 3; ++i) {
       const int cc = tri[o][half][i];
-      t->v[i][0] = (x + corner[cc][0]) * g.pitch;
-      t->v[i][1] = (y + corner[cc][1]) * g.pitch;
+      t->v[i][0] = (x + corner[cc][0]) * h;
+      t->v[i][1] = (y + corner[cc][1]) * h;
       t->v[i][2] = g.layer_z[layer];
     }
   } else {
@@ -458,8 +466,8 @@ void key_triangle(const Grid& g, int32_t key, FillTri* t) {
     const int up[2][3] = {{0, 0, 1}, {0, 1, 1}};
     for (int i = 0; i < 3; ++i) {
       const int cc = cs3[half - 2][i];
-      t->v[i][0] = (x + corner[cc][0]) * g.pitch;
-      t->v[i][1] = (y + corner[cc][1]) * g.pitch;
+      t->v[i][0] = (x + corner[cc][0]) * h;
+      t->v[i][1] = (y + corner[cc][1]) * h;
       t->v[i][2] = g.layer_z[layer + up[half - 2][i]];
     }
   }
@@ -534,16 +542,20 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   // triangle's follows from the first's and the offset, with the uniform and random ones it does
   // not, so both enter the class
   std::vector<int> ori(T);
-  for (int t = 0; t < T; ++t) ori[t] = orient(g, (keys[t] >> 2) % 128 - 4, ((keys[t] >> 2) / 128) % 128 - 4);
+  std::vector<int4> parts(T);   // layer, x, y, half on the fine lattice
+  for (int t = 0; t < T; ++t) {
+    int l, x, y, h;
+    key_parts(g, keys[t], &l, &x, &y, &h);
+    parts[t] = make_int4(l, x, y, h);
+    ori[t] = orient(g, x, y);
+  }
   for (int p = 0; p < T; ++p) {
-    const int32_t kp = keys[p];
-    const int hp = kp & 3, xp = (kp >> 2) % 128, yp = ((kp >> 2) / 128) % 128, lp = (kp >> 2) / (128 * 128);
+    const int lp = parts[p].x, xp = parts[p].y, yp = parts[p].z, hp = parts[p].w;
     for (int q = 0; q < T; ++q) {
-      const int32_t kq = keys[q];
-      const int hq = kq & 3, xq = (kq >> 2) % 128, yq = ((kq >> 2) / 128) % 128, lq = (kq >> 2) / (128 * 128);
+      const int lq = parts[q].x, xq = parts[q].y, yq = parts[q].z, hq = parts[q].w;
       const long long key =
-          ((((((((static_cast<long long>(lp) * 8 + lq) * 2 + ori[p]) * 2 + ori[q]) * 4 + hp) * 4 + hq) * 512 +
-             (xq - xp + 256)) * 512) + (yq - yp + 256));
+          ((((((((static_cast<long long>(lp) * 8 + lq) * 2 + ori[p]) * 2 + ori[q]) * 4 + hp) * 4 + hq) * 2048 +
+             (xq - xp + 1024)) * 2048) + (yq - yp + 1024));
       auto it = cls_of.find(key);
       int c;
       if (it == cls_of.end()) {

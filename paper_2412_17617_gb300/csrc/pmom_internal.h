@@ -23,11 +23,18 @@ struct Grid {
   int layers = 0, nx = 0, ny = 0, medium = 0, n_states = 2, n_ports = 0;
   int diag_pattern = 0;    // 0 alternating, 1 uniform, 2 random (pmom_grid_desc)
   uint64_t diag_seed = 0;
+  int sub = 1;             // sub-squares per pixel side (pmom_grid_desc)
   double pitch = 0, h_total = 0, eps_r = 1, tan_d = 0;
   std::vector<double> layer_z;
   std::vector<pmom_port> ports;
   int pixels() const { return layers * nx * ny; }
-  bool vias() const { return n_states >= 3 && layers >= 2; }
+  int subs() const { return sub > 1 ? sub : 1; }
+  // inner BFs of one pixel (s^2 diagonals + 2 s (s - 1) inner edges) and always-present BFs of a
+  // port stub (both stub pixels' inner BFs + the s gap edges); port p's gap BFs are
+  // p * stub_bfs() + inner_bfs() + k, k < s, in the table and in every support set
+  int inner_bfs() const { return subs() * subs() + 2 * subs() * (subs() - 1); }
+  int stub_bfs() const { return 2 * inner_bfs() + subs(); }
+  bool vias() const { return n_states >= 3 && layers >= 2 && subs() == 1; }
   // first pixel index that cannot hold the via state (the last layer has no layer above it)
   int via_top() const { return vias() ? (layers - 1) * nx * ny : pixels(); }
 };
@@ -53,6 +60,7 @@ struct EvalArgs {
   const void* Z;           // [F][M][M] resident database
   int z_c128;              // 1: double2 storage, 0: float2
   double port_len[kMaxPorts];
+  int gap_stride, gap_off, gap_n;   // port p's gap BFs: p * gap_stride + gap_off + k, k < gap_n
   double Z0;
   double2* S;              // [B][F][P][P]
   uint32_t* flags;         // [B] bit flags per candidate

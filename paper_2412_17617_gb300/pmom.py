@@ -51,7 +51,7 @@ class _GridDesc(ctypes.Structure):
                 ("layer_z_m", ctypes.POINTER(ctypes.c_double)), ("h_total_m", ctypes.c_double),
                 ("eps_r", ctypes.c_double), ("tan_d", ctypes.c_double), ("n_states", ctypes.c_int32),
                 ("n_ports", ctypes.c_int32), ("ports", ctypes.POINTER(_Port)),
-                ("diag_pattern", ctypes.c_int32), ("diag_seed", ctypes.c_uint64)]
+                ("diag_pattern", ctypes.c_int32), ("diag_seed", ctypes.c_uint64), ("sub", ctypes.c_int32)]
 
 
 _lib = None
@@ -167,14 +167,12 @@ class Evaluator:
     def __init__(self, grid):
         self.L = load_library()
         self.grid = grid
-        if getattr(grid, "sub", 1) != 1:
-            raise PmomError(7, "pmom_create: 8- and 18-triangle pixel meshes are not in this build")
         self._last_kind = "eval"
         self._z = (ctypes.c_double * grid.layers)(*grid.layer_z_m)
         self._ports = (_Port * len(grid.ports))(*[_Port(p.layer, p.side, p.pos) for p in grid.ports])
         desc = _GridDesc(grid.layers, grid.nx, grid.ny, grid.pitch_m, grid.medium, self._z, grid.h_total_m,
                          grid.eps_r, grid.tan_d, grid.n_states, len(grid.ports), self._ports,
-                         getattr(grid, "diag_pattern", 0), getattr(grid, "diag_seed", 0))
+                         getattr(grid, "diag_pattern", 0), getattr(grid, "diag_seed", 0), getattr(grid, "sub", 1))
         h = ctypes.c_void_p()
         st = self.L.pmom_create(ctypes.byref(desc), ctypes.byref(h))
         if st != PMOM_OK:

@@ -41,6 +41,11 @@ def _grids():
     import dataclasses
     gs.append(dataclasses.replace(PI.grid_stripline_16x16x2(), name="stripline_16x16x2_uniform", diag_pattern=1))
     gs.append(dataclasses.replace(gs[-3], name="sides_5x3x2_via_random", diag_pattern=2, diag_seed=77))
+    # 8- and 18-triangle pixels (multi-edge port gaps), with every orientation pattern
+    gs.append(dataclasses.replace(PI.grid_tiny(3), name="tiny_s2", sub=2))
+    gs.append(dataclasses.replace(PI.grid_tiny(4, PI.MEDIUM_STRIPLINE, 2), name="strip_s3_random", sub=3,
+                                  diag_pattern=2, diag_seed=5))
+    gs.append(dataclasses.replace(gs[5], name="sides_5x3x2_s2_uniform", sub=2, diag_pattern=1))
     return gs
 
 
@@ -74,11 +79,13 @@ def test_argument_validation(lib):
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(pat)
     assert e.value.status == 1
-    # the 8- and 18-triangle pixel meshes are in the oracle only: the library refuses them loudly
+    # 2, 8 or 18 triangles per pixel; a via needs the two-triangle pixel
     import dataclasses
-    with pytest.raises(pmom.PmomError) as e:
-        pmom.Evaluator(dataclasses.replace(g, sub=2))
-    assert e.value.status == 7
+    for bad_grid in (dataclasses.replace(g, sub=4),
+                     dataclasses.replace(PI.grid_stripline_20x20x3(n_states=3), sub=2)):
+        with pytest.raises(pmom.PmomError) as e:
+            pmom.Evaluator(bad_grid)
+        assert e.value.status == 1
     four = PI.Grid("four", 2, 3, 3, 1e-3, 0, (0.5e-3, 1e-3), 1e-3, 3.5, 0.0, 4, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:
         pmom.Evaluator(four)
