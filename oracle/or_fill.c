@@ -396,20 +396,36 @@ static void tri_point(const tri_t* t, const double* b, double* r) {
   r[2] = point_z(t, b);
 }
 
-/* Height ids of the quadrature points of vertical triangles: appended to `z` (which starts with the
- * layer heights) as they are met; returns the new count. */
+/* Height ids of the quadrature points of vertical triangles: the distinct heights are appended to
+ * `z` (which starts with the layer heights) in ascending order, so that the id order of any two
+ * heights, and with it every fitted tail, does not depend on which triangles are present; returns
+ * the new count. */
 static int assign_heights(tri_t* tris, int T, double* z, int nz) {
-  for (int t = 0; t < T; ++t) {
-    if (!tris[t].vert) continue;
-    for (int r = 0; r < 2; ++r) {
-      const double *b, *w;
-      int n = or_tri_rule(r == 0 ? 7 : 13, &b, &w);
-      for (int i = 0; i < n; ++i) {
-        double zz = point_z(&tris[t], b + 3 * i);
-        int id = -1;
-        for (int j = 0; j < nz; ++j) if (z[j] == zz) { id = j; break; }
-        if (id < 0) { id = nz; z[nz++] = zz; }
-        tris[t].zid[r][i] = id;
+  int n0 = nz;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int t = 0; t < T; ++t) {
+      if (!tris[t].vert) continue;
+      for (int r = 0; r < 2; ++r) {
+        const double *b, *w;
+        int n = or_tri_rule(r == 0 ? 7 : 13, &b, &w);
+        for (int i = 0; i < n; ++i) {
+          double zz = point_z(&tris[t], b + 3 * i);
+          int id = -1;
+          for (int j = 0; j < nz; ++j) if (z[j] == zz) { id = j; break; }
+          if (pass == 0) {
+            if (id < 0) z[nz++] = zz;
+          } else {
+            tris[t].zid[r][i] = id;
+          }
+        }
+      }
+    }
+    if (pass == 0) {   /* sort the appended heights (insertion sort: a few dozen values) */
+      for (int i = n0 + 1; i < nz; ++i) {
+        double v = z[i];
+        int j = i - 1;
+        while (j >= n0 && z[j] > v) { z[j + 1] = z[j]; --j; }
+        z[j + 1] = v;
       }
     }
   }
@@ -592,10 +608,9 @@ static int collect_triangles(const or_grid* g, const int32_t* table, int M, int3
   return T;
 }
 
-double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threads, double complex* Z) {
-  int M = or_count_bfs(g);
-  int32_t* table = (int32_t*)malloc(sizeof(int32_t) * OR_BF_COLS * M);
-  or_bf_table(g, table);
+/* Z of the BFs listed in `table` (M rows): the parent's, or a sub-structure's. */
+static double fill_table(const or_grid* g, const int32_t* table, int M, const double* freqs, int F, int mode,
+                         int threads, double complex* Z) {
   /* distinct triangles referenced by the BFs */
   int32_t kmax = 0;
   for (int m = 0; m < M; ++m)
@@ -638,10 +653,31 @@ double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threa
   free(jobs);
   free(keys);
   free(key_to_tri);
-  free(table);
   free(tris);
   free(z);
   return amax > 0.0 ? dmax / amax : 0.0;
+}
+
+double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threads, double complex* Z) {
+  int M = or_count_bfs(g);
+  int32_t* table = (int32_t*)malloc(sizeof(int32_t) * OR_BF_COLS * M);
+  or_bf_table(g, table);
+  double asym = fill_table(g, table, M, freqs, F, mode, threads, Z);
+  free(table);
+  return asym;
+}
+
+double or_fill_subset(const or_grid* g, const double* freqs, int F, int mode, int threads, const int32_t* bf, int N,
+                      double complex* Z) {
+  int M = or_count_bfs(g);
+  int32_t* table = (int32_t*)malloc(sizeof(int32_t) * OR_BF_COLS * M);
+  or_bf_table(g, table);
+  int32_t* sub = (int32_t*)malloc(sizeof(int32_t) * OR_BF_COLS * (N > 0 ? N : 1));
+  for (int a = 0; a < N; ++a) memcpy(sub + OR_BF_COLS * a, table + OR_BF_COLS * bf[a], sizeof(int32_t) * OR_BF_COLS);
+  double asym = fill_table(g, sub, N, freqs, F, mode, threads, Z);
+  free(sub);
+  free(table);
+  return asym;
 }
 
 /* Test hook: the ten integrals of one triangle pair (keys of the grid's lattice). */

@@ -61,6 +61,8 @@ def lib():
             L.or_active_set.argtypes = [P, P, ctypes.c_int, P, P]
             L.or_fill.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.or_fill.restype = ctypes.c_double
+            L.or_fill_subset.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P]
+            L.or_fill_subset.restype = ctypes.c_double
             for fn in ("or_green", "or_green_modal"):
                 getattr(L, fn).argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
                 getattr(L, fn).restype = _C128
@@ -144,6 +146,17 @@ def fill(grid: Grid, freqs, mode: int = 1, threads: int = 0):
         threads = min(len(f), os.cpu_count() or 1)
     asym = lib().or_fill(grid.ref, _ptr(f), len(f), mode, threads, _ptr(Z))
     return Z, asym
+
+
+def fill_subset(grid: Grid, freqs, bf, mode: int = 0, threads: int = 0):
+    """Z of the sub-structure made of BFs `bf` only, filled directly ([F][N][N], symmetrised)."""
+    f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(bf, dtype=np.int32))
+    Z = np.zeros((len(f), len(b), len(b)), dtype=np.complex128)
+    if threads <= 0:
+        threads = min(len(f), os.cpu_count() or 1)
+    lib().or_fill_subset(grid.ref, _ptr(f), len(f), mode, threads, _ptr(b), len(b), _ptr(Z))
+    return Z
 
 
 def green(grid: Grid, freq: float, lp: int, lq: int, rho: float, route: str = "default", K: int = 64) -> complex:
@@ -262,7 +275,8 @@ def port_lengths(grid: Grid) -> np.ndarray:
 def eval_map_lapack(grid: Grid, Z: np.ndarray, pixel_map: np.ndarray, Z0: float = 50.0) -> np.ndarray:
     """S[F][P][P] of one map by the same definition as eval_map -- gather Z_sub = Z(f)[I, I]
     (Eq. 5, complex64 storage promoted exactly to complex128), unit delta-gap excitation of each
-    port edge, Y_ij = l_i x_i^(j) and S = (1 + Z0 Y)^-1 (1 - Z0 Y) (Eq. 6-7) -- with LAPACK's
+    port's gap BFs, Y_ij = sum over port i's gap of l_k x_k^(j) and S = (1 + Z0 Y)^-1 (1 - Z0 Y)
+    (Eq. 6-7) -- with LAPACK's
     dense solve (numpy.linalg.solve) as the solve step, for support sets of thousands of BFs
     where the plain C LU takes minutes."""
     idx = active_set(grid, pixel_map)

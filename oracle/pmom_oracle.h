@@ -81,6 +81,10 @@ void or_triangle(const or_grid* g, int32_t key, double v[3][3]);
  * mode 0: every triangle pair integrated; mode 1: pairs related by a lattice translation share
  * one integration.  Returns max |Z - Z^T| / max |Z| before symmetrisation (Z <- (Z + Z^T)/2). */
 double or_fill(const or_grid* g, const double* freqs, int F, int mode, int threads, double complex* Z);
+/* Z(f) of the sub-structure made of the listed BFs only ([F][N][N]), filled directly by the same
+ * per-pair code (the premise of Eq. 4-5: it equals the parent's rows and columns bf). */
+double or_fill_subset(const or_grid* g, const double* freqs, int F, int mode, int threads, const int32_t* bf, int N,
+                      double complex* Z);
 
 /* Green's function of the stack-up between metal layers lp and lq at lateral distance rho. */
 double complex or_green(const or_grid* g, double freq, int lp, int lq, double rho);

@@ -151,3 +151,25 @@ def test_other_orientations_fill(pattern):
     for Zf in Zt:
         herm = 0.5 * (Zf + Zf.conj().T)
         assert np.linalg.eigvalsh(herm).min() >= -1e-10 * np.abs(Zf).max()
+
+
+@pytest.mark.parametrize("case", ["microstrip", "vias"])
+def test_substructure_premise(case):
+    """Eq. (4)-(5): the interaction matrix of a candidate's own mesh, filled directly with only its
+    active BFs, is bit for bit the parent's rows and columns of those BFs (same per-pair code), so a
+    database of the all-metal parent serves every candidate."""
+    import dataclasses
+    if case == "microstrip":
+        g = PI.grid_tiny(3)
+        maps = PI.all_maps(g)[[5, 200, 511]]
+    else:
+        g = dataclasses.replace(PI.grid_tiny(3, PI.MEDIUM_STRIPLINE, 2, pitch_m=0.5e-3), n_states=3)
+        maps = PI.state_changes(PI.seed_map_vias(g, 0.6, 0.5, 1), 1, 3, 2)
+        assert (maps == 2).any()
+    G = O.Grid(g)
+    f = [2.4e9, 5.2e9]
+    Z, _ = O.fill(G, f, mode=0)
+    for m in maps:
+        idx = O.active_set(G, m)
+        Zs = O.fill_subset(G, f, idx, mode=0)
+        assert np.array_equal(Zs.view(np.uint64), np.ascontiguousarray(Z[:, idx][:, :, idx]).view(np.uint64))
