@@ -173,3 +173,20 @@ def test_substructure_premise(case):
         idx = O.active_set(G, m)
         Zs = O.fill_subset(G, f, idx, mode=0)
         assert np.array_equal(Zs.view(np.uint64), np.ascontiguousarray(Z[:, idx][:, :, idx]).view(np.uint64))
+
+
+@pytest.mark.parametrize("medium", [PI.MEDIUM_MICROSTRIP, PI.MEDIUM_STRIPLINE])
+def test_low_frequency_limit(medium):
+    """As f -> 0, f Z(f) tends to the static capacitive term (the scalar potential of Eq. 1 over
+    j 2 pi eps) and the first correction is quadratic in f: the O(k) terms of each source and its
+    image cancel, and the Dirichlet mode sum is analytic in k^2.  Doubling f quadruples the
+    departure from the static limit (to 1e-4 here); an unbalanced image or a wrong k would leave
+    a linear term."""
+    g = PI.grid_tiny(3) if medium == PI.MEDIUM_MICROSTRIP else PI.grid_tiny(3, PI.MEDIUM_STRIPLINE, 2)
+    G = O.Grid(g)
+    fs = [1e3, 2e7, 4e7, 8e7]
+    Z, _ = O.fill(G, fs)
+    X = np.array([f * Z[i] for i, f in enumerate(fs)])
+    d = [np.abs(X[i] - X[0]).max() for i in (1, 2, 3)]
+    assert d[0] < 1e-5 * np.abs(X[0]).max()
+    assert abs(d[1] / d[0] - 4.0) < 1e-4 and abs(d[2] / d[1] - 4.0) < 1e-4
