@@ -101,3 +101,31 @@ def test_search_with_vias_reaches_brute_force_optimum():
                                                     n_states=3)
     assert best_F == pytest.approx(gmin, rel=1e-12)
     assert (best_map == 2).any() == (allm[int(np.argmin(allf))] == 2).any()
+
+
+@pytest.mark.parametrize("n_states", [2, 3])
+def test_depth1_neighbourhood_equals_brute_force(n_states):
+    """The children the search evaluates at depth 1 are exactly the maps that differ from the node
+    in the chosen column only (every other valid state of that column), checked against a filter
+    over every map of a 2 x 2 two-layer grid, in the search's order (column states ascending)."""
+    import itertools
+    L, ny, nx = 2, 2, 2
+    top = 3 if n_states == 3 else 2
+    allm = np.stack([np.array([lo, hi], np.uint8).reshape(L, ny, nx)
+                     for lo in itertools.product(range(top), repeat=4) for hi in itertools.product(range(2), repeat=4)])
+    init = allm[37].copy()
+    seen = []
+
+    def evaluate(maps):
+        seen.append(np.array(maps))
+        return np.arange(len(maps), 0, -1, dtype=float)   # the last child is best: it is accepted
+    OS.tree_search(evaluate, init, seed=3, d_max=1, m_of_d=(1,), max_evals=2, n_states=n_states)
+    kids = seen[1]
+    j = OS.key(3, 0, 0, 0, 0) % (ny * nx)
+    y, x = divmod(j, nx)
+    mask = np.ones((L, ny, nx), bool)
+    mask[:, y, x] = False
+    brute = [m for m in allm if np.array_equal(m[mask], init[mask]) and not np.array_equal(m, init)]
+    assert len(kids) == len(brute) == int(np.prod(OS.radices(L, n_states))) - 1
+    order = sorted(brute, key=lambda m: OS.column_state(m, j, n_states))
+    assert all(np.array_equal(a, b) for a, b in zip(kids, order))
