@@ -39,10 +39,12 @@ SM_MAX_MHZ = 2070.0
 
 
 # DRAM bytes (read + write) of one launch of the tensor-core evaluation kernel on the full
-# 512-candidate x 41-frequency stripline batch, from one ncu capture of this build
-# (profiles/eval_kernel_stripline16x16x2_launches.md gives the command); reported only for that
-# kernel on that workload.
-TRAFFIC_PER_LAUNCH = {("stripline_16x16x2_f41_b512", "tc"): 1.05e12 + 551.98e9}
+# 512-candidate x 41-frequency stripline batch, from one ncu capture (profiles/
+# eval_kernel_stripline16x16x2_launches.md gives the command).  The kernel has changed since that
+# capture (a shorter bounded wait, port gaps as BF ranges), so `traffic` is null until it is taken
+# again; the last capture is reported beside it, labelled.
+TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_LAST_CAPTURE = {("stripline_16x16x2_f41_b512", "tc"): 1.05e12 + 551.98e9}
 
 
 def _peaks():
@@ -327,6 +329,9 @@ def run_ours(args):
         peak = bf16 * 1.1 / 2.25
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_LAUNCH.get((w.name, "tc")) if Bsz == w.batch else None,
+                "traffic_last_capture": TRAFFIC_LAST_CAPTURE.get((w.name, "tc")) if Bsz == w.batch else None,
+                "traffic_last_capture_note": "dram read + write bytes per launch, captured on the build before "
+                                             "the bounded-wait and port-gap changes",
                 "kernel": "eval_kernel<float2,float2,mixed,tc%s>" % (",large" if large else ""),
                 "peak_source": "measured bf16 %.1f TFLOP/s x 1.1/2.25 (TF32 dense); %s" % (
                     bf16, "of measured" if peaks.get("bf16_tflops") else "of fallback"),
