@@ -329,6 +329,27 @@ pmom_status pmom_search(pmom_ctx* ctx, const pmom_search_params* params, const u
 pmom_status pmom_save_Z(pmom_ctx* ctx, const char* path, void* stream);
 pmom_status pmom_load_Z_file(pmom_ctx* ctx, const char* path, void* stream);
 
+/* Checkpoint of a search (pmom_search_resume): the caller owns the struct and both maps
+ * ([layers][ny][nx] host bytes).  valid = 0 starts from init_map; a state returned by an earlier
+ * call continues exactly where that call stopped (the same decisions as one uninterrupted run),
+ * restart and iteration being the generator keys of R17. */
+typedef struct {
+  int32_t valid;
+  int32_t depth, counter;
+  int64_t evals;          /* evaluations since the search started */
+  uint64_t restart, iteration;
+  double fom, best_fom;   /* FoM of the current map and of the best map */
+  uint8_t* map;           /* current map, host, caller-owned */
+  uint8_t* best_map;      /* best map, host, caller-owned */
+} pmom_search_state;
+/* Algorithm 1 as pmom_search, from or to a checkpoint: runs until state->evals reaches
+ * params->max_evals (a started tree is finished), then leaves the state valid.  trace_host
+ * receives the current FoM after each iteration of this call.  Errors as pmom_search, and
+ * INVALID_ARG for a state without maps. */
+pmom_status pmom_search_resume(pmom_ctx* ctx, const pmom_search_params* params, const uint8_t* init_map_host,
+                               pmom_search_state* state, double* trace_host, int32_t trace_cap, int32_t* trace_len,
+                               void* stream);
+
 /* Counters of the last eval call (host int64 [8]): tasks, refinement iterations summed over tasks,
  * max iterations of one task, tasks re-solved in FP64, tensor-core waits that ran out (the
  * task's candidate then reports PMOM_CAND_NONFINITE), reserved, kernel launches issued,

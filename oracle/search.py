@@ -79,9 +79,13 @@ def set_column(m: np.ndarray, j: int, s: int, n_states: int = 2) -> np.ndarray:
     return c
 
 
-def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, max_evals: int, n_states: int = 2):
+def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, max_evals: int, n_states: int = 2,
+                state: dict = None, return_state: bool = False):
     """evaluate(maps[B][L][ny][nx]) -> FoM[B].  Returns (best_map, best_F, evals, trace) where
-    trace[i] is the current F after iteration i."""
+    trace[i] is the current F after iteration i of this call; with return_state also the search
+    state (current map and F, best map and F, evaluation count, depth, counter, restart and
+    iteration keys), from which a later call with state=... continues exactly as the uninterrupted
+    search would (max_evals counts every evaluation since the start)."""
     L, ny, nx = init_map.shape
     ncol, K = ny * nx, int(np.prod(radices(L, n_states)))
 
@@ -89,11 +93,17 @@ def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, m
         f = np.asarray(evaluate(np.ascontiguousarray(maps)), dtype=np.float64)
         return np.where(np.isfinite(f), f, np.inf)
 
-    P = init_map.copy()
-    F = float(F_of(P[None])[0])
-    evals = 1
-    best_P, best_F = P.copy(), F
-    D, counter, restart, it = 1, 0, 0, 0
+    if state is None:
+        P = init_map.copy()
+        F = float(F_of(P[None])[0])
+        evals = 1
+        best_P, best_F = P.copy(), F
+        D, counter, restart, it = 1, 0, 0, 0
+    else:
+        P, F = state["map"].copy(), float(state["fom"])
+        best_P, best_F = state["best_map"].copy(), float(state["best_fom"])
+        evals, D, counter = int(state["evals"]), int(state["depth"]), int(state["counter"])
+        restart, it = int(state["restart"]), int(state["iteration"])
     trace = []
     while evals < max_evals:
         nodes = [(frozenset(), P)]
@@ -131,4 +141,8 @@ def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, m
                 best_P, best_F = P.copy(), F
         trace.append(F)
         it += 1
+    if return_state:
+        st = {"map": P.copy(), "fom": F, "best_map": best_P.copy(), "best_fom": best_F, "evals": evals, "depth": D,
+              "counter": counter, "restart": restart, "iteration": it}
+        return best_P, best_F, evals, trace, st
     return best_P, best_F, evals, trace

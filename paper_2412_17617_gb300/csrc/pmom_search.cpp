@@ -65,10 +65,13 @@ void set_col(uint8_t* m, const Shape& s, int j, int v) {
 
 }  // namespace
 
-extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, const uint8_t* init_map,
-                                   uint8_t* best_map, double* best_fom, int64_t* evals_used, double* trace,
-                                   int32_t trace_cap, int32_t* trace_len, void* stream) {
-  if (!c || !prm || !init_map || !best_map || !best_fom || prm->d_max < 1 || prm->d_max > 8 || prm->max_evals < 1)
+extern "C" pmom_status pmom_search_resume(pmom_ctx* c, const pmom_search_params* prm, const uint8_t* init_map,
+                                          pmom_search_state* state, double* trace, int32_t trace_cap,
+                                          int32_t* trace_len, void* stream) {
+  if (!c || !prm || !state || !state->map || !state->best_map || (!state->valid && !init_map) || prm->d_max < 1 ||
+      prm->d_max > 8 || prm->max_evals < 1)
+    return PMOM_ERR_INVALID_ARG;
+  if (state->valid && (state->depth < 1 || state->depth > prm->d_max || state->counter < 0 || state->evals < 1))
     return PMOM_ERR_INVALID_ARG;
   int32_t M = 0, P = 0;
   pmom_num_bfs(c, &M, &P);
@@ -89,14 +92,31 @@ extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, c
     for (int b = 0; b < B; ++b) out[b] = std::isfinite(fom[b]) ? fom[b] : std::numeric_limits<double>::infinity();
     return PMOM_OK;
   };
-  std::vector<uint8_t> cur(init_map, init_map + npix), best(cur);
-  std::vector<double> f1;
-  pmom_status st = evaluate(cur, 1, f1);
-  if (st) return st;
-  double F = f1[0], bestF = F;
-  int64_t evals = 1;
+  std::vector<uint8_t> cur, best;
+  double F = 0.0, bestF = 0.0;
+  int64_t evals = 0;
   int D = 1, counter = 0, tlen = 0;
   uint64_t restart = 0, it = 0;
+  std::vector<double> f1;
+  pmom_status st = PMOM_OK;
+  if (state->valid) {
+    cur.assign(state->map, state->map + npix);
+    best.assign(state->best_map, state->best_map + npix);
+    F = state->fom;
+    bestF = state->best_fom;
+    evals = state->evals;
+    D = state->depth;
+    counter = state->counter;
+    restart = state->restart;
+    it = state->iteration;
+  } else {
+    cur.assign(init_map, init_map + npix);
+    best = cur;
+    st = evaluate(cur, 1, f1);
+    if (st) return st;
+    F = bestF = f1[0];
+    evals = 1;
+  }
   struct Node {
     std::vector<int> path;   // columns chosen on the way down
     std::vector<uint8_t> map;
@@ -164,9 +184,33 @@ extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, c
     ++tlen;
     ++it;
   }
-  std::memcpy(best_map, best.data(), npix);
-  *best_fom = bestF;
-  if (evals_used) *evals_used = evals;
+  std::memcpy(state->map, cur.data(), npix);
+  std::memcpy(state->best_map, best.data(), npix);
+  state->fom = F;
+  state->best_fom = bestF;
+  state->evals = evals;
+  state->depth = D;
+  state->counter = counter;
+  state->restart = restart;
+  state->iteration = it;
+  state->valid = 1;
   if (trace_len) *trace_len = tlen < trace_cap ? tlen : trace_cap;
+  return PMOM_OK;
+}
+
+extern "C" pmom_status pmom_search(pmom_ctx* c, const pmom_search_params* prm, const uint8_t* init_map,
+                                   uint8_t* best_map, double* best_fom, int64_t* evals_used, double* trace,
+                                   int32_t trace_cap, int32_t* trace_len, void* stream) {
+  if (!c || !prm || !init_map || !best_map || !best_fom) return PMOM_ERR_INVALID_ARG;
+  const pmom::Grid& g = pmom::grid_of(c);
+  std::vector<uint8_t> cur(static_cast<size_t>(g.layers) * g.ny * g.nx);
+  pmom_search_state state{};
+  state.valid = 0;
+  state.map = cur.data();
+  state.best_map = best_map;
+  const pmom_status st = pmom_search_resume(c, prm, init_map, &state, trace, trace_cap, trace_len, stream);
+  if (st) return st;
+  *best_fom = state.best_fom;
+  if (evals_used) *evals_used = state.evals;
   return PMOM_OK;
 }

@@ -32,7 +32,8 @@ EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pm
            "pmom_autotune", "pmom_search", "pmom_eval_bordered",
            "pmom_mlp_create", "pmom_mlp_destroy", "pmom_mlp_last_error", "pmom_mlp_num_params", "pmom_mlp_get_params",
            "pmom_mlp_set_params", "pmom_mlp_forward", "pmom_mlp_backward", "pmom_mlp_adam", "pmom_mlp_predict_fom",
-           "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait", "pmom_save_Z", "pmom_load_Z_file")
+           "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait", "pmom_save_Z", "pmom_load_Z_file",
+           "pmom_search_resume")
 
 
 class PmomError(RuntimeError):
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_capacity": [V, I32, P, P],
         "pmom_selftest_wait": [ctypes.c_int64, I32, P, P, V],
         "pmom_save_Z": [V, ctypes.c_char_p, V],
+        "pmom_search_resume": [V, P, P, P, P, I32, P, V],
         "pmom_load_Z_file": [V, ctypes.c_char_p, V],
         "pmom_eval_bordered": [V, P, P, I32, I32, P, P, P, V],
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
@@ -159,6 +161,13 @@ def selftest_wait(polls: int, arrive: bool, stream=None):
     if st != PMOM_OK:
         raise PmomError(st, "pmom_selftest_wait")
     return bool(to.value), ms.value
+
+
+class _SearchState(ctypes.Structure):
+    _fields_ = [("valid", ctypes.c_int32), ("depth", ctypes.c_int32), ("counter", ctypes.c_int32),
+                ("evals", ctypes.c_int64), ("restart", ctypes.c_uint64), ("iteration", ctypes.c_uint64),
+                ("fom", ctypes.c_double), ("best_fom", ctypes.c_double),
+                ("map", ctypes.c_void_p), ("best_map", ctypes.c_void_p)]
 
 
 class Evaluator:
@@ -386,6 +395,29 @@ class Evaluator:
                                        ctypes.c_void_p(tr.ctypes.data), trace_cap, ctypes.byref(tl),
                                        ctypes.c_void_p(_stream_ptr(stream))))
         return best, bf.value, ev.value, tr[: tl.value].copy()
+
+    def search_resume(self, init_map: np.ndarray, seed: int, d_max: int = 2, m_of_d=(10, 3), max_evals: int = 1000,
+                      precision: str = "mixed", state: dict = None, trace_cap: int = 100000, stream=None):
+        """Algorithm 1 from or to a checkpoint (pmom_search_resume).  Returns (best_map, best_fom,
+        evals, trace of this call, state); pass the state back to continue the same search."""
+        m = list(m_of_d) + [m_of_d[-1]] * (8 - len(m_of_d))
+        prm = _SearchParams(seed, d_max, (ctypes.c_int32 * 8)(*m[:8]), max_evals,
+                            PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED)
+        init = np.ascontiguousarray(init_map, dtype=np.uint8)
+        cur = init.copy() if state is None else np.ascontiguousarray(state["map"], dtype=np.uint8).copy()
+        best = init.copy() if state is None else np.ascontiguousarray(state["best_map"], dtype=np.uint8).copy()
+        st = _SearchState(0, 1, 0, 0, 0, 0, 0.0, 0.0, cur.ctypes.data, best.ctypes.data)
+        if state is not None:
+            st.valid, st.depth, st.counter, st.evals = 1, state["depth"], state["counter"], state["evals"]
+            st.restart, st.iteration, st.fom, st.best_fom = state["restart"], state["iteration"], state["fom"], state["best_fom"]
+        tr = np.zeros(trace_cap, np.float64)
+        tl = ctypes.c_int32(0)
+        self._check(self.L.pmom_search_resume(self.h, ctypes.byref(prm), ctypes.c_void_p(init.ctypes.data),
+                                              ctypes.byref(st), ctypes.c_void_p(tr.ctypes.data), trace_cap,
+                                              ctypes.byref(tl), ctypes.c_void_p(_stream_ptr(stream))))
+        out = {"map": cur, "fom": st.fom, "best_map": best, "best_fom": st.best_fom, "evals": st.evals,
+               "depth": st.depth, "counter": st.counter, "restart": st.restart, "iteration": st.iteration}
+        return best.copy(), st.best_fom, st.evals, tr[: tl.value].copy(), out
 
     def stats(self) -> dict:
         out = np.zeros(8, dtype=np.int64)

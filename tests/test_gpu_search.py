@@ -58,3 +58,23 @@ def test_search_decisions_match_oracle(built, case, prec):
     assert np.allclose(t_gpu, t_ref, rtol=tol, atol=0)      # identical decisions, same FoM path
     assert np.array_equal(m_gpu, m_ref)
     assert f_gpu == pytest.approx(f_ref, rel=tol)
+
+
+def test_native_search_resume_matches_uninterrupted_and_oracle(built):
+    """Checkpoint / resume on the GPU evaluator: a search stopped after 120 evaluations and resumed
+    to 300 makes the decisions of the uninterrupted native run and of the oracle's search."""
+    g, freqs, bands = PI.grid_tiny(3), np.array([2.0e9, 2.5e9, 3.5e9, 5.0e9]), PI.PLAIN_BANDS
+    Z, band, evaluate = _problem(g, freqs, bands)
+    ev = built.Evaluator(g)
+    ev.load_Z(freqs, torch.from_numpy(Z).cuda())
+    ev.set_fom(band)
+    init = PI.seed_map(g, 0.5, 5)
+    args = dict(seed=42, d_max=2, m_of_d=(10, 3))
+    full = ev.search(init, max_evals=300, precision="fp64", **args)
+    a = ev.search_resume(init, max_evals=120, precision="fp64", **args)
+    b = ev.search_resume(init, max_evals=300, precision="fp64", state=a[4], **args)
+    ev.close()
+    assert b[2] == full[2] and np.array_equal(b[0], full[0]) and b[1] == pytest.approx(full[1], rel=1e-10)
+    assert np.allclose(np.concatenate([a[3], b[3]]), full[3], rtol=1e-10, atol=0)
+    ref = OS.tree_search(evaluate, init, max_evals=300, **args)
+    assert ref[2] == b[2] and np.array_equal(ref[0], b[0])

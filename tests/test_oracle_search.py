@@ -129,3 +129,19 @@ def test_depth1_neighbourhood_equals_brute_force(n_states):
     assert len(kids) == len(brute) == int(np.prod(OS.radices(L, n_states))) - 1
     order = sorted(brute, key=lambda m: OS.column_state(m, j, n_states))
     assert all(np.array_equal(a, b) for a, b in zip(kids, order))
+
+
+@pytest.mark.parametrize("split", [60, 151, 290])
+def test_resumed_search_equals_uninterrupted(split):
+    """Checkpoint / resume: a search stopped after `split` evaluations and continued from its state
+    makes the same decisions as one uninterrupted run (same trace, best map, best FoM and
+    evaluation count), including across restarts."""
+    g, evaluate = _tiny_problem()
+    init = PI.seed_map(g, 0.5, 2)
+    args = dict(seed=5, d_max=2, m_of_d=(3, 1))
+    full = OS.tree_search(evaluate, init, max_evals=400, **args)
+    a = OS.tree_search(evaluate, init, max_evals=split, return_state=True, **args)
+    b = OS.tree_search(evaluate, init, max_evals=400, state=a[4], **args)
+    assert np.array_equal(b[0], full[0]) and b[1] == full[1] and b[2] == full[2]
+    assert a[3] + b[3] == full[3]
+    assert a[4]["restart"] >= 0 and (split < 100 or a[4]["restart"] >= 1 or a[4]["iteration"] > 10)
