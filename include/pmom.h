@@ -40,7 +40,8 @@ enum {
   PMOM_ERR_Z_SHAPE_MISMATCH = 4, /* Z / frequency / band shapes disagree with the grid */
   PMOM_ERR_CUDA = 5,             /* a CUDA runtime call failed; see pmom_last_error */
   PMOM_ERR_NOT_READY = 6,        /* call order: Z or the FoM bands not loaded yet */
-  PMOM_ERR_UNSUPPORTED = 7,      /* feature outside this build (e.g. more than three pixel states) */
+  PMOM_ERR_UNSUPPORTED = 7,      /* a feature the library does not implement (e.g. more than three pixel
+                                    states, the bordered update on pixels of more than two triangles) */
   PMOM_ERR_IO = 8                /* database file: open / read / write failed, not a database file,
                                     truncated, or its checksum disagrees */
 };
