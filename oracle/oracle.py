@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
-SOURCES = ["or_mesh.c", "or_fill.c", "or_solve.c"]
+SOURCES = ["or_mesh.c", "or_fill.c", "or_solve.c", "or_layered.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -74,6 +74,9 @@ def lib():
             L.or_green_heights.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, ctypes.c_int]
             L.or_green_heights.restype = _C128
+            L.or_slab_green.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
+            L.or_slab_green.restype = _C128
             L.or_tri_potentials.argtypes = [P, P, P, P]
             L.or_tri_rule.argtypes = [ctypes.c_int, P, P]
             L.or_eps_eff.argtypes = [P]
@@ -166,6 +169,14 @@ def green(grid: Grid, freq: float, lp: int, lq: int, rho: float, route: str = "d
     if route == "modal":
         return _c(L.or_green_modal(grid.ref, freq, lp, lq, rho))
     return _c(L.or_green(grid.ref, freq, lp, lq, rho))
+
+
+def slab_green(grid: Grid, freq: float, kind: int, z: float, zp: float, rho: float, er_top: float = 1.0,
+               reg: bool = False):
+    """Grounded-slab kernel (0: G_phi, 1: G_A) by Sommerfeld integrals; returns (G, C)."""
+    c = ctypes.c_double(0.0)
+    v = lib().or_slab_green(grid.ref, freq, kind, z, zp, rho, er_top, 1 if reg else 0, ctypes.byref(c))
+    return _c(v), c.value
 
 
 def bessel_k0(w: complex, any_arg: bool = False) -> complex:

@@ -98,6 +98,12 @@ double complex or_bessel_k0_any(double complex w);
  * route 0: the fill's evaluation, 1: image series with K images, 2: mode series. */
 double complex or_green_heights(const or_grid* g, double freq, int kind, double zp, double zq, double rho,
                                 int route, int K);
+/* Grounded-slab (microstrip) kernels by Sommerfeld integrals: kind 0 = G_phi (eps0-normalised scalar
+ * potential), 1 = G_A (horizontal vector potential), between heights z, zp inside or on the slab
+ * (thickness = the highest metal layer) at lateral distance rho; er_top = relative permittivity of
+ * the half-space above.  reg != 0 subtracts C / (4 pi R); C (the quasi-static constant) -> c_out. */
+double complex or_slab_green(const or_grid* g, double freq, int kind, double z, double zp, double rho,
+                             double er_top, int reg, double* c_out);
 /* Analytic potential integrals over a planar triangle (used by the singular part of the fill). */
 void or_tri_potentials(const double tri[3][3], const double r[3], double* I1, double Iv[3]);
 /* Quadrature rules on the reference triangle: n = 7 or 13; returns barycentric rows and weights. */
