@@ -79,7 +79,9 @@ typedef struct {
 typedef struct {
   int32_t layers, nx, ny;
   double pitch_m;              /* pixel side a */
-  int32_t medium;              /* 0: microstrip (ground at z = 0), 1: stripline (grounds at 0, h_total) */
+  int32_t medium;              /* 0: microstrip (ground at z = 0, homogeneous effective medium),
+                                  1: stripline (grounds at 0, h_total); 2 (a grounded slab under air,
+                                  Sommerfeld kernels) is refused with UNSUPPORTED */
   const double* layer_z_m;     /* [layers], host; heights of the metal layers */
   double h_total_m;            /* stripline plate spacing */
   double eps_r, tan_d;         /* homogenised substrate */

@@ -146,7 +146,7 @@ double complex or_bessel_k0(double complex w) {
 }
 
 double or_eps_eff(const or_grid* g) {
-  if (g->medium != 0) return g->eps_r;
+  if (g->medium == 1) return g->eps_r;
   /* Hammerstad & Jensen (1980) effective permittivity of a strip of width w = pitch at height h */
   double h = g->layer_z[0];
   for (int l = 1; l < g->layers; ++l) if (g->layer_z[l] > h) h = g->layer_z[l];
@@ -210,6 +210,12 @@ typedef struct {
   int nz;                 /* distinct heights: the metal layers first (id = layer), then via points */
   const double* z;
   double complex* fit;    /* stripline: [kind][nz][nz][3] tail coefficients */
+  /* layered microstrip (medium 2): Sommerfeld remainders of G_phi (0) and G_A (1) per pair of
+   * heights on rho_i = i htab, their quasi-static constants, the slab wavenumber (md->k) */
+  int layered, ntab;
+  double htab;
+  double complex* tab;    /* [2][nz][nz][ntab] */
+  double* ctab;           /* [2][nz][nz] */
 } medium_t;
 
 static double complex gfree(double complex k, double R) { return cexp(-I * k * R) / (4.0 * OR_PI * R); }
@@ -254,14 +260,43 @@ static double complex strip_modal(const medium_t* md, int kind, double zp, doubl
 static void medium_init(medium_t* md, const or_grid* g, double freq, int nz, const double* z) {
   md->g = g;
   md->omega = 2.0 * OR_PI * freq;
-  double er = or_eps_eff(g);
-  md->eps = EPS0 * er * (1.0 - I * g->tan_d);
+  md->layered = g->medium == 2;
+  md->tab = NULL;
+  md->ctab = NULL;
+  if (md->layered) {
+    /* the slab's permittivity enters through the kernels; the scalar term is eps0-normalised */
+    md->eps = EPS0;
+  } else {
+    double er = or_eps_eff(g);
+    md->eps = EPS0 * er * (1.0 - I * g->tan_d);
+  }
   md->k = md->omega * csqrt(MU0 * md->eps);
   md->H = g->h_total;
   md->rho_s = 0.5 * g->h_total;
   md->nz = nz;
   md->z = z;
   md->fit = NULL;
+  if (md->layered && nz > 0) {
+    double d = z[0];
+    for (int i = 1; i < nz; ++i) if (z[i] > d) d = z[i];
+    double rho_max = g->pitch * sqrt((g->nx + 6.0) * (g->nx + 6.0) + (g->ny + 6.0) * (g->ny + 6.0));
+    md->htab = d / 16.0;
+    md->ntab = (int)ceil(rho_max / md->htab) + 4;
+    md->tab = (double complex*)malloc(sizeof(double complex) * 2 * nz * nz * md->ntab);
+    md->ctab = (double*)malloc(sizeof(double) * 2 * nz * nz);
+    for (int kind = 0; kind < 2; ++kind)
+      for (int p = 0; p < nz; ++p)
+        for (int q = p; q < nz; ++q) {
+          double complex* t = md->tab + ((size_t)(kind * nz + p) * nz + q) * md->ntab;
+          double c;
+          double complex k1;
+          or_slab_table(g, freq, kind, z[p], z[q], 1.0, md->htab, md->ntab, t, &c, &k1);
+          md->ctab[(kind * nz + p) * nz + q] = md->ctab[(kind * nz + q) * nz + p] = c;
+          md->k = k1;
+          if (q != p)   /* reciprocity */
+            memcpy(md->tab + ((size_t)(kind * nz + q) * nz + p) * md->ntab, t, sizeof(double complex) * md->ntab);
+        }
+  }
   if (g->medium == 1) {
     md->fit = (double complex*)malloc(sizeof(double complex) * 2 * nz * nz * 3);
     for (int kind = 0; kind < 2; ++kind) {
@@ -293,13 +328,40 @@ static void medium_init(medium_t* md, const or_grid* g, double freq, int nz, con
   }
 }
 
-static void medium_free(medium_t* md) { free(md->fit); md->fit = NULL; }
+static void medium_free(medium_t* md) {
+  free(md->fit);
+  free(md->tab);
+  free(md->ctab);
+  md->fit = NULL;
+  md->tab = NULL;
+  md->ctab = NULL;
+}
+
+/* Cubic Lagrange interpolation of a table on rho_i = i h. */
+static double complex table_interp(const double complex* t, int n, double h, double rho) {
+  double x = rho / h;
+  int i = (int)floor(x);
+  int j0 = i - 1;
+  if (j0 < 0) j0 = 0;
+  if (j0 > n - 4) j0 = n - 4;
+  double u = x - j0;
+  double l0 = -(u - 1) * (u - 2) * (u - 3) / 6.0, l1 = u * (u - 2) * (u - 3) / 2.0;
+  double l2 = -u * (u - 1) * (u - 3) / 2.0, l3 = u * (u - 1) * (u - 2) / 6.0;
+  return l0 * t[j0] + l1 * t[j0 + 1] + l2 * t[j0 + 2] + l3 * t[j0 + 3];
+}
 
 /* G (reg = 0) or G - 1/(4 pi R_direct) (reg = 1) of kernel `kind` between heights z[ip], z[iq] at
  * lateral distance rho. */
 static double complex green_eval(const medium_t* md, int kind, int ip, int iq, double rho, int reg) {
   const or_grid* g = md->g;
   double zp = md->z[ip], zq = md->z[iq];
+  if (md->layered) {   /* kind 0: G_phi, 2: G_A (horizontal) */
+    int tk = kind == 2 ? 1 : 0;
+    double c = md->ctab[(tk * md->nz + ip) * md->nz + iq];
+    double R = sqrt(rho * rho + (zp - zq) * (zp - zq));
+    double complex direct = reg ? c * gfree_reg(md->k, R) : c * gfree(md->k, R);
+    return direct + table_interp(md->tab + ((size_t)(tk * md->nz + ip) * md->nz + iq) * md->ntab, md->ntab, md->htab, rho);
+  }
   if (g->medium == 0) {
     double Rd = sqrt(rho * rho + (zp - zq) * (zp - zq)), Ri = sqrt(rho * rho + (zp + zq) * (zp + zq));
     double complex gi = gfree(md->k, Ri);
@@ -452,17 +514,25 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
     double wpo = wo[i] * p->area;
     int izp = p->zid[near][i];
     if (near) {
+      /* the subtracted 1 / (4 pi R) carries each kernel's quasi-static constant (1 but in a
+       * layered medium, where G_phi and G_A have their own) */
+      double cphi = 1.0, cA = 1.0;
+      if (md->layered) {
+        int izq0 = q->zid[1][0];
+        cphi = md->ctab[(0 * md->nz + izp) * md->nz + izq0];
+        cA = md->ctab[(1 * md->nz + izp) * md->nz + izq0];
+      }
       double I1, Iv[3], rv[3];
       or_tri_potentials(q->v, r, &I1, Iv);
       sub3(r, q->v[0], rv);
       double d = dot3(q->n, rv);
       double r0[3] = {r[0] - d * q->n[0], r[1] - d * q->n[1], r[2] - d * q->n[2]};   /* projection on T_q's plane */
-      out[0] += wpo * I1 / (4.0 * OR_PI);
+      out[0] += cphi * wpo * I1 / (4.0 * OR_PI);
       for (int b = 0; b < 3; ++b) {
         double vb[3], t[3];
         sub3(r0, q->v[b], vb);
         for (int k = 0; k < 3; ++k) t[k] = Iv[k] + vb[k] * I1;
-        for (int a = 0; a < 3; ++a) out[1 + 3 * a + b] += wpo * dot3(ra[a], t) / (4.0 * OR_PI);
+        for (int a = 0; a < 3; ++a) out[1 + 3 * a + b] += cA * wpo * dot3(ra[a], t) / (4.0 * OR_PI);
       }
     }
     for (int j = 0; j < ni; ++j) {
@@ -471,6 +541,8 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
       int izq = q->zid[near][j];
       double rho = hypot(r[0] - rq[0], r[1] - rq[1]);
       double complex GD = green_eval(md, 0, izp, izq, rho, near);
+      /* horizontal vector part: the same kernel in a homogeneous medium, G_A in a layered one */
+      double complex GA = md->layered ? green_eval(md, 2, izp, izq, rho, near) : GD;
       double complex GN = both_vert ? green_eval(md, 1, izp, izq, rho, near) : 0.0;
       double complex w = wpo * wi[j] * q->area;
       out[0] += w * GD;
@@ -479,7 +551,7 @@ static void pair_integrals(const medium_t* md, const tri_t* p, const tri_t* q, d
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           double dh = ra[a][0] * rb[b][0] + ra[a][1] * rb[b][1], dz = ra[a][2] * rb[b][2];
-          out[1 + 3 * a + b] += w * (dh * GD + (both_vert ? dz * GN : 0.0));
+          out[1 + 3 * a + b] += w * (dh * GA + (both_vert ? dz * GN : 0.0));
         }
     }
   }

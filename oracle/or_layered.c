@@ -261,3 +261,14 @@ double complex or_slab_green(const or_grid* g, double freq, int kind, double z, 
   if (c_out) *c_out = c;
   return direct + sommerfeld_remainder(&s, kind, z, zp, rho);
 }
+
+/* Table of the Sommerfeld remainder of kernel `kind` between heights z, zp at rho_i = i h,
+ * i < n, for the fill: G = C e^{-j k1 R} / (4 pi R) + remainder(rho).  Returns C and k1. */
+void or_slab_table(const or_grid* g, double freq, int kind, double z, double zp, double er_top, double h, int n,
+                   double complex* out, double* c_out, double complex* k1_out) {
+  slab_t s;
+  slab_init(&s, g, freq, er_top, h * (n - 1));
+  for (int i = 0; i < n; ++i) out[i] = sommerfeld_remainder(&s, kind, z, zp, h * i);
+  *c_out = quasi_static_c(&s, kind, z, zp);
+  *k1_out = s.k1;
+}

@@ -116,6 +116,8 @@ class Grid:
                        getattr(g, "diag_pattern", 0), getattr(g, "diag_seed", 0), getattr(g, "sub", 1))
         if getattr(g, "sub", 1) not in (1, 2, 3) or (getattr(g, "sub", 1) > 1 and g.n_states > 2):
             raise ValueError("sub-squares per pixel side: 1, 2 or 3; the via state needs 1")
+        if g.medium == 2 and g.n_states > 2:
+            raise ValueError("the layered microstrip kernels are for horizontal currents: no via state")
         self.ref = ctypes.byref(self.c)
         self.M = lib().or_count_bfs(self.ref)
         self.P = len(g.ports)

@@ -30,7 +30,9 @@ extern "C" {
 typedef struct {
   int layers, nx, ny;
   double pitch;            /* pixel side a [m] */
-  int medium;              /* 0: microstrip (one ground plane at z = 0), 1: stripline (planes at 0 and h_total) */
+  int medium;              /* 0: microstrip (one ground plane at z = 0) in the homogeneous effective-medium
+                              reading, 1: stripline (planes at 0 and h_total), 2: microstrip as a
+                              grounded dielectric slab under air (Sommerfeld kernels) */
   const double* layer_z;   /* [layers] metal heights [m] */
   double h_total;          /* stripline plate spacing [m] (microstrip: unused) */
   double eps_r, tan_d;
@@ -104,6 +106,9 @@ double complex or_green_heights(const or_grid* g, double freq, int kind, double 
  * the half-space above.  reg != 0 subtracts C / (4 pi R); C (the quasi-static constant) -> c_out. */
 double complex or_slab_green(const or_grid* g, double freq, int kind, double z, double zp, double rho,
                              double er_top, int reg, double* c_out);
+/* The fill's table of the Sommerfeld remainder at rho_i = i h (i < n); C and k1 returned. */
+void or_slab_table(const or_grid* g, double freq, int kind, double z, double zp, double er_top, double h, int n,
+                   double complex* out, double* c_out, double complex* k1_out);
 /* Analytic potential integrals over a planar triangle (used by the singular part of the fill). */
 void or_tri_potentials(const double tri[3][3], const double r[3], double* I1, double Iv[3]);
 /* Quadrature rules on the reference triangle: n = 7 or 13; returns barycentric rows and weights. */

@@ -224,8 +224,9 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   if (!g || !out) return PMOM_ERR_INVALID_ARG;
   *out = nullptr;
   if (g->layers < 1 || g->layers > 8 || g->nx < 1 || g->ny < 1 || g->nx > 100 || g->ny > 100 || g->pitch_m <= 0 ||
-      g->n_ports < 1 || g->n_ports > pmom::kMaxPorts || !g->ports || !g->layer_z_m || (g->medium != 0 && g->medium != 1))
+      g->n_ports < 1 || g->n_ports > pmom::kMaxPorts || !g->ports || !g->layer_z_m || g->medium < 0 || g->medium > 2)
     return PMOM_ERR_INVALID_ARG;
+  if (g->medium == 2) return PMOM_ERR_UNSUPPORTED;   // layered (Sommerfeld) microstrip kernels: not in the GPU fill
   if (g->n_states != 2 && g->n_states != 3) return PMOM_ERR_UNSUPPORTED;
   if (g->n_states == 3 && g->layers < 2) return PMOM_ERR_INVALID_ARG;   // a via needs a layer above
   if (g->diag_pattern < 0 || g->diag_pattern > 2) return PMOM_ERR_INVALID_ARG;
