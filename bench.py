@@ -120,54 +120,91 @@ def lu_flops(N: np.ndarray, F: int, P: int) -> float:
     return float(F * np.sum(8.0 / 3.0 * N ** 3 + 8.0 * N ** 2 * P))
 
 
-def cpu_baseline(w, seconds_target: float = 15.0):
-    """The oracle (plain C, complex128) on the host cores, on a bounded sample: a few candidates of
-    the same batch at a few of its frequencies, scaled to candidate evaluations per second."""
-    from oracle import oracle as O
-    freqs = w.freqs()
-    fsel = np.linspace(0, w.n_freq - 1, 4).round().astype(int)
-    OG = O.Grid(w.grid)
-    Z, _ = O.fill(OG, freqs[fsel])
-    Z = Z.astype(np.complex64) if w.z_dtype == "c64" else Z
-    maps = PI.workload_maps(w, seed=0)
-    cores = os.cpu_count() or 1
-    nb = max(1, min(maps.shape[0], cores))
-    t0 = time.perf_counter()
-    O.eval_batch(OG, Z, maps[:nb], threads=cores)
-    dt = time.perf_counter() - t0
-    evals = nb * len(fsel) / w.n_freq
-    # grow the sample towards the time target
-    if dt < seconds_target / 4:
-        nb2 = min(maps.shape[0], max(nb, int(nb * seconds_target / max(dt, 1e-3) / 2)))
+class OracleSample:
+    """The oracle (plain C, complex128) on a bounded sample of a workload: the first candidates of
+    rank 0's batch at four of its frequencies, on the oracle's own fill of the database at those
+    frequencies (rounded to complex64 and promoted exactly when the workload stores complex64, as
+    the library's input is)."""
+
+    def __init__(self, w, batch: int = 0):
+        from oracle import oracle as O
+        self.O, self.w = O, w
+        self.fsel = np.linspace(0, w.n_freq - 1, 4).round().astype(int)
+        self.freqs = w.freqs()[self.fsel]
+        self.OG = O.Grid(w.grid)
+        Z, _ = O.fill(self.OG, self.freqs)
+        self.Z = Z.astype(np.complex64) if w.z_dtype == "c64" else Z
+        self.maps = rank_batch(w, 0, batch)
+        self.cores = os.cpu_count() or 1
+
+    def run(self, nb: int):
+        """Evaluates the first nb candidates at the sampled frequencies; returns (S, seconds)."""
         t0 = time.perf_counter()
-        O.eval_batch(OG, Z, maps[:nb2], threads=cores)
-        dt = time.perf_counter() - t0
-        nb = nb2
-        evals = nb * len(fsel) / w.n_freq
-    return {"value": evals / dt, "unit": "candidate evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nb} candidates x {len(fsel)} of {w.n_freq} frequencies (scaled), complex128 LU, all host threads",
-            "seconds": dt}
+        S, _ = self.O.eval_batch(self.OG, self.Z, self.maps[:nb], threads=self.cores)
+        return S, time.perf_counter() - t0
+
+    def rate(self, nb: int, seconds: float) -> float:
+        """Candidate evaluations (all frequencies of a candidate = one) per second."""
+        return nb * len(self.fsel) / self.w.n_freq / seconds
+
+    def describe(self, nb: int) -> str:
+        return (f"{nb} candidates x {len(self.fsel)} of {self.w.n_freq} frequencies (scaled), complex128 LU, "
+                f"{self.cores} host threads")
+
+    def calibrate(self, seconds_target: float) -> int:
+        """The sample size whose evaluation takes about seconds_target."""
+        nb = max(1, min(self.maps.shape[0], self.cores))
+        _, dt = self.run(nb)
+        if dt < seconds_target / 2:
+            nb = min(self.maps.shape[0], max(nb, int(nb * seconds_target / max(dt, 1e-3))))
+        return nb
+
+
+def cpu_baseline(w, seconds_target: float = 15.0, sample: "OracleSample" = None):
+    """The oracle on the host cores, on a bounded sample of the workload, scaled to candidate
+    evaluations per second.  Also returns (sample, candidates, S) for the accuracy check of the GPU
+    paths against the oracle."""
+    smp = sample or OracleSample(w)
+    nb = smp.calibrate(seconds_target / 2)
+    S, dt = smp.run(nb)
+    return {"value": smp.rate(nb, dt), "unit": "candidate evals/s", "cores": smp.cores, "kind": "oracle",
+            "sample": smp.describe(nb), "seconds": dt}, (smp, nb, S)
+
+
+def workload_config(w, N: np.ndarray, M: int, batch: int, world: int) -> dict:
+    """The `config` object of the JSON line (the same in both arms)."""
+    h = np.histogram(N, bins=6)
+    return {"workload": w.name, "global_batch": batch * world, "freqs": w.n_freq, "M": int(M),
+            "N_mean": float(N.mean()), "N_min": int(N.min()), "N_max": int(N.max()),
+            "N_hist": [[int(e) for e in h[1]], [int(c) for c in h[0]]],
+            "l2": "inputs larger than L2 (Z database %.2f GB)" % (
+                w.n_freq * M * M * (8 if w.z_dtype == "c64" else 16) / 1e9),
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on the host cores.  Each step evaluates one
+    fixed bounded sample of the workload (sized during the first warm-up step so that the whole
+    run stays within about two minutes); ms_per_step is the measured time of that sample."""
     rank, world, _ = _dist()
     if rank != 0:
         return
     w = workload(args.workload)
-    vals = []
-    for _ in range(args.warmup):
-        pass
-    info = None
-    for _ in range(max(1, args.steps)):
-        info = cpu_baseline(w, seconds_target=max(4.0, 60.0 / max(1, args.steps)))
-        vals.append(info["value"])
-    v = float(np.median(vals))
+    smp = OracleSample(w, args.batch)
+    N = np.array([len(smp.O.active_set(smp.OG, m)) for m in smp.maps])
+    per_step = min(15.0, max(0.5, 120.0 / max(1, args.steps + args.warmup)))
+    nb = smp.calibrate(per_step) if args.warmup > 0 else max(1, min(smp.maps.shape[0], smp.cores))
+    for _ in range(max(0, args.warmup - 1)):
+        smp.run(nb)
+    secs = [smp.run(nb)[1] for _ in range(max(1, args.steps))]
+    ms = 1000.0 * float(np.mean(secs))
+    v = smp.rate(nb, ms * 1e-3)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidate evals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.batch / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": w.name, "global_batch": w.batch, "freqs": w.n_freq},
-            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": v,
-                             "unit": "candidate evals/s"},
+            "config": workload_config(w, N, smp.OG.M, smp.maps.shape[0], world),
+            "cpu_baseline": {"kind": "oracle", "cores": smp.cores, "sample": "per step: " + smp.describe(nb),
+                             "value": v, "unit": "candidate evals/s"},
             "e2e": {"value": v, "unit": "candidate evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -194,6 +231,29 @@ def max_over_ranks(ms: float, dist, device) -> float:
 def aggregate_rate(world: int, batch: int, ms: float) -> float:
     """Whole-job candidate evaluations per second: every rank's batch over the slowest rank's time."""
     return world * batch / (ms * 1e-3)
+
+
+def accuracy_vs_oracle(smp: "OracleSample", nb: int, S_or: np.ndarray) -> dict:
+    """Both GPU paths against the oracle on the oracle's bounded sample: S per entry and the FoM of
+    the sampled frequencies (Eq. 8-9 over the four-frequency sweep, on both sides)."""
+    import torch
+    from paper_2412_17617_gb300 import Evaluator, band_codes
+    w = smp.w
+    ev = Evaluator(w.grid)
+    ev.load_Z(smp.freqs, torch.from_numpy(np.ascontiguousarray(smp.Z)).cuda())
+    ev.set_fom(band_codes(smp.freqs, w.bands), w.z0_ohm)
+    fom_or = smp.O.fom_batch(S_or, smp.O.bands(smp.freqs, w.bands))
+    out = {"candidates": nb, "frequencies": [int(f) for f in smp.fsel]}
+    maps = torch.from_numpy(np.ascontiguousarray(smp.maps[:nb])).cuda()
+    for prec in ("mixed", "fp64"):
+        S, fom, st = ev.eval(maps, prec)
+        torch.cuda.synchronize()
+        S, fom, st = S.cpu().numpy(), fom.cpu().numpy(), st.cpu().numpy()
+        out[prec] = {"max_abs_dS": float(np.abs(S - S_or).max()),
+                     "max_rel_fom": float((np.abs(fom - fom_or) / np.abs(fom_or)).max()),
+                     "status_ok": int((st == 0).sum())}
+    ev.close()
+    return out
 
 
 def run_ours(args):
@@ -253,22 +313,29 @@ def run_ours(args):
     st = ev.stats()
     status_np = status.cpu().numpy()
     value = aggregate_rate(world, Bsz, ms)
-    # ---- plain FP64 path on a subset of the same batch (its cost is ~50x higher)
+    # ---- plain FP64 path on a subset of the same batch (its cost is ~25-50x higher), replayed
+    #      from a CUDA graph like the headline: one warm-up, then the median of three replays
     three_state = w.grid.n_states == 3
     huge = int(N.max()) > 3000          # FP64 LU of N ~ 4000 at 101 frequencies: ~20 s per candidate
-    nfp = min(Bsz, 2 if huge else 8 if three_state else 32)
+    nfp = min(Bsz, 2 if huge else 8 if three_state else 128)
+    reps = 1 if huge else 3
     sub = maps[:nfp]
     S_mixed, fom_mixed = S[:nfp].clone(), fom[:nfp].clone()
     sub_out = (S[:nfp], fom[:nfp], status[:nfp])
-    ev.eval(sub, "fp64", out=sub_out)
+    ev.graph_capture(sub, "fp64", out=sub_out, ncap=int(N[:nfp].max()))
+    ev.graph_launch()
     barrier()
-    e0.record(stream)
-    ev.eval(sub, "fp64", out=sub_out)
-    e1.record(stream)
-    barrier()
-    fp64_ms = e0.elapsed_time(e1)
+    fp64_runs = []
+    for _ in range(reps):
+        e0.record(stream)
+        ev.graph_launch()
+        e1.record(stream)
+        barrier()
+        fp64_runs.append(e0.elapsed_time(e1))
+    fp64_ms = float(np.median(fp64_runs))
     fp64_value = world * nfp / (fp64_ms * 1e-3)
     S_ref64, fom_ref64 = S[:nfp].clone(), fom[:nfp].clone()
+    fp64_status_ok = int((status[:nfp] == 0).sum().item())
 
     def accuracy(Sx, fx):
         return {"max_abs_dS_vs_fp64": float((Sx - S_ref64).abs().max().item()),
@@ -343,14 +410,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "candidate evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 LU + f64 refinement", "data": "synthetic",
-        "config": {"workload": w.name, "global_batch": Bsz * world, "freqs": w.n_freq, "M": ev.M,
-                   "N_mean": float(N.mean()), "N_min": int(N.min()), "N_max": int(N.max()),
-                   "N_hist": [[int(e) for e in np.histogram(N, bins=6)[1]], [int(c) for c in np.histogram(N, bins=6)[0]]],
-                   "l2": "inputs larger than L2 (Z database %.2f GB)" % (
-                       w.n_freq * ev.M * ev.M * (8 if w.z_dtype == "c64" else 16) / 1e9),
-                   "parallelism": f"replicas x{world}"},
+        "vs_baseline": None,
+        "dtype": "c64 (fp32/3xTF32 LU and solves, float-float refinement residual, f64 corrections, Y, S, FoM)",
+        "data": "synthetic",
+        "config": workload_config(w, N, ev.M, Bsz, world),
         "fp64_path": {"value": fp64_value, "unit": "candidate evals/s", "candidates": nfp,
+                      "ms_per_step": fp64_ms, "runs_ms": fp64_runs, "status_ok": fp64_status_ok,
+                      "timing": "CUDA-graph replay of the FP64 pipeline on the first %d candidates, "
+                                "median of %d after one warm-up" % (nfp, reps),
                       "speedup_mixed_over_fp64": value / fp64_value},
         "accuracy": accuracy(S_mixed, fom_mixed),
         "bordered_update": bordered,
@@ -367,12 +434,56 @@ def run_ours(args):
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w)
+        # the oracle on a bounded sample (timed), and both GPU paths on the same sample: the
+        # oracle's own database at the sampled frequencies, loaded into a second evaluator
+        info, (smp, nb, S_or) = cpu_baseline(w, sample=OracleSample(w, args.batch))
+        line["cpu_baseline"] = info
+        line["accuracy_vs_oracle"] = accuracy_vs_oracle(smp, nb, S_or)
     if rank == 0:
         print(json.dumps(line))
     ev.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_peaks():
+    """Measured throughput ceilings of this GPU for the roofline denominators that the measured
+    peaks file does not carry: dense TF32, FP32 and FP64 matrix products through torch.matmul
+    (cuBLAS) and, for comparison, BF16 and a device-to-device copy.  Best of ten, CUDA events."""
+    import torch
+    torch.cuda.init()
+    dev = torch.cuda.get_device_properties(0)
+    res = {"gpu": dev.name, "sms": dev.multi_processor_count, "torch": torch.__version__}
+
+    def best(fn, reps=10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return min(t)
+
+    for name, dt, n, tf32 in (("bf16_tflops", torch.bfloat16, 8192, False), ("tf32_tflops", torch.float32, 8192, True),
+                              ("fp32_tflops", torch.float32, 8192, False), ("fp64_tflops", torch.float64, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda").to(dt)
+        b = torch.randn(n, n, device="cuda").to(dt)
+        ms = best(lambda: torch.matmul(a, b))
+        res[name] = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+        res[name.replace("_tflops", "_shape")] = f"{n}^3"
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    x = torch.empty(1 << 30, dtype=torch.bfloat16, device="cuda")
+    y = torch.empty_like(x)
+    ms = best(lambda: y.copy_(x))
+    res["hbm_copy_gbs"] = 2.0 * x.numel() * 2 / (ms * 1e-3) / 1e9
+    res["how"] = "torch.matmul n^3 (2 n^3 flop), best of 10 after one warm-up, CUDA events; copy of 1 Gi bf16 (read + write)"
+    print(json.dumps(res))
 
 
 def main():
@@ -390,8 +501,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-bordered", dest="bordered", action="store_false",
                     help="skip the bordered-update measurement of the same batch")
+    ap.add_argument("--peaks", action="store_true", help="measure TF32 / FP32 / FP64 / BF16 matmul and copy "
+                                                           "throughput of this GPU and print them as JSON")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.peaks:
+        run_peaks()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

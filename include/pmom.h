@@ -194,10 +194,11 @@ pmom_status pmom_eval_candidates_host(pmom_ctx* ctx, const uint8_t* maps_host, i
                                       double* S_out_host, double* fom_out_host, int32_t* status_host,
                                       void* stream);
 
-/* Allocation-free evaluation, for callers that must not allocate device memory during the
- * call: code running inside a CUDA-graph capture or another framework's memory pool, real-time
- * loops that forbid allocator latency, and hosts whose device memory is fully reserved up front.
- * The paper has no counterpart to this entry point; it is a deployment convenience.
+/* Allocation-free evaluation.  Some callers cannot let a library call cudaMalloc or cudaFree
+ * while they run: a host that hands all device memory to another framework's caching pool at
+ * start-up (a late cudaMalloc then fails or fragments that pool), and real-time loops for which
+ * the allocator's latency, and the device synchronization that cudaFree implies, are not
+ * acceptable.  The paper has no counterpart to this entry point; it is a deployment convenience.
  * Same arguments and results as pmom_eval_candidates (S_out_dev may be NULL only if the batch's
  * S still fits the scratch), but every temporary (support sets, per-task workspaces, counters)
  * lives in one fixed array of PMOM_NOALLOC_SCRATCH_BYTES (32 MiB) that the library declares in
@@ -205,9 +206,13 @@ pmom_status pmom_eval_candidates_host(pmom_ctx* ctx, const uint8_t* maps_host, i
  * exits.  The call issues no cudaMalloc/cudaFree.  Preconditions: Z loaded or filled and the
  * FoM bands set on `ctx` (those earlier calls may allocate).  A batch whose scratch does not fit
  * is rejected with PMOM_ERR_INVALID_ARG and a message stating the bytes needed (in practice the
- * FP64 workspace of one task must fit: M up to about 1400 for the mixed path).
+ * FP64 workspace of one task must fit: M up to about 1400 for the mixed path).  Workspaces are
+ * sized for the whole parent (M BFs), so the tasks share min(resident task slots,
+ * (32 MiB - batch bookkeeping) / workspace(M)) workspaces: near the limit only one or two, and the
+ * batch then runs on one or two SMs (results unchanged, throughput far below
+ * pmom_eval_candidates).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call outside any stream capture.  All calls share the one array and it keeps the
+ * that first call before any stream capture.  All calls share the one array and it keeps the
  * previous call's contents: the entry point clears the parts that must start at zero itself,
  * but two calls that overlap on the GPU (different streams, contexts or host threads without
  * ordering) race on the array and corrupt each other.  pmom_stats / pmom_kernel_times do not
@@ -310,7 +315,7 @@ pmom_status pmom_capacity(pmom_ctx* ctx, int32_t precision, int32_t* n_default, 
  *   FoM after each iteration, up to trace_cap entries. */
 typedef struct {
   uint64_t seed;
-  int32_t d_max;          /* 1..8 */
+  int32_t d_max;          /* 1..8, and at most nx * ny (INVALID_ARG otherwise) */
   int32_t m_of_d[8];      /* non-improving iterations tolerated at each depth */
   int64_t max_evals;      /* FoM evaluation budget */
   int32_t precision;      /* PMOM_FP64 or PMOM_MIXED_REFINED */

@@ -88,6 +88,10 @@ def tree_search(evaluate, init_map: np.ndarray, seed: int, d_max: int, m_of_d, m
     search would (max_evals counts every evaluation since the start)."""
     L, ny, nx = init_map.shape
     ncol, K = ny * nx, int(np.prod(radices(L, n_states)))
+    if not 1 <= d_max <= ncol:
+        raise ValueError(f"d_max = {d_max}: a depth-D tree changes D distinct columns of the {ncol} on the grid")
+    if state is not None and not 1 <= int(state["depth"]) <= d_max:
+        raise ValueError("resumed depth outside 1..d_max")
 
     def F_of(maps):
         f = np.asarray(evaluate(np.ascontiguousarray(maps)), dtype=np.float64)

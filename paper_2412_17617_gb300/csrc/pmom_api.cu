@@ -311,6 +311,7 @@ pmom_status pmom_load_Z(pmom_ctx* c, const double* freqs, int32_t F, const void*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (bytes != c->z_bytes) {
     free_dev(c->d_Z);
+    c->z_bytes = 0;   // no database until the new allocation succeeds
     PMOM_CUDA(c, cudaMalloc(&c->d_Z, bytes));
     c->z_bytes = bytes;
   }
@@ -944,9 +945,10 @@ pmom_status pmom_fill_Z(pmom_ctx* c, const double* freqs, int32_t F, int32_t dty
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free evaluation
-// Some callers cannot let the library allocate device memory inside a call (graph capture,
-// pools owned by another framework, real-time loops).  For them every temporary of the
-// evaluation comes out of one fixed device array declared here; the kernels are the same ones
+// Some callers cannot let the library allocate device memory inside a call: device memory
+// handed to another framework's pool at start-up, or loops that cannot take the allocator's
+// latency and the synchronization of cudaFree.  For them every temporary of the evaluation comes
+// out of one fixed device array declared here; the kernels are the same ones
 // pmom_eval_candidates launches, given pointers into this array instead of context workspaces.
 namespace {
 

@@ -77,6 +77,8 @@ extern "C" pmom_status pmom_search_resume(pmom_ctx* c, const pmom_search_params*
   pmom_num_bfs(c, &M, &P);
   const pmom::Grid& g = pmom::grid_of(c);
   const Shape sh{g.layers, g.ny, g.nx, g.vias()};
+  // a tree of depth D changes D distinct columns: deeper than the column count has no node to draw
+  if (prm->d_max > sh.cols()) return PMOM_ERR_INVALID_ARG;
   const size_t npix = sh.pix();
   const int K = sh.states();
   std::vector<uint8_t> batch;

@@ -102,3 +102,16 @@ def test_argument_validation(lib):
     st = lib.pmom_eval_candidates(ev.h, None, 4, 1, None, None, None, None)
     assert st == 1
     ev.close()
+
+
+def test_search_rejects_depth_beyond_the_column_count(lib):
+    """pmom_search on a 2 x 2 grid (four columns) with d_max = 8: INVALID_ARG before any
+    evaluation, where a deeper tree would have no free column to draw."""
+    g = PI.grid_tiny(2)
+    ev = pmom.Evaluator(g)
+    init = PI.seed_map(g, 0.5, 1)
+    for call in (ev.search, ev.search_resume):
+        with pytest.raises(pmom.PmomError) as e:
+            call(init, seed=1, d_max=8, m_of_d=(1,) * 8, max_evals=10)
+        assert e.value.status == 1
+    ev.close()

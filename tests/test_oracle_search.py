@@ -145,3 +145,14 @@ def test_resumed_search_equals_uninterrupted(split):
     assert np.array_equal(b[0], full[0]) and b[1] == full[1] and b[2] == full[2]
     assert a[3] + b[3] == full[3]
     assert a[4]["restart"] >= 0 and (split < 100 or a[4]["restart"] >= 1 or a[4]["iteration"] > 10)
+
+
+def test_depth_beyond_the_column_count_is_rejected():
+    """A depth-D tree changes D distinct columns: on a 2 x 2 grid (four columns) d_max = 8 has no
+    node to draw at depth 5, so the search refuses it instead of drawing from an empty list."""
+    g = PI.grid_tiny(2)
+    init = PI.seed_map(g, 0.5, 1)
+    with pytest.raises(ValueError):
+        OS.tree_search(lambda m: np.zeros(len(m)), init, seed=1, d_max=8, m_of_d=(1,) * 8, max_evals=10)
+    with pytest.raises(ValueError):
+        OS.tree_search(lambda m: np.zeros(len(m)), init, seed=1, d_max=0, m_of_d=(1,), max_evals=10)
