@@ -35,6 +35,31 @@ __device__ __forceinline__ int group_id() { return threadIdx.x / kThreads; }
 __device__ __forceinline__ void gsync() {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "r"(kThreads) : "memory");
 }
+// Phase clocks, for profiling builds only (compiled with -DPMOM_PHASES): thread 0 of each task
+// group adds the cycles since its previous mark (the variable t) to a per-phase device counter.
+// In normal builds the marks expand to nothing.
+constexpr int kPhaseSlots = 16;
+enum Phase : int {
+  kPhGather = 0, kPhLu = 1, kPhSolve0 = 2, kPhResid = 3, kPhSolveCorr = 4, kPhOther = 5,
+  kPhColGemm = 8, kPhPanel = 9, kPhSwap = 10, kPhInnerU = 11, kPhInnerUpd = 12, kPhRowGemm = 13, kPhTrsm = 14,
+  kPhTasks = 15
+};
+#ifdef PMOM_PHASES
+__device__ unsigned long long g_phase_cycles[kPhaseSlots];
+#define PMOM_PHASE_START(t) long long t = clock64()
+#define PMOM_PHASE(slot, t)                                                                      \
+  do {                                                                                           \
+    if (gtid() == 0) {                                                                           \
+      const long long n_ = clock64();                                                            \
+      atomicAdd(&g_phase_cycles[slot], static_cast<unsigned long long>(n_ - (t)));               \
+      (t) = n_;                                                                                  \
+    }                                                                                            \
+  } while (0)
+#else
+#define PMOM_PHASE_START(t) do { } while (0)
+#define PMOM_PHASE(slot, t) do { } while (0)
+#endif
+
 constexpr int kTile = 64;        // trailing-update tile (rows and columns)
 constexpr int kOuter = 64;       // outer panel width of the two-level (tensor-core) LU
 constexpr int kMaxRefine = 10;
@@ -101,6 +126,13 @@ template <> __device__ __forceinline__ double2 zload<double2, double2>(const dou
 template <> __device__ __forceinline__ float2 zload<double2, float2>(const double2* p) {
   return from_d2<float2>(__ldg(p));
 }
+
+// the same conversions for a value already loaded (from shared memory)
+template <typename ZT, typename T> __device__ __forceinline__ T zconv(ZT v);
+template <> __device__ __forceinline__ float2 zconv<float2, float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 zconv<float2, double2>(float2 v) { return to_d2(v); }
+template <> __device__ __forceinline__ double2 zconv<double2, double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 zconv<double2, float2>(double2 v) { return from_d2<float2>(v); }
 
 __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ double shfl_f(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -210,149 +242,189 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
   return br;
 }
 
-// ------------------------------------------------------------------ tensor-core trailing update
-// State of the task group's tensor-core pipeline: 96 KB operand staging (A_hi | A_lo, each a
-// 128 x 32 K-major fp32 tile, then B_hi | B_lo, each 256 x 32), a 256-column TMEM accumulator and
-// the MMA-completion barrier.
+// ------------------------------------------------------------------ tensor-core block updates
+// The single-precision LU runs as a Crout (left-and-right-looking) blocked factorization over
+// kOuter-column outer panels: before outer panel J is factored, its columns receive all earlier
+// panels' contributions at once (column update, K = J kOuter), and after it is factored, its rows
+// receive them to the right of the panel (row update, K = J kOuter) before its triangular solve.
+// Each update is one long-K contraction per 128-row output tile, so the tile is read and written
+// once per panel instead of once per earlier panel, and the tensor cores run long MMA streams.
+//
+// Pipeline state of the task group: kStages operand stages of one K chunk (kChunk complex values
+// = 16 real K) each -- A_hi | A_lo (128 x 16 fp32, 8 KB each) then B_hi | B_lo (128 x 16) -- a
+// 128-column TMEM accumulator and one MMA-completion mbarrier per stage.
+constexpr int kStages = 3;
+constexpr int kGatherBufs = 8;   // parent rows in flight in the bulk gather
+constexpr int kChunk = 8;
+constexpr uint32_t kStageBytes = 32768;
 struct TcState {
   unsigned char* stage;
   uint32_t tmem;
-  uint64_t* mbar;
-  uint32_t phase;
+  uint64_t* mbar;     // [kStages]
+  uint32_t sph;       // bit s: parity of the next completion awaited on stage s
   bool failed;
 };
 // bounded wait: 2^18 polls of mbarrier.try_wait (about 1 s at the measured 3.8 us per unanswered
-// poll); a stall flags the task instead of hanging, a healthy completion answers in microseconds
+// poll); a stall flags the task instead of hanging, a healthy completion answers in microseconds.
+// Once a wait of the task has failed the later ones are skipped (the task is flagged already).
 constexpr long long kTcWaitPolls = 1ll << 18;
-constexpr int kTcCols = 128;                     // complex output columns per tile (MMA N = 256 real)
+constexpr int kTcCols = 128;                     // complex output columns per TMEM allocation half
 constexpr uint32_t kTmemCols = 2 * kTcCols;      // TMEM columns per task group
 
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float v) {
+__device__ __forceinline__ void stage_wait(TcState& st, int s) {
+  if (!st.failed && !tc::mbar_wait(&st.mbar[s], (st.sph >> s) & 1u, kTcWaitPolls)) st.failed = true;
+  st.sph ^= 1u << s;
+}
+
+// hi + lo TF32 split of v stored at byte offset `off` of the hi and lo tiles
+__device__ __forceinline__ void put_split16(unsigned char* hi, unsigned char* lo, uint32_t off, float v) {
   const float h = tc::to_tf32(v);
-  const uint32_t off = tc::kmajor_off(row, k);
   *reinterpret_cast<float*>(hi + off) = h;
   *reinterpret_cast<float*>(lo + off) = tc::to_tf32(v - h);
 }
 
-// Outer-panel update A22 -= L21 U12 on the tensor cores, with K = jb <= 64 complex columns taken
-// in chunks of 16.  Per 128 x 128 complex output tile, each chunk is one real GEMM
-// [Lr | Li] (128 x 32) times B (32 x 256), B's first 128 columns being [Ur; -Ui] (real parts of
-// the product) and its last 128 [Ui; Ur] (imaginary parts), i.e. one M = 128, N = 256 MMA shape.
-// Every fp32 operand is split into two TF32 terms (hi + lo) and the three significant products
-// (lo*hi, hi*lo, hi*hi) accumulate in fp32 in TMEM across the chunks (3xTF32).  One thread
-// issues; the completion arrives on an mbarrier that the group waits on with an iteration limit.
-__device__ void trailing_tc(float2* __restrict__ A, int lda, int N, int j0, int jb, TcState& st) {
+// Complex update on the tensor cores, C -= X Y with K = K complex terms (K a multiple of kChunk).
+// Column update (ROWG = false): C = A[r_out + i][c_out + j], i < m (128-row tiles), j < nc <= 64;
+//   X = A[r_out + i][0:K] (L rows), Y = A[0:K][c_out + j] (U columns).
+// Row update (ROWG = true), computed transposed so that the long dimension fills the MMA's rows:
+//   C^T[i][j] = A[r_out + j][c_out + i], i < m (128-column tiles), j < nc <= 64;
+//   X = A[0:K][c_out + i]^T (U columns), Y = A[r_out + j][0:K]^T (L rows).
+// The complex product is realified as [Xr | Xi] (128 x 2K) times [[Yr, Yi], [-Yi, Yr]] (2K x 128),
+// one M = 128, N = 128 MMA shape whose first 64 output columns are the real parts and last 64 the
+// imaginary parts; X is negated while staged so TMEM accumulates -X Y.  Each fp32 operand is split
+// into TF32 hi + lo and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32
+// (3xTF32).  All threads stage: chunk c + 2 is loaded into registers while chunk c is split into
+// stage c % kStages, whose previous MMAs (chunk c - kStages) must have completed; one thread
+// issues each chunk's six MMAs and commits them to that stage's mbarrier, so the tensor cores
+// work through chunk c while the threads stage chunk c + 1.
+template <bool ROWG>
+__device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c_out, int m, int nc, int K,
+                               TcState& st) {
   const int tid = gtid(), warp = tid >> 5, lane = tid & 31;
-  const int rb = j0 + jb, n2 = N - rb;
-  const int nk = (jb + 15) >> 4;
-  unsigned char* Ah = st.stage;
-  unsigned char* Al = st.stage + 16384;
-  unsigned char* Bh = st.stage + 32768;
-  unsigned char* Bl = st.stage + 65536;
-  const uint32_t idesc = tc::idesc_tf32(128, 2 * kTcCols);
-  for (int c0 = rb; c0 < N; c0 += kTcCols) {
-    for (int r0 = 0; r0 < n2; r0 += 128) {
-      for (int kc = 0; kc < nk; ++kc) {
-        const int kbase = j0 + 16 * kc, kw = min(16, jb - 16 * kc);
-        {
-          // all loads first (independent, in flight together), then the split stores.  Each warp
-          // covers whole core matrices (8 operand rows x 4 K values): lane = 4 (row % 8) + k % 4,
-          // so its shared-memory stores are conflict-free and its loads still use full sectors.
-          float2 u[8], l[8];
+  const uint32_t idesc = tc::idesc_tf32(128, 128);
+  const int nk = K / kChunk;
+  // element coordinates of this thread's staging slots: four of X (1024 elements per chunk), two
+  // of Y (512).  Each warp covers 8 operand rows x 4 K values, so the canonical-layout stores are
+  // conflict-free, and the global loads run along the contiguous index (full sectors).
+  int xi[4], xk[4], yj[2], yk[2];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
-            const int t = (w >> 4) * 4 + (ln & 3), c = (w & 15) * 8 + (ln >> 2);
-            u[i] = (t < kw && c0 + c < N) ? A[static_cast<size_t>(kbase + t) * lda + c0 + c] : make_float2(0.f, 0.f);
-          }
+  for (int u = 0; u < 4; ++u) {
+    const int e = tid + u * kThreads, ln = e & 31, wt = e >> 5;
+    xi[u] = (wt & 15) * 8 + (ROWG ? (ln & 7) : (ln >> 2));
+    xk[u] = (wt >> 4) * 4 + (ROWG ? (ln >> 3) : (ln & 3));
+  }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
-            const int t = (w & 3) * 4 + (ln & 3), r = (w >> 2) * 8 + (ln >> 2);
-            l[i] = (t < kw && r0 + r < n2) ? A[static_cast<size_t>(rb + r0 + r) * lda + kbase + t] : make_float2(0.f, 0.f);
-          }
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * kThreads, ln = e & 31, wt = e >> 5;
+    yj[u] = (wt & 7) * 8 + (ROWG ? (ln >> 2) : (ln & 7));
+    yk[u] = (wt >> 3) * 4 + (ROWG ? (ln & 3) : (ln >> 3));
+  }
+  for (int t0 = 0; t0 < m; t0 += 128) {
+    const int mt = min(128, m - t0);
+    float2 px[4], py[2], qx[4], qy[2];
+    auto load = [&](int c, float2* vx, float2* vy) {
+      const int kb = c * kChunk;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
-            const int t = (w >> 4) * 4 + (ln & 3), c = (w & 15) * 8 + (ln >> 2);
-            put_split(Bh, Bl, c, t, u[i].x);
-            put_split(Bh, Bl, c, 16 + t, -u[i].y);
-            put_split(Bh, Bl, kTcCols + c, t, u[i].y);
-            put_split(Bh, Bl, kTcCols + c, 16 + t, u[i].x);
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int e = tid + i * kThreads, ln = e & 31, w = e >> 5;
-            const int t = (w & 3) * 4 + (ln & 3), r = (w >> 2) * 8 + (ln >> 2);
-            put_split(Ah, Al, r, t, l[i].x);
-            put_split(Ah, Al, r, 16 + t, l[i].y);
-          }
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        gsync();
-        tc::fence_after_sync();
-        if (tid == 0) {
-          const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al), bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
-          uint32_t acc = kc > 0 ? 1u : 0u;
-#pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            const uint32_t ao = term == 0 ? al : ah;     // small terms first: lo*hi, hi*lo, hi*hi
-            const uint32_t bo = term == 1 ? bl : bh;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              tc::mma_tf32(st.tmem, tc::smem_desc(ao + ks * 256), tc::smem_desc(bo + ks * 256), idesc, acc);
-              acc = 1;
-            }
-          }
-          tc::commit(st.mbar);
-        }
-        // one warp waits for the MMAs (they read the staged operands); the barrier releases the rest
-        if (warp == 0) {
-          if (!tc::mbar_wait(st.mbar, st.phase, kTcWaitPolls)) st.failed = true;
-        }
-        st.phase ^= 1u;
-        gsync();
+      for (int u = 0; u < 4; ++u) {
+        const size_t o = ROWG ? static_cast<size_t>(kb + xk[u]) * lda + c_out + t0 + xi[u]
+                              : static_cast<size_t>(r_out + t0 + xi[u]) * lda + kb + xk[u];
+        vx[u] = xi[u] < mt ? A[o] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const size_t o = ROWG ? static_cast<size_t>(r_out + yj[u]) * lda + kb + yk[u]
+                              : static_cast<size_t>(kb + yk[u]) * lda + c_out + yj[u];
+        vy[u] = yj[u] < nc ? A[o] : make_float2(0.f, 0.f);
+      }
+    };
+    load(0, px, py);
+    if (nk > 1) load(1, qx, qy);
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % kStages;
+      if (c >= kStages) stage_wait(st, s);   // the MMAs of chunk c - kStages have read this stage
+      unsigned char* xh = st.stage + s * kStageBytes;
+      unsigned char* xl = xh + 8192;
+      unsigned char* yh = xh + 16384;
+      unsigned char* yl = xh + 24576;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        put_split16(xh, xl, tc::kmajor16_off(xi[u], xk[u]), -px[u].x);
+        put_split16(xh, xl, tc::kmajor16_off(xi[u], kChunk + xk[u]), -px[u].y);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        put_split16(yh, yl, tc::kmajor16_off(yj[u], yk[u]), py[u].x);
+        put_split16(yh, yl, tc::kmajor16_off(yj[u], kChunk + yk[u]), -py[u].y);
+        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], yk[u]), py[u].y);
+        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], kChunk + yk[u]), py[u].x);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) px[u] = qx[u];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) py[u] = qy[u];
+      if (c + 2 < nk) load(c + 2, qx, qy);
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      gsync();
       tc::fence_after_sync();
-      // TMEM (row = lane) -> shared result tile (the operand staging is free) -> coalesced update,
-      // 64 complex columns at a time
-      float2* T = reinterpret_cast<float2*>(st.stage);
-      constexpr int LDT = 65;
-      for (int hc = 0; hc < kTcCols; hc += 64) {
-        {
-          const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
-          float re[32], im[32];
-          tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + hc + 32 * h, re);
-          tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + kTcCols + hc + 32 * h, im);
+      if (tid == 0) {
+        const uint32_t ah = tc::smem_u32(xh), al = tc::smem_u32(xl), bh = tc::smem_u32(yh), bl = tc::smem_u32(yl);
+        uint32_t acc = c > 0 ? 1u : 0u;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
-        }
-        tc::fence_before_sync();
-        gsync();
-        // 32 elements per thread in two batches of 16 independent loads, then the stores
+        for (int term = 0; term < 3; ++term) {
+          const uint32_t ao = term == 0 ? al : ah;     // small terms first: lo*hi, hi*lo, hi*hi
+          const uint32_t bo = term == 1 ? bl : bh;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float2 v[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = hc + (e & 63);
-            v[i] = (r0 + r < n2 && c0 + c < N) ? A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int e = tid + (half * 16 + i) * kThreads, r = e >> 6, c = hc + (e & 63);
-            if (r0 + r < n2 && c0 + c < N) {
-              const float2 d = T[r * LDT + (e & 63)];
-              A[static_cast<size_t>(rb + r0 + r) * lda + c0 + c] = make_float2(v[i].x - d.x, v[i].y - d.y);
-            }
+          for (int ks = 0; ks < 2; ++ks) {
+            tc::mma_tf32(st.tmem, tc::smem_desc16(ao + ks * 256), tc::smem_desc16(bo + ks * 256), idesc, acc);
+            acc = 1;
           }
         }
-        tc::fence_before_sync();
-        gsync();
-        tc::fence_after_sync();
+        tc::commit(&st.mbar[s]);
       }
     }
+    // every outstanding chunk completes (commits complete in order: the last one first)
+    for (int c = nk - 1; c >= 0 && c >= nk - kStages; --c) stage_wait(st, c % kStages);
+    tc::fence_after_sync();
+    // TMEM (row = lane) -> shared result tile (the stages are free) -> coalesced update
+    float2* T = reinterpret_cast<float2*>(st.stage);
+    constexpr int LDT = 65;
+    {
+      const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
+      float re[32], im[32];
+      tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * h, re);
+      tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 + 32 * h, im);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
+    }
+    tc::fence_before_sync();
+    gsync();
+    // 32 elements per thread in two batches of 16 independent loads, then the stores
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float2 v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + (half * 16 + u) * kThreads;
+        const int i = ROWG ? (e & 127) : (e >> 6), j = ROWG ? (e >> 7) : (e & 63);
+        const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + i
+                              : static_cast<size_t>(r_out + t0 + i) * lda + c_out + j;
+        v[u] = (i < mt && j < nc) ? A[o] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + (half * 16 + u) * kThreads;
+        const int i = ROWG ? (e & 127) : (e >> 6), j = ROWG ? (e >> 7) : (e & 63);
+        if (i < mt && j < nc) {
+          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + i
+                                : static_cast<size_t>(r_out + t0 + i) * lda + c_out + j;
+          const float2 d = T[i * LDT + j];
+          A[o] = make_float2(v[u].x + d.x, v[u].y + d.y);
+        }
+      }
+    }
+    tc::fence_before_sync();
+    gsync();
   }
 }
 
@@ -408,10 +480,18 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
   // Updates made by each NB-column panel stop at column `cend`: N for the one-level CUDA-core
   // path; the end of the current kOuter-column outer panel for the two-level tensor-core path
   int cend = N;
+  PMOM_PHASE_START(tph);
   for (int k0 = 0; k0 < N; k0 += NB) {
     const int kb = min(NB, N - k0);
     const int nr = N - k0;
-    if (tcs != nullptr && k0 % kOuter == 0) cend = min(N, k0 + kOuter);
+    if (tcs != nullptr && k0 % kOuter == 0) {
+      cend = min(N, k0 + kOuter);
+      if constexpr (std::is_same<CT, float2>::value) {
+        // Crout column update of the new outer panel: A[k0:N, k0:cend] -= L[k0:N, 0:k0] U[0:k0, k0:cend]
+        if (k0 > 0) gemm_update_tc<false>(A, lda, k0, k0, N - k0, cend - k0, k0, *tcs);
+      }
+      PMOM_PHASE(kPhColGemm, tph);
+    }
     // 1. panel -> shared memory (eight independent loads in flight per thread)
     for (int e0 = tid; e0 < nr * NB; e0 += 8 * kThreads) {
       CT v[8];
@@ -466,6 +546,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       const int r = e / NB, c = e % NB;
       if (c < kb) A[static_cast<size_t>(k0 + r) * lda + k0 + c] = Pn[r * LDP + c];
     }
+    PMOM_PHASE(kPhPanel, tph);
     // 4. the panel's row interchanges on the columns outside it (a barrier only after an actual
     //    interchange: the pivot is usually the diagonal row); four columns per thread in flight
     for (int j = 0; j < kb; ++j) {
@@ -495,6 +576,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
     }
     gsync();
+    PMOM_PHASE(kPhSwap, tph);
     // 5. U12 = L11^-1 A12 (one column per thread, unit lower L11 from shared memory), columns up
     //    to the end of the current outer panel
     for (int c = k0 + kb + tid; c < cend; c += kThreads) {
@@ -510,6 +592,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         if (i < kb) A[static_cast<size_t>(k0 + i) * lda + c] = u[i];
     }
     gsync();
+    PMOM_PHASE(kPhInnerU, tph);
     // 6. trailing update A22 -= L21 U12 on the CUDA cores (64 x 64 tiles, 4 x 4 complex outputs per
     //    thread), for the columns up to the end of the current outer panel
     const int r_begin = k0 + kb, n2 = N - r_begin;
@@ -564,14 +647,17 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
     }
     gsync();
-    // 7-8. end of an outer panel (tensor-core path): U12 for the columns to its right, then one
-    //      K = 64 update of the remaining matrix on the tensor cores
+    PMOM_PHASE(kPhInnerUpd, tph);
+    // 7-8. end of an outer panel (tensor-core path): the Crout row update of its rows to the right
+    //      of the panel, A[j0:cend, cend:N] -= L[j0:cend, 0:j0] U[0:j0, cend:N], then U12 of those
+    //      rows (the rows below receive these panels' contributions in their own column updates)
     if constexpr (std::is_same<CT, float2>::value) {
       if (tcs != nullptr && k0 + kb == cend && cend < N) {
         const int j0 = cend - ((cend - 1) % kOuter + 1);
+        if (j0 > 0) gemm_update_tc<true>(A, lda, j0, cend, N - cend, cend - j0, j0, *tcs);
+        PMOM_PHASE(kPhRowGemm, tph);
         outer_trsm(A, lda, N, j0, cend - j0, reinterpret_cast<float2*>(tcs->stage));
-        trailing_tc(A, lda, N, j0, cend - j0, *tcs);
-        gsync();
+        PMOM_PHASE(kPhTrsm, tph);
       }
     }
   }
@@ -782,11 +868,15 @@ __device__ __forceinline__ void dd_add(float& ah, float& al, float bh, float bl)
 // V[e0+p][p] = 1.
 // F32OUT (identity columns only): the residual is formed in float-float and written rounded to
 // float into rw (the precision of the correction solve that consumes it), with no FP64 work.
+// cols (optional): Z_sub is read in place from the parent Z(f) (row-major, leading dimension lda =
+// M) through the support set, Z_sub[i][t] = Zs[cols[i] * lda + cols[t]] -- the frequency-major
+// task order keeps Z(f) resident in L2 while its candidates are processed -- instead of from a
+// gathered copy.
 template <int NP, bool F32OUT = false>
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
                             const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
                             int e0 = -1, float2* __restrict__ rw = nullptr, int gap_stride = 3, int gap_off = 1,
-                            int gap_n = 1) {
+                            int gap_n = 1, const int* __restrict__ cols = nullptr) {
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
@@ -804,19 +894,21 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
     const float2* zrow[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int i = i0 + q * kWarps;
-      zrow[q] = Zs + static_cast<size_t>(i < N ? i : 0) * lda;
+      const int i = i0 + q * kWarps, ic = i < N ? i : 0;
+      zrow[q] = Zs + static_cast<size_t>(cols ? cols[ic] : ic) * lda;
     }
     // the next column step's entries are loaded while this one's are used (one step of prefetch)
     float2 zn[R];
+    int cn = lane < N ? (cols ? cols[lane] : lane) : 0;
 #pragma unroll
-    for (int q = 0; q < R; ++q) zn[q] = (i0 + q * kWarps < N && lane < N) ? zrow[q][lane] : make_float2(0.f, 0.f);
+    for (int q = 0; q < R; ++q) zn[q] = (i0 + q * kWarps < N && lane < N) ? zrow[q][cn] : make_float2(0.f, 0.f);
     for (int t = lane; t < N; t += 32) {
       float2 z[R];
+      cn = t + 32 < N ? (cols ? cols[t + 32] : t + 32) : 0;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         z[q] = zn[q];
-        zn[q] = (i0 + q * kWarps < N && t + 32 < N) ? zrow[q][t + 32] : make_float2(0.f, 0.f);
+        zn[q] = (i0 + q * kWarps < N && t + 32 < N) ? zrow[q][cn] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -1083,7 +1175,9 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   __shared__ int s_flag_g[kMaxGroups];
   __shared__ double s_dx_g[kMaxGroups][2];   // refinement: last correction norm, ||x||_inf
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups];
+  __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups][kStages];
+  __shared__ __align__(8) uint64_t s_gbar_g[kMaxGroups][kGatherBufs];
+  __shared__ int s_gfail_g[kMaxGroups];   // a bulk gather wait gave up: later tasks are flagged
   constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
   const int g = group_id();
   const int ngroups = blockDim.x / kThreads;
@@ -1106,9 +1200,20 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   TcState tcs;
   tcs.stage = nullptr;
   tcs.tmem = 0;
-  tcs.mbar = &s_mbar_g[g];
-  tcs.phase = 0;
+  tcs.mbar = s_mbar_g[g];
+  tcs.sph = 0;
   tcs.failed = false;
+  uint64_t* gbar = s_gbar_g[g];
+  volatile int& s_gfail = s_gfail_g[g];
+  uint32_t gph = 0;   // bit b: parity of the next completion awaited on gather buffer b
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ngroups; ++i) {
+      s_gfail_g[i] = 0;
+      for (int j = 0; j < kGatherBufs; ++j) tc::mbar_init(&s_gbar_g[i][j], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   if (use_tc) {
     // 1024-byte aligned operand staging inside this group's tensor-core region
     const uint32_t base = tc::smem_u32(smem + tc_off);
@@ -1118,7 +1223,8 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       tc::tmem_relinquish();
     }
     if (threadIdx.x == 0) {
-      for (int i = 0; i < ngroups; ++i) tc::mbar_init(&s_mbar_g[i], 1);
+      for (int i = 0; i < ngroups; ++i)
+        for (int j = 0; j < kStages; ++j) tc::mbar_init(&s_mbar_g[i][j], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
@@ -1143,6 +1249,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     const int tq = s_task;
     gsync();
     if (tq >= ntasks) break;
+    PMOM_PHASE_START(tev);
     const int t = a.ntasks_list ? a.repair_list[tq] : tq;
     const int f = t / a.B, b = a.order ? a.order[t % a.B] : t % a.B;
     const int N = a.n_act[b];
@@ -1171,30 +1278,73 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     const int32_t* gidx = a.idx + static_cast<size_t>(b) * M;
     for (int i = tid; i < N; i += kThreads) s_idx[i] = gidx[i];
     gsync();
-    // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I
-    // (eight independent loads in flight per thread, then the stores)
-    constexpr bool kZsCopy = MIXED && std::is_same<ZT, float2>::value;
-    const int NN = N * N;
-    for (int e0 = tid; e0 < NN; e0 += 8 * kThreads) {
-      CT v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
-        v[u] = e < NN ? zload<ZT, CT>(Zf + static_cast<size_t>(s_idx[i]) * M + s_idx[j]) : czero(v[0]);
+    // gather Z_sub (Eq. 5): row i of Z_sub = row I_i of Z(f) at the columns I.  Whole parent rows
+    // stream into shared memory by bulk asynchronous copies (up to kGatherBufs rows in flight from
+    // the L2-resident Z(f)); the group picks the support set's columns out of each staged row and
+    // writes row i of the workspace with coalesced stores.  Parents whose rows do not fit two
+    // buffers, or are not a multiple of 16 bytes, take the element-wise gather.
+    // The exact complex64 copy is kept only for factor-only launches (the bordered update's refined
+    // inverse reads it); the evaluation's own residual reads Z(f) in place through the support set.
+    constexpr bool kZsMixed = MIXED && std::is_same<ZT, float2>::value;
+    const bool zs_copy = kZsMixed && a.factor_only;
+    const uint32_t row_bytes = static_cast<uint32_t>(M) * sizeof(ZT);
+    const int nbuf = min(kGatherBufs, static_cast<int>(u_off / row_bytes));
+    if (nbuf >= 2 && (row_bytes & 15u) == 0 && !s_gfail) {
+      ZT* gbuf = reinterpret_cast<ZT*>(smem);
+      if (tid == 0) {
+        for (int b = 0; b < nbuf && b < N; ++b) {
+          tc::mbar_arrive_expect_tx(&gbar[b], row_bytes);
+          tc::bulk_g2s(gbuf + static_cast<size_t>(b) * M, Zf + static_cast<size_t>(s_idx[b]) * M, row_bytes, &gbar[b]);
+        }
       }
+      for (int i = 0; i < N; ++i) {
+        const int b = i % nbuf;
+        if (!tc::mbar_wait(&gbar[b], (gph >> b) & 1u, kTcWaitPolls)) s_gfail = 1;
+        gph ^= 1u << b;
+        const ZT* row = gbuf + static_cast<size_t>(b) * M;
+        for (int j = tid; j < N; j += kThreads) {
+          const CT v = zconv<ZT, CT>(row[s_idx[j]]);
+          A[static_cast<size_t>(i) * lda + j] = v;
+          if constexpr (kZsMixed) {
+            if (zs_copy) Zs[static_cast<size_t>(i) * lda + j] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+          }
+        }
+        tc::fence_async_smem();   // these reads come before the next bulk write into the buffer
+        gsync();
+        if (tid == 0 && i + nbuf < N) {
+          tc::mbar_arrive_expect_tx(&gbar[b], row_bytes);
+          tc::bulk_g2s(gbuf + static_cast<size_t>(b) * M, Zf + static_cast<size_t>(s_idx[i + nbuf]) * M, row_bytes,
+                       &gbar[b]);
+        }
+      }
+    } else {
+      // element-wise: eight independent loads in flight per thread, then the stores
+      const int NN = N * N;
+      for (int e0 = tid; e0 < NN; e0 += 8 * kThreads) {
+        CT v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
-        if (e < NN) {
-          A[static_cast<size_t>(i) * lda + j] = v[u];
-          if constexpr (kZsCopy) Zs[static_cast<size_t>(i) * lda + j] = make_float2(static_cast<float>(v[u].x), static_cast<float>(v[u].y));
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
+          v[u] = e < NN ? zload<ZT, CT>(Zf + static_cast<size_t>(s_idx[i]) * M + s_idx[j]) : czero(v[0]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kThreads, i = e / N, j = e - i * N;
+          if (e < NN) {
+            A[static_cast<size_t>(i) * lda + j] = v[u];
+            if constexpr (kZsMixed) {
+              if (zs_copy) Zs[static_cast<size_t>(i) * lda + j] = make_float2(static_cast<float>(v[u].x), static_cast<float>(v[u].y));
+            }
+          }
         }
       }
     }
     gsync();
+    PMOM_PHASE(kPhGather, tev);
     const bool singular = lu_factor<CT, NB>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
+    PMOM_PHASE(kPhLu, tev);
     if (a.factor_only) {   // factors stay in slot t; a zero pivot or a failed tensor-core wait is flagged
-      if (tid == 0 && (singular || tcs.failed)) atomicOr(flag_of, kFlagSingular);
+      if (tid == 0 && (singular || tcs.failed || s_gfail)) atomicOr(flag_of, kFlagSingular);
       tcs.failed = false;
       gsync();
       continue;
@@ -1210,6 +1360,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     lu_solve<CT>(A, lda, N, piv, W, P, Dg);
     for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
     gsync();
+    PMOM_PHASE(kPhSolve0, tev);
     int iters = 0;
     bool repaired = false;
     if (MIXED) {
@@ -1228,11 +1379,13 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
             xmax = fmax(xmax, fabs(v.x) + fabs(v.y));
           }
           gsync();
+          const float2* Zf32 = reinterpret_cast<const float2*>(Zf);
           if (P <= 3)
-            residual_df<3>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off, a.gap_n);
+            residual_df<3>(Zf32, M, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off, a.gap_n,
+                           s_idx);
           else
-            residual_df<kMaxPorts>(Zs, lda, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off,
-                                   a.gap_n);
+            residual_df<kMaxPorts>(Zf32, M, N, xf, P, lport, Rv, s_red, s_norm, -1, nullptr, a.gap_stride, a.gap_off,
+                                   a.gap_n, s_idx);
         } else {
           for (int e = tid; e < N * P; e += kThreads) {
             xs[e] = X[e];
@@ -1241,6 +1394,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
           gsync();
           residual<ZT>(Zf, M, s_idx, N, xs, P, lport, Rv, s_red, s_norm, a.gap_stride, a.gap_off, a.gap_n);
         }
+        PMOM_PHASE(kPhResid, tev);
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) xmax = fmax(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
         if ((tid & 31) == 0) s_red[tid >> 5] = xmax;
@@ -1267,7 +1421,9 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
         }
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
         gsync();
+        PMOM_PHASE(kPhOther, tev);
         lu_solve<CT>(A, lda, N, piv, W, P, Dg);
+        PMOM_PHASE(kPhSolveCorr, tev);
         double dmax = 0.0;   // ||correction||_inf
         for (int e = tid; e < N * P; e += kThreads) {
           const double2 d = to_d2(W[e]);
@@ -1308,7 +1464,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       } else if (singular) {
         atomicOr(&a.flags[b], kFlagSingular);
       }
-      if (tcs.failed) {   // a tensor-core completion wait ran out: the task's numbers are not trusted
+      if (tcs.failed || s_gfail) {   // a completion wait ran out: the task's numbers are not trusted
         atomicOr(&a.flags[b], kFlagNonfinite);
         atomicAdd(&a.counters[4], 1ull);
       }
@@ -1327,6 +1483,10 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       Sout[tid] = y;
     }
     gsync();
+    PMOM_PHASE(kPhOther, tev);
+#ifdef PMOM_PHASES
+    if (tid == 0) atomicAdd(&g_phase_cycles[kPhTasks], 1ull);
+#endif
   }
   if (use_tc) {   // both groups are done with the tensor memory
     tc::fence_before_sync();

@@ -45,6 +45,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// The same descriptor for a tile whose rows hold K = 16 fp32 values (8-row groups SBO = 512 bytes
+// apart): the operand stages of the pipelined column/row updates, one K chunk of 8 complex values.
+constexpr uint32_t kSBO16 = 512;
+__device__ __forceinline__ uint64_t smem_desc16(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((kLBO >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((kSBO16 >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  return d;
+}
+// byte offset of (row, k) in the canonical K-major no-swizzle tile with K = 16
+__device__ __forceinline__ uint32_t kmajor16_off(int row, int k) {
+  return static_cast<uint32_t>((row >> 3) * kSBO16 + (k >> 2) * kLBO + (row & 7) * 16 + (k & 3) * 4);
+}
+
 // instruction descriptor of kind::tf32 with fp32 accumulation, both operands K-major
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
@@ -85,6 +101,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
   for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
+}
+
+// Bulk asynchronous copy (the TMA engine's untiled form) of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) from global to this CTA's shared memory; completion is counted in
+// bytes on the mbarrier, which the issuing thread first arms with the expected byte count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 // TMEM allocation: executed by one whole warp; the address is written to shared memory.
