@@ -250,13 +250,24 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
 // Each update is one long-K contraction per 128-row output tile, so the tile is read and written
 // once per panel instead of once per earlier panel, and the tensor cores run long MMA streams.
 //
-// Pipeline state of the task group: kStages operand stages of one K chunk (kChunk complex values
-// = 16 real K) each -- A_hi | A_lo (128 x 16 fp32, 8 KB each) then B_hi | B_lo (128 x 16) -- a
-// 128-column TMEM accumulator and one MMA-completion mbarrier per stage.
+// Operand pipeline of a task group, per K chunk (kChunk complex values = 16 real K):
+//   raw stage   : the chunk's X and Y entries copied from the workspace by 16-byte asynchronous
+//                 copies (kRaw chunks in flight, no registers held), rows padded against bank
+//                 conflicts;
+//   MMA stage   : the A operand (128 rows x 16, hi and lo TF32 parts) in tensor memory, written
+//                 by the threads (one row each), and the B operand (128 x 16, hi and lo, canonical
+//                 K-major layout) in shared memory; kStages of them, one MMA-completion mbarrier
+//                 each.
+// Shared memory of a group's staging area: [kRaw raw stages | kStages B stages].  TMEM columns:
+// [0, 128) accumulator, [128 + 32 s, 160 + 32 s) A of MMA stage s (hi: +0..15, lo: +16..31).
+constexpr int kRaw = 3;
 constexpr int kStages = 3;
 constexpr int kGatherBufs = 8;   // parent rows in flight in the bulk gather
 constexpr int kChunk = 8;
-constexpr uint32_t kStageBytes = 32768;
+constexpr uint32_t kRawXBytes = 10240;    // 128 rows x 80 B (column update) / 8 x 1024 B (row update)
+constexpr uint32_t kRawBytes = 16384;     // + Y: 8 x 576 B (column update) / 64 x 96 B (row update)
+constexpr uint32_t kStageBytes = 16384;   // B hi | B lo of one MMA stage
+constexpr uint32_t kAccCols = 128;
 struct TcState {
   unsigned char* stage;
   uint32_t tmem;
@@ -274,6 +285,7 @@ constexpr uint32_t kTmemCols = 2 * kTcCols;      // TMEM columns per task group
 __device__ __forceinline__ void stage_wait(TcState& st, int s) {
   if (!st.failed && !tc::mbar_wait(&st.mbar[s], (st.sph >> s) & 1u, kTcWaitPolls)) st.failed = true;
   st.sph ^= 1u << s;
+  tc::fence_after_sync();
 }
 
 // hi + lo TF32 split of v stored at byte offset `off` of the hi and lo tiles
@@ -293,136 +305,165 @@ __device__ __forceinline__ void put_split16(unsigned char* hi, unsigned char* lo
 // one M = 128, N = 128 MMA shape whose first 64 output columns are the real parts and last 64 the
 // imaginary parts; X is negated while staged so TMEM accumulates -X Y.  Each fp32 operand is split
 // into TF32 hi + lo and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32
-// (3xTF32).  All threads stage: chunk c + 2 is loaded into registers while chunk c is split into
-// stage c % kStages, whose previous MMAs (chunk c - kStages) must have completed; one thread
-// issues each chunk's six MMAs and commits them to that stage's mbarrier, so the tensor cores
-// work through chunk c while the threads stage chunk c + 1.
+// (3xTF32).  Iteration c of the chunk loop: the asynchronous copies of chunk c have landed; one
+// barrier; one thread issues chunk c - 1's six MMAs (converted in the previous iteration) and
+// commits them to its stage's mbarrier; the copies of chunk c + kRaw - 1 are issued into the raw
+// stage chunk c - 1 used; chunk c is converted into MMA stage c % kStages once chunk
+// c - kStages's MMAs have completed.  The epilogue reads the accumulator row by row from TMEM and
+// adds it to C in global memory.  Rows and columns outside the tile are never copied: their stale
+// staging entries reach only accumulator rows and columns that are not stored.
 template <bool ROWG>
 __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c_out, int m, int nc, int K,
                                TcState& st) {
   const int tid = gtid(), warp = tid >> 5, lane = tid & 31;
   const uint32_t idesc = tc::idesc_tf32(128, 128);
   const int nk = K / kChunk;
-  // element coordinates of this thread's staging slots: four of X (1024 elements per chunk), two
-  // of Y (512).  Each warp covers 8 operand rows x 4 K values, so the canonical-layout stores are
-  // conflict-free, and the global loads run along the contiguous index (full sectors).
-  int xi[4], xk[4], yj[2], yk[2];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int e = tid + u * kThreads, ln = e & 31, wt = e >> 5;
-    xi[u] = (wt & 15) * 8 + (ROWG ? (ln & 7) : (ln >> 2));
-    xk[u] = (wt >> 4) * 4 + (ROWG ? (ln >> 3) : (ln & 3));
-  }
+  // conversion slots: X -- this thread's TMEM lane (row xi of the tile) and K half (4 complex values
+  // at 4 xh); Y -- two (k, j) elements, each warp covering 8 rows of the B tile x 4 K values
+  // (conflict-free canonical-layout stores)
+  const int q = warp & 3, xh = warp >> 2, xi = 32 * q + lane;
+  const uint32_t lane_base = st.tmem + (static_cast<uint32_t>(32 * q) << 16);
+  int yj[2], yk[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int e = tid + u * kThreads, ln = e & 31, wt = e >> 5;
     yj[u] = (wt & 7) * 8 + (ROWG ? (ln >> 2) : (ln & 7));
     yk[u] = (wt >> 3) * 4 + (ROWG ? (ln & 3) : (ln >> 3));
   }
+  unsigned char* raw0 = st.stage;
+  unsigned char* bst0 = st.stage + kRaw * kRawBytes;
   for (int t0 = 0; t0 < m; t0 += 128) {
     const int mt = min(128, m - t0);
-    float2 px[4], py[2], qx[4], qy[2];
-    auto load = [&](int c, float2* vx, float2* vy) {
+    // this thread's 16-byte pieces of chunk c: two of X, one of Y
+    auto issue = [&](int c) {
+      unsigned char* rx = raw0 + (c % kRaw) * kRawBytes;
+      unsigned char* ry = rx + kRawXBytes;
       const int kb = c * kChunk;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const size_t o = ROWG ? static_cast<size_t>(kb + xk[u]) * lda + c_out + t0 + xi[u]
-                              : static_cast<size_t>(r_out + t0 + xi[u]) * lda + kb + xk[u];
-        vx[u] = xi[u] < mt ? A[o] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const size_t o = ROWG ? static_cast<size_t>(r_out + yj[u]) * lda + kb + yk[u]
-                              : static_cast<size_t>(kb + yk[u]) * lda + c_out + yj[u];
-        vy[u] = yj[u] < nc ? A[o] : make_float2(0.f, 0.f);
+        const int e = tid + u * kThreads;
+        if (ROWG) {   // X[k][i]: 8 rows of 128 complex values (64 pieces each)
+          const int k = e >> 6, part = e & 63;
+          if (2 * part < mt) tc::cp_async16(rx + k * 1024 + part * 16, A + static_cast<size_t>(kb + k) * lda + c_out + t0 + 2 * part);
+        } else {      // X[i][k]: 128 rows of 8 complex values (4 pieces each), rows 80 bytes apart
+          const int i = e >> 2, part = e & 3;
+          if (i < mt) tc::cp_async16(rx + i * 80 + part * 16, A + static_cast<size_t>(r_out + t0 + i) * lda + kb + 2 * part);
+        }
+      }
+      if (ROWG) {     // Y[j][k]: 64 rows of 8 complex values, rows 96 bytes apart
+        const int j = tid >> 2, part = tid & 3;
+        if (j < nc) tc::cp_async16(ry + j * 96 + part * 16, A + static_cast<size_t>(r_out + j) * lda + kb + 2 * part);
+      } else {        // Y[k][j]: 8 rows of 64 complex values, rows 576 bytes apart
+        const int k = tid >> 5, part = tid & 31;
+        if (2 * part < nc) tc::cp_async16(ry + k * 576 + part * 16, A + static_cast<size_t>(kb + k) * lda + c_out + 2 * part);
       }
     };
-    load(0, px, py);
-    if (nk > 1) load(1, qx, qy);
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % kStages;
-      if (c >= kStages) stage_wait(st, s);   // the MMAs of chunk c - kStages have read this stage
-      unsigned char* xh = st.stage + s * kStageBytes;
-      unsigned char* xl = xh + 8192;
-      unsigned char* yh = xh + 16384;
-      unsigned char* yl = xh + 24576;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        put_split16(xh, xl, tc::kmajor16_off(xi[u], xk[u]), -px[u].x);
-        put_split16(xh, xl, tc::kmajor16_off(xi[u], kChunk + xk[u]), -px[u].y);
+    for (int p = 0; p < kRaw - 1; ++p) {
+      if (p < nk) issue(p);
+      tc::cp_async_commit();   // one group per chunk slot, empty past the end, so the counts line up
+    }
+    for (int c = 0; c <= nk; ++c) {
+      if (c < nk) {
+        tc::cp_async_wait<kRaw - 2>();                 // this thread's pieces of chunk c have landed
+        if (c >= kStages) stage_wait(st, c % kStages);  // chunk c - kStages's MMAs have read stage c % kStages
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        put_split16(yh, yl, tc::kmajor16_off(yj[u], yk[u]), py[u].x);
-        put_split16(yh, yl, tc::kmajor16_off(yj[u], kChunk + yk[u]), -py[u].y);
-        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], yk[u]), py[u].y);
-        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], kChunk + yk[u]), py[u].x);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) px[u] = qx[u];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) py[u] = qy[u];
-      if (c + 2 < nk) load(c + 2, qx, qy);
+      tc::tmem_wait_st();
       tc::fence_async_smem();
       tc::fence_before_sync();
       gsync();
       tc::fence_after_sync();
-      if (tid == 0) {
-        const uint32_t ah = tc::smem_u32(xh), al = tc::smem_u32(xl), bh = tc::smem_u32(yh), bl = tc::smem_u32(yl);
-        uint32_t acc = c > 0 ? 1u : 0u;
+      if (tid == 0 && c > 0) {
+        const int s1 = (c - 1) % kStages;
+        const uint32_t xa = st.tmem + kAccCols + 32 * s1;
+        const uint32_t bh = tc::smem_u32(bst0 + s1 * kStageBytes), bl = bh + 8192;
+        uint32_t acc = c > 1 ? 1u : 0u;
 #pragma unroll
         for (int term = 0; term < 3; ++term) {
-          const uint32_t ao = term == 0 ? al : ah;     // small terms first: lo*hi, hi*lo, hi*hi
+          const uint32_t ao = xa + (term == 0 ? 16u : 0u);   // small terms first: lo*hi, hi*lo, hi*hi
           const uint32_t bo = term == 1 ? bl : bh;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            tc::mma_tf32(st.tmem, tc::smem_desc16(ao + ks * 256), tc::smem_desc16(bo + ks * 256), idesc, acc);
+            tc::mma_tf32_ts(st.tmem, ao + 8 * ks, tc::smem_desc16(bo + ks * 256), idesc, acc);
             acc = 1;
           }
         }
-        tc::commit(&st.mbar[s]);
+        tc::commit(&st.mbar[s1]);
+      }
+      if (c == nk) break;
+      if (c + kRaw - 1 < nk) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
+      tc::cp_async_commit();
+      // convert chunk c: X -> TMEM (negated, split; real parts at K columns 4 xh + u, imaginary at
+      // 8 + 4 xh + u), Y -> canonical B tile
+      const int s = c % kStages;
+      const unsigned char* rx = raw0 + (c % kRaw) * kRawBytes;
+      const unsigned char* ry = rx + kRawXBytes;
+      {
+        float2 x[4];
+        if (ROWG) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float2*>(rx + (4 * xh + u) * 1024 + xi * 8);
+        } else {
+          const float4 a = *reinterpret_cast<const float4*>(rx + xi * 80 + xh * 32);
+          const float4 b = *reinterpret_cast<const float4*>(rx + xi * 80 + xh * 32 + 16);
+          x[0] = make_float2(a.x, a.y); x[1] = make_float2(a.z, a.w);
+          x[2] = make_float2(b.x, b.y); x[3] = make_float2(b.z, b.w);
+        }
+        float hr[4], lr[4], hi[4], li[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float re = -x[u].x, im = -x[u].y;
+          hr[u] = tc::to_tf32(re); lr[u] = tc::to_tf32(re - hr[u]);
+          hi[u] = tc::to_tf32(im); li[u] = tc::to_tf32(im - hi[u]);
+        }
+        const uint32_t col = lane_base + kAccCols + 32 * s + 4 * xh;
+        tc::tmem_st4(col, hr[0], hr[1], hr[2], hr[3]);
+        tc::tmem_st4(col + 8, hi[0], hi[1], hi[2], hi[3]);
+        tc::tmem_st4(col + 16, lr[0], lr[1], lr[2], lr[3]);
+        tc::tmem_st4(col + 24, li[0], li[1], li[2], li[3]);
+      }
+      unsigned char* yh = bst0 + s * kStageBytes;
+      unsigned char* yl = yh + 8192;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float2 y = *reinterpret_cast<const float2*>(ROWG ? ry + yj[u] * 96 + yk[u] * 8 : ry + yk[u] * 576 + yj[u] * 8);
+        put_split16(yh, yl, tc::kmajor16_off(yj[u], yk[u]), y.x);
+        put_split16(yh, yl, tc::kmajor16_off(yj[u], kChunk + yk[u]), -y.y);
+        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], yk[u]), y.y);
+        put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], kChunk + yk[u]), y.x);
       }
     }
+    tc::cp_async_wait<0>();
     // every outstanding chunk completes (commits complete in order: the last one first)
     for (int c = nk - 1; c >= 0 && c >= nk - kStages; --c) stage_wait(st, c % kStages);
-    tc::fence_after_sync();
-    // TMEM (row = lane) -> shared result tile (the stages are free) -> coalesced update
-    float2* T = reinterpret_cast<float2*>(st.stage);
-    constexpr int LDT = 65;
-    {
-      const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
-      float re[32], im[32];
-      tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * h, re);
-      tc::tmem_ld32(st.tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 + 32 * h, im);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) T[row * LDT + 32 * h + j] = make_float2(re[j], im[j]);
-    }
-    tc::fence_before_sync();
-    gsync();
-    // 32 elements per thread in two batches of 16 independent loads, then the stores
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    // epilogue: this thread's accumulator row (TMEM lane xi), complex columns 32 xh .. 32 xh + 31,
+    // in two halves of 16, added to C with independent loads in flight
+    const bool xv = xi < mt;
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+      const int j0 = 32 * xh + 16 * hh;
+      float re[16], im[16];
+      tc::tmem_ld16(lane_base + j0, re);
+      tc::tmem_ld16(lane_base + 64 + j0, im);
       float2 v[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const int e = tid + (half * 16 + u) * kThreads;
-        const int i = ROWG ? (e & 127) : (e >> 6), j = ROWG ? (e >> 7) : (e & 63);
-        const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + i
-                              : static_cast<size_t>(r_out + t0 + i) * lda + c_out + j;
-        v[u] = (i < mt && j < nc) ? A[o] : make_float2(0.f, 0.f);
+        const int j = j0 + u;
+        const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
+                              : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
+        v[u] = (xv && j < nc) ? A[o] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const int e = tid + (half * 16 + u) * kThreads;
-        const int i = ROWG ? (e & 127) : (e >> 6), j = ROWG ? (e >> 7) : (e & 63);
-        if (i < mt && j < nc) {
-          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + i
-                                : static_cast<size_t>(r_out + t0 + i) * lda + c_out + j;
-          const float2 d = T[i * LDT + j];
-          A[o] = make_float2(v[u].x + d.x, v[u].y + d.y);
+        const int j = j0 + u;
+        if (xv && j < nc) {
+          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
+                                : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
+          A[o] = make_float2(v[u].x + re[u], v[u].y + im[u]);
         }
       }
     }
+    // the accumulator is read and the staging area is free before the next tile starts
     tc::fence_before_sync();
     gsync();
   }
@@ -507,37 +548,109 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
     }
     gsync();
-    // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row)
-    for (int j = 0; j < kb; ++j) {
+    // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row), one barrier per
+    //    column: each warp publishes its best candidate row for the next column (value, index and
+    //    the whole row) in a double-buffered slot; after the barrier every thread picks the pivot
+    //    from the slots and updates the rows it owns (row r belongs to thread r mod kThreads), the
+    //    owner of row j swapping: it writes the pivot row (from the slot) into row j and its own
+    //    old row, updated, into row p, which nobody else touches in that column.
+    {
+      CT* cdat = Ut;                                            // [2][kWarps][NB]
+      R* cval = reinterpret_cast<R*>(Ut + 2 * kWarps * NB);     // [2][kWarps]
+      int* crow = reinterpret_cast<int*>(cval + 2 * kWarps);    // [2][kWarps]
+      const int lane = tid & 31, warp = tid >> 5;
+      // publish this warp's best candidate (v, r) into slot parity `par`
+      auto publish = [&](R v, int r, int par) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          const R ov = __shfl_xor_sync(0xffffffffu, v, d);
+          const int orow = __shfl_xor_sync(0xffffffffu, r, d);
+          if (ov > v || (ov == v && orow >= 0 && (r < 0 || orow < r))) { v = ov; r = orow; }
+        }
+        if (lane == 0) {
+          cval[par * kWarps + warp] = v;
+          crow[par * kWarps + warp] = r;
+        }
+        __syncwarp();   // the winning row was written by a lane of this warp
+        if (r >= 0 && lane < NB) cdat[(par * kWarps + warp) * NB + lane] = Pn[r * LDP + lane];
+      };
       R best = -1;
       int brow = -1;
-      for (int r = j + tid; r < nr; r += kThreads) {
-        const R v = cabs2(Pn[r * LDP + j]);
+      for (int r = tid; r < nr; r += kThreads) {
+        const R v = cabs2(Pn[r * LDP]);
         if (v > best) { best = v; brow = r; }
       }
-      const int p = block_argmax<R>(best, brow, s_val, s_row);
-      if (tid == 0) piv[k0 + j] = k0 + p;
-      if (p != j && tid < kb) {
-        const CT t = Pn[j * LDP + tid];
-        Pn[j * LDP + tid] = Pn[p * LDP + tid];
-        Pn[p * LDP + tid] = t;
-      }
-      gsync();
-      const CT d = Pn[j * LDP + j];
-      const bool zero = cabs2(d) == R(0);
-      if (zero) singular = true;
-      const CT inv = zero ? czero(d) : cinv(d);
-      // pivot row in registers; the column loop unrolled over the panel width so that the
-      // shared-memory loads of one row are in flight together
-      CT prow[NB];
+      publish(best, brow, 0);
+      for (int j = 0; j < kb; ++j) {
+        const int par = j & 1;
+        gsync();
+        R pv = -1;
+        int p = -1, pw = 0;
 #pragma unroll
-      for (int c = 1; c < NB; ++c) prow[c] = (j + c < kb) ? Pn[j * LDP + j + c] : czero(d);
-      for (int r = j + 1 + tid; r < nr; r += kThreads) {
-        const CT l = cmul(Pn[r * LDP + j], inv);
-        Pn[r * LDP + j] = l;
+        for (int w = 0; w < kWarps; ++w) {
+          const R v = cval[par * kWarps + w];
+          const int r = crow[par * kWarps + w];
+          if (r >= 0 && (v > pv || (v == pv && (p < 0 || r < p)))) { pv = v; p = r; pw = w; }
+        }
+        const CT* prow = cdat + (par * kWarps + pw) * NB;
+        if (p < 0) {   // no comparable candidate (non-finite column): no interchange, flagged singular
+          p = j;
+          prow = Pn + j * LDP;
+          singular = true;
+        }
+        if (tid == 0) piv[k0 + j] = k0 + p;
+        const CT d = prow[j];
+        const bool zero = cabs2(d) == R(0);
+        if (zero) singular = true;
+        const CT inv = zero ? czero(d) : cinv(d);
+        CT pr[NB];
 #pragma unroll
-        for (int c = 1; c < NB; ++c)
-          if (j + c < kb) Pn[r * LDP + j + c] = cfms(l, prow[c], Pn[r * LDP + j + c]);
+        for (int c = 1; c < NB; ++c) pr[c] = (j + c < kb) ? prow[j + c] : czero(d);
+        best = -1;
+        brow = -1;
+        // rows below the pivot that this thread owns (row p moves to the owner of row j)
+        for (int r = j + 1 + ((tid - j - 1) & (kThreads - 1)); r < nr; r += kThreads) {
+          if (r == p) continue;
+          const CT l = cmul(Pn[r * LDP + j], inv);
+          Pn[r * LDP + j] = l;
+#pragma unroll
+          for (int c = 1; c < NB; ++c)
+            if (j + c < kb) Pn[r * LDP + j + c] = cfms(l, pr[c], Pn[r * LDP + j + c]);
+          if (j + 1 < kb) {
+            const R v = cabs2(Pn[r * LDP + j + 1]);
+            if (v > best || (v == best && r < brow)) { best = v; brow = r; }
+          }
+        }
+        if (p != j && tid == (j & (kThreads - 1))) {
+          // the swap: the pivot row into row j, this thread's old row j (updated) into row p
+          CT o[NB];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) o[c] = c < kb ? Pn[j * LDP + c] : czero(d);
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c < kb) Pn[j * LDP + c] = prow[c];
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c == j) o[c] = cmul(o[c], inv);
+          CT lj = czero(d);
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c == j) lj = o[c];
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c > j && c < kb) o[c] = cfms(lj, prow[c], o[c]);
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c < kb) Pn[p * LDP + c] = o[c];
+          if (j + 1 < kb) {
+            R v = R(0);
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+              if (c == j + 1) v = cabs2(o[c]);
+            if (v > best || (v == best && p < brow)) { best = v; brow = p; }
+          }
+        }
+        if (j + 1 < kb) publish(best, brow, par ^ 1);
       }
       gsync();
     }
@@ -1264,6 +1377,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     // right-hand sides / corrections (W), the x cache of the residual
     unsigned char* vec = LARGE ? ws + sl.wx_off : smem;
     CT* W = reinterpret_cast<CT*>(vec);
+    auto solve = [&]() { lu_solve<CT>(A, lda, N, piv, W, P, Dg); };
     uint32_t* flag_of = &a.flags[a.factor_only ? t : b];
     if (N <= 0 || N > a.ncap) {
       // bad pixel states, or a support set larger than the shared memory this launch was sized
@@ -1357,7 +1471,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       W[e] = from_d2<CT>(make_double2(gap ? lport[p] : 0.0, 0.0));
     }
     gsync();
-    lu_solve<CT>(A, lda, N, piv, W, P, Dg);
+    solve();
     for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
     gsync();
     PMOM_PHASE(kPhSolve0, tev);
@@ -1422,7 +1536,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
         gsync();
         PMOM_PHASE(kPhOther, tev);
-        lu_solve<CT>(A, lda, N, piv, W, P, Dg);
+        solve();
         PMOM_PHASE(kPhSolveCorr, tev);
         double dmax = 0.0;   // ||correction||_inf
         for (int e = tid; e < N * P; e += kThreads) {
