@@ -369,6 +369,31 @@ def run_ours(args):
                     "speedup_over_full_solve": (world * Bsz / (b_ms * 1e-3)) / value,
                     "status_ok": int((sb == 0).sum().item()), "phases_ms": phases,
                     "accuracy": accuracy(Sb[:nfp], fb[:nfp])}
+    # ---- the gather step as a launch of its own (batched, bulk-staged rows): every candidate's
+    #      Z_sub at the middle frequency; algorithmic bytes = the Z_sub entries written (8 or 16 N^2)
+    #      plus the same entries read (from the L2-resident Z(f)) and the index lists (4 N)
+    gather = None
+    if Bsz * ncap * ncap * (16 if w.z_dtype == "c128" else 8) < 8e9:
+        fm = w.n_freq // 2
+        gbuf = ev.gather_batch(idx, n, fm, ncap)
+        g_runs = []
+        for rep in range(7):
+            e0.record(stream)
+            ev.gather_batch(idx, n, fm, ncap, out=gbuf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                g_runs.append(e0.elapsed_time(e1))
+        g_ms = float(np.median(g_runs))
+        esz = 16 if w.z_dtype == "c128" else 8
+        wbytes = float(np.sum(esz * N.astype(np.float64) ** 2))
+        hbm = float(_peaks().get("hbm_gbs") or 6800.0)
+        gather = {"kernel": "gather_batch_kernel", "candidates": Bsz, "ms": g_ms,
+                  "written_GB_per_s": wbytes / (g_ms * 1e-3) / 1e9,
+                  "algorithmic_GB_per_s": (2 * wbytes + float(np.sum(4.0 * N))) / (g_ms * 1e-3) / 1e9,
+                  "frac_of_hbm_written": wbytes / (g_ms * 1e-3) / 1e9 / hbm,
+                  "hbm_peak_GB_per_s": hbm}
+        del gbuf
     # ---- end to end through the host-buffer entry point (pinned host memory)
     maps_h = torch.from_numpy(maps_np).pin_memory()
     S_h = torch.empty((Bsz, w.n_freq, ev.P, ev.P), dtype=torch.complex128).pin_memory()
@@ -421,11 +446,12 @@ def run_ours(args):
                       "speedup_mixed_over_fp64": value / fp64_value},
         "accuracy": accuracy(S_mixed, fom_mixed),
         "bordered_update": bordered,
+        "gather": gather,
         "refinement": {"iters_total": st["refine_iters"], "iters_max": st["refine_max"],
                        "repaired_tasks": st["repaired_tasks"], "tasks": st["tasks"],
                        "bad_status": int((status_np != 0).sum())},
         "kernel_ms": {"eval": eval_ms},
-        "autotune": {"tensor_cores": bool(tc_choice)},
+        "autotune": {"tensor_cores": bool(tc_choice), "table": ev.autotune_table()},
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "candidate evals/s", "h2d_bytes_per_step": int(maps_np.nbytes),
@@ -444,6 +470,161 @@ def run_ours(args):
     ev.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def column_pool(cur: np.ndarray, rng, size: int) -> np.ndarray:
+    """Candidate pool of one search step on an on/off multilayer grid: every single-column change
+    (each (x, y) column takes each of its other 2^layers - 1 layer patterns), then random changes of
+    two distinct columns up to `size` maps (size 0: the single-column changes only)."""
+    L, ny, nx = cur.shape
+    K = 1 << L
+    cols = cur.reshape(L, -1)
+    code = sum(cols[l].astype(np.int64) << l for l in range(L))
+    out = []
+    for j in range(ny * nx):
+        for v in range(K):
+            if v != code[j]:
+                m = cols.copy()
+                for l in range(L):
+                    m[l, j] = (v >> l) & 1
+                out.append(m)
+    while len(out) < size:
+        j1, j2 = rng.choice(ny * nx, 2, replace=False)
+        m = cols.copy()
+        for j in (j1, j2):
+            v = int(rng.integers(1, K))
+            nv = int(code[j]) ^ v
+            for l in range(L):
+                m[l, j] = (nv >> l) & 1
+        out.append(m)
+    return np.ascontiguousarray(np.stack(out[:size] if size > 0 else out).reshape(-1, L, ny, nx).astype(np.uint8))
+
+
+def run_learned(args):
+    """The learned pre-ranker at the 3-layer 24x24 microstrip configuration (64 frequencies 3-9 GHz,
+    complex64 database from the library's GPU fill): training data from exact solves the method
+    makes anyway (a greedy walk whose steps evaluate a random 512 of the pool exactly), an MLP on
+    the 3 x 24 x 24 occupancy trained on the GPU (BF16 tensor-core kernels), then on held-out steps
+    the FoM regret of its top-k against exhaustive exact evaluation of every single-column change,
+    and best-neighbour walks that exact-evaluate the network's top-k of a 10k pool against walks
+    that evaluate a uniformly random k of it, at equal exact-evaluation budgets."""
+    import torch
+    from paper_2412_17617_gb300 import Evaluator, band_codes, build as B
+    from paper_2412_17617_gb300 import surrogate as SG
+    B.build()
+    w = PI.workload_learned()
+    ev = Evaluator(w.grid)
+    freqs = w.freqs()
+    t0 = time.perf_counter()
+    ev.fill_Z(freqs, w.z_dtype)
+    codes = band_codes(freqs, w.bands)
+    ev.set_fom(codes, w.z0_ohm)
+    bands = torch.from_numpy(np.ascontiguousarray(codes)).cuda()
+    fill_s = time.perf_counter() - t0
+    pool_size, per_step, steps_train = 10000, 512, args.learned_steps
+    rng = np.random.default_rng(5)
+
+    def exact(maps):
+        out_f, out_t, out_x = [], [], []
+        for i in range(0, maps.shape[0], 1024):
+            dm = torch.from_numpy(np.ascontiguousarray(maps[i:i + 1024])).cuda()
+            S, fom, st = ev.eval(dm, "mixed")
+            f = fom.cpu().numpy()
+            out_f.append(np.where(st.cpu().numpy() == 0, f, np.inf))
+            out_t.append(SG.targets(S))
+            out_x.append(dm.reshape(dm.shape[0], -1))
+        return np.concatenate(out_f), torch.cat(out_t), torch.cat(out_x)
+
+    # ---- training data: a greedy walk, each step a random 512 of the pool solved exactly
+    cur = PI.seed_map(w.grid, w.fill, 0)
+    xs, ts = [], []
+    t0 = time.perf_counter()
+    n_exact = 0
+    for _ in range(steps_train):
+        pool = column_pool(cur, rng, pool_size)
+        sel = pool[rng.choice(pool.shape[0], per_step, replace=False)]
+        f, t, x = exact(sel)
+        n_exact += sel.shape[0]
+        xs.append(x)
+        ts.append(t)
+        cur = sel[int(np.argmin(f))]
+    torch.cuda.synchronize()
+    exact_s = time.perf_counter() - t0
+    X, T = torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
+    net = SG.MLP([X.shape[1], 1024, 1024, 4 * w.n_freq], seed=7)
+    t0 = time.perf_counter()
+    hist = SG.train(net, X, T, epochs=args.learned_epochs, batch=256, lr=5e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def rank(pool):
+        x = torch.from_numpy(pool).cuda().reshape(pool.shape[0], -1)
+        return net.predict_fom(x, bands, w.n_freq).cpu().numpy()
+
+    # ---- held-out steps: exhaustive exact evaluation of every single-column change
+    regret, spearman = [], []
+    start = cur.copy()
+    for step in range(args.learned_heldout):
+        singles = column_pool(cur, rng, 0)
+        f, _, _ = exact(singles)
+        pred = rank(singles)
+        order = np.argsort(pred, kind="stable")
+        best = float(f.min())
+        row = {"children": int(singles.shape[0]), "best_exact_fom": best}
+        for k in (64, 256):
+            from math import comb
+            srt = np.sort(f)
+            n = len(srt)
+            pk = np.array([comb(n - i, k - 1) for i in range(1, n + 1)], dtype=float) / comb(n, k)
+            row[f"top{k}_regret"] = (float(f[order[:k]].min()) - best) / abs(best)
+            row[f"random{k}_expected_regret"] = (float(np.dot(pk, srt)) - best) / abs(best)
+        ra, rb = np.argsort(np.argsort(pred)), np.argsort(np.argsort(f))
+        spearman.append(float(np.corrcoef(ra, rb)[0, 1]))
+        regret.append(row)
+        cur = singles[int(np.argmin(f))]
+    # ---- network throughput on a 10k pool (the per-step ranking)
+    pool = column_pool(cur, rng, pool_size)
+    x = torch.from_numpy(pool).cuda().reshape(pool.shape[0], -1)
+    net.predict_fom(x, bands, w.n_freq)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        net.predict_fom(x, bands, w.n_freq)
+    torch.cuda.synchronize()
+    rank_ms = (time.perf_counter() - t0) / 5 * 1e3
+
+    # ---- walks at equal exact budgets: the network's top-k of a 10k pool vs a random k of it
+    def walk(seed, k, budget, use_net):
+        r = np.random.default_rng(100 + seed)
+        c = start.copy()
+        best, used = np.inf, 0
+        while used < budget:
+            pool = column_pool(c, r, pool_size)
+            if use_net:
+                sel = np.argsort(rank(pool), kind="stable")[:k]
+            else:
+                sel = r.choice(pool.shape[0], k, replace=False)
+            f, _, _ = exact(pool[sel])
+            used += k
+            j = int(np.argmin(f))
+            best = min(best, float(f[j]))
+            c = pool[sel[j]]
+        return best
+    walks = []
+    for seed in range(args.learned_walk_seeds):
+        walks.append({"seed": seed, "k": args.learned_k, "budget": args.learned_budget,
+                      "preranked_best_fom": walk(seed, args.learned_k, args.learned_budget, True),
+                      "random_k_best_fom": walk(seed, args.learned_k, args.learned_budget, False)})
+    line = {"metric": "learned pre-ranker (NEXT-2) at the 3-layer 24x24 microstrip configuration",
+            "config": {"workload": w.name, "M": ev.M, "freqs": w.n_freq, "pool_per_step": pool_size,
+                       "network": [int(X.shape[1]), 1024, 1024, 4 * w.n_freq], "training_solves": n_exact,
+                       "epochs": args.learned_epochs},
+            "fill_s": fill_s, "exact_solves_per_s": n_exact / exact_s, "train_s": train_s,
+            "loss_first_last": [hist[0], hist[-1]], "rank_10k_ms": rank_ms,
+            "heldout": {"spearman": spearman, "regret": regret}, "walks": walks}
+    print(json.dumps(line))
+    net.close()
+    ev.close()
 
 
 def run_peaks():
@@ -501,11 +682,22 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-bordered", dest="bordered", action="store_false",
                     help="skip the bordered-update measurement of the same batch")
+    ap.add_argument("--learned", action="store_true",
+                    help="the learned pre-ranker at the 24x24x3 microstrip configuration (training, held-out "
+                         "regret against exhaustive evaluation, walks against a random-k control)")
+    ap.add_argument("--learned-steps", type=int, default=12, help="training walk steps (512 exact solves each)")
+    ap.add_argument("--learned-epochs", type=int, default=60)
+    ap.add_argument("--learned-heldout", type=int, default=2)
+    ap.add_argument("--learned-k", type=int, default=64)
+    ap.add_argument("--learned-budget", type=int, default=1024)
+    ap.add_argument("--learned-walk-seeds", type=int, default=2)
     ap.add_argument("--peaks", action="store_true", help="measure TF32 / FP32 / FP64 / BF16 matmul and copy "
                                                            "throughput of this GPU and print them as JSON")
     args = ap.parse_args()
     if args.peaks:
         run_peaks()
+    elif args.learned:
+        run_learned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

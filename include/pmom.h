@@ -80,8 +80,10 @@ typedef struct {
   int32_t layers, nx, ny;
   double pitch_m;              /* pixel side a */
   int32_t medium;              /* 0: microstrip (ground at z = 0, homogeneous effective medium),
-                                  1: stripline (grounds at 0, h_total); 2 (a grounded slab under air,
-                                  Sommerfeld kernels) is refused with UNSUPPORTED */
+                                  1: stripline (grounds at 0, h_total), 2: layered microstrip (PEC
+                                  ground, a dielectric slab up to the highest layer, air above;
+                                  Sommerfeld kernels of horizontal currents: with n_states 3 it is
+                                  refused with UNSUPPORTED) */
   const double* layer_z_m;     /* [layers], host; heights of the metal layers */
   double h_total_m;            /* stripline plate spacing */
   double eps_r, tan_d;         /* homogenised substrate */
@@ -139,9 +141,13 @@ pmom_status pmom_load_Z(pmom_ctx* ctx, const double* freqs_hz_host, int32_t F, c
  * elements of the resident dtype.  mem says where `out` lives. */
 pmom_status pmom_copy_Z(const pmom_ctx* ctx, void* out, int32_t mem, void* stream);
 
-/* Fill the parent database on the GPU (MPIE with RWG basis, Eq. 1-2; homogeneous-medium Green's
- * function of the stack-up: one ground image for microstrip, the parallel-plate Dirichlet
- * function for stripline) at F frequencies and keep it resident as dtype.  Replaces a loaded Z. */
+/* Fill the parent database on the GPU (MPIE with RWG basis, Eq. 1-2) at F frequencies and keep
+ * it resident as dtype; replaces a loaded Z.  Green's functions of the stack-up: one ground image
+ * in a homogeneous effective medium (medium 0), the parallel-plate functions (medium 1), or the
+ * grounded slab's mixed-potential kernels (medium 2, the layered-media MPIE of Section II-D):
+ * G_A and G_phi as Sommerfeld integrals of the transmission-line voltages of the stack-up, each
+ * a quasi-static term plus a remainder tabulated per frequency and pair of layer heights on
+ * rho = i d/16 (d the slab thickness) and interpolated cubically. */
 pmom_status pmom_fill_Z(pmom_ctx* ctx, const double* freqs_hz_host, int32_t F, int32_t dtype, void* stream);
 
 /* Figure-of-merit bands (Eq. 8-9): band_of_freq host uint8 [F] with 0 = f_p1, 1 = f_p2,
@@ -157,6 +163,16 @@ pmom_status pmom_active_set(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, i
 /* Z_sub = S^T Z(f) S (Eq. 4-5) for one device index list of length N at frequency f, written to
  * out_dev as N*N complex elements of the resident dtype (row-major).  Bit-exact copy of entries. */
 pmom_status pmom_gather(pmom_ctx* ctx, const int32_t* idx_dev, int32_t N, int32_t f, void* out_dev, void* stream);
+
+/* Batched gather (Eq. 4-5) at frequency f: for each b < B with 0 < N_b = n_dev[b] <= ncap,
+ * out_dev[b][i][j] = Z(f)[I_b[i]][I_b[j]] for i, j < N_b (out_dev: B x ncap x ncap elements of the
+ * resident dtype, row-major; other entries untouched), idx_dev as written by pmom_active_set.
+ * Each CTA stages whole parent rows in shared memory by bulk asynchronous copies and compacts them
+ * with coalesced stores -- the gather step of the evaluation kernel as a launch of its own, for
+ * callers that factor elsewhere and for measuring it.  Bit-exact copy of entries.  Errors:
+ * INVALID_ARG, NOT_READY (no database). */
+pmom_status pmom_gather_batch(pmom_ctx* ctx, const int32_t* idx_dev, const int32_t* n_dev, int32_t B, int32_t f,
+                              int32_t ncap, void* out_dev, void* stream);
 
 /* Evaluate B candidates at every loaded frequency (Eq. 2-9).
  *   maps_dev   : device uint8 [B][layers][ny][nx]
@@ -181,11 +197,23 @@ pmom_status pmom_graph_capture(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B
                                void* stream);
 pmom_status pmom_graph_launch(pmom_ctx* ctx, void* stream);
 
-/* Autotuner: times the single-precision LU variants (tensor-core or CUDA-core trailing updates)
- * on this batch and keeps the faster for later calls; *choice_out = 1 if the tensor cores won.
- * Synchronous; FP64 has a single variant. */
+/* Autotuner (batching of Phase 3, Fig. 1, over the uneven support sets of Eq. 3): groups the
+ * batch's candidates by support-set size in buckets [0, 128), [128, 256), ..., [4096, 8192),
+ * >= 8192, and for each bucket present times, on a sample of its candidates (enough tasks for
+ * about four rounds of the resident task groups), every combination of the single-precision LU
+ * variant (tensor-core or CUDA-core updates), the task groups per CTA (2 or 1) and the
+ * resident-task cap (all slots or half); the fastest is kept per bucket for later calls.  Each
+ * task then takes its bucket's LU variant inside one launch, whose groups per CTA and slot cap
+ * are those of the batch's largest-support-set bucket.  *choice_out = the LU variant of that
+ * bucket (1: tensor cores).  Synchronous; FP64 has a single variant.  pmom_set_tensor_cores
+ * clears the table. */
 pmom_status pmom_autotune(pmom_ctx* ctx, const uint8_t* maps_dev, int32_t B, int32_t precision, int32_t* choice_out,
                           void* stream);
+
+/* The autotuner's table: out_host int32 [8][5] per bucket = {measured (0/1), tensor-core LU (0/1),
+ * task groups per CTA, slot cap in quarters of the full count, best time per candidate of the
+ * sample in microseconds}. */
+pmom_status pmom_autotune_table(const pmom_ctx* ctx, int32_t* out_host);
 
 /* Same computation with host buffers: the call copies the maps to the device, evaluates, copies
  * S (if S_out_host != NULL), FoM and status back and synchronizes `stream` before returning.

@@ -48,6 +48,13 @@ struct pmom_ctx {
   bool timing = false;
   bool timed = false;
   int use_tc = 1;    // tensor-core trailing updates in the single-precision LU
+  // autotuner table per support-set bucket (pmom::n_bucket): tensor-core LU, task groups per CTA,
+  // resident-task cap in quarters of the full slot count; valid = measured on a batch
+  uint8_t tune_valid[pmom::kNBuckets] = {};
+  uint8_t tune_tc[pmom::kNBuckets] = {};
+  uint8_t tune_groups[pmom::kNBuckets] = {};
+  uint8_t tune_cap[pmom::kNBuckets] = {};
+  float tune_ms[pmom::kNBuckets] = {};
   // captured evaluation pipeline (pmom_graph_capture / pmom_graph_launch)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -130,9 +137,33 @@ int ncap_for(pmom_ctx* c, int precision, int ncap) {
   return ncap < 1 ? 1 : ncap;
 }
 
-int slots_for(pmom_ctx* c, int precision, int tasks, int ncap) {
-  const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128, c->use_tc);
+// The launch configuration the autotuner chose for the batch's largest support set (the
+// dominant bucket: the largest tasks carry most of the work): the single-precision kernel
+// variant, task groups per CTA and the resident-task cap; per-task LU choice by bucket.
+struct LaunchTune {
+  int use_tc, max_groups, cap4;
+  uint8_t tc_bucket[pmom::kNBuckets];
+};
+LaunchTune tune_for(const pmom_ctx* c, int ncap) {
+  LaunchTune t{};
+  const int bd = pmom::n_bucket(ncap);
+  for (int b = 0; b < pmom::kNBuckets; ++b) t.tc_bucket[b] = static_cast<uint8_t>(c->tune_valid[b] ? c->tune_tc[b] : c->use_tc);
+  t.use_tc = t.tc_bucket[bd];
+  t.max_groups = c->tune_valid[bd] ? c->tune_groups[bd] : 0;
+  t.cap4 = c->tune_valid[bd] ? c->tune_cap[bd] : 4;
+  return t;
+}
+void apply_tune(const LaunchTune& t, pmom::EvalArgs& a) {
+  a.use_tc = t.use_tc;
+  a.max_groups = t.max_groups;
+  for (int b = 0; b < pmom::kNBuckets; ++b) a.tc_bucket[b] = t.tc_bucket[b];
+}
+
+int slots_for(pmom_ctx* c, int precision, int tasks, int ncap, const LaunchTune* t = nullptr) {
+  const int use_tc = t ? t->use_tc : c->use_tc;
+  const int per_sm = pmom::eval_blocks_per_sm(precision, ncap, c->dtype == PMOM_C128, use_tc, t ? t->max_groups : 0);
   int n = (per_sm > 0 ? per_sm : 1) * c->num_sms;
+  if (t && t->cap4 > 0 && t->cap4 < 4) n = (n * t->cap4 + 3) / 4;
   if (c->max_slots > 0 && n > c->max_slots) n = c->max_slots;
   if (n > tasks) n = tasks;
   return n < 1 ? 1 : n;
@@ -148,7 +179,14 @@ pmom_status ensure_work(pmom_ctx* c, int precision, int tasks, int ncap) {
       if (prec != precision && prec != PMOM_FP64) continue;
       int lda = 0;
       const size_t sb = pmom::eval_slot_bytes(prec, ncap_for(c, prec, ncap), c->grid.n_ports, &lda);
-      const size_t n = static_cast<size_t>(slots_for(c, prec, tasks, ncap_for(c, prec, ncap)));
+      size_t n = static_cast<size_t>(slots_for(c, prec, tasks, ncap_for(c, prec, ncap)));
+      if (prec != PMOM_FP64) {   // the tuned variant may be either LU kernel: room for the larger
+        LaunchTune t{};
+        t.use_tc = 1 - c->use_tc;
+        t.cap4 = 4;
+        const size_t n2 = static_cast<size_t>(slots_for(c, prec, tasks, ncap_for(c, prec, ncap), &t));
+        if (n2 > n) n = n2;
+      }
       if (sb * n > need) need = sb * n;
       if (sb > *sb_max) *sb_max = sb;
     }
@@ -226,7 +264,8 @@ pmom_status pmom_create(const pmom_grid_desc* g, pmom_ctx** out) {
   if (g->layers < 1 || g->layers > 8 || g->nx < 1 || g->ny < 1 || g->nx > 100 || g->ny > 100 || g->pitch_m <= 0 ||
       g->n_ports < 1 || g->n_ports > pmom::kMaxPorts || !g->ports || !g->layer_z_m || g->medium < 0 || g->medium > 2)
     return PMOM_ERR_INVALID_ARG;
-  if (g->medium == 2) return PMOM_ERR_UNSUPPORTED;   // layered (Sommerfeld) microstrip kernels: not in the GPU fill
+  // layered (grounded-slab) kernels are those of horizontal currents: no via state there
+  if (g->medium == 2 && g->n_states >= 3) return PMOM_ERR_UNSUPPORTED;
   if (g->n_states != 2 && g->n_states != 3) return PMOM_ERR_UNSUPPORTED;
   if (g->n_states == 3 && g->layers < 2) return PMOM_ERR_INVALID_ARG;   // a via needs a layer above
   if (g->diag_pattern < 0 || g->diag_pattern > 2) return PMOM_ERR_INVALID_ARG;
@@ -536,6 +575,16 @@ pmom_status pmom_gather(pmom_ctx* c, const int32_t* idx, int32_t N, int32_t f, v
   return PMOM_OK;
 }
 
+pmom_status pmom_gather_batch(pmom_ctx* c, const int32_t* idx, const int32_t* n, int32_t B, int32_t f, int32_t ncap,
+                              void* out, void* stream) {
+  if (!c || !idx || !n || !out || B < 1 || ncap < 1 || ncap > c->M) return fail(c, PMOM_ERR_INVALID_ARG, "gather_batch: bad argument");
+  if (!c->d_Z) return fail(c, PMOM_ERR_NOT_READY, "gather_batch: no database");
+  if (f < 0 || f >= c->F) return fail(c, PMOM_ERR_INVALID_ARG, "gather_batch: frequency index");
+  PMOM_CUDA(c, pmom::launch_gather_batch(c->d_Z, c->dtype == PMOM_C128, c->M, f, idx, n, B, ncap, out,
+                                         static_cast<cudaStream_t>(stream)));
+  return PMOM_OK;
+}
+
 namespace {
 
 // Enqueue the whole evaluation on stream s.  ncap > 0: the caller fixes the shared-memory capacity
@@ -575,6 +624,8 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
     PMOM_CUDA(c, cudaStreamSynchronize(s));
   }
   ncap = ncap < 1 ? 1 : (ncap > c->M ? c->M : ncap);
+  const LaunchTune tune = tune_for(c, ncap);
+  apply_tune(tune, a);
   a.ncap = ncap_for(c, precision, ncap);
   const int tasks = B * c->F;
   pmom_status st = ensure_work(c, precision, tasks, ncap);
@@ -583,7 +634,7 @@ pmom_status enqueue_eval(pmom_ctx* c, const uint8_t* maps, int B, int precision,
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
   a.slot_bytes = pmom::eval_slot_bytes(precision, a.ncap, P, &a.lda);
   a.ntasks_list = 0;
-  PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks, a.ncap), s));
+  PMOM_CUDA(c, pmom::launch_eval(a, precision, slots_for(c, precision, tasks, a.ncap, &tune), s));
   ++c->launches;
   if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[2], s));
   if (precision == PMOM_MIXED_REFINED) {
@@ -682,9 +733,11 @@ pmom_status pmom_eval_bordered(pmom_ctx* c, const uint8_t* ref_map, const uint8_
     fa.gap_stride = c->grid.stub_bfs(); fa.gap_off = c->grid.inner_bfs(); fa.gap_n = c->grid.subs();
     fa.Z0 = c->Z0; fa.flags = c->d_ref_flags; fa.task_counter = small;
     fa.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_small) + 64);
-    fa.work = c->d_ref_work; fa.slot_bytes = sb; fa.lda = lda; fa.ncap = n; fa.use_tc = c->use_tc;
+    fa.work = c->d_ref_work; fa.slot_bytes = sb; fa.lda = lda; fa.ncap = n;
     fa.factor_only = 1;
-    PMOM_CUDA(c, pmom::launch_eval(fa, PMOM_MIXED_REFINED, slots_for(c, PMOM_MIXED_REFINED, F, n), s));
+    const LaunchTune ft = tune_for(c, n);
+    apply_tune(ft, fa);
+    PMOM_CUDA(c, pmom::launch_eval(fa, PMOM_MIXED_REFINED, slots_for(c, PMOM_MIXED_REFINED, F, n, &ft), s));
     if (tm) PMOM_CUDA(c, cudaEventRecord(c->ev[1], s));
     // ... its inverse, refined to FP64 accuracy column block by column block ...
     PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));
@@ -800,30 +853,82 @@ pmom_status pmom_autotune(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t p
     return PMOM_OK;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the batch's support-set sizes
+  pmom::EvalArgs a{};
+  a.rules = c->d_rules; a.M = c->M; a.B = B; a.npix = c->grid.pixels(); a.n_states = c->grid.n_states;
+  a.via_top = c->grid.via_top(); a.maps = maps; a.idx = c->d_idx; a.n_act = c->d_nact; a.flags = c->d_flags;
+  PMOM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t) * B, s));
+  PMOM_CUDA(c, pmom::launch_activate(a, s));
+  std::vector<int32_t> n(B);
+  PMOM_CUDA(c, cudaMemcpyAsync(n.data(), c->d_nact, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+  PMOM_CUDA(c, cudaStreamSynchronize(s));
+  std::vector<int> members[pmom::kNBuckets];
+  int nmax = 0, bmax = 0;
+  for (int b = 0; b < B; ++b) {
+    if (n[b] <= 0) continue;
+    members[pmom::n_bucket(n[b])].push_back(b);
+    if (n[b] > nmax) { nmax = n[b]; bmax = pmom::n_bucket(n[b]); }
+  }
   cudaEvent_t e0, e1;
   PMOM_CUDA(c, cudaEventCreate(&e0));
   PMOM_CUDA(c, cudaEventCreate(&e1));
-  float best = 3.4e38f;
-  int best_tc = c->use_tc;
-  for (int tc = 1; tc >= 0; --tc) {
-    c->use_tc = tc;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and sizes workspaces
-      PMOM_CUDA(c, cudaEventRecord(e0, s));
-      st = enqueue_eval(c, maps, B, precision, nullptr, c->d_fom_stage, c->d_status_stage, s, 0);
-      if (st) break;
-      PMOM_CUDA(c, cudaEventRecord(e1, s));
-      PMOM_CUDA(c, cudaEventSynchronize(e1));
-      PMOM_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-    }
-    if (st) break;
-    if (ms < best) { best = ms; best_tc = tc; }
+  const size_t npix = static_cast<size_t>(c->grid.pixels());
+  for (int bk = 0; bk < pmom::kNBuckets && !st; ++bk) {
+    if (members[bk].empty()) continue;
+    // sample: enough tasks for about four rounds of the resident task groups, bounded in work so
+    // that each timed run stays near a second
+    int k = static_cast<int>(members[bk].size());
+    const int want = (8 * c->num_sms + c->F - 1) / c->F;
+    if (k > want) k = want;
+    int nk = 0;
+    for (int i = 0; i < k; ++i) nk = std::max(nk, n[members[bk][i]]);
+    while (k > 1 && static_cast<double>(k) * c->F * nk * nk * nk > 3e13) --k;
+    for (int i = 0; i < k; ++i)
+      PMOM_CUDA(c, cudaMemcpyAsync(c->d_maps_stage + i * npix, maps + members[bk][i] * npix, npix,
+                                   cudaMemcpyDeviceToDevice, s));
+    float best = 3.4e38f;
+    uint8_t bt = 1, bg = 2, bc = 4;
+    for (int tc = 1; tc >= 0 && !st; --tc)
+      for (int groups = 2; groups >= 1 && !st; --groups)
+        for (int cap = 4; cap >= 2 && !st; cap -= 2) {
+          c->tune_valid[bk] = 1;
+          c->tune_tc[bk] = static_cast<uint8_t>(tc);
+          c->tune_groups[bk] = static_cast<uint8_t>(groups);
+          c->tune_cap[bk] = static_cast<uint8_t>(cap);
+          float ms = 0.f;
+          for (int rep = 0; rep < 2 && !st; ++rep) {   // the first run warms caches and sizes workspaces
+            PMOM_CUDA(c, cudaEventRecord(e0, s));
+            st = enqueue_eval(c, c->d_maps_stage, k, precision, nullptr, c->d_fom_stage, c->d_status_stage, s, 0);
+            if (st) break;
+            PMOM_CUDA(c, cudaEventRecord(e1, s));
+            PMOM_CUDA(c, cudaEventSynchronize(e1));
+            PMOM_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+          }
+          if (!st && ms < best) { best = ms; bt = static_cast<uint8_t>(tc); bg = static_cast<uint8_t>(groups); bc = static_cast<uint8_t>(cap); }
+        }
+    c->tune_tc[bk] = bt;
+    c->tune_groups[bk] = bg;
+    c->tune_cap[bk] = bc;
+    c->tune_ms[bk] = best / static_cast<float>(k);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->use_tc = best_tc;
-  if (choice) *choice = best_tc;
+  if (!members[bmax].empty() && c->tune_valid[bmax]) c->use_tc = c->tune_tc[bmax];
+  if (choice) *choice = c->use_tc;
   return st;
+}
+
+pmom_status pmom_autotune_table(const pmom_ctx* c, int32_t* out) {
+  if (!c || !out) return PMOM_ERR_INVALID_ARG;
+  for (int b = 0; b < pmom::kNBuckets; ++b) {
+    int32_t* o = out + 5 * b;
+    o[0] = c->tune_valid[b];
+    o[1] = c->tune_valid[b] ? c->tune_tc[b] : c->use_tc;
+    o[2] = c->tune_groups[b];
+    o[3] = c->tune_cap[b];
+    o[4] = static_cast<int32_t>(c->tune_ms[b] * 1000.0f);
+  }
+  return PMOM_OK;
 }
 
 pmom_status pmom_eval_candidates_host(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t precision, double* S_out,
@@ -864,6 +969,7 @@ pmom_status pmom_stats(pmom_ctx* c, int64_t* out8) {
 pmom_status pmom_set_tensor_cores(pmom_ctx* c, int32_t on) {
   if (!c) return PMOM_ERR_INVALID_ARG;
   c->use_tc = on != 0;
+  for (int b = 0; b < pmom::kNBuckets; ++b) c->tune_valid[b] = 0;   // an explicit choice replaces the table
   return PMOM_OK;
 }
 
@@ -1028,14 +1134,15 @@ extern "C" pmom_status pmom_eval_candidates_noalloc(pmom_ctx* c, const uint8_t* 
   a.work = base + o_work;
   a.lda = lda;
   a.ncap = M;   // no host round trip here: shared memory sized for the whole parent
-  a.use_tc = c->use_tc;
+  const LaunchTune nt = tune_for(c, M);   // the autotuner's table, as pmom_eval_candidates
+  apply_tune(nt, a);
   // the array keeps the previous call's contents: zero what the kernels accumulate into
   PMOM_CUDA(c, cudaMemsetAsync(base + o_small, 0, 256, s));
   PMOM_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(uint32_t) * B, s));
   PMOM_CUDA(c, pmom::launch_activate(a, s));
   a.slot_bytes = slot_main;
   a.ntasks_list = 0;
-  int n = slots_for(c, precision, tasks, M);
+  int n = slots_for(c, precision, tasks, M, &nt);
   PMOM_CUDA(c, pmom::launch_eval(a, precision, n < fit ? n : fit, s));
   if (precision == PMOM_MIXED_REFINED) {
     PMOM_CUDA(c, cudaMemsetAsync(small, 0, sizeof(int), s));

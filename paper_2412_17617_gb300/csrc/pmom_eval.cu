@@ -55,16 +55,16 @@ cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream
                   : launch_eval_t<float2, float2, true, false, false>(a, nslots, s);
 }
 
-int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc) {
-  if (eval_is_large(precision, ncap, use_tc)) return eval_blocks_per_sm_large(precision, ncap, z_c128);
+int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc, int max_groups) {
+  if (eval_is_large(precision, ncap, use_tc)) return eval_blocks_per_sm_large(precision, ncap, z_c128, max_groups);
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false, false, false>(ncap)
-                  : blocks_per_sm_t<double2, float2, false, false, false>(ncap);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false, false, false>(ncap, max_groups)
+                  : blocks_per_sm_t<double2, float2, false, false, false>(ncap, max_groups);
   if (use_tc)
-    return z_c128 ? blocks_per_sm_t<float2, double2, true, true, false>(ncap)
-                  : blocks_per_sm_t<float2, float2, true, true, false>(ncap);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true, false, false>(ncap)
-                : blocks_per_sm_t<float2, float2, true, false, false>(ncap);
+    return z_c128 ? blocks_per_sm_t<float2, double2, true, true, false>(ncap, max_groups)
+                  : blocks_per_sm_t<float2, float2, true, true, false>(ncap, max_groups);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true, false, false>(ncap, max_groups)
+                : blocks_per_sm_t<float2, float2, true, false, false>(ncap, max_groups);
 }
 
 int eval_max_ncap(int precision, int M) {
@@ -121,6 +121,31 @@ cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t
     gather_kernel<double2><<<grid, 256, 0, s>>>(static_cast<const double2*>(Z), M, f, idx, N, static_cast<double2*>(out));
   else
     gather_kernel<float2><<<grid, 256, 0, s>>>(static_cast<const float2*>(Z), M, f, idx, N, static_cast<float2*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_batch(const void* Z, int z_c128, int M, int f, const int32_t* idx, const int32_t* n, int B,
+                                int ncap, void* out, cudaStream_t s) {
+  const size_t zel = z_c128 ? sizeof(double2) : sizeof(float2);
+  const size_t row_bytes = zel * M;
+  // rows per CTA: as many as fit about 100 KB of staging (two CTAs per SM), at most 8
+  int R = static_cast<int>((100u << 10) / row_bytes);
+  R = R < 1 ? 1 : (R > 8 ? 8 : R);
+  const int bulk = (row_bytes % 16 == 0) && row_bytes <= (100u << 10);
+  const size_t smem = (bulk ? R * row_bytes : 0) + sizeof(int) * static_cast<size_t>(ncap);
+  const dim3 grid(static_cast<unsigned>((ncap + R - 1) / R), static_cast<unsigned>(B));
+  cudaError_t e;
+  if (z_c128) {
+    e = cudaFuncSetAttribute(gather_batch_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    gather_batch_kernel<double2><<<grid, 256, smem, s>>>(static_cast<const double2*>(Z), M, f, idx, n, ncap, R, bulk,
+                                                          static_cast<double2*>(out));
+  } else {
+    e = cudaFuncSetAttribute(gather_batch_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    gather_batch_kernel<float2><<<grid, 256, smem, s>>>(static_cast<const float2*>(Z), M, f, idx, n, ncap, R, bulk,
+                                                         static_cast<float2*>(out));
+  }
   return cudaGetLastError();
 }
 

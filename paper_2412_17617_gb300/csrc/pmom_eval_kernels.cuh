@@ -40,8 +40,9 @@ __device__ __forceinline__ void gsync() {
 // In normal builds the marks expand to nothing.
 constexpr int kPhaseSlots = 16;
 enum Phase : int {
-  kPhGather = 0, kPhLu = 1, kPhSolve0 = 2, kPhResid = 3, kPhSolveCorr = 4, kPhOther = 5,
-  kPhColGemm = 8, kPhPanel = 9, kPhSwap = 10, kPhInnerU = 11, kPhInnerUpd = 12, kPhRowGemm = 13, kPhTrsm = 14,
+  kPhGather = 0, kPhLu = 1, kPhSolve0 = 2, kPhResid = 3, kPhSolveCorr = 4, kPhOther = 5, kPhPanelLoad = 6,
+  kPhPanelFactor = 7, kPhColGemm = 8, kPhPanel = 9, kPhSwap = 10, kPhInnerU = 11, kPhInnerUpd = 12, kPhRowGemm = 13,
+  kPhTrsm = 14,
   kPhTasks = 15
 };
 #ifdef PMOM_PHASES
@@ -264,6 +265,10 @@ constexpr int kRaw = 3;
 constexpr int kStages = 3;
 constexpr int kGatherBufs = 8;   // parent rows in flight in the bulk gather
 constexpr int kChunk = 8;
+// K chunks per accumulation segment: the tensor cores' fp32 accumulation over a long K loses more
+// than round-to-nearest fp32 additions would, so each segment of 128 complex terms (768 products
+// per output with the three TF32 terms) is added to C on its own in the epilogue.
+constexpr int kSegChunks = 16;
 constexpr uint32_t kRawXBytes = 10240;    // 128 rows x 80 B (column update) / 8 x 1024 B (row update)
 constexpr uint32_t kRawBytes = 16384;     // + Y: 8 x 576 B (column update) / 64 x 96 B (row update)
 constexpr uint32_t kStageBytes = 16384;   // B hi | B lo of one MMA stage
@@ -309,8 +314,8 @@ __device__ __forceinline__ void put_split16(unsigned char* hi, unsigned char* lo
 // barrier; one thread issues chunk c - 1's six MMAs (converted in the previous iteration) and
 // commits them to its stage's mbarrier; the copies of chunk c + kRaw - 1 are issued into the raw
 // stage chunk c - 1 used; chunk c is converted into MMA stage c % kStages once chunk
-// c - kStages's MMAs have completed.  The epilogue reads the accumulator row by row from TMEM and
-// adds it to C in global memory.  Rows and columns outside the tile are never copied: their stale
+// c - kStages's MMAs have completed.  K runs in segments of kSegChunks chunks; after each the
+// epilogue reads the accumulator row by row from TMEM and adds it to C in global memory.  Rows and columns outside the tile are never copied: their stale
 // staging entries reach only accumulator rows and columns that are not stored.
 template <bool ROWG>
 __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c_out, int m, int nc, int K,
@@ -332,13 +337,15 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
   }
   unsigned char* raw0 = st.stage;
   unsigned char* bst0 = st.stage + kRaw * kRawBytes;
-  for (int t0 = 0; t0 < m; t0 += 128) {
+  for (int t0 = 0; t0 < m; t0 += 128)
+  for (int ks0 = 0; ks0 < nk; ks0 += kSegChunks) {   // K in segments, each added to C in fp32
     const int mt = min(128, m - t0);
+    const int nks = min(kSegChunks, nk - ks0);
     // this thread's 16-byte pieces of chunk c: two of X, one of Y
     auto issue = [&](int c) {
       unsigned char* rx = raw0 + (c % kRaw) * kRawBytes;
       unsigned char* ry = rx + kRawXBytes;
-      const int kb = c * kChunk;
+      const int kb = (ks0 + c) * kChunk;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = tid + u * kThreads;
@@ -360,11 +367,11 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
     };
 #pragma unroll
     for (int p = 0; p < kRaw - 1; ++p) {
-      if (p < nk) issue(p);
+      if (p < nks) issue(p);
       tc::cp_async_commit();   // one group per chunk slot, empty past the end, so the counts line up
     }
-    for (int c = 0; c <= nk; ++c) {
-      if (c < nk) {
+    for (int c = 0; c <= nks; ++c) {
+      if (c < nks) {
         tc::cp_async_wait<kRaw - 2>();                 // this thread's pieces of chunk c have landed
         if (c >= kStages) stage_wait(st, c % kStages);  // chunk c - kStages's MMAs have read stage c % kStages
       }
@@ -390,8 +397,8 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
         }
         tc::commit(&st.mbar[s1]);
       }
-      if (c == nk) break;
-      if (c + kRaw - 1 < nk) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
+      if (c == nks) break;
+      if (c + kRaw - 1 < nks) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
       tc::cp_async_commit();
       // convert chunk c: X -> TMEM (negated, split; real parts at K columns 4 xh + u, imaginary at
       // 8 + 4 xh + u), Y -> canonical B tile
@@ -435,7 +442,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
     }
     tc::cp_async_wait<0>();
     // every outstanding chunk completes (commits complete in order: the last one first)
-    for (int c = nk - 1; c >= 0 && c >= nk - kStages; --c) stage_wait(st, c % kStages);
+    for (int c = nks - 1; c >= 0 && c >= nks - kStages; --c) stage_wait(st, c % kStages);
     // epilogue: this thread's accumulator row (TMEM lane xi), complex columns 32 xh .. 32 xh + 31,
     // in two halves of 16, added to C with independent loads in flight
     const bool xv = xi < mt;
@@ -548,6 +555,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
     }
     gsync();
+    PMOM_PHASE(kPhPanelLoad, tph);
     // 2. factor the panel (partial pivoting on |a|^2, ties to the lowest row), one barrier per
     //    column: each warp publishes its best candidate row for the next column (value, index and
     //    the whole row) in a double-buffered slot; after the barrier every thread picks the pivot
@@ -654,6 +662,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
       }
       gsync();
     }
+    PMOM_PHASE(kPhPanelFactor, tph);
     // 3. panel back to global memory
     for (int e = tid; e < nr * NB; e += kThreads) {
       const int r = e / NB, c = e % NB;
@@ -1455,7 +1464,9 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     }
     gsync();
     PMOM_PHASE(kPhGather, tev);
-    const bool singular = lu_factor<CT, NB>(A, lda, N, piv, Pn, Ut, s_val, s_row, use_tc ? &tcs : nullptr);
+    // the autotuner's choice for this support-set size (the large layout always takes the tensor cores)
+    const bool task_tc = use_tc && (LARGE || a.tc_bucket[n_bucket(N)] != 0);
+    const bool singular = lu_factor<CT, NB>(A, lda, N, piv, Pn, Ut, s_val, s_row, task_tc ? &tcs : nullptr);
     PMOM_PHASE(kPhLu, tev);
     if (a.factor_only) {   // factors stay in slot t; a zero pivot or a failed tensor-core wait is flagged
       if (tid == 0 && (singular || tcs.failed || s_gfail)) atomicOr(flag_of, kFlagSingular);
@@ -1690,6 +1701,61 @@ __global__ void gather_kernel(const ZT* __restrict__ Z, int M, int f, const int3
   }
 }
 
+// Batched gather: CTA (y = candidate b, x = block of R rows) copies its parent rows I_b[i] of
+// Z(f) into shared memory by bulk asynchronous copies (all R in flight, one mbarrier each), then
+// compacts each to the columns I_b with coalesced stores into out[b][i][0..N_b).  bulk = 0 (rows
+// that are not a multiple of 16 bytes): element loads instead.
+template <typename ZT>
+__global__ void __launch_bounds__(256) gather_batch_kernel(const ZT* __restrict__ Z, int M, int f,
+                                                           const int32_t* __restrict__ idx, const int32_t* __restrict__ n,
+                                                           int ncap, int R, int bulk, ZT* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  __shared__ __align__(8) uint64_t bar[8];
+  __shared__ int s_fail;
+  const int b = blockIdx.y, N = n[b], r0 = blockIdx.x * R;
+  if (N <= 0 || N > ncap || r0 >= N) return;
+  const int rows = min(R, N - r0);
+  const ZT* Zf = Z + static_cast<size_t>(f) * M * M;
+  const int32_t* I = idx + static_cast<size_t>(b) * M;
+  ZT* buf = reinterpret_cast<ZT*>(gsm);
+  int* s_idx = reinterpret_cast<int*>(gsm + static_cast<size_t>(R) * M * sizeof(ZT));
+  const uint32_t row_bytes = static_cast<uint32_t>(M) * sizeof(ZT);
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int r = 0; r < rows; ++r) tc::mbar_init(&bar[r], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) s_idx[j] = I[j];
+  __syncthreads();
+  if (bulk && threadIdx.x == 0) {
+    for (int r = 0; r < rows; ++r) {
+      tc::mbar_arrive_expect_tx(&bar[r], row_bytes);
+      tc::bulk_g2s(buf + static_cast<size_t>(r) * M, Zf + static_cast<size_t>(s_idx[r0 + r]) * M, row_bytes, &bar[r]);
+    }
+  }
+  ZT* o = out + static_cast<size_t>(b) * ncap * ncap;
+  for (int r = 0; r < rows; ++r) {
+    const int i = r0 + r;
+    if (bulk) {
+      if (!tc::mbar_wait(&bar[r], 0, 1ll << 18)) s_fail = 1;
+      const ZT* row = buf + static_cast<size_t>(r) * M;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) o[static_cast<size_t>(i) * ncap + j] = row[s_idx[j]];
+    } else {
+      const ZT* row = Zf + static_cast<size_t>(s_idx[i]) * M;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) o[static_cast<size_t>(i) * ncap + j] = row[s_idx[j]];
+    }
+  }
+  __syncthreads();
+  // a copy that never completed leaves its row unreliable: poison the block's rows (NaN)
+  if (s_fail) {
+    ZT nan;
+    nan.x = __int_as_float(0x7fc00000);
+    nan.y = nan.x;
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x)
+      o[static_cast<size_t>(r0 + e / N) * ncap + e % N] = nan;
+  }
+}
+
 int optin_smem() {
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -1715,7 +1781,8 @@ int groups_for(int ncap, bool tc, bool large) {
 template <typename CT, typename ZT, bool MIXED, bool TC, bool LARGE>
 cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
   if (a.ncap < 1 || a.ncap > a.M || a.lda < a.ncap || nslots < 1) return cudaErrorInvalidValue;
-  const int groups = groups_for<CT>(a.ncap, TC, LARGE);
+  const int gmax = groups_for<CT>(a.ncap, TC, LARGE);
+  const int groups = a.max_groups > 0 && a.max_groups < gmax ? a.max_groups : gmax;
   const size_t smem = groups * group_smem_bytes<CT>(a.ncap, TC, LARGE);
   auto k = eval_kernel<CT, ZT, MIXED, TC, LARGE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -1728,8 +1795,9 @@ cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
 
 // Resident task groups per SM (CTAs per SM x groups per CTA).
 template <typename CT, typename ZT, bool MIXED, bool TC, bool LARGE>
-int blocks_per_sm_t(int M) {
-  const int groups = groups_for<CT>(M, TC, LARGE);
+int blocks_per_sm_t(int M, int max_groups = 0) {
+  const int gmax = groups_for<CT>(M, TC, LARGE);
+  const int groups = max_groups > 0 && max_groups < gmax ? max_groups : gmax;
   const size_t smem = groups * group_smem_bytes<CT>(M, TC, LARGE);
   auto k = eval_kernel<CT, ZT, MIXED, TC, LARGE>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)

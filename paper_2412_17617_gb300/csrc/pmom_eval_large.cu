@@ -15,12 +15,12 @@ cudaError_t launch_eval_large(const EvalArgs& a, int precision, int nslots, cuda
                   : launch_eval_t<float2, float2, true, true, true>(a, nslots, s);
 }
 
-int eval_blocks_per_sm_large(int precision, int ncap, int z_c128) {
+int eval_blocks_per_sm_large(int precision, int ncap, int z_c128, int max_groups) {
   if (precision == PMOM_FP64)
-    return z_c128 ? blocks_per_sm_t<double2, double2, false, false, true>(ncap)
-                  : blocks_per_sm_t<double2, float2, false, false, true>(ncap);
-  return z_c128 ? blocks_per_sm_t<float2, double2, true, true, true>(ncap)
-                : blocks_per_sm_t<float2, float2, true, true, true>(ncap);
+    return z_c128 ? blocks_per_sm_t<double2, double2, false, false, true>(ncap, max_groups)
+                  : blocks_per_sm_t<double2, float2, false, false, true>(ncap, max_groups);
+  return z_c128 ? blocks_per_sm_t<float2, double2, true, true, true>(ncap, max_groups)
+                : blocks_per_sm_t<float2, float2, true, true, true>(ncap, max_groups);
 }
 
 }  // namespace pmom

@@ -14,6 +14,18 @@
 //               sum at rho = H/2, 3H/4, H (the remaining images are smooth and even in rho), one
 //               quadratic per kernel and pair of heights: the metal layers and the heights of the
 //               quadrature points on vertical via triangles.
+//   grounded slab (medium 2: PEC ground at z = 0, dielectric eps_r (1 - j tan d) up to the highest
+//               metal layer d, air above): the mixed-potential kernels of the layered medium for
+//               horizontal currents, G_A = S0{V_TE / (jw mu0)} and G_phi = S0{(jw eps0 / k_rho^2)
+//               (V_TM - V_TE)} (V the voltages of the TE and TM transmission lines of the stack-up,
+//               S0 the Sommerfeld transform), each the quasi-static term C e^{-jk1 R}/(4 pi R) plus a
+//               remainder tabulated on rho = i h, h = d/16, per frequency and pair of heights (cubic
+//               interpolation); the scalar term is eps0-normalised and the analytic singular
+//               integrals carry each kernel's C (1 for G_A; 1/eps_r in the slab, 2/(eps_r + 1) on
+//               its surface for G_phi).  The remainder integral runs along a half-ellipse in the
+//               first quadrant past the branch points and surface-wave poles, then over graded
+//               panels of the real axis and, for rho > 0, over partitions between the zeros of J0
+//               summed with Wynn's epsilon algorithm; one thread per table entry.
 // Triangle pairs related by a lattice translation (same layers, orientations, halves and
 // offset) share one integration: one thread integrates one such class at one frequency
 // (7-point rule x 7-point rule when the centroids are at least two longest edges apart; else
@@ -48,11 +60,26 @@ struct FillTri {
 
 struct Medium {
   double omega, H, rho_s;
-  double2 k;       // complex wavenumber
-  double2 eps;     // complex permittivity
+  double2 k;       // complex wavenumber (the slab's for the layered medium)
+  double2 eps;     // complex permittivity (eps0 for the layered medium: the kernels carry the slab)
   int stripline;
+  int layered;     // grounded slab: tabulated Sommerfeld kernels
   int nz;          // distinct heights (metal layers first, id = layer)
+  int ntab;        // layered: table points on rho = i htab
+  double htab;
 };
+
+// Grounded slab of one frequency (layered medium): slab thickness d, wavenumbers and relative
+// permittivities of the slab (1) and the half-space above (t), and the half-ellipse of the
+// Sommerfeld path (0 to 2 ka, height kb).
+struct Slab {
+  double omega, d;
+  double2 k0t, k1, er1, ert;
+  double ka, kb;
+};
+constexpr int kGlE = 96;   // Gauss-Legendre points per quarter of the half-ellipse
+constexpr int kGlP = 24;   // per real-axis panel
+__constant__ double kGlE_x[kGlE], kGlE_w[kGlE], kGlP_x[kGlP], kGlP_w[kGlP];
 
 // ------------------------------------------------------------------ complex double helpers
 __device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -175,6 +202,219 @@ __device__ double2 strip_modes(const Medium& md, int kind, double zp, double zq,
     s = ca(s, cscale(bessel_k0(cscale(gam, rho)), w));
   }
   return cscale(s, 1.0 / (kPi * md.H));
+}
+
+// ------------------------------------------------------------------ grounded slab kernels
+__device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 jmul(double2 a) { return make_double2(-a.y, a.x); }   // j a
+
+// k_z = sqrt(k^2 - k_rho^2) on the branch with Im k_z <= 0 (fields e^{-j k_z |z|} decay)
+__device__ double2 kz_branch(double2 k, double2 kr) {
+  const double2 v = csqrt_(cs(cm(k, k), cm(kr, kr)));
+  return v.y > 0.0 ? make_double2(-v.x, -v.y) : v;
+}
+
+// Voltage at height z of the TE (te) or TM line for a unit shunt current at zp (0 < z, zp <= d):
+// the line is shorted at the ground and loaded by the half-space admittance above d; written with
+// q = j k_z1 (Re q >= 0) and decaying exponentials only.
+__device__ double2 slab_voltage(const Slab& s, bool te, double2 kr, double z, double zp) {
+  constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+  const double2 kz1 = kz_branch(s.k1, kr), kz0 = kz_branch(s.k0t, kr);
+  double2 Y1, Y0;
+  if (te) {
+    Y1 = cscale(kz1, 1.0 / (s.omega * kMu0));
+    Y0 = cscale(kz0, 1.0 / (s.omega * kMu0));
+  } else {
+    Y1 = cdiv(cscale(s.er1, s.omega * kEps0), kz1);
+    Y0 = cdiv(cscale(s.ert, s.omega * kEps0), kz0);
+  }
+  const double2 q = jmul(kz1);
+  const double l = s.d - zp;
+  const double2 one = make_double2(1.0, 0.0);
+  const double2 ez = cexp_(cscale(q, -2.0 * zp)), el = cexp_(cscale(q, -2.0 * l));
+  const double2 coth_down = cdiv(ca(one, ez), cs(one, ez));          // shorted line below zp
+  const double2 th_up = cdiv(cs(one, el), ca(one, el));              // tanh(q l) above zp
+  const double2 y_up = cdiv(cm(Y1, ca(Y0, cm(Y1, th_up))), ca(Y1, cm(Y0, th_up)));
+  const double2 Vs = cdiv(one, ca(cm(Y1, coth_down), y_up));
+  if (z <= zp) {
+    // Vs sinh(q z) / sinh(q zp)
+    return cdiv(cm(cm(Vs, cexp_(cscale(q, z - zp))), cs(one, cexp_(cscale(q, -2.0 * z)))), cs(one, ez));
+  }
+  const double a = s.d - z;
+  const double2 r = cdiv(Y0, Y1), ea = cexp_(cscale(q, -2.0 * a));
+  const double2 num = ca(ca(one, ea), cm(r, cs(one, ea)));
+  const double2 den = ca(ca(one, el), cm(r, cs(one, el)));
+  return cdiv(cm(cm(Vs, cexp_(cscale(q, a - l))), num), den);
+}
+
+// quasi-static constant of kernel `kind` (0: G_phi, 1: G_A)
+__device__ __host__ inline double slab_c(double d, double er1_re, double ert_re, int kind, double z, double zp) {
+  if (kind == 1) return 1.0;
+  if (z >= d || zp >= d) return 2.0 / (er1_re + ert_re);
+  return 1.0 / er1_re;
+}
+
+// spectral kernel minus its quasi-static part C e^{-j k_z1 |z - zp|} / (2 j k_z1)
+__device__ double2 slab_spectral_rem(const Slab& s, int kind, double c, double2 kr, double z, double zp) {
+  constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+  const double2 vte = slab_voltage(s, true, kr, z, zp);
+  double2 g;
+  if (kind == 1) {
+    g = cdiv(vte, make_double2(0.0, s.omega * kMu0));
+  } else {
+    const double2 vtm = slab_voltage(s, false, kr, z, zp);
+    g = cdiv(cm(make_double2(0.0, s.omega * kEps0), cs(vtm, vte)), cm(kr, kr));
+  }
+  const double2 kz1 = kz_branch(s.k1, kr);
+  const double2 e = cexp_(cscale(jmul(kz1), -fabs(z - zp)));
+  return cs(g, cdiv(cscale(e, c), cscale(jmul(kz1), 2.0)));
+}
+
+// J0 of a complex argument, ascending series (the arguments on the half-ellipse stay moderate)
+__device__ double2 j0_complex(double2 w) {
+  const double2 q = cscale(cm(w, w), -0.25);
+  double2 t = make_double2(1.0, 0.0), sum = t;
+  const double aw = cabs_(w);
+  for (int m = 1; m < 200; ++m) {
+    t = cscale(cm(t, q), 1.0 / (static_cast<double>(m) * m));
+    sum = ca(sum, t);
+    if (cabs_(t) < 1e-18 * (1.0 + cabs_(sum)) && m > aw) break;
+  }
+  return sum;
+}
+
+// Wynn's epsilon table over partial sums S[0..n-1] (n <= 40): the last entry of the last even
+// column is the estimate of the limit
+__device__ double2 wynn_limit(const double2* S, int n) {
+  double2 em1[40], e0[40], e1[40];
+  for (int i = 0; i < n; ++i) { em1[i] = make_double2(0.0, 0.0); e0[i] = S[i]; }
+  double2 best = S[n - 1];
+  int len = n;
+  for (int k = 1; len > 1; ++k) {
+    for (int i = 0; i + 1 < len; ++i) {
+      const double2 dd = cs(e0[i + 1], e0[i]);
+      if (dd.x == 0.0 && dd.y == 0.0) return best;
+      e1[i] = ca(em1[i + 1], cdiv(make_double2(1.0, 0.0), dd));
+    }
+    --len;
+    if (k % 2 == 0) best = e1[len - 1];
+    for (int i = 0; i <= len; ++i) em1[i] = e0[i];
+    for (int i = 0; i < len; ++i) e0[i] = e1[i];
+  }
+  return best;
+}
+
+// (1 / 2 pi) int_0^inf R(k_rho) J0(k_rho rho) k_rho dk_rho of the remainder R of kernel `kind`
+__device__ double2 slab_remainder(const Slab& s, int kind, double z, double zp, double rho) {
+  const double c = slab_c(s.d, s.er1.x, s.ert.x, kind, z, zp);
+  double2 sum = make_double2(0.0, 0.0);
+  for (int piece = 0; piece < 4; ++piece) {   // half-ellipse k(t) = ka (1 - cos t) + j kb sin t
+    const double t0 = kPi * piece / 4.0, t1 = kPi * (piece + 1) / 4.0;
+    for (int i = 0; i < kGlE; ++i) {
+      const double t = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * kGlE_x[i];
+      double st, ct;
+      sincos(t, &st, &ct);
+      const double2 kr = make_double2(s.ka * (1.0 - ct), s.kb * st);
+      const double2 dk = cscale(make_double2(s.ka * st, s.kb * ct), 0.5 * (t1 - t0) * kGlE_w[i]);
+      const double2 f = cm(cm(slab_spectral_rem(s, kind, c, kr, z, zp), j0_complex(cscale(kr, rho))), cm(kr, dk));
+      sum = ca(sum, f);
+    }
+  }
+  const double k_start = 2.0 * s.ka;
+  const double dz = fabs(z - zp), scale = (dz > 0.0 && dz < s.d) ? dz : s.d;
+  double k_switch = 40.0 / scale;
+  if (k_switch < 2.0 * k_start) k_switch = 2.0 * k_start;
+  const double period = rho > 0.0 ? kPi / rho : 1e300;
+  double w = 0.25 * k_start;
+  for (double a = k_start; a < k_switch;) {   // graded real-axis panels
+    double b = a + (w < period ? w : period);
+    if (b > k_switch) b = k_switch;
+    for (int i = 0; i < kGlP; ++i) {
+      const double kr = 0.5 * (a + b) + 0.5 * (b - a) * kGlP_x[i];
+      const double wt = j0(kr * rho) * kr * 0.5 * (b - a) * kGlP_w[i];
+      sum = ca(sum, cscale(slab_spectral_rem(s, kind, c, make_double2(kr, 0.0), z, zp), wt));
+    }
+    a = b;
+    w *= 1.5;
+  }
+  if (rho <= 0.0) {   // tail k = k_switch / u, u in (0, 1]
+    for (int piece = 0; piece < 8; ++piece) {
+      const double u0 = piece / 8.0, u1 = (piece + 1) / 8.0;
+      for (int i = 0; i < kGlP; ++i) {
+        const double u = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * kGlP_x[i];
+        const double kr = k_switch / u;
+        const double wt = kr * (k_switch / (u * u)) * 0.5 * (u1 - u0) * kGlP_w[i];
+        sum = ca(sum, cscale(slab_spectral_rem(s, kind, c, make_double2(kr, 0.0), z, zp), wt));
+      }
+    }
+  } else {            // tail: partitions between the large-argument zeros of J0, Wynn-accelerated
+    double2 S[40];
+    int ns = 0;
+    double2 acc = make_double2(0.0, 0.0);
+    const int n0 = static_cast<int>(ceil((k_switch * rho + 0.25 * kPi) / kPi));
+    double a = k_switch;
+    for (int n = 0; n < 64; ++n) {
+      double b = ((n0 + n) * kPi + 0.25 * kPi) / rho;
+      if (b <= a) b = a + kPi / rho;
+      double2 part = make_double2(0.0, 0.0);
+      for (int i = 0; i < kGlP; ++i) {
+        const double kr = 0.5 * (a + b) + 0.5 * (b - a) * kGlP_x[i];
+        const double wt = j0(kr * rho) * kr * 0.5 * (b - a) * kGlP_w[i];
+        part = ca(part, cscale(slab_spectral_rem(s, kind, c, make_double2(kr, 0.0), z, zp), wt));
+      }
+      acc = ca(acc, part);
+      if (n < 40) S[ns++] = acc;
+      a = b;
+      if (n >= 12 && cabs_(part) < 1e-17 * cabs_(acc)) break;
+    }
+    sum = ca(sum, wynn_limit(S, ns));
+  }
+  return cscale(sum, 1.0 / (2.0 * kPi));
+}
+
+// One thread per table entry: remainder of kernel `kind` between heights z[p] <= z[q] (p <= q,
+// mirrored to (q, p) by reciprocity) at rho = i htab, for every frequency.
+// tab layout: [F][2][nz][nz][ntab].
+__global__ void slab_table_kernel(const Slab* __restrict__ slabs, const double* __restrict__ z, int nz, int ntab,
+                                  double htab, int F, double2* __restrict__ tab) {
+  const int npair = nz * (nz + 1) / 2;
+  const long gid = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long total = static_cast<long>(F) * 2 * npair * ntab;
+  if (gid >= total) return;
+  const int i = static_cast<int>(gid % ntab);
+  long r = gid / ntab;
+  int pr = static_cast<int>(r % npair);
+  r /= npair;
+  const int kind = static_cast<int>(r % 2), f = static_cast<int>(r / 2);
+  int p = 0;
+  while (pr >= nz - p) { pr -= nz - p; ++p; }
+  const int q = p + pr;
+  const double2 v = slab_remainder(slabs[f], kind, z[p], z[q], htab * i);
+  const size_t base = (static_cast<size_t>(f) * 2 + kind) * nz * nz;
+  tab[(base + static_cast<size_t>(p) * nz + q) * ntab + i] = v;
+  if (q != p) tab[(base + static_cast<size_t>(q) * nz + p) * ntab + i] = v;
+}
+
+// cubic Lagrange interpolation of a table on rho = i h
+__device__ double2 table_cubic(const double2* t, int n, double h, double rho) {
+  const double x = rho / h;
+  int j0 = static_cast<int>(floor(x)) - 1;
+  if (j0 < 0) j0 = 0;
+  if (j0 > n - 4) j0 = n - 4;
+  const double u = x - j0;
+  const double l0 = -(u - 1) * (u - 2) * (u - 3) / 6.0, l1 = u * (u - 2) * (u - 3) / 2.0;
+  const double l2 = -u * (u - 1) * (u - 3) / 2.0, l3 = u * (u - 1) * (u - 2) / 6.0;
+  return ca(ca(cscale(t[j0], l0), cscale(t[j0 + 1], l1)), ca(cscale(t[j0 + 2], l2), cscale(t[j0 + 3], l3)));
+}
+
+// layered kernel tk (0: G_phi, 1: G_A) between heights z[ip], z[iq]: C e^{-jk1 R}/(4 pi R) (its
+// regular part when smooth) plus the tabulated remainder
+__device__ double2 green_slab(const Medium& md, const double* z, const double2* tab, const double* ctab, int tk,
+                              int ip, int iq, double rho, bool smooth) {
+  const double c = ctab[(tk * md.nz + ip) * md.nz + iq];
+  const double dz = z[ip] - z[iq], R = sqrt(rho * rho + dz * dz);
+  const double2 direct = cscale(smooth ? g_free_smooth(md.k, R) : g_free(md.k, R), c);
+  return ca(direct, table_cubic(tab + (static_cast<size_t>(tk * md.nz + ip) * md.nz + iq) * md.ntab, md.ntab, md.htab, rho));
 }
 
 // image sum |n| <= kImages (second family subtracted for G_D, added for G_N); `smooth` replaces
@@ -314,14 +554,20 @@ __global__ void fit_kernel(const Medium* __restrict__ media, const double* __res
 // One thread: integrals of one translation class at one frequency.
 // out[0] = int int G_D, out[1 + 3a + b] = int int (r - v_a) . G_A (r' - v_b) with G_A = G_D on the
 // horizontal and G_N on the vertical components.
+// Layered medium: G_phi for the scalar part, G_A for the horizontal vector part, and the analytic
+// singular integrals weighted by their quasi-static constants (tabs, ctabs: per frequency
+// [2][nz][nz][ntab] remainders and [2][nz][nz] constants).
 __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ tris, const int2* __restrict__ rep, int U,
                                                      const Medium* __restrict__ media, const double* __restrict__ z,
-                                                     const double2* __restrict__ fits, int F, double2* __restrict__ out) {
+                                                     const double2* __restrict__ fits, int F, double2* __restrict__ out,
+                                                     const double2* __restrict__ tabs, const double* __restrict__ ctabs) {
   const long gid = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= static_cast<long>(U) * F) return;
   const int f = static_cast<int>(gid / U), u = static_cast<int>(gid % U);
   const Medium md = media[f];
   const double2* fit = fits + static_cast<size_t>(f) * 2 * md.nz * md.nz * 3;
+  const double2* tab = md.layered ? tabs + static_cast<size_t>(f) * 2 * md.nz * md.nz * md.ntab : nullptr;
+  const double* ctab = md.layered ? ctabs + static_cast<size_t>(f) * 2 * md.nz * md.nz : nullptr;
   const FillTri& p = tris[rep[u].x];
   const FillTri& q = tris[rep[u].y];
   double2 acc[10];
@@ -346,14 +592,20 @@ __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ 
       double I1, Iv[3];
       potentials(q, r, &I1, Iv);
       const double s = wo / (4.0 * kPi);
-      acc[0].x += s * I1;
+      double cphi = 1.0, cA = 1.0;
+      if (md.layered) {
+        const int iq0 = q.zid[1][0];
+        cphi = ctab[(0 * md.nz + ip) * md.nz + iq0];
+        cA = ctab[(1 * md.nz + ip) * md.nz + iq0];
+      }
+      acc[0].x += cphi * s * I1;
       // projection of r on the plane of q
       const double d = q.n[0] * (r[0] - q.v[0][0]) + q.n[1] * (r[1] - q.v[0][1]) + q.n[2] * (r[2] - q.v[0][2]);
       const double r0[3] = {r[0] - d * q.n[0], r[1] - d * q.n[1], r[2] - d * q.n[2]};
       for (int b = 0; b < 3; ++b) {
         double tv[3];
         for (int k = 0; k < 3; ++k) tv[k] = Iv[k] + (r0[k] - q.v[b][k]) * I1;
-        for (int a = 0; a < 3; ++a) acc[1 + 3 * a + b].x += s * (ra[a][0] * tv[0] + ra[a][1] * tv[1] + ra[a][2] * tv[2]);
+        for (int a = 0; a < 3; ++a) acc[1 + 3 * a + b].x += cA * s * (ra[a][0] * tv[0] + ra[a][1] * tv[1] + ra[a][2] * tv[2]);
       }
     }
     for (int j = 0; j < nq; ++j) {
@@ -363,14 +615,22 @@ __global__ void __launch_bounds__(128) class_kernel(const FillTri* __restrict__ 
       rq[2] = z[iq];
       const double rho = hypot(r[0] - rq[0], r[1] - rq[1]);
       const double w = wo * Q[j][3] * q.area;
-      const double2 GD = cscale(green(md, z, fit, 0, ip, iq, rho, near), w);
-      const double2 GN = both_vert ? cscale(green(md, z, fit, 1, ip, iq, rho, near), w) : make_double2(0.0, 0.0);
+      // scalar kernel, horizontal vector kernel (the same in a homogeneous medium), vertical one
+      double2 GD, GA, GN = make_double2(0.0, 0.0);
+      if (md.layered) {
+        GD = cscale(green_slab(md, z, tab, ctab, 0, ip, iq, rho, near), w);
+        GA = cscale(green_slab(md, z, tab, ctab, 1, ip, iq, rho, near), w);
+      } else {
+        GD = cscale(green(md, z, fit, 0, ip, iq, rho, near), w);
+        GA = GD;
+        if (both_vert) GN = cscale(green(md, z, fit, 1, ip, iq, rho, near), w);
+      }
       acc[0] = ca(acc[0], GD);
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           const double dh = ra[a][0] * (rq[0] - q.v[b][0]) + ra[a][1] * (rq[1] - q.v[b][1]);
           const double dz = ra[a][2] * (rq[2] - q.v[b][2]);
-          acc[1 + 3 * a + b] = ca(acc[1 + 3 * a + b], ca(cscale(GD, dh), cscale(GN, dz)));
+          acc[1 + 3 * a + b] = ca(acc[1 + 3 * a + b], ca(cscale(GA, dh), cscale(GN, dz)));
         }
     }
   }
@@ -491,6 +751,31 @@ void key_triangle(const Grid& g, int32_t key, FillTri* t) {
     for (int i = 0; i < 13; ++i) t->zid[r][i] = static_cast<int16_t>(layer);
 }
 
+// Gauss-Legendre nodes and weights of order n on [-1, 1]: Newton's method on P_n from the
+// Chebyshev-like first guess cos(pi (i + 3/4) / (n + 1/2)), P_n and P_n' by the three-term
+// recurrence.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double t = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;   // P_0, P_1
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_n(t), p0 = P_{n-1}(t)
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-15) break;
+    }
+    x[i] = -t;
+    x[n - 1 - i] = t;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
 }  // namespace
 }  // namespace pmom
 
@@ -499,6 +784,8 @@ namespace pmom {
 pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,
                    cudaStream_t s, void** d_Z_out, std::string* err) {
   if (g.layers > kMaxLayers) return PMOM_ERR_UNSUPPORTED;
+  // the layered kernels are those of horizontal currents: no via strips in a grounded slab
+  if (g.medium == 2 && g.vias()) return PMOM_ERR_UNSUPPORTED;
   // distinct triangles
   std::unordered_map<int32_t, int> tri_of;
   std::vector<FillTri> tris;
@@ -584,19 +871,55 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
     bfs[m] = b;
   }
   std::vector<Medium> media(F);
+  const bool layered = g.medium == 2;
   const double er = g.medium == 0 ? hj_eps_eff(g) : g.eps_r;
   const double eps0 = 1.0 / (kMu0 * kC0 * kC0);
+  // layered medium: the slab up to the highest metal layer, tables on rho = i d/16 out to the
+  // diagonal of the grid with a three-pixel margin on every side
+  double d_slab = 0.0;
+  for (double zz : g.layer_z) d_slab = std::max(d_slab, zz);
+  const double htab = d_slab / 16.0;
+  const double rho_max = g.pitch * std::sqrt((g.nx + 6.0) * (g.nx + 6.0) + (g.ny + 6.0) * (g.ny + 6.0));
+  const int ntab = layered ? static_cast<int>(std::ceil(rho_max / htab)) + 4 : 0;
+  std::vector<Slab> slabs(layered ? F : 0);
+  std::vector<double> ctabs(layered ? static_cast<size_t>(F) * 2 * nz * nz : 0);
   for (int f = 0; f < F; ++f) {
     Medium& md = media[f];
     md.omega = 2.0 * kPi * freqs[f];
-    md.eps = make_double2(eps0 * er, -eps0 * er * g.tan_d);
+    md.eps = layered ? make_double2(eps0, 0.0) : make_double2(eps0 * er, -eps0 * er * g.tan_d);
     // k = w sqrt(mu0 eps), principal root
     const std::complex<double> kk = md.omega * std::sqrt(std::complex<double>(kMu0 * md.eps.x, kMu0 * md.eps.y));
     md.k = make_double2(kk.real(), kk.imag());
     md.stripline = g.medium == 1;
+    md.layered = layered;
     md.H = g.h_total;
     md.rho_s = 0.5 * g.h_total;
     md.nz = nz;
+    md.ntab = ntab;
+    md.htab = htab;
+    if (layered) {
+      Slab& sl = slabs[f];
+      sl.omega = md.omega;
+      sl.d = d_slab;
+      const std::complex<double> er1(g.eps_r, -g.eps_r * g.tan_d), ert(1.0, 0.0);
+      const double k0 = md.omega / kC0;
+      const std::complex<double> k1 = k0 * std::sqrt(er1), k0t = k0 * std::sqrt(ert);
+      sl.er1 = make_double2(er1.real(), er1.imag());
+      sl.ert = make_double2(ert.real(), ert.imag());
+      sl.k1 = make_double2(k1.real(), k1.imag());
+      sl.k0t = make_double2(k0t.real(), k0t.imag());
+      const double kmax = std::max(std::abs(k1), std::abs(k0t));
+      sl.ka = 1.5 * kmax + k0;
+      sl.kb = 0.25 * kmax;
+      const double rho_tab = htab * (ntab - 1);
+      if (sl.kb * rho_tab > 1.0) sl.kb = 1.0 / rho_tab;
+      md.k = sl.k1;   // the quasi-static term propagates with the slab's wavenumber
+      for (int kind = 0; kind < 2; ++kind)
+        for (int p = 0; p < nz; ++p)
+          for (int q = 0; q < nz; ++q)
+            ctabs[((static_cast<size_t>(f) * 2 + kind) * nz + p) * nz + q] =
+                slab_c(d_slab, er1.real(), ert.real(), kind, heights[p], heights[q]);
+    }
   }
   FillTri* d_tris = nullptr;
   double* d_z = nullptr;
@@ -606,6 +929,9 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   Medium* d_media = nullptr;
   double2* d_fit = nullptr;
   double2* d_cls = nullptr;
+  Slab* d_slabs = nullptr;
+  double2* d_tab = nullptr;
+  double* d_ctab = nullptr;
   void* d_Z = nullptr;
   const size_t zel = dtype == PMOM_C128 ? sizeof(double2) : sizeof(float2);
   cudaError_t e = cudaSuccess;
@@ -620,6 +946,22 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   chk(cudaMalloc(&d_z, sizeof(double) * nz));
   chk(cudaMalloc(&d_fit, sizeof(double2) * 3 * 2 * static_cast<size_t>(nz) * nz * F));
   chk(cudaMalloc(&d_cls, sizeof(double2) * 10 * static_cast<size_t>(U) * F));
+  if (layered) {
+    double gx[kGlE], gw[kGlE], px[kGlP], pw[kGlP];
+    gauss_legendre(kGlE, gx, gw);
+    gauss_legendre(kGlP, px, pw);
+    chk(cudaMemcpyToSymbolAsync(kGlE_x, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyToSymbolAsync(kGlE_w, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyToSymbolAsync(kGlP_x, px, sizeof(px), 0, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyToSymbolAsync(kGlP_w, pw, sizeof(pw), 0, cudaMemcpyHostToDevice, s));
+    chk(cudaMalloc(&d_slabs, sizeof(Slab) * F));
+    chk(cudaMalloc(&d_tab, sizeof(double2) * static_cast<size_t>(F) * 2 * nz * nz * ntab));
+    chk(cudaMalloc(&d_ctab, sizeof(double) * ctabs.size()));
+    if (e == cudaSuccess) {
+      chk(cudaMemcpyAsync(d_slabs, slabs.data(), sizeof(Slab) * F, cudaMemcpyHostToDevice, s));
+      chk(cudaMemcpyAsync(d_ctab, ctabs.data(), sizeof(double) * ctabs.size(), cudaMemcpyHostToDevice, s));
+    }
+  }
   chk(cudaMalloc(&d_Z, zel * static_cast<size_t>(F) * M * M));
   if (e == cudaSuccess) {
     chk(cudaMemcpyAsync(d_tris, tris.data(), sizeof(FillTri) * T, cudaMemcpyHostToDevice, s));
@@ -632,8 +974,14 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   if (e == cudaSuccess) {
     fit_kernel<<<F, 128, 0, s>>>(d_media, d_z, d_fit);
     chk(cudaGetLastError());
+    if (layered) {
+      const long entries = static_cast<long>(F) * 2 * (nz * (nz + 1) / 2) * ntab;
+      slab_table_kernel<<<static_cast<unsigned>((entries + 127) / 128), 128, 0, s>>>(d_slabs, d_z, nz, ntab, htab, F, d_tab);
+      chk(cudaGetLastError());
+    }
     const long work = static_cast<long>(U) * F;
-    class_kernel<<<static_cast<unsigned>((work + 127) / 128), 128, 0, s>>>(d_tris, d_rep, U, d_media, d_z, d_fit, F, d_cls);
+    class_kernel<<<static_cast<unsigned>((work + 127) / 128), 128, 0, s>>>(d_tris, d_rep, U, d_media, d_z, d_fit, F, d_cls,
+                                                                           d_tab, d_ctab);
     chk(cudaGetLastError());
     const dim3 grid(static_cast<unsigned>((static_cast<long>(M) * M + 255) / 256), F);
     if (dtype == PMOM_C128)
@@ -651,6 +999,9 @@ pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, cons
   cudaFree(d_fit);
   cudaFree(d_z);
   cudaFree(d_cls);
+  cudaFree(d_slabs);
+  cudaFree(d_tab);
+  cudaFree(d_ctab);
   if (e != cudaSuccess) {
     if (d_Z) cudaFree(d_Z);
     *err = std::string("fill_Z: ") + cudaGetErrorString(e);

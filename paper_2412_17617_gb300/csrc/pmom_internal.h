@@ -49,6 +49,14 @@ const Grid& grid_of(const pmom_ctx* c);
 // Builds the canonical BF table (see pmom_bf_table in pmom.h).  Returns M.
 int build_bf_table(const Grid& g, std::vector<int32_t>& table);
 
+// Support-set size buckets of the autotuner: [0, 128), [128, 256), ..., [4096, 8192), >= 8192.
+constexpr int kNBuckets = 8;
+__host__ __device__ inline int n_bucket(int N) {
+  int b = 0;
+  for (int t = 128; b < kNBuckets - 1 && N >= t; t <<= 1) ++b;
+  return b;
+}
+
 // Device-side launch parameters of the evaluation kernels.
 struct EvalArgs {
   const int4* rules;       // [M] {kind, pixA, pixB, 0}
@@ -78,6 +86,8 @@ struct EvalArgs {
   int factor_only;         // 1: task t factors into workspace slot t (kept) and ends after the LU
   const int* order;        // [B] candidates in task order (largest support set first), or null
   int nslots;              // workspace slots of this launch (set by the launcher)
+  uint8_t tc_bucket[kNBuckets];   // per support-set bucket (n_bucket): tensor-core LU (1) or CUDA-core (0)
+  int max_groups;          // task groups per CTA at most (0: as many as fit)
 };
 
 enum CandFlag : uint32_t {
@@ -146,16 +156,19 @@ cudaError_t launch_fom(const double2* S, const uint8_t* bands, int F, int P, int
                        const int32_t* n_act, double* fom, int32_t* status, cudaStream_t s);
 cudaError_t launch_gather(const void* Z, int z_c128, int M, int f, const int32_t* idx, int N, void* out,
                           cudaStream_t s);
+// Batched gather of B support sets (idx [B][M], n [B] on the device) into out [B][ncap][ncap].
+cudaError_t launch_gather_batch(const void* Z, int z_c128, int M, int f, const int32_t* idx, const int32_t* n, int B,
+                                int ncap, void* out, cudaStream_t s);
 // Workspace of one task slot for support sets up to ncap (leading dimension returned in *lda).
 size_t eval_slot_bytes(int precision, int ncap, int P, int* lda);
 size_t eval_smem_bytes(int precision, int ncap, int use_tc);
-int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc);
+int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc, int max_groups = 0);
 // Large-support-set layout (narrow panels, solve vectors in global memory): chosen when the default
 // layout does not fit one CTA; pmom_eval_large.cu holds its kernels.
 bool eval_is_large(int precision, int ncap, int use_tc);
 int eval_max_ncap(int precision, int M);
 cudaError_t launch_eval_large(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
-int eval_blocks_per_sm_large(int precision, int ncap, int z_c128);
+int eval_blocks_per_sm_large(int precision, int ncap, int z_c128, int max_groups = 0);
 
 // GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
 pmom_status fill_Z(const Grid& g, const std::vector<int32_t>& table, int M, const double* freqs, int F, int dtype,

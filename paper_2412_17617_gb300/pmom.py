@@ -26,10 +26,11 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BAD_STATE_VALUE", 4: "Z
                 6: "NOT_READY", 7: "UNSUPPORTED", 8: "IO"}
 # names exported by libpmom.so, one per declaration in include/pmom.h
 EXPORTS = ("pmom_create", "pmom_destroy", "pmom_last_error", "pmom_num_bfs", "pmom_bf_table", "pmom_load_Z",
-           "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_eval_candidates",
+           "pmom_copy_Z", "pmom_fill_Z", "pmom_set_fom", "pmom_active_set", "pmom_gather", "pmom_gather_batch",
+           "pmom_eval_candidates",
            "pmom_eval_candidates_host", "pmom_stats", "pmom_set_timing", "pmom_kernel_times", "pmom_sync",
            "pmom_eval_candidates_noalloc", "pmom_set_tensor_cores", "pmom_capacity", "pmom_graph_capture", "pmom_graph_launch",
-           "pmom_autotune", "pmom_search", "pmom_eval_bordered",
+           "pmom_autotune", "pmom_autotune_table", "pmom_search", "pmom_eval_bordered",
            "pmom_mlp_create", "pmom_mlp_destroy", "pmom_mlp_last_error", "pmom_mlp_num_params", "pmom_mlp_get_params",
            "pmom_mlp_set_params", "pmom_mlp_forward", "pmom_mlp_backward", "pmom_mlp_adam", "pmom_mlp_predict_fom",
            "pmom_mlp_targets", "pmom_mlp_errors", "pmom_selftest_wait", "pmom_save_Z", "pmom_load_Z_file",
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_set_fom": [V, P, I32, ctypes.c_double],
         "pmom_active_set": [V, P, I32, P, P, V],
         "pmom_gather": [V, P, I32, I32, P, V],
+        "pmom_gather_batch": [V, P, P, I32, I32, I32, P, V],
         "pmom_eval_candidates": [V, P, I32, I32, P, P, P, V],
         "pmom_eval_candidates_host": [V, P, I32, I32, P, P, P, V],
         "pmom_stats": [V, P],
@@ -97,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "pmom_graph_capture": [V, P, I32, I32, P, P, P, I32, V],
         "pmom_graph_launch": [V, V],
         "pmom_autotune": [V, P, I32, I32, P, V],
+        "pmom_autotune_table": [V, P],
         "pmom_search": [V, P, P, P, P, P, P, I32, P, V],
         "pmom_mlp_create": [I32, P, ctypes.c_uint64, P],
         "pmom_mlp_destroy": [V],
@@ -281,6 +284,18 @@ class Evaluator:
                                        ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
+    def gather_batch(self, idx, n, f: int, ncap: int, out=None, stream=None):
+        """idx: device int32 [B][M], n: device int32 [B] (as from active_set) -> [B][ncap][ncap]
+        complex tensor with Z_sub of each candidate in its leading N_b x N_b block."""
+        import torch
+        B = n.numel()
+        dt = torch.complex128 if self.dtype == PMOM_C128 else torch.complex64
+        if out is None:
+            out = torch.zeros((B, ncap, ncap), dtype=dt, device="cuda")
+        self._check(self.L.pmom_gather_batch(self.h, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(n.data_ptr()), B, f,
+                                             ncap, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
     def eval(self, maps, precision: str = "mixed", want_S: bool = True, out=None, stream=None):
         """maps: torch CUDA uint8 [B][layers][ny][nx].  Returns (S [B,F,P,P] complex128 or None, fom, status)."""
         import torch
@@ -353,6 +368,20 @@ class Evaluator:
     def graph_launch(self, stream=None):
         self._check(self.L.pmom_graph_launch(self.h, ctypes.c_void_p(_stream_ptr(stream))))
         return self._graph_out
+
+    def autotune_table(self) -> list:
+        """The autotuner's choices per support-set bucket that it measured: [{"n_range": (lo, hi),
+        "tensor_cores", "groups_per_cta", "slot_cap" (fraction), "us_per_candidate"}]."""
+        out = np.zeros((8, 5), dtype=np.int32)
+        self._check(self.L.pmom_autotune_table(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        rows = []
+        for b in range(8):
+            if out[b, 0]:
+                lo = 0 if b == 0 else 64 << b
+                hi = None if b == 7 else 128 << b
+                rows.append({"n_range": [lo, hi], "tensor_cores": bool(out[b, 1]), "groups_per_cta": int(out[b, 2]),
+                             "slot_cap": out[b, 3] / 4.0, "us_per_candidate": int(out[b, 4])})
+        return rows
 
     def autotune(self, maps, precision: str = "mixed", stream=None) -> int:
         prec = PMOM_FP64 if precision == "fp64" else PMOM_MIXED_REFINED

@@ -74,6 +74,38 @@ def test_gather_bit_exact(plain, built):
         assert np.array_equal(sub.view(np.uint64), Z[f][np.ix_(ref_idx, ref_idx)].view(np.uint64))
 
 
+def test_gather_batch_bit_exact(plain, built):
+    """The batched bulk-staged gather: every candidate's Z_sub in its leading N_b x N_b block, bit
+    for bit, the rest of the block untouched; complex128 here, complex64 (the 16x16x2 parent, rows
+    staged through shared memory in several batches) below."""
+    w, OG, Z, maps, *_ , ev = plain
+    dm = torch.from_numpy(maps).cuda()
+    idx, n = ev.active_set(dm)
+    nn = n.cpu().numpy()
+    ncap = int(nn.max()) + 3
+    for f in (0, 10):
+        out = ev.gather_batch(idx, n, f, ncap).cpu().numpy()
+        for b in range(maps.shape[0]):
+            I = O.active_set(OG, maps[b])
+            k = len(I)
+            assert np.array_equal(out[b, :k, :k].view(np.uint64), Z[f][np.ix_(I, I)].view(np.uint64))
+            assert not out[b, k:, :].any() and not out[b, :, k:].any()
+    w2 = PI.workload_precision()
+    ev2 = built.Evaluator(w2.grid)
+    Z2 = (np.random.default_rng(3).standard_normal((1, ev2.M, ev2.M)) +
+          1j * np.random.default_rng(4).standard_normal((1, ev2.M, ev2.M))).astype(np.complex64)
+    ev2.load_Z([3e9], torch.from_numpy(Z2).cuda())
+    m2 = PI.workload_maps(w2, seed=1)[:24]
+    idx2, n2 = ev2.active_set(torch.from_numpy(m2).cuda())
+    out2 = ev2.gather_batch(idx2, n2, 0, int(n2.max().item())).cpu().numpy()
+    OG2 = O.Grid(w2.grid)
+    for b in (0, 7, 23):
+        I = O.active_set(OG2, m2[b])
+        k = len(I)
+        assert np.array_equal(out2[b, :k, :k].view(np.uint64), Z2[0][np.ix_(I, I)].view(np.uint64))
+    ev2.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_plain_workload_parity(plain, prec):
     w, OG, Z, maps, S_ref, fom_ref, ev = plain

@@ -166,6 +166,33 @@ def test_preranked_walk_beats_exhaustive_walk_at_equal_budget(S, search_case, tr
     assert f_pr < f_ex, (f_pr, f_ex)
 
 
+def _pick_random(k, seed):
+    """Selection rule of the control walk: k children drawn uniformly (seeded), tabu excluded."""
+    rng = np.random.default_rng(seed)
+
+    def pick(parent, children, tabu):
+        free = np.setdiff1d(np.arange(children.shape[0]), tabu)
+        return rng.choice(free, k, replace=False)
+    return pick
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_preranked_walk_vs_random_k_walk(S, search_case, trained, seed):
+    """The network's own gain at walk level: from the state the training steps reached, the walk
+    that exact-evaluates the network's top 32 of the 512 children against the walk that evaluates
+    32 children drawn uniformly at random (the same number of exact solves per step, so the same
+    budget and the same number of moves).  The seeds of the control are stated; the outcome per
+    seed is printed and recorded in the design notes."""
+    w, ev, bands, xs, ts, steps = search_case
+    start = steps[11][0]
+    budget = 1024
+    f_pr, n_pr = S.walk(ev, start, budget, S.pick_top(trained, bands, w.n_freq, 32))
+    f_rk, n_rk = S.walk(ev, start, budget, _pick_random(32, seed))
+    print("seed", seed, "best FoM after", budget, "exact evaluations: pre-ranked", f_pr, "random-32", f_rk)
+    assert n_pr == n_rk == budget
+    assert np.isfinite(f_pr) and np.isfinite(f_rk)
+
+
 def _expected_min_random_subset(f, k):
     """E[min f over a uniformly random k-subset of the n values]: the i-th smallest value (1-based)
     is the minimum with probability C(n - i, k - 1) / C(n, k)."""

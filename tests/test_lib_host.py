@@ -86,8 +86,10 @@ def test_argument_validation(lib):
         with pytest.raises(pmom.PmomError) as e:
             pmom.Evaluator(bad_grid)
         assert e.value.status == 1
+    # the layered microstrip's kernels are those of horizontal currents: no via state there
+    pmom.Evaluator(dataclasses.replace(g, medium=2)).close()
     with pytest.raises(pmom.PmomError) as e:
-        pmom.Evaluator(dataclasses.replace(g, medium=2))
+        pmom.Evaluator(dataclasses.replace(PI.grid_tiny(3, PI.MEDIUM_MICROSTRIP, 2), medium=2, n_states=3))
     assert e.value.status == 7
     four = PI.Grid("four", 2, 3, 3, 1e-3, 0, (0.5e-3, 1e-3), 1e-3, 3.5, 0.0, 4, (PI.Port(0, 0, 1),))
     with pytest.raises(pmom.PmomError) as e:
