@@ -266,9 +266,9 @@ constexpr int kStages = 3;
 constexpr int kGatherBufs = 8;   // parent rows in flight in the bulk gather
 constexpr int kChunk = 8;
 // K chunks per accumulation segment: the tensor cores' fp32 accumulation over a long K loses more
-// than round-to-nearest fp32 additions would, so each segment of 128 complex terms (768 products
+// than round-to-nearest fp32 additions would, so each segment of 256 complex terms (1536 products
 // per output with the three TF32 terms) is added to C on its own in the epilogue.
-constexpr int kSegChunks = 16;
+constexpr int kSegChunks = 32;
 constexpr uint32_t kRawXBytes = 10240;    // 128 rows x 80 B (column update) / 8 x 1024 B (row update)
 constexpr uint32_t kRawBytes = 16384;     // + Y: 8 x 576 B (column update) / 64 x 96 B (row update)
 constexpr uint32_t kStageBytes = 16384;   // B hi | B lo of one MMA stage
@@ -337,15 +337,14 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
   }
   unsigned char* raw0 = st.stage;
   unsigned char* bst0 = st.stage + kRaw * kRawBytes;
-  for (int t0 = 0; t0 < m; t0 += 128)
-  for (int ks0 = 0; ks0 < nk; ks0 += kSegChunks) {   // K in segments, each added to C in fp32
+  for (int t0 = 0; t0 < m; t0 += 128) {
     const int mt = min(128, m - t0);
-    const int nks = min(kSegChunks, nk - ks0);
+    const bool xv = xi < mt;
     // this thread's 16-byte pieces of chunk c: two of X, one of Y
     auto issue = [&](int c) {
       unsigned char* rx = raw0 + (c % kRaw) * kRawBytes;
       unsigned char* ry = rx + kRawXBytes;
-      const int kb = (ks0 + c) * kChunk;
+      const int kb = c * kChunk;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = tid + u * kThreads;
@@ -365,41 +364,87 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
         if (2 * part < nc) tc::cp_async16(ry + k * 576 + part * 16, A + static_cast<size_t>(kb + k) * lda + c_out + 2 * part);
       }
     };
+    // MMA completions are consumed in chunk order: 0 .. waited
+    int waited = -1;
+    auto wait_chunk = [&](int x) {
+      while (waited < x) {
+        ++waited;
+        stage_wait(st, waited % kStages);
+      }
+    };
+    // segment epilogue: this thread's accumulator row (TMEM lane xi), complex columns 32 xh ..
+    // 32 xh + 31, in two halves of 16, added to C with independent loads in flight
+    auto epilogue = [&]() {
+#pragma unroll 1
+      for (int hh = 0; hh < 2; ++hh) {
+        const int j0 = 32 * xh + 16 * hh;
+        float re[16], im[16];
+        tc::tmem_ld16(lane_base + j0, re);
+        tc::tmem_ld16(lane_base + 64 + j0, im);
+        float2 v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = j0 + u;
+          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
+                                : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
+          v[u] = (xv && j < nc) ? A[o] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = j0 + u;
+          if (xv && j < nc) {
+            const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
+                                  : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
+            A[o] = make_float2(v[u].x + re[u], v[u].y + im[u]);
+          }
+        }
+      }
+    };
 #pragma unroll
     for (int p = 0; p < kRaw - 1; ++p) {
-      if (p < nks) issue(p);
+      if (p < nk) issue(p);
       tc::cp_async_commit();   // one group per chunk slot, empty past the end, so the counts line up
     }
-    for (int c = 0; c <= nks; ++c) {
-      if (c < nks) {
-        tc::cp_async_wait<kRaw - 2>();                 // this thread's pieces of chunk c have landed
-        if (c >= kStages) stage_wait(st, c % kStages);  // chunk c - kStages's MMAs have read stage c % kStages
+    for (int c = 0; c <= nk; ++c) {
+      if (c < nk) {
+        tc::cp_async_wait<kRaw - 2>();          // this thread's pieces of chunk c have landed
+        if (c >= kStages) wait_chunk(c - kStages);   // chunk c - kStages's MMAs have read stage c % kStages
       }
       tc::tmem_wait_st();
       tc::fence_async_smem();
       tc::fence_before_sync();
       gsync();
       tc::fence_after_sync();
-      if (tid == 0 && c > 0) {
-        const int s1 = (c - 1) % kStages;
-        const uint32_t xa = st.tmem + kAccCols + 32 * s1;
-        const uint32_t bh = tc::smem_u32(bst0 + s1 * kStageBytes), bl = bh + 8192;
-        uint32_t acc = c > 1 ? 1u : 0u;
+      if (c > 0) {
+        if (tid == 0) {
+          const int s1 = (c - 1) % kStages;
+          const uint32_t xa = st.tmem + kAccCols + 32 * s1;
+          const uint32_t bh = tc::smem_u32(bst0 + s1 * kStageBytes), bl = bh + 8192;
+          uint32_t acc = (c - 1) % kSegChunks != 0 ? 1u : 0u;   // a new segment starts from zero
 #pragma unroll
-        for (int term = 0; term < 3; ++term) {
-          const uint32_t ao = xa + (term == 0 ? 16u : 0u);   // small terms first: lo*hi, hi*lo, hi*hi
-          const uint32_t bo = term == 1 ? bl : bh;
+          for (int term = 0; term < 3; ++term) {
+            const uint32_t ao = xa + (term == 0 ? 16u : 0u);   // small terms first: lo*hi, hi*lo, hi*hi
+            const uint32_t bo = term == 1 ? bl : bh;
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            tc::mma_tf32_ts(st.tmem, ao + 8 * ks, tc::smem_desc16(bo + ks * 256), idesc, acc);
-            acc = 1;
+            for (int ks = 0; ks < 2; ++ks) {
+              tc::mma_tf32_ts(st.tmem, ao + 8 * ks, tc::smem_desc16(bo + ks * 256), idesc, acc);
+              acc = 1;
+            }
           }
+          tc::commit(&st.mbar[s1]);
         }
-        tc::commit(&st.mbar[s1]);
+        // end of a segment: its accumulator added to C (the next segment's copies stay in flight;
+        // its first MMA waits for the barrier of the next iteration, after these TMEM reads)
+        if ((c - 1) % kSegChunks == kSegChunks - 1 || c == nk) {
+          wait_chunk(c - 1);
+          epilogue();
+          tc::fence_before_sync();
+        }
       }
-      if (c == nks) break;
-      if (c + kRaw - 1 < nks) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
+      if (c == nk) break;
+      if (c + kRaw - 1 < nk) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
       tc::cp_async_commit();
+      if (c >= kStages) wait_chunk(c - kStages);   // (consumed above unless a segment ended)
       // convert chunk c: X -> TMEM (negated, split; real parts at K columns 4 xh + u, imaginary at
       // 8 + 4 xh + u), Y -> canonical B tile
       const int s = c % kStages;
@@ -441,37 +486,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
       }
     }
     tc::cp_async_wait<0>();
-    // every outstanding chunk completes (commits complete in order: the last one first)
-    for (int c = nks - 1; c >= 0 && c >= nks - kStages; --c) stage_wait(st, c % kStages);
-    // epilogue: this thread's accumulator row (TMEM lane xi), complex columns 32 xh .. 32 xh + 31,
-    // in two halves of 16, added to C with independent loads in flight
-    const bool xv = xi < mt;
-#pragma unroll 1
-    for (int hh = 0; hh < 2; ++hh) {
-      const int j0 = 32 * xh + 16 * hh;
-      float re[16], im[16];
-      tc::tmem_ld16(lane_base + j0, re);
-      tc::tmem_ld16(lane_base + 64 + j0, im);
-      float2 v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int j = j0 + u;
-        const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
-                              : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
-        v[u] = (xv && j < nc) ? A[o] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int j = j0 + u;
-        if (xv && j < nc) {
-          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
-                                : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
-          A[o] = make_float2(v[u].x + re[u], v[u].y + im[u]);
-        }
-      }
-    }
     // the accumulator is read and the staging area is free before the next tile starts
-    tc::fence_before_sync();
     gsync();
   }
 }
