@@ -574,10 +574,14 @@ def run_learned(args):
         best = float(f.min())
         row = {"children": int(singles.shape[0]), "best_exact_fom": best}
         for k in (64, 256):
-            from math import comb
+            from math import lgamma
             srt = np.sort(f)
             n = len(srt)
-            pk = np.array([comb(n - i, k - 1) for i in range(1, n + 1)], dtype=float) / comb(n, k)
+
+            def lcomb(a, b):
+                return lgamma(a + 1) - lgamma(b + 1) - lgamma(a - b + 1) if 0 <= b <= a else -np.inf
+            # probability that the i-th smallest of n is the minimum of a uniform k-subset
+            pk = np.exp(np.array([lcomb(n - i, k - 1) for i in range(1, n + 1)]) - lcomb(n, k))
             row[f"top{k}_regret"] = (float(f[order[:k]].min()) - best) / abs(best)
             row[f"random{k}_expected_regret"] = (float(np.dot(pk, srt)) - best) / abs(best)
         ra, rb = np.argsort(np.argsort(pred)), np.argsort(np.argsort(f))

@@ -888,8 +888,12 @@ pmom_status pmom_autotune(pmom_ctx* c, const uint8_t* maps, int32_t B, int32_t p
                                    cudaMemcpyDeviceToDevice, s));
     float best = 3.4e38f;
     uint8_t bt = 1, bg = 2, bc = 4;
-    for (int tc = 1; tc >= 0 && !st; --tc)
-      for (int groups = 2; groups >= 1 && !st; --groups)
+    // variants that differ in what runs: the CUDA-core LU only where its layout holds the bucket's
+    // largest support set without the large layout (which always takes the tensor cores), two
+    // task groups per CTA only where they fit
+    const bool simt_ok = !pmom::eval_is_large(PMOM_MIXED_REFINED, nk, 0);
+    for (int tc = 1; tc >= (simt_ok ? 0 : 1) && !st; --tc)
+      for (int groups = pmom::eval_groups_max(PMOM_MIXED_REFINED, nk, tc) >= 2 ? 2 : 1; groups >= 1 && !st; --groups)
         for (int cap = 4; cap >= 2 && !st; cap -= 2) {
           c->tune_valid[bk] = 1;
           c->tune_tc[bk] = static_cast<uint8_t>(tc);

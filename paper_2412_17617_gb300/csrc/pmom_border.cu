@@ -31,6 +31,7 @@ constexpr int kBK = kBorderK;   // BFs removed / added per candidate at most
 // backward error reaches kEtaInverse or stops improving; it is accepted at kEtaTarget.
 constexpr double kEtaInverse = 1e-14;
 constexpr int kInvCols = 4;     // inverse columns per CTA (the solve's right-hand-side width)
+constexpr int kInvLd = 5;       // row stride of the mixed route's shared solution and correction
 
 // Reference-state bits per frequency: kRefSingular (the reference matrix has a zero pivot),
 // kRefFailed (the single-precision reference could not be refined: redo it in FP64), kRefRedone
@@ -113,9 +114,10 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
   const int n = *r.ref_n, ldn = r.ldn, lda = r.lda;
   const int nblk = (n + kInvCols - 1) / kInvCols, ntasks = r.F * nblk;
   const int tid = gtid();
-  float4* X = reinterpret_cast<float4*>(smem);                                                    // n x 4
-  float2* W = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * sizeof(float4));   // n x 4
-  float2* D = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(float2)));
+  // X and W rows kInvLd apart (odd): the four columns of consecutive rows fall in distinct banks
+  float4* X = reinterpret_cast<float4*>(smem);                                                  // n x kInvLd
+  float2* W = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvLd * sizeof(float4));   // n x kInvLd
+  float2* D = reinterpret_cast<float2*>(smem + static_cast<size_t>(n) * kInvLd * (sizeof(float4) + sizeof(float2)));
   const Slot sl = slot_layout(r.ncap, lda, r.P, sizeof(float2));
   double lone[kMaxPorts] = {1.0, 1.0, 1.0, 1.0};
   for (;;) {
@@ -138,18 +140,25 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
     const int* piv = reinterpret_cast<const int*>(ws + sl.piv_off);
     for (int e = tid; e < n * kInvCols; e += kThreads) {
       const int i = e / kInvCols, c = e % kInvCols;
-      W[e] = make_float2(i == j0 + c ? 1.f : 0.f, 0.f);
+      W[i * kInvLd + c] = make_float2(i == j0 + c ? 1.f : 0.f, 0.f);
     }
     gsync();
-    lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
-    for (int e = tid; e < n * kInvCols; e += kThreads) X[e] = make_float4(W[e].x, 0.f, W[e].y, 0.f);
+    lu_solve<float2>(A, lda, n, piv, W, kInvCols, D, kInvLd);
+    for (int e = tid; e < n * kInvCols; e += kThreads) {
+      const int o = (e / kInvCols) * kInvLd + e % kInvCols;
+      X[o] = make_float4(W[o].x, 0.f, W[o].y, 0.f);
+    }
     gsync();
     bool converged = false;
     double rprev = 0.0;
     for (int it = 0; it <= kMaxRefine; ++it) {
       float xmax = 0.f;
-      for (int e = tid; e < n * kInvCols; e += kThreads) xmax = fmaxf(xmax, fabsf(X[e].x) + fabsf(X[e].z));
-      residual_df<kInvCols, true>(Zs, lda, n, X, kInvCols, lone, nullptr, s_red, s_norm, j0, W);
+      for (int e = tid; e < n * kInvCols; e += kThreads) {
+        const int o = (e / kInvCols) * kInvLd + e % kInvCols;
+        xmax = fmaxf(xmax, fabsf(X[o].x) + fabsf(X[o].z));
+      }
+      residual_df<kInvCols, true>(Zs, lda, n, X, kInvCols, lone, nullptr, s_red, s_norm, j0, W, 3, 1, 1, nullptr,
+                                  kInvLd);
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) xmax = fmaxf(xmax, __shfl_down_sync(0xffffffffu, xmax, d));
       if ((tid & 31) == 0) s_xmax[tid >> 5] = xmax;
@@ -172,12 +181,13 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
         converged = flag == 1;
         break;
       }
-      lu_solve<float2>(A, lda, n, piv, W, kInvCols, D);
+      lu_solve<float2>(A, lda, n, piv, W, kInvCols, D, kInvLd);
       for (int e = tid; e < n * kInvCols; e += kThreads) {   // X += correction, in float-float
-        float4 x = X[e];
-        dd_add(x.x, x.y, W[e].x, 0.f);
-        dd_add(x.z, x.w, W[e].y, 0.f);
-        X[e] = x;
+        const int o = (e / kInvCols) * kInvLd + e % kInvCols;
+        float4 x = X[o];
+        dd_add(x.x, x.y, W[o].x, 0.f);
+        dd_add(x.z, x.w, W[o].y, 0.f);
+        X[o] = x;
       }
       gsync();
     }
@@ -187,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) ref_inv_mixed_kernel(RefInvArgs r) {
       float4* Gq = reinterpret_cast<float4*>(r.G) + static_cast<size_t>(f) * n * ldn;
       for (int e = tid; e < n * kInvCols; e += kThreads) {
         const int i = e / kInvCols, c = e % kInvCols;
-        Gq[static_cast<size_t>(i) * ldn + j0 + c] = X[e];
+        Gq[static_cast<size_t>(i) * ldn + j0 + c] = X[i * kInvLd + c];
       }
     }
     gsync();
@@ -572,7 +582,7 @@ cudaError_t launch_ref_g_to_df(double2* G, const int32_t* ref_n, int ldn, const 
 }
 
 size_t ref_inverse_mixed_smem(int n) {
-  return static_cast<size_t>(n) * kInvCols * (sizeof(float4) + sizeof(float2)) + 32 * 33 * sizeof(float2);
+  return static_cast<size_t>(n) * kInvLd * (sizeof(float4) + sizeof(float2)) + 32 * 33 * sizeof(float2);
 }
 
 bool ref_inverse_mixed_fits(int n) { return ref_inverse_mixed_smem(n) + 4096 <= static_cast<size_t>(optin_smem()); }

@@ -67,6 +67,12 @@ int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc, int max_
                 : blocks_per_sm_t<float2, float2, true, false, false>(ncap, max_groups);
 }
 
+int eval_groups_max(int precision, int ncap, int use_tc) {
+  const bool large = eval_is_large(precision, ncap, use_tc);
+  if (precision == PMOM_FP64) return groups_for<double2>(ncap, false, large);
+  return groups_for<float2>(ncap, large || use_tc != 0, large);
+}
+
 int eval_max_ncap(int precision, int M) {
   // largest support set whose large-layout task group fits one CTA (binary search on the layout)
   const size_t optin = static_cast<size_t>(optin_smem());

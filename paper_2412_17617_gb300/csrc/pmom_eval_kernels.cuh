@@ -809,7 +809,7 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 // steps per iteration: 2 RW independent loads in flight, and each W load serves RW rows.
 template <typename CT>
 __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda, int i0, int bs, int tb, int te,
-                                               CT* __restrict__ W, int P) {
+                                               CT* __restrict__ W, int P, int ldw) {
   constexpr int RW = sizeof(CT) == sizeof(float2) ? 4 : 2;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   for (int ii0 = warp; ii0 < bs; ii0 += kWarps * RW) {
@@ -833,7 +833,7 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) {
         if (p < P) {
-          const CT w0 = W[t * P + p], w1 = W[(t + 32) * P + p];
+          const CT w0 = W[t * ldw + p], w1 = W[(t + 32) * ldw + p];
 #pragma unroll
           for (int q = 0; q < RW; ++q) {
             acc[q][p] = cfms(l0[q], w0, acc[q][p]);
@@ -849,7 +849,7 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) {
         if (p < P) {
-          const CT w0 = W[t * P + p];
+          const CT w0 = W[t * ldw + p];
 #pragma unroll
           for (int q = 0; q < RW; ++q) acc[q][p] = cfms(l0[q], w0, acc[q][p]);
         }
@@ -870,10 +870,10 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
           v.y += o.y;
         }
         if (lane == 0) {
-          CT w = W[(i0 + ii) * P + p];
+          CT w = W[(i0 + ii) * ldw + p];
           w.x += v.x;   // acc holds -sum, so adding applies the subtraction
           w.y += v.y;
-          W[(i0 + ii) * P + p] = w;
+          W[(i0 + ii) * ldw + p] = w;
         }
       }
     }
@@ -882,15 +882,18 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
 
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
-                         int P, CT* __restrict__ D) {
+                         int P, CT* __restrict__ D, int ldw = 0) {
+  // ldw: row stride of W (>= P; an odd stride keeps the right-hand sides of consecutive rows in
+  // distinct shared-memory banks when P is even)
+  if (ldw < P) ldw = P;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
     for (int k = 0; k < N; ++k) {
       const int p = piv[k];
       if (p != k && lane < P) {
-        const CT t = W[k * P + lane];
-        W[k * P + lane] = W[p * P + lane];
-        W[p * P + lane] = t;
+        const CT t = W[k * ldw + lane];
+        W[k * ldw + lane] = W[p * ldw + lane];
+        W[p * ldw + lane] = t;
       }
       __syncwarp();
     }
@@ -907,14 +910,14 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (i0 == 0) gsync();
     if (i0 > 0) {
-      offdiag_update<CT>(A, lda, i0, bs, 0, i0, W, P);
+      offdiag_update<CT>(A, lda, i0, bs, 0, i0, W, P, ldw);
       gsync();
     }
     if (warp == 0) {
       const int i = i0 + lane;
       CT w[kMaxPorts];
 #pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
+      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * ldw + p] : czero(w[0]);
       for (int t = 0; t < bs; ++t) {
         const CT l = (lane < bs && lane > t) ? D[lane * 33 + t] : czero(w[0]);
 #pragma unroll
@@ -925,7 +928,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
       }
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p)
-        if (lane < bs && p < P) W[i * P + p] = w[p];
+        if (lane < bs && p < P) W[i * ldw + p] = w[p];
     }
     gsync();
   }
@@ -938,14 +941,14 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
     if (i1 == N) gsync();
     if (i1 < N) {
-      offdiag_update<CT>(A, lda, i0, bs, i1, N, W, P);
+      offdiag_update<CT>(A, lda, i0, bs, i1, N, W, P, ldw);
       gsync();
     }
     if (warp == 0) {
       const int i = i0 + lane;
       CT w[kMaxPorts];
 #pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * P + p] : czero(w[0]);
+      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * ldw + p] : czero(w[0]);
       for (int t = bs - 1; t >= 0; --t) {
         if (lane == t) {
           const CT d = D[lane * 33 + lane];
@@ -962,7 +965,7 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
       }
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p)
-        if (lane < bs && p < P) W[i * P + p] = w[p];
+        if (lane < bs && p < P) W[i * ldw + p] = w[p];
     }
     gsync();
   }
@@ -1013,7 +1016,8 @@ template <int NP, bool F32OUT = false>
 __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const float4* xs, int P,
                             const double* lport, double2* __restrict__ r, double* s_red, double* s_out,
                             int e0 = -1, float2* __restrict__ rw = nullptr, int gap_stride = 3, int gap_off = 1,
-                            int gap_n = 1, const int* __restrict__ cols = nullptr) {
+                            int gap_n = 1, const int* __restrict__ cols = nullptr, int ldx = 0) {
+  if (ldx < P) ldx = P;   // row stride of xs (and of rw)
   // four rows per warp at a time: independent float-float chains interleave and each x load
   // serves four rows
   constexpr int R = 4;
@@ -1050,7 +1054,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (p < P) {
-          const float4 x = xs[t * P + p];
+          const float4 x = xs[t * ldx + p];
 #pragma unroll
           for (int q = 0; q < R; ++q) {
             df_mac(z[q].x, x.x, x.y, rh[q][p], rl[q][p]);
@@ -1085,7 +1089,7 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
             float a = -xh, b = -xl;
             dd_add(a, b, i == e0 + p ? 1.f : 0.f, 0.f);
             const float rx = a + b, ry = -(yh + yl);
-            rw[i * P + p] = make_float2(rx, ry);
+            rw[i * ldx + p] = make_float2(rx, ry);
             rmaxf = fmaxf(rmaxf, fabsf(rx) + fabsf(ry));
           } else {
             const double vx = static_cast<double>(xh) + static_cast<double>(xl);

@@ -167,6 +167,8 @@ int eval_blocks_per_sm(int precision, int ncap, int z_c128, int use_tc, int max_
 // layout does not fit one CTA; pmom_eval_large.cu holds its kernels.
 bool eval_is_large(int precision, int ncap, int use_tc);
 int eval_max_ncap(int precision, int M);
+// Task groups per CTA that the layout of this launch allows (1 or 2).
+int eval_groups_max(int precision, int ncap, int use_tc);
 cudaError_t launch_eval_large(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
 int eval_blocks_per_sm_large(int precision, int ncap, int z_c128, int max_groups = 0);
 
