@@ -65,6 +65,8 @@ ref_lu_kernel(const ZT* __restrict__ Z, int M, const int32_t* __restrict__ ref_i
   }
   gsync();
   const bool singular = lu_factor<double2, NB>(A, ldn, n, piv + static_cast<size_t>(f) * n, Pn, Ut, s_val, s_row, nullptr);
+  gsync();
+  lu_invert_diag<double2>(A, ldn, n, large ? Pn : Ut);   // the form lu_solve reads
   if (tid == 0) ref_flags[f] = (singular ? kRefSingular : 0u) | (gated ? kRefRedone : 0u);
 }
 

@@ -38,12 +38,17 @@ __device__ __forceinline__ void gsync() {
 // Phase clocks, for profiling builds only (compiled with -DPMOM_PHASES): thread 0 of each task
 // group adds the cycles since its previous mark (the variable t) to a per-phase device counter.
 // In normal builds the marks expand to nothing.
-constexpr int kPhaseSlots = 16;
+// Slots 16 and up split phases further (their cycles are also counted in the enclosing phase);
+// they are lapped into local accumulators and added once per call (PMOM_LAP / PMOM_LAP_FLUSH).
+constexpr int kPhaseSlots = 32;
 enum Phase : int {
   kPhGather = 0, kPhLu = 1, kPhSolve0 = 2, kPhResid = 3, kPhSolveCorr = 4, kPhOther = 5, kPhPanelLoad = 6,
   kPhPanelFactor = 7, kPhColGemm = 8, kPhPanel = 9, kPhSwap = 10, kPhInnerU = 11, kPhInnerUpd = 12, kPhRowGemm = 13,
   kPhTrsm = 14,
-  kPhTasks = 15
+  kPhTasks = 15,
+  kPhSolvePerm = 16, kPhSolveStage = 17, kPhSolveOff = 18, kPhSolveDiag = 19, kPhPanelWork = 20, kPhPanelWait = 21,
+  kPhGemmCopyWait = 22, kPhGemmStageWait = 23, kPhGemmSync = 24, kPhGemmMma = 25, kPhGemmEpi = 26,
+  kPhGemmIssue = 27, kPhGemmConv = 28
 };
 #ifdef PMOM_PHASES
 __device__ unsigned long long g_phase_cycles[kPhaseSlots];
@@ -56,9 +61,23 @@ __device__ unsigned long long g_phase_cycles[kPhaseSlots];
       (t) = n_;                                                                                  \
     }                                                                                            \
   } while (0)
+#define PMOM_LAP(acc, t)                                                                         \
+  do {                                                                                           \
+    if (gtid() == 0) {                                                                           \
+      const long long n_ = clock64();                                                            \
+      (acc) += n_ - (t);                                                                         \
+      (t) = n_;                                                                                  \
+    }                                                                                            \
+  } while (0)
+#define PMOM_LAP_FLUSH(slot, acc)                                                                \
+  do {                                                                                           \
+    if (gtid() == 0) atomicAdd(&g_phase_cycles[slot], static_cast<unsigned long long>(acc));     \
+  } while (0)
 #else
 #define PMOM_PHASE_START(t) do { } while (0)
 #define PMOM_PHASE(slot, t) do { } while (0)
+#define PMOM_LAP(acc, t) do { } while (0)
+#define PMOM_LAP_FLUSH(slot, acc) do { } while (0)
 #endif
 
 constexpr int kTile = 64;        // trailing-update tile (rows and columns)
@@ -91,6 +110,11 @@ __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
   return c;
 }
 // c + a*b
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x); c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y); c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
   c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
   c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
@@ -337,6 +361,10 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
   }
   unsigned char* raw0 = st.stage;
   unsigned char* bst0 = st.stage + kRaw * kRawBytes;
+  PMOM_PHASE_START(tg);
+#ifdef PMOM_PHASES
+  long long l_cp = 0, l_stw = 0, l_sync = 0, l_mma = 0, l_epi = 0, l_iss = 0, l_conv = 0;
+#endif
   for (int t0 = 0; t0 < m; t0 += 128) {
     const int mt = min(128, m - t0);
     const bool xv = xi < mt;
@@ -405,16 +433,20 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
       if (p < nk) issue(p);
       tc::cp_async_commit();   // one group per chunk slot, empty past the end, so the counts line up
     }
+    PMOM_LAP(l_iss, tg);
     for (int c = 0; c <= nk; ++c) {
       if (c < nk) {
         tc::cp_async_wait<kRaw - 2>();          // this thread's pieces of chunk c have landed
+        PMOM_LAP(l_cp, tg);
         if (c >= kStages) wait_chunk(c - kStages);   // chunk c - kStages's MMAs have read stage c % kStages
+        PMOM_LAP(l_stw, tg);
       }
       tc::tmem_wait_st();
       tc::fence_async_smem();
       tc::fence_before_sync();
       gsync();
       tc::fence_after_sync();
+      PMOM_LAP(l_sync, tg);
       if (c > 0) {
         if (tid == 0) {
           const int s1 = (c - 1) % kStages;
@@ -433,6 +465,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
           }
           tc::commit(&st.mbar[s1]);
         }
+        PMOM_LAP(l_mma, tg);
         // end of a segment: its accumulator added to C (the next segment's copies stay in flight;
         // its first MMA waits for the barrier of the next iteration, after these TMEM reads)
         if ((c - 1) % kSegChunks == kSegChunks - 1 || c == nk) {
@@ -440,11 +473,14 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
           epilogue();
           tc::fence_before_sync();
         }
+        PMOM_LAP(l_epi, tg);
       }
       if (c == nk) break;
       if (c + kRaw - 1 < nk) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
       tc::cp_async_commit();
+      PMOM_LAP(l_iss, tg);
       if (c >= kStages) wait_chunk(c - kStages);   // (consumed above unless a segment ended)
+      PMOM_LAP(l_stw, tg);
       // convert chunk c: X -> TMEM (negated, split; real parts at K columns 4 xh + u, imaginary at
       // 8 + 4 xh + u), Y -> canonical B tile
       const int s = c % kStages;
@@ -484,11 +520,22 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
         put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], yk[u]), y.y);
         put_split16(yh, yl, tc::kmajor16_off(64 + yj[u], kChunk + yk[u]), y.x);
       }
+      PMOM_LAP(l_conv, tg);
     }
     tc::cp_async_wait<0>();
     // the accumulator is read and the staging area is free before the next tile starts
     gsync();
+    PMOM_LAP(l_sync, tg);
   }
+#ifdef PMOM_PHASES
+  PMOM_LAP_FLUSH(kPhGemmCopyWait, l_cp);
+  PMOM_LAP_FLUSH(kPhGemmStageWait, l_stw);
+  PMOM_LAP_FLUSH(kPhGemmSync, l_sync);
+  PMOM_LAP_FLUSH(kPhGemmMma, l_mma);
+  PMOM_LAP_FLUSH(kPhGemmEpi, l_epi);
+  PMOM_LAP_FLUSH(kPhGemmIssue, l_iss);
+  PMOM_LAP_FLUSH(kPhGemmConv, l_conv);
+#endif
 }
 
 // U12 = L11^-1 A12 for an outer panel: L11 = unit lower A[j0..j0+jb, j0..j0+jb) (jb <= 64, staged in
@@ -604,9 +651,15 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         if (v > best) { best = v; brow = r; }
       }
       publish(best, brow, 0);
+      PMOM_PHASE_START(tpc);
+#ifdef PMOM_PHASES
+      long long l_work = 0, l_wait = 0;
+#endif
       for (int j = 0; j < kb; ++j) {
         const int par = j & 1;
+        PMOM_LAP(l_work, tpc);
         gsync();
+        PMOM_LAP(l_wait, tpc);
         R pv = -1;
         int p = -1, pw = 0;
 #pragma unroll
@@ -676,6 +729,10 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         if (j + 1 < kb) publish(best, brow, par ^ 1);
       }
       gsync();
+#ifdef PMOM_PHASES
+      PMOM_LAP_FLUSH(kPhPanelWork, l_work);
+      PMOM_LAP_FLUSH(kPhPanelWait, l_wait);
+#endif
     }
     PMOM_PHASE(kPhPanelFactor, tph);
     // 3. panel back to global memory
@@ -801,6 +858,101 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
   return singular;
 }
 
+// ------------------------------------------------------------------ diagonal-block inverses
+// After lu_factor: each 32 x 32 diagonal block of the packed factors (unit lower L_bb below the
+// diagonal, U_bb on and above it) is replaced by the packed inverses (L_bb^-1 strictly below the
+// diagonal, its unit diagonal implicit; U_bb^-1 on and above it), so every later triangular solve
+// turns each diagonal step into an independent triangular matrix-vector product instead of a
+// 32-step dependent chain.  The factors serve every refinement solve of a task, so the inversion
+// is paid once.  D: the group's 32 x 33 staging block.  Warp 0 inverts L_bb, warp 1 U_bb (the
+// two touch disjoint entries of D); lane c forms column c by substitution, rows in lockstep, each
+// row read before any lane overwrites it.  A zero pivot gets a zero inverse (the task is flagged
+// singular by lu_factor).
+template <typename CT>
+__device__ void lu_invert_diag(CT* __restrict__ A, int lda, int N, CT* __restrict__ D) {
+  const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
+  for (int i0 = 0; i0 < N; i0 += 32) {
+    const int bs = min(32, N - i0);
+    for (int e = tid; e < 32 * 32; e += kThreads) {
+      const int r = e >> 5, c = e & 31;
+      if (r < bs && c < bs) D[r * 33 + c] = A[static_cast<size_t>(i0 + r) * lda + i0 + c];
+    }
+    gsync();
+    const int c = lane;
+    if (warp == 0) {
+      // column c of L^-1: x_c = 1, x_r = -sum_{t=c}^{r-1} L[r][t] x_t for r > c
+      for (int r = 1; r < bs; ++r) {
+        CT acc = czero(D[0]);
+        if (c < r) {
+          acc = D[r * 33 + c];
+          for (int t = c + 1; t < r; ++t) acc = cfma(D[r * 33 + t], D[t * 33 + c], acc);
+          acc.x = -acc.x;
+          acc.y = -acc.y;
+        }
+        __syncwarp();
+        if (c < r) D[r * 33 + c] = acc;
+        __syncwarp();
+      }
+    } else if (warp == 1) {
+      // column c of U^-1: x_c = 1/u_cc, x_r = -(sum_{t=r+1}^{c} U[r][t] x_t) / u_rr for r < c
+      CT dinv = czero(D[0]);
+      if (c < bs) {
+        const CT d = D[c * 33 + c];
+        if (cabs2(d) > 0) dinv = cinv(d);
+      }
+      __syncwarp();
+      if (c < bs) D[c * 33 + c] = dinv;
+      __syncwarp();
+      for (int r = bs - 2; r >= 0; --r) {
+        CT ir;
+        ir.x = __shfl_sync(0xffffffffu, dinv.x, r);
+        ir.y = __shfl_sync(0xffffffffu, dinv.y, r);
+        CT acc = czero(D[0]);
+        if (c > r && c < bs) {
+          for (int t = r + 1; t <= c; ++t) acc = cfma(D[r * 33 + t], D[t * 33 + c], acc);
+          acc = cmul(acc, ir);
+          acc.x = -acc.x;
+          acc.y = -acc.y;
+        }
+        __syncwarp();
+        if (c > r && c < bs) D[r * 33 + c] = acc;
+        __syncwarp();
+      }
+    }
+    gsync();
+    for (int e = tid; e < 32 * 32; e += kThreads) {
+      const int r = e >> 5, cc = e & 31;
+      if (r < bs && cc < bs) A[static_cast<size_t>(i0 + r) * lda + i0 + cc] = D[r * 33 + cc];
+    }
+    gsync();
+  }
+}
+
+// The row permutation of the pivots (interchanges k <-> piv[k] applied in order): row k of P b is
+// row perm[k] of b.  One thread walks the interchanges in shared memory (scratch: 2 N ints), the
+// group copies the result out.
+__device__ void pivots_to_perm(const int* __restrict__ piv, int N, int* __restrict__ scratch, int* __restrict__ perm) {
+  const int tid = gtid();
+  for (int k = tid; k < N; k += kThreads) {
+    scratch[k] = k;
+    scratch[N + k] = piv[k];
+  }
+  gsync();
+  if (tid == 0) {
+    for (int k = 0; k < N; ++k) {
+      const int p = scratch[N + k];
+      if (p != k) {
+        const int t = scratch[k];
+        scratch[k] = scratch[p];
+        scratch[p] = t;
+      }
+    }
+  }
+  gsync();
+  for (int k = tid; k < N; k += kThreads) perm[k] = scratch[k];
+  gsync();
+}
+
 // ------------------------------------------------------------------ triangular solves
 // W (shared, N x P) holds the right-hand sides on entry and the solution on exit.
 // D: shared 32 x 33 staging of the current diagonal block (read once, coalesced).
@@ -882,12 +1034,17 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
 
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
-                         int P, CT* __restrict__ D, int ldw = 0) {
-  // ldw: row stride of W (>= P; an odd stride keeps the right-hand sides of consecutive rows in
-  // distinct shared-memory banks when P is even)
+                         int P, CT* __restrict__ D, int ldw = 0, bool permuted = false) {
+  // A: packed factors with inverted diagonal blocks (lu_invert_diag).  ldw: row stride of W (>= P;
+  // an odd stride keeps the right-hand sides of consecutive rows in distinct shared-memory banks
+  // when P is even).  permuted: W already holds P b (the caller applied the interchanges).
   if (ldw < P) ldw = P;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
-  if (warp == 0) {
+  PMOM_PHASE_START(tso);
+#ifdef PMOM_PHASES
+  long long l_perm = 0, l_stage = 0, l_off = 0, l_diag = 0;
+#endif
+  if (warp == 0 && !permuted) {
     for (int k = 0; k < N; ++k) {
       const int p = piv[k];
       if (p != k && lane < P) {
@@ -899,77 +1056,83 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
     }
   }
   gsync();
+  PMOM_LAP(l_perm, tso);
   // forward: L y = P b, unit diagonal, blocks of 32 rows.  The whole group stages each 32 x 32
-  // diagonal block (independent loads, in flight with the off-diagonal products) for warp 0's
-  // triangular solve.
+  // diagonal block (independent loads, in flight with the off-diagonal products); warp 0 applies
+  // the block's inverse, lane r forming row r of L_bb^-1 w_b.
   for (int i0 = 0; i0 < N; i0 += 32) {
     const int bs = min(32, N - i0);
     for (int e = tid; e < 32 * 32; e += kThreads) {
       const int r = e >> 5, c = e & 31;
       D[r * 33 + c] = (r < bs && c < bs) ? A[static_cast<size_t>(i0 + r) * lda + i0 + c] : czero(D[0]);
     }
+    PMOM_LAP(l_stage, tso);
     if (i0 == 0) gsync();
     if (i0 > 0) {
       offdiag_update<CT>(A, lda, i0, bs, 0, i0, W, P, ldw);
       gsync();
     }
+    PMOM_LAP(l_off, tso);
     if (warp == 0) {
       const int i = i0 + lane;
       CT w[kMaxPorts];
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * ldw + p] : czero(w[0]);
-      for (int t = 0; t < bs; ++t) {
+      for (int t = 0; t < bs - 1; ++t) {
         const CT l = (lane < bs && lane > t) ? D[lane * 33 + t] : czero(w[0]);
 #pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          const CT y = shfl_c(w[p], t);
-          if (lane > t) w[p] = cfms(l, y, w[p]);
-        }
+        for (int p = 0; p < kMaxPorts; ++p)
+          if (p < P) w[p] = cfma(l, W[(i0 + t) * ldw + p], w[p]);
       }
+      __syncwarp();
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p)
         if (lane < bs && p < P) W[i * ldw + p] = w[p];
     }
     gsync();
+    PMOM_LAP(l_diag, tso);
   }
-  // backward: U x = y, blocks of 32 rows from the bottom
-  for (int i1 = N; i1 > 0; i1 -= 32) {
-    const int i0 = max(0, i1 - 32), bs = i1 - i0;
+  // backward: U x = y, the same 32-row blocks (those of the inverted diagonal) from the last up
+  for (int i0 = ((N - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
+    const int bs = min(32, N - i0), i1 = i0 + bs;
     for (int e = tid; e < 32 * 32; e += kThreads) {
       const int r = e >> 5, c = e & 31;
       D[r * 33 + c] = (r < bs && c < bs) ? A[static_cast<size_t>(i0 + r) * lda + i0 + c] : czero(D[0]);
     }
+    PMOM_LAP(l_stage, tso);
     if (i1 == N) gsync();
     if (i1 < N) {
       offdiag_update<CT>(A, lda, i0, bs, i1, N, W, P, ldw);
       gsync();
     }
-    if (warp == 0) {
+    PMOM_LAP(l_off, tso);
+    if (warp == 0) {   // lane r forms row r of U_bb^-1 w_b
       const int i = i0 + lane;
       CT w[kMaxPorts];
 #pragma unroll
-      for (int p = 0; p < kMaxPorts; ++p) w[p] = (lane < bs && p < P) ? W[i * ldw + p] : czero(w[0]);
-      for (int t = bs - 1; t >= 0; --t) {
-        if (lane == t) {
-          const CT d = D[lane * 33 + lane];
-          const CT inv = cabs2(d) > 0 ? cinv(d) : czero(d);
+      for (int p = 0; p < kMaxPorts; ++p) w[p] = czero(w[0]);
+      for (int t = 0; t < bs; ++t) {
+        const CT u = (lane <= t) ? D[lane * 33 + t] : czero(w[0]);
 #pragma unroll
-          for (int p = 0; p < kMaxPorts; ++p) w[p] = cmul(w[p], inv);
-        }
-        const CT u = (lane < t) ? D[lane * 33 + t] : czero(w[0]);
-#pragma unroll
-        for (int p = 0; p < kMaxPorts; ++p) {
-          const CT y = shfl_c(w[p], t);
-          if (lane < t) w[p] = cfms(u, y, w[p]);
-        }
+        for (int p = 0; p < kMaxPorts; ++p)
+          if (p < P) w[p] = cfma(u, W[(i0 + t) * ldw + p], w[p]);
       }
+      __syncwarp();
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p)
         if (lane < bs && p < P) W[i * ldw + p] = w[p];
     }
     gsync();
+    PMOM_LAP(l_diag, tso);
   }
+#ifdef PMOM_PHASES
+  PMOM_LAP_FLUSH(kPhSolvePerm, l_perm);
+  PMOM_LAP_FLUSH(kPhSolveStage, l_stage);
+  PMOM_LAP_FLUSH(kPhSolveOff, l_off);
+  PMOM_LAP_FLUSH(kPhSolveDiag, l_diag);
+#endif
 }
+
 
 // ------------------------------------------------------------------ refinement residual
 // Error-free transformations on the FP32 pipe (Knuth's TwoSum, FMA-based TwoProduct); the
@@ -1240,10 +1403,11 @@ __global__ void ys_kernel(double2* __restrict__ S, int ntask, int F, int P, doub
 }
 
 // ------------------------------------------------------------------ the evaluation kernel
-// Per-slot workspace: [LU matrix | exact complex64 copy of Z_sub (mixed path with complex64
-// storage: the refinement residual reads it row by row) | pivots | x | residual].
+// Per-slot workspace: [LU matrix | exact complex64 copy of Z_sub (factor-only launches of the
+// mixed path: the bordered update's refined inverse reads it row by row) | pivots | row
+// permutation | x | residual].
 struct Slot {
-  size_t a_off, zs_off, piv_off, x_off, r_off, wx_off, end;
+  size_t a_off, zs_off, piv_off, perm_off, x_off, r_off, wx_off, end;
 };
 __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_bytes) {
   Slot s;
@@ -1252,7 +1416,9 @@ __host__ __device__ inline Slot slot_layout(int M, int lda, int P, size_t ct_byt
   s.zs_off = (s.zs_off + 255) & ~size_t(255);
   s.piv_off = s.zs_off + static_cast<size_t>(M) * lda * sizeof(float2);
   s.piv_off = (s.piv_off + 255) & ~size_t(255);
-  s.x_off = s.piv_off + static_cast<size_t>(M) * sizeof(int);
+  s.perm_off = s.piv_off + static_cast<size_t>(M) * sizeof(int);
+  s.perm_off = (s.perm_off + 255) & ~size_t(255);
+  s.x_off = s.perm_off + static_cast<size_t>(M) * sizeof(int);
   s.x_off = (s.x_off + 255) & ~size_t(255);
   s.r_off = s.x_off + static_cast<size_t>(M) * P * sizeof(double2);
   s.r_off = (s.r_off + 255) & ~size_t(255);
@@ -1400,12 +1566,14 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
     float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
     int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
+    int* perm = reinterpret_cast<int*>(ws + sl.perm_off);
     double2* X = reinterpret_cast<double2*>(ws + sl.x_off);
     double2* Rv = reinterpret_cast<double2*>(ws + sl.r_off);
     // right-hand sides / corrections (W), the x cache of the residual
     unsigned char* vec = LARGE ? ws + sl.wx_off : smem;
     CT* W = reinterpret_cast<CT*>(vec);
-    auto solve = [&]() { lu_solve<CT>(A, lda, N, piv, W, P, Dg); };
+    // the right-hand sides are written already permuted (row k of W = row perm[k])
+    auto solve = [&]() { lu_solve<CT>(A, lda, N, piv, W, P, Dg, 0, true); };
     uint32_t* flag_of = &a.flags[a.factor_only ? t : b];
     if (N <= 0 || N > a.ncap) {
       // bad pixel states, or a support set larger than the shared memory this launch was sized
@@ -1486,6 +1654,8 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     // the autotuner's choice for this support-set size (the large layout always takes the tensor cores)
     const bool task_tc = use_tc && (LARGE || a.tc_bucket[n_bucket(N)] != 0);
     const bool singular = lu_factor<CT, NB>(A, lda, N, piv, Pn, Ut, s_val, s_row, task_tc ? &tcs : nullptr);
+    gsync();
+    lu_invert_diag<CT>(A, lda, N, Dg);
     PMOM_PHASE(kPhLu, tev);
     if (a.factor_only) {   // factors stay in slot t; a zero pivot or a failed tensor-core wait is flagged
       if (tid == 0 && (singular || tcs.failed || s_gfail)) atomicOr(flag_of, kFlagSingular);
@@ -1493,10 +1663,11 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       gsync();
       continue;
     }
+    pivots_to_perm(piv, N, reinterpret_cast<int*>(Pn), perm);
     // right-hand sides: V[k][p] = l_p on port p's gap BFs (a delta gap of 1 V; one BF, 3p+1,
-    // with two-triangle pixels)
+    // with two-triangle pixels), rows in pivot order
     for (int e = tid; e < N * P; e += kThreads) {
-      const int i = e / P, p = e % P;
+      const int i = perm[e / P], p = e % P;
       const bool gap = static_cast<unsigned>(i - (p * a.gap_stride + a.gap_off)) < static_cast<unsigned>(a.gap_n);
       W[e] = from_d2<CT>(make_double2(gap ? lport[p] : 0.0, 0.0));
     }
@@ -1563,7 +1734,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
           converged = flag == 1;
           break;
         }
-        for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[e]);
+        for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[perm[e / P] * P + e % P]);
         gsync();
         PMOM_PHASE(kPhOther, tev);
         solve();
