@@ -679,21 +679,18 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
         const bool zero = cabs2(d) == R(0);
         if (zero) singular = true;
         const CT inv = zero ? czero(d) : cinv(d);
-        CT pr[NB];
-#pragma unroll
-        for (int c = 1; c < NB; ++c) pr[c] = (j + c < kb) ? prow[j + c] : czero(d);
         best = -1;
         brow = -1;
-        // rows below the pivot that this thread owns (row p moves to the owner of row j)
+        // rows below the pivot that this thread owns (row p moves to the owner of row j); only the
+        // panel's columns right of j are touched (the pivot row's entries read from the slot)
         for (int r = j + 1 + ((tid - j - 1) & (kThreads - 1)); r < nr; r += kThreads) {
           if (r == p) continue;
-          const CT l = cmul(Pn[r * LDP + j], inv);
-          Pn[r * LDP + j] = l;
-#pragma unroll
-          for (int c = 1; c < NB; ++c)
-            if (j + c < kb) Pn[r * LDP + j + c] = cfms(l, pr[c], Pn[r * LDP + j + c]);
+          CT* row = Pn + r * LDP;
+          const CT l = cmul(row[j], inv);
+          row[j] = l;
+          for (int c = j + 1; c < kb; ++c) row[c] = cfms(l, prow[c], row[c]);
           if (j + 1 < kb) {
-            const R v = cabs2(Pn[r * LDP + j + 1]);
+            const R v = cabs2(row[j + 1]);
             if (v > best || (v == best && r < brow)) { best = v; brow = r; }
           }
         }
