@@ -290,9 +290,14 @@ constexpr int kStages = 3;
 constexpr int kGatherBufs = 8;   // parent rows in flight in the bulk gather
 constexpr int kChunk = 8;
 // K chunks per accumulation segment: the tensor cores' fp32 accumulation over a long K loses more
-// than round-to-nearest fp32 additions would, so each segment of 256 complex terms (1536 products
-// per output with the three TF32 terms) is added to C on its own in the epilogue.
+// than round-to-nearest fp32 additions would, so each segment is added to C on its own in the
+// epilogue.  Default layout: segments of 256 complex terms (1536 products per output with the
+// three TF32 terms; one accumulation over K up to 640 needed 12 % more corrections, while 64-, 128-
+// and 256-term segments measured the same).  Large-support-set layout: 1024 complex terms (K runs
+// to about 4100 there; 1024-term segments took 7 % less time than 256-term ones at N = 4100 with
+// the same corrections per task and no repaired task).
 constexpr int kSegChunks = 32;
+constexpr int kSegChunksLarge = 128;
 constexpr uint32_t kRawXBytes = 10240;    // 128 rows x 80 B (column update) / 8 x 1024 B (row update)
 constexpr uint32_t kRawBytes = 16384;     // + Y: 8 x 576 B (column update) / 64 x 96 B (row update)
 constexpr uint32_t kStageBytes = 16384;   // B hi | B lo of one MMA stage
@@ -303,6 +308,7 @@ struct TcState {
   uint64_t* mbar;     // [kStages]
   uint32_t sph;       // bit s: parity of the next completion awaited on stage s
   bool failed;
+  int seg_chunks;     // K chunks per accumulation segment
 };
 // bounded wait: 2^18 polls of mbarrier.try_wait (about 1 s at the measured 3.8 us per unanswered
 // poll); a stall flags the task instead of hanging, a healthy completion answers in microseconds.
@@ -338,7 +344,7 @@ __device__ __forceinline__ void put_split16(unsigned char* hi, unsigned char* lo
 // barrier; one thread issues chunk c - 1's six MMAs (converted in the previous iteration) and
 // commits them to its stage's mbarrier; the copies of chunk c + kRaw - 1 are issued into the raw
 // stage chunk c - 1 used; chunk c is converted into MMA stage c % kStages once chunk
-// c - kStages's MMAs have completed.  K runs in segments of kSegChunks chunks; after each the
+// c - kStages's MMAs have completed.  K runs in segments of st.seg_chunks chunks; after each the
 // epilogue reads the accumulator row by row from TMEM and adds it to C in global memory.  Rows and columns outside the tile are never copied: their stale
 // staging entries reach only accumulator rows and columns that are not stored.
 template <bool ROWG>
@@ -452,7 +458,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
           const int s1 = (c - 1) % kStages;
           const uint32_t xa = st.tmem + kAccCols + 32 * s1;
           const uint32_t bh = tc::smem_u32(bst0 + s1 * kStageBytes), bl = bh + 8192;
-          uint32_t acc = (c - 1) % kSegChunks != 0 ? 1u : 0u;   // a new segment starts from zero
+          uint32_t acc = (c - 1) % st.seg_chunks != 0 ? 1u : 0u;   // a new segment starts from zero
 #pragma unroll
           for (int term = 0; term < 3; ++term) {
             const uint32_t ao = xa + (term == 0 ? 16u : 0u);   // small terms first: lo*hi, hi*lo, hi*hi
@@ -468,7 +474,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
         PMOM_LAP(l_mma, tg);
         // end of a segment: its accumulator added to C (the next segment's copies stay in flight;
         // its first MMA waits for the barrier of the next iteration, after these TMEM reads)
-        if ((c - 1) % kSegChunks == kSegChunks - 1 || c == nk) {
+        if ((c - 1) % st.seg_chunks == st.seg_chunks - 1 || c == nk) {
           wait_chunk(c - 1);
           epilogue();
           tc::fence_before_sync();
@@ -1504,6 +1510,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   TcState tcs;
   tcs.stage = nullptr;
   tcs.tmem = 0;
+  tcs.seg_chunks = LARGE ? kSegChunksLarge : kSegChunks;
   tcs.mbar = s_mbar_g[g];
   tcs.sph = 0;
   tcs.failed = false;
