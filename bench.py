@@ -38,13 +38,13 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
-# DRAM bytes (read + write) of one launch of the tensor-core evaluation kernel on the full
-# 512-candidate x 41-frequency stripline batch, from one ncu capture (profiles/
-# eval_kernel_stripline16x16x2_launches.md gives the command).  The kernel has changed since that
-# capture (a shorter bounded wait, port gaps as BF ranges), so `traffic` is null until it is taken
-# again; the last capture is reported beside it, labelled.
-TRAFFIC_PER_LAUNCH = {}
-TRAFFIC_LAST_CAPTURE = {("stripline_16x16x2_f41_b512", "tc"): 1.05e12 + 551.98e9}
+# DRAM bytes (read + write) per task of the tensor-core evaluation kernel, from one ncu capture
+# of a graph-replayed launch on the first 64 candidates x 41 frequencies of the 16x16x2 stripline
+# batch (2624 tasks, 107.46 GB read + 34.39 GB written; profiles/
+# eval_kernel_stripline16x16x2_b64_full.md gives the command).  Every task of the 512-candidate
+# batch has the same structure (support sets of 683-693 BFs, one workspace slot each), so a
+# launch over B x F tasks moves this figure times B x F bytes.
+TRAFFIC_PER_TASK = {("stripline_16x16x2_f41_b512", "tc"): (107.459021e9 + 34.392171e9) / 2624}
 
 
 def _peaks():
@@ -422,10 +422,10 @@ def run_ours(args):
         bf16 = float(peaks.get("bf16_tflops") or 1900.0)
         peak = bf16 * 1.1 / 2.25
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_PER_LAUNCH.get((w.name, "tc")) if Bsz == w.batch else None,
-                "traffic_last_capture": TRAFFIC_LAST_CAPTURE.get((w.name, "tc")) if Bsz == w.batch else None,
-                "traffic_last_capture_note": "dram read + write bytes per launch, captured on the build before "
-                                             "the bounded-wait and port-gap changes",
+                "traffic": (TRAFFIC_PER_TASK[(w.name, "tc")] * Bsz * w.n_freq
+                            if (w.name, "tc") in TRAFFIC_PER_TASK and not large else None),
+                "traffic_note": "dram read + write bytes per launch: the per-task figure of a 64-candidate "
+                                "capture of this kernel times the launch's tasks",
                 "kernel": "eval_kernel<float2,float2,mixed,tc%s>" % (",large" if large else ""),
                 "peak_source": "measured bf16 %.1f TFLOP/s x 1.1/2.25 (TF32 dense); %s" % (
                     bf16, "of measured" if peaks.get("bf16_tflops") else "of fallback"),
