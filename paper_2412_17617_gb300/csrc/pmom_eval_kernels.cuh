@@ -1037,10 +1037,13 @@ __device__ __forceinline__ void offdiag_update(const CT* __restrict__ A, int lda
 
 template <typename CT>
 __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __restrict__ piv, CT* __restrict__ W,
-                         int P, CT* __restrict__ D, int ldw = 0, bool permuted = false) {
+                         int P, CT* __restrict__ D, int ldw = 0, bool permuted = false, int fwd_from = 0) {
   // A: packed factors with inverted diagonal blocks (lu_invert_diag).  ldw: row stride of W (>= P;
   // an odd stride keeps the right-hand sides of consecutive rows in distinct shared-memory banks
   // when P is even).  permuted: W already holds P b (the caller applied the interchanges).
+  // fwd_from: rows of P b above it are zero (so are those of y = L^-1 P b, L being unit lower
+  // triangular): the forward pass starts at its 32-row block and takes no products with the
+  // zero part of y.
   if (ldw < P) ldw = P;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   PMOM_PHASE_START(tso);
@@ -1063,16 +1066,17 @@ __device__ void lu_solve(const CT* __restrict__ A, int lda, int N, const int* __
   // forward: L y = P b, unit diagonal, blocks of 32 rows.  The whole group stages each 32 x 32
   // diagonal block (independent loads, in flight with the off-diagonal products); warp 0 applies
   // the block's inverse, lane r forming row r of L_bb^-1 w_b.
-  for (int i0 = 0; i0 < N; i0 += 32) {
+  const int f0 = (max(0, fwd_from) / 32) * 32;
+  for (int i0 = f0; i0 < N; i0 += 32) {
     const int bs = min(32, N - i0);
     for (int e = tid; e < 32 * 32; e += kThreads) {
       const int r = e >> 5, c = e & 31;
       D[r * 33 + c] = (r < bs && c < bs) ? A[static_cast<size_t>(i0 + r) * lda + i0 + c] : czero(D[0]);
     }
     PMOM_LAP(l_stage, tso);
-    if (i0 == 0) gsync();
-    if (i0 > 0) {
-      offdiag_update<CT>(A, lda, i0, bs, 0, i0, W, P, ldw);
+    if (i0 == f0) gsync();
+    if (i0 > f0) {
+      offdiag_update<CT>(A, lda, i0, bs, f0, i0, W, P, ldw);
       gsync();
     }
     PMOM_LAP(l_off, tso);
@@ -1184,9 +1188,10 @@ __device__ void residual_df(const float2* __restrict__ Zs, int lda, int N, const
                             int e0 = -1, float2* __restrict__ rw = nullptr, int gap_stride = 3, int gap_off = 1,
                             int gap_n = 1, const int* __restrict__ cols = nullptr, int ldx = 0) {
   if (ldx < P) ldx = P;   // row stride of xs (and of rw)
-  // four rows per warp at a time: independent float-float chains interleave and each x load
-  // serves four rows
-  constexpr int R = 4;
+  // two rows per warp at a time: independent float-float chains interleave and each x load
+  // serves two rows (measured on the 16x16x2 batch: 1, 2, 3, 4 and 6 rows 706, 699, 716, 715 and 762 ms
+  // per launch, bit-identical results; more rows cost registers the kernel does not have)
+  constexpr int R = 2;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   double rmax = 0.0, zmax = 0.0;
   float rmaxf = 0.f, zmaxf = 0.f;
@@ -1577,7 +1582,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     unsigned char* vec = LARGE ? ws + sl.wx_off : smem;
     CT* W = reinterpret_cast<CT*>(vec);
     // the right-hand sides are written already permuted (row k of W = row perm[k])
-    auto solve = [&]() { lu_solve<CT>(A, lda, N, piv, W, P, Dg, 0, true); };
+    auto solve = [&](int fwd_from) { lu_solve<CT>(A, lda, N, piv, W, P, Dg, 0, true, fwd_from); };
     uint32_t* flag_of = &a.flags[a.factor_only ? t : b];
     if (N <= 0 || N > a.ncap) {
       // bad pixel states, or a support set larger than the shared memory this launch was sized
@@ -1667,6 +1672,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       gsync();
       continue;
     }
+    if (tid == 0) s_flag = N;   // the first nonzero row of P V (pivot order), found below
     pivots_to_perm(piv, N, reinterpret_cast<int*>(Pn), perm);
     // right-hand sides: V[k][p] = l_p on port p's gap BFs (a delta gap of 1 V; one BF, 3p+1,
     // with two-triangle pixels), rows in pivot order
@@ -1674,9 +1680,10 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       const int i = perm[e / P], p = e % P;
       const bool gap = static_cast<unsigned>(i - (p * a.gap_stride + a.gap_off)) < static_cast<unsigned>(a.gap_n);
       W[e] = from_d2<CT>(make_double2(gap ? lport[p] : 0.0, 0.0));
+      if (gap) atomicMin(&s_flag, e / P);
     }
     gsync();
-    solve();
+    solve(s_flag);
     for (int e = tid; e < N * P; e += kThreads) X[e] = to_d2(W[e]);
     gsync();
     PMOM_PHASE(kPhSolve0, tev);
@@ -1741,7 +1748,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
         for (int e = tid; e < N * P; e += kThreads) W[e] = from_d2<CT>(Rv[perm[e / P] * P + e % P]);
         gsync();
         PMOM_PHASE(kPhOther, tev);
-        solve();
+        solve(0);
         PMOM_PHASE(kPhSolveCorr, tev);
         double dmax = 0.0;   // ||correction||_inf
         for (int e = tid; e < N * P; e += kThreads) {
