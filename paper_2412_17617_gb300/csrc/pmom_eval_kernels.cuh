@@ -132,6 +132,8 @@ __device__ __forceinline__ double2 cinv(double2 a) {
 }
 __device__ __forceinline__ float2 czero(float2) { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ double2 czero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 make_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double2 make_neg(double2 a) { return make_double2(-a.x, -a.y); }
 
 template <typename T> __device__ __forceinline__ T from_f2(float2 z);
 template <> __device__ __forceinline__ float2 from_f2<float2>(float2 z) { return z; }
@@ -415,21 +417,52 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
         float re[16], im[16];
         tc::tmem_ld16(lane_base + j0, re);
         tc::tmem_ld16(lane_base + 64 + j0, im);
-        float2 v[16];
+        if constexpr (!ROWG) {
+          // column update: a thread's 16 outputs lie in one row of C, so lane-per-row accesses
+          // would touch 32 rows per warp access.  Each warp passes its 32 x 16 block through a
+          // padded shared-memory block instead (in the B stages, idle once the segment's MMAs are
+          // complete) and moves C in 128-byte row pieces: lane l takes row 4 rr + l / 8 of the
+          // warp's 32 and complex columns 2 (l % 8), 2 (l % 8) + 1 (16-byte aligned: lda, c_out
+          // and j0 are even).  C is loaded before the accumulator is staged.
+          float2* scr = reinterpret_cast<float2*>(bst0) + warp * (32 * 17);
+          const int rl = lane >> 3, cp = 2 * (lane & 7), jc = j0 + cp;
+          float4 v4[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int j = j0 + u;
-          const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
-                                : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
-          v[u] = (xv && j < nc) ? A[o] : make_float2(0.f, 0.f);
-        }
+          for (int rr = 0; rr < 8; ++rr) {
+            const int xr = 32 * q + 4 * rr + rl;
+            const float2* crow = A + static_cast<size_t>(r_out + t0 + xr) * lda + c_out + jc;
+            if (xr < mt && jc + 1 < nc) v4[rr] = *reinterpret_cast<const float4*>(crow);
+            else if (xr < mt && jc < nc) v4[rr] = make_float4(crow[0].x, crow[0].y, 0.f, 0.f);
+            else v4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int j = j0 + u;
-          if (xv && j < nc) {
-            const size_t o = ROWG ? static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi
-                                  : static_cast<size_t>(r_out + t0 + xi) * lda + c_out + j;
-            A[o] = make_float2(v[u].x + re[u], v[u].y + im[u]);
+          for (int u = 0; u < 16; ++u) scr[lane * 17 + u] = make_float2(re[u], im[u]);
+          __syncwarp();
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) {
+            const int row = 4 * rr + rl, xr = 32 * q + row;
+            const float2 a0 = scr[row * 17 + cp], a1 = scr[row * 17 + cp + 1];
+            float2* crow = A + static_cast<size_t>(r_out + t0 + xr) * lda + c_out + jc;
+            if (xr < mt && jc + 1 < nc)
+              *reinterpret_cast<float4*>(crow) = make_float4(v4[rr].x + a0.x, v4[rr].y + a0.y, v4[rr].z + a1.x, v4[rr].w + a1.y);
+            else if (xr < mt && jc < nc)
+              crow[0] = make_float2(v4[rr].x + a0.x, v4[rr].y + a0.y);
+          }
+          __syncwarp();   // the block is rewritten by the second half
+        } else {
+          // row update: C^T[xi][j] = A[r_out + j][c_out + t0 + xi], so for each j the warp's lanes
+          // touch consecutive columns of one row of A
+          float2 v[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int j = j0 + u;
+            const size_t o = static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi;
+            v[u] = (xv && j < nc) ? A[o] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int j = j0 + u;
+            if (xv && j < nc) A[static_cast<size_t>(r_out + j) * lda + c_out + t0 + xi] = make_float2(v[u].x + re[u], v[u].y + im[u]);
           }
         }
       }
@@ -478,6 +511,7 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
           wait_chunk(c - 1);
           epilogue();
           tc::fence_before_sync();
+          if constexpr (!ROWG) gsync();   // the transpose blocks are free before stage c % kStages is written
         }
         PMOM_LAP(l_epi, tg);
       }
@@ -579,6 +613,69 @@ __device__ void outer_trsm(float2* __restrict__ A, int lda, int N, int j0, int j
     }
   }
   gsync();
+}
+
+// Trailing update of an NB-column panel on the CUDA cores: A[r_begin:N, r_begin:cend] -= L21 U12,
+// L21 = the panel's rows below it (shared memory, leading dimension NB + 1), U12 = A[k0:k0+kb,
+// r_begin:cend], in tiles of (1024 / TW) rows x TW columns, 4 x 4 complex outputs per thread.  TW
+// follows the columns left to update (within an outer panel of 64 they shrink to 48, 32 and 16),
+// so no thread computes columns that are not stored.
+template <typename CT, int NB, int TW>
+__device__ void inner_trailing(CT* __restrict__ A, int lda, const CT* __restrict__ Pn, CT* __restrict__ Ut, int k0,
+                               int kb, int r_begin, int n2, int cend) {
+  constexpr int LDP = NB + 1;
+  constexpr int LDU = kTile + 1;
+  constexpr int TX = TW / 4;                // threads across a tile's columns
+  constexpr int TR = 4 * (kThreads / TX);   // tile rows
+  static_assert(TW <= kTile && kThreads % TX == 0, "tile wider than the U12 staging block");
+  const int tid = gtid(), ty = tid / TX, tx = tid % TX;
+  const int ntile = (n2 + TR - 1) / TR;
+  const int ntile_c = (cend - r_begin + TW - 1) / TW;
+  for (int tc = 0; tc < ntile_c; ++tc) {
+    const int c0 = r_begin + tc * TW;
+#pragma unroll
+    for (int e0 = 0; e0 < NB * TW; e0 += kThreads) {   // compile-time trip count: loads in flight together
+      const int e = e0 + tid, t = e / TW, cc = e % TW;
+      if (e < NB * TW)
+        Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
+    }
+    gsync();
+    for (int tr = 0; tr < ntile; ++tr) {
+      const int r0 = tr * TR;   // relative to r_begin
+      CT acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int r = r0 + ty + (TR / 4) * i, c = c0 + tx + TX * jj;
+          acc[i][jj] = (r < n2 && c < cend) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
+        }
+#pragma unroll 4
+      for (int t = 0; t < NB; ++t) {
+        if (t >= kb) break;
+        CT a[4], u[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = r0 + ty + (TR / 4) * i;
+          a[i] = r < n2 ? Pn[(kb + r) * LDP + t] : czero(a[0]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) u[jj] = Ut[t * LDU + tx + TX * jj];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cfms(a[i], u[jj], acc[i][jj]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int r = r0 + ty + (TR / 4) * i, c = c0 + tx + TX * jj;
+          if (r < n2 && c < cend) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
+        }
+    }
+    gsync();
+  }
 }
 
 // ------------------------------------------------------------------ blocked LU in global memory
@@ -790,58 +887,14 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
     }
     gsync();
     PMOM_PHASE(kPhInnerU, tph);
-    // 6. trailing update A22 -= L21 U12 on the CUDA cores (64 x 64 tiles, 4 x 4 complex outputs per
-    //    thread), for the columns up to the end of the current outer panel
+    // 6. trailing update A22 -= L21 U12 on the CUDA cores, for the columns up to the end of the
+    //    current outer panel (the tile as wide as the columns left to update, up to 64)
     const int r_begin = k0 + kb, n2 = N - r_begin;
     if (n2 > 0 && cend > r_begin) {
-      const int ty = tid >> 4, tx = tid & 15;
-      const int ntile = (n2 + kTile - 1) / kTile;
-      const int ntile_c = (cend - r_begin + kTile - 1) / kTile;
-      for (int tc = 0; tc < ntile_c; ++tc) {
-        const int c0 = r_begin + tc * kTile;
-#pragma unroll
-        for (int e0 = 0; e0 < NB * kTile; e0 += kThreads) {   // compile-time trip count: loads in flight together
-          const int e = e0 + tid, t = e / kTile, cc = e % kTile;
-          if (e < NB * kTile)
-            Ut[t * LDU + cc] = (t < kb && c0 + cc < cend) ? A[static_cast<size_t>(k0 + t) * lda + c0 + cc] : czero(Ut[0]);
-        }
-        gsync();
-        for (int tr = 0; tr < ntile; ++tr) {
-          const int r0 = tr * kTile;   // relative to r_begin
-          CT acc[4][4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              acc[i][jj] = (r < n2 && c < cend) ? A[static_cast<size_t>(r_begin + r) * lda + c] : czero(acc[0][0]);
-            }
-#pragma unroll 4
-          for (int t = 0; t < NB; ++t) {
-            if (t >= kb) break;
-            CT a[4], u[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int r = r0 + ty + 16 * i;
-              a[i] = r < n2 ? Pn[(kb + r) * LDP + t] : czero(a[0]);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) u[jj] = Ut[t * LDU + tx + 16 * jj];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cfms(a[i], u[jj], acc[i][jj]);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * jj;
-              if (r < n2 && c < cend) A[static_cast<size_t>(r_begin + r) * lda + c] = acc[i][jj];
-            }
-        }
-        gsync();
-      }
+      const int w = cend - r_begin;
+      if (w <= 16) inner_trailing<CT, NB, 16>(A, lda, Pn, Ut, k0, kb, r_begin, n2, cend);
+      else if (w <= 32) inner_trailing<CT, NB, 32>(A, lda, Pn, Ut, k0, kb, r_begin, n2, cend);
+      else inner_trailing<CT, NB, 64>(A, lda, Pn, Ut, k0, kb, r_begin, n2, cend);
     }
     gsync();
     PMOM_PHASE(kPhInnerUpd, tph);
@@ -867,65 +920,116 @@ __device__ bool lu_factor(CT* __restrict__ A, int lda, int N, int* __restrict__ 
 // diagonal, its unit diagonal implicit; U_bb^-1 on and above it), so every later triangular solve
 // turns each diagonal step into an independent triangular matrix-vector product instead of a
 // 32-step dependent chain.  The factors serve every refinement solve of a task, so the inversion
-// is paid once.  D: the group's 32 x 33 staging block.  Warp 0 inverts L_bb, warp 1 U_bb (the
-// two touch disjoint entries of D); lane c forms column c by substitution, rows in lockstep, each
-// row read before any lane overwrites it.  A zero pivot gets a zero inverse (the task is flagged
-// singular by lu_factor).
+// is paid once.  D: the group's 32 x 33 staging block.  Each block is inverted by halves: with
+// L = [[L11, 0], [L21, L22]] and U = [[U11, U12], [0, U22]] (16 x 16 sub-blocks),
+//   L^-1 = [[L11^-1, 0], [-L22^-1 L21 L11^-1, L22^-1]],  U^-1 = [[U11^-1, -U11^-1 U12 U22^-1], [0, U22^-1]].
+// Warps 0-3 invert L11, L22, U11, U22 in place (lane c forms column c by substitution, rows in
+// lockstep, each row read before any lane overwrites it; the four touch disjoint entries of D),
+// then the whole group forms the two off-diagonal blocks as 16 x 16 products, one output of each
+// per thread.  A zero pivot gets a zero inverse (the task is flagged singular by lu_factor).
 template <typename CT>
 __device__ void lu_invert_diag(CT* __restrict__ A, int lda, int N, CT* __restrict__ D) {
+  constexpr int LD = 33;
   const int tid = gtid(), lane = tid & 31, warp = tid >> 5;
   for (int i0 = 0; i0 < N; i0 += 32) {
     const int bs = min(32, N - i0);
+    const int h1 = min(16, bs), h2 = bs - h1;   // sizes of the two diagonal sub-blocks
     for (int e = tid; e < 32 * 32; e += kThreads) {
       const int r = e >> 5, c = e & 31;
-      if (r < bs && c < bs) D[r * 33 + c] = A[static_cast<size_t>(i0 + r) * lda + i0 + c];
+      if (r < bs && c < bs) D[r * LD + c] = A[static_cast<size_t>(i0 + r) * lda + i0 + c];
     }
     gsync();
-    const int c = lane;
-    if (warp == 0) {
-      // column c of L^-1: x_c = 1, x_r = -sum_{t=c}^{r-1} L[r][t] x_t for r > c
-      for (int r = 1; r < bs; ++r) {
-        CT acc = czero(D[0]);
-        if (c < r) {
-          acc = D[r * 33 + c];
-          for (int t = c + 1; t < r; ++t) acc = cfma(D[r * 33 + t], D[t * 33 + c], acc);
-          acc.x = -acc.x;
-          acc.y = -acc.y;
+    if (warp < 4) {
+      const int off = (warp & 1) ? 16 : 0, n = (warp & 1) ? h2 : h1, c = lane;
+      CT* Db = D + off * LD + off;
+      if (warp < 2) {
+        // column c of the unit lower inverse: x_c = 1, x_r = -sum_{t=c}^{r-1} L[r][t] x_t for r > c
+        for (int r = 1; r < n; ++r) {
+          CT acc = czero(D[0]);
+          if (c < r) {
+            acc = Db[r * LD + c];
+#pragma unroll
+            for (int t = 1; t < 16; ++t)
+              if (t > c && t < r) acc = cfma(Db[r * LD + t], Db[t * LD + c], acc);
+            acc.x = -acc.x;
+            acc.y = -acc.y;
+          }
+          __syncwarp();
+          if (c < r) Db[r * LD + c] = acc;
+          __syncwarp();
+        }
+      } else {
+        // column c of the upper inverse: x_c = 1/u_cc, x_r = -(sum_{t=r+1}^{c} U[r][t] x_t) / u_rr for r < c
+        CT dinv = czero(D[0]);
+        if (c < n) {
+          const CT d = Db[c * LD + c];
+          if (cabs2(d) > 0) dinv = cinv(d);
         }
         __syncwarp();
-        if (c < r) D[r * 33 + c] = acc;
+        if (c < n) Db[c * LD + c] = dinv;
         __syncwarp();
-      }
-    } else if (warp == 1) {
-      // column c of U^-1: x_c = 1/u_cc, x_r = -(sum_{t=r+1}^{c} U[r][t] x_t) / u_rr for r < c
-      CT dinv = czero(D[0]);
-      if (c < bs) {
-        const CT d = D[c * 33 + c];
-        if (cabs2(d) > 0) dinv = cinv(d);
-      }
-      __syncwarp();
-      if (c < bs) D[c * 33 + c] = dinv;
-      __syncwarp();
-      for (int r = bs - 2; r >= 0; --r) {
-        CT ir;
-        ir.x = __shfl_sync(0xffffffffu, dinv.x, r);
-        ir.y = __shfl_sync(0xffffffffu, dinv.y, r);
-        CT acc = czero(D[0]);
-        if (c > r && c < bs) {
-          for (int t = r + 1; t <= c; ++t) acc = cfma(D[r * 33 + t], D[t * 33 + c], acc);
-          acc = cmul(acc, ir);
-          acc.x = -acc.x;
-          acc.y = -acc.y;
+        for (int r = n - 2; r >= 0; --r) {
+          CT ir;
+          ir.x = __shfl_sync(0xffffffffu, dinv.x, r);
+          ir.y = __shfl_sync(0xffffffffu, dinv.y, r);
+          CT acc = czero(D[0]);
+          if (c > r && c < n) {
+#pragma unroll
+            for (int t = 1; t < 16; ++t)
+              if (t > r && t <= c) acc = cfma(Db[r * LD + t], Db[t * LD + c], acc);
+            acc = cmul(acc, ir);
+            acc.x = -acc.x;
+            acc.y = -acc.y;
+          }
+          __syncwarp();
+          if (c > r && c < n) Db[r * LD + c] = acc;
+          __syncwarp();
         }
-        __syncwarp();
-        if (c > r && c < bs) D[r * 33 + c] = acc;
-        __syncwarp();
       }
+    }
+    gsync();
+    if (h2 > 0) {
+      // T_L = L21 L11^-1 and T_U = U12 U22^-1 (row i, column j), then L21 <- -L22^-1 T_L and
+      // U12 <- -U11^-1 T_U
+      const int i = tid >> 4, j = tid & 15;
+      CT tl = czero(D[0]), tu = czero(D[0]);
+      if (i < h2) {
+        tl = D[(16 + i) * LD + j];
+#pragma unroll
+        for (int t = 1; t < 16; ++t)
+          if (t > j) tl = cfma(D[(16 + i) * LD + t], D[t * LD + j], tl);
+      }
+      if (j < h2) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t <= j) tu = cfma(D[i * LD + 16 + t], D[(16 + t) * LD + 16 + j], tu);
+      }
+      gsync();
+      if (i < h2) D[(16 + i) * LD + j] = tl;
+      if (j < h2) D[i * LD + 16 + j] = tu;
+      gsync();
+      if (i < h2) {
+        CT a = D[(16 + i) * LD + j];
+#pragma unroll
+        for (int t = 0; t < 15; ++t)
+          if (t < i) a = cfma(D[(16 + i) * LD + 16 + t], D[(16 + t) * LD + j], a);
+        tl = make_neg(a);
+      }
+      if (j < h2) {
+        CT a = czero(D[0]);
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t >= i) a = cfma(D[i * LD + t], D[t * LD + 16 + j], a);
+        tu = make_neg(a);
+      }
+      gsync();
+      if (i < h2) D[(16 + i) * LD + j] = tl;
+      if (j < h2) D[i * LD + 16 + j] = tu;
     }
     gsync();
     for (int e = tid; e < 32 * 32; e += kThreads) {
       const int r = e >> 5, cc = e & 31;
-      if (r < bs && cc < bs) A[static_cast<size_t>(i0 + r) * lda + i0 + cc] = D[r * 33 + cc];
+      if (r < bs && cc < bs) A[static_cast<size_t>(i0 + r) * lda + i0 + cc] = D[r * LD + cc];
     }
     gsync();
   }
