@@ -40,11 +40,11 @@ SM_MAX_MHZ = 2070.0
 
 # DRAM bytes (read + write) per task of the tensor-core evaluation kernel, from one ncu capture
 # of a graph-replayed launch on the first 64 candidates x 41 frequencies of the 16x16x2 stripline
-# batch (2624 tasks, 107.45 GB read + 35.23 GB written; profiles/
+# batch (2624 tasks, 110.26 GB read + 35.03 GB written; profiles/
 # eval_kernel_stripline16x16x2_b64_full.md gives the command).  Every task of the 512-candidate
 # batch has the same structure (support sets of 683-693 BFs, one workspace slot each), so a
 # launch over B x F tasks moves this figure times B x F bytes.
-TRAFFIC_PER_TASK = {("stripline_16x16x2_f41_b512", "tc"): (107.447631e9 + 35.228290e9) / 2624}
+TRAFFIC_PER_TASK = {("stripline_16x16x2_f41_b512", "tc"): (110.260378e9 + 35.028002e9) / 2624}
 
 
 def _peaks():

@@ -13,6 +13,8 @@
 //   fom_kernel      : FoM of Eq. (8)-(9) per candidate, frequencies summed in order.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor maps are encoded through the runtime's driver entry point)
+
 #include <cfloat>
 #include <cstdint>
 #include <type_traits>
@@ -278,9 +280,10 @@ __device__ __forceinline__ int block_argmax(R v, int row, R* s_val, int* s_row) 
 // once per panel instead of once per earlier panel, and the tensor cores run long MMA streams.
 //
 // Operand pipeline of a task group, per K chunk (kChunk complex values = 16 real K):
-//   raw stage   : the chunk's X and Y entries copied from the workspace by 16-byte asynchronous
-//                 copies (kRaw chunks in flight, no registers held), rows padded against bank
-//                 conflicts;
+//   raw stage   : the chunk's X and Y tiles copied from the task's workspace by two tensor copies
+//                 (TMA boxes of the launch's tensor maps, issued by one thread, completion counted
+//                 in bytes on the stage's mbarrier; kRaw chunks in flight, no registers held), rows
+//                 padded against bank conflicts;
 //   MMA stage   : the A operand (128 rows x 16, hi and lo TF32 parts) in tensor memory, written
 //                 by the threads (one row each), and the B operand (128 x 16, hi and lo, canonical
 //                 K-major layout) in shared memory; kStages of them, one MMA-completion mbarrier
@@ -304,6 +307,17 @@ constexpr uint32_t kRawXBytes = 10240;    // 128 rows x 80 B (column update) / 8
 constexpr uint32_t kRawBytes = 16384;     // + Y: 8 x 576 B (column update) / 64 x 96 B (row update)
 constexpr uint32_t kStageBytes = 16384;   // B hi | B lo of one MMA stage
 constexpr uint32_t kAccCols = 128;
+// Tensor maps of the updates' operand tiles over a launch's workspace slots: 8-byte elements (one
+// complex64 entry), dimensions {lda, ncap rows, slots}, strides {lda * 8, slot bytes}.  Boxes (columns
+// x rows) reproduce the raw-stage layouts: column update X 10 x 128 (rows 80 bytes apart), Y 72 x 8
+// (576 bytes), row update X 128 x 8 (1024 bytes), Y 12 x 64 (96 bytes); the extra columns land in
+// the padding and are never read.
+struct TmaMaps {
+  CUtensorMap m[4];
+};
+enum : int { kMapColX = 0, kMapColY = 1, kMapRowX = 2, kMapRowY = 3 };
+constexpr uint32_t kColBoxBytes = 10 * 128 * 8 + 72 * 8 * 8;   // X + Y of a column-update chunk
+constexpr uint32_t kRowBoxBytes = 128 * 8 * 8 + 12 * 64 * 8;   // X + Y of a row-update chunk
 struct TcState {
   unsigned char* stage;
   uint32_t tmem;
@@ -311,6 +325,10 @@ struct TcState {
   uint32_t sph;       // bit s: parity of the next completion awaited on stage s
   bool failed;
   int seg_chunks;     // K chunks per accumulation segment
+  const TmaMaps* maps;   // operand tile maps of this launch
+  int tz;                // the task's workspace slot (third map coordinate)
+  uint64_t* rbar;        // [kRaw] completion of a raw stage's tensor copies
+  uint32_t rph;          // bit r: parity of the next completion awaited on raw stage r
 };
 // bounded wait: 2^18 polls of mbarrier.try_wait (about 1 s at the measured 3.8 us per unanswered
 // poll); a stall flags the task instead of hanging, a healthy completion answers in microseconds.
@@ -342,13 +360,15 @@ __device__ __forceinline__ void put_split16(unsigned char* hi, unsigned char* lo
 // one M = 128, N = 128 MMA shape whose first 64 output columns are the real parts and last 64 the
 // imaginary parts; X is negated while staged so TMEM accumulates -X Y.  Each fp32 operand is split
 // into TF32 hi + lo and the three significant products (lo*hi, hi*lo, hi*hi) accumulate in fp32
-// (3xTF32).  Iteration c of the chunk loop: the asynchronous copies of chunk c have landed; one
+// (3xTF32).  Iteration c of the chunk loop: the tensor copies of chunk c have landed; one
 // barrier; one thread issues chunk c - 1's six MMAs (converted in the previous iteration) and
 // commits them to its stage's mbarrier; the copies of chunk c + kRaw - 1 are issued into the raw
 // stage chunk c - 1 used; chunk c is converted into MMA stage c % kStages once chunk
 // c - kStages's MMAs have completed.  K runs in segments of st.seg_chunks chunks; after each the
-// epilogue reads the accumulator row by row from TMEM and adds it to C in global memory.  Rows and columns outside the tile are never copied: their stale
-// staging entries reach only accumulator rows and columns that are not stored.
+// epilogue reads the accumulator row by row from TMEM and adds it to C in global memory.  The boxes
+// are always full (128 rows or columns of X): entries outside the tile, stale workspace values or
+// the zeros of the copy beyond the matrix, reach only accumulator rows and columns that are not
+// stored.
 template <bool ROWG>
 __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c_out, int m, int nc, int K,
                                TcState& st) {
@@ -369,6 +389,10 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
   }
   unsigned char* raw0 = st.stage;
   unsigned char* bst0 = st.stage + kRaw * kRawBytes;
+  // the operands were written by this group's ordinary stores; the tensor copies read them through
+  // the async proxy, so every writer orders its stores before them (proxy fence, then the barrier)
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  gsync();
   PMOM_PHASE_START(tg);
 #ifdef PMOM_PHASES
   long long l_cp = 0, l_stw = 0, l_sync = 0, l_mma = 0, l_epi = 0, l_iss = 0, l_conv = 0;
@@ -376,29 +400,28 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
   for (int t0 = 0; t0 < m; t0 += 128) {
     const int mt = min(128, m - t0);
     const bool xv = xi < mt;
-    // this thread's 16-byte pieces of chunk c: two of X, one of Y
+    // chunk c's X and Y tiles: two tensor copies into raw stage c % kRaw, issued by thread 0 and
+    // counted in bytes on that stage's barrier
     auto issue = [&](int c) {
-      unsigned char* rx = raw0 + (c % kRaw) * kRawBytes;
+      if (tid != 0) return;
+      const int r = c % kRaw, kb = c * kChunk;
+      unsigned char* rx = raw0 + r * kRawBytes;
       unsigned char* ry = rx + kRawXBytes;
-      const int kb = c * kChunk;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int e = tid + u * kThreads;
-        if (ROWG) {   // X[k][i]: 8 rows of 128 complex values (64 pieces each)
-          const int k = e >> 6, part = e & 63;
-          if (2 * part < mt) tc::cp_async16(rx + k * 1024 + part * 16, A + static_cast<size_t>(kb + k) * lda + c_out + t0 + 2 * part);
-        } else {      // X[i][k]: 128 rows of 8 complex values (4 pieces each), rows 80 bytes apart
-          const int i = e >> 2, part = e & 3;
-          if (i < mt) tc::cp_async16(rx + i * 80 + part * 16, A + static_cast<size_t>(r_out + t0 + i) * lda + kb + 2 * part);
-        }
+      const int mx = ROWG ? kMapRowX : kMapColX, my = ROWG ? kMapRowY : kMapColY;
+      tc::mbar_arrive_expect_tx(&st.rbar[r], ROWG ? kRowBoxBytes : kColBoxBytes);
+      if (ROWG) {   // X[k][i] = A[kb + k][c_out + t0 + i], Y[j][k] = A[r_out + j][kb + k]
+        tc::tma_load_3d(rx, &st.maps->m[mx], c_out + t0, kb, st.tz, &st.rbar[r]);
+        tc::tma_load_3d(ry, &st.maps->m[my], kb, r_out, st.tz, &st.rbar[r]);
+      } else {      // X[i][k] = A[r_out + t0 + i][kb + k], Y[k][j] = A[kb + k][c_out + j]
+        tc::tma_load_3d(rx, &st.maps->m[mx], kb, r_out + t0, st.tz, &st.rbar[r]);
+        tc::tma_load_3d(ry, &st.maps->m[my], c_out, kb, st.tz, &st.rbar[r]);
       }
-      if (ROWG) {     // Y[j][k]: 64 rows of 8 complex values, rows 96 bytes apart
-        const int j = tid >> 2, part = tid & 3;
-        if (j < nc) tc::cp_async16(ry + j * 96 + part * 16, A + static_cast<size_t>(r_out + j) * lda + kb + 2 * part);
-      } else {        // Y[k][j]: 8 rows of 64 complex values, rows 576 bytes apart
-        const int k = tid >> 5, part = tid & 31;
-        if (2 * part < nc) tc::cp_async16(ry + k * 576 + part * 16, A + static_cast<size_t>(kb + k) * lda + c_out + 2 * part);
-      }
+    };
+    // chunk c's tiles have landed (every thread waits, in chunk order)
+    auto raw_wait = [&](int c) {
+      const int r = c % kRaw;
+      if (!st.failed && !tc::mbar_wait(&st.rbar[r], (st.rph >> r) & 1u, kTcWaitPolls)) st.failed = true;
+      st.rph ^= 1u << r;
     };
     // MMA completions are consumed in chunk order: 0 .. waited
     int waited = -1;
@@ -468,14 +491,12 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
       }
     };
 #pragma unroll
-    for (int p = 0; p < kRaw - 1; ++p) {
+    for (int p = 0; p < kRaw - 1; ++p)
       if (p < nk) issue(p);
-      tc::cp_async_commit();   // one group per chunk slot, empty past the end, so the counts line up
-    }
     PMOM_LAP(l_iss, tg);
     for (int c = 0; c <= nk; ++c) {
       if (c < nk) {
-        tc::cp_async_wait<kRaw - 2>();          // this thread's pieces of chunk c have landed
+        raw_wait(c);
         PMOM_LAP(l_cp, tg);
         if (c >= kStages) wait_chunk(c - kStages);   // chunk c - kStages's MMAs have read stage c % kStages
         PMOM_LAP(l_stw, tg);
@@ -517,7 +538,6 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
       }
       if (c == nk) break;
       if (c + kRaw - 1 < nk) issue(c + kRaw - 1);   // into the raw stage chunk c - 1 used
-      tc::cp_async_commit();
       PMOM_LAP(l_iss, tg);
       if (c >= kStages) wait_chunk(c - kStages);   // (consumed above unless a segment ended)
       PMOM_LAP(l_stw, tg);
@@ -562,8 +582,8 @@ __device__ void gemm_update_tc(float2* __restrict__ A, int lda, int r_out, int c
       }
       PMOM_LAP(l_conv, tg);
     }
-    tc::cp_async_wait<0>();
-    // the accumulator is read and the staging area is free before the next tile starts
+    // the accumulator is read and the staging area is free before the next tile starts (every
+    // issued copy has been waited for)
     gsync();
     PMOM_LAP(l_sync, tg);
   }
@@ -1583,7 +1603,7 @@ template <> struct XCache<double2> { using type = double2; };
 // panels and the solve vectors in global memory, for support sets beyond the shared-memory
 // capacity of the default layout (one task group per CTA).
 template <typename CT, typename ZT, bool MIXED, bool TC, bool LARGE>
-__global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs a) {
+__global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs a, const __grid_constant__ TmaMaps tmaps) {
   using R = typename Real<CT>::type;
   extern __shared__ __align__(16) unsigned char smem_all[];
   __shared__ R s_val_g[kMaxGroups][kWarps + 1];
@@ -1595,6 +1615,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   __shared__ double s_dx_g[kMaxGroups][2];   // refinement: last correction norm, ||x||_inf
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mbar_g[kMaxGroups][kStages];
+  __shared__ __align__(8) uint64_t s_rbar_g[kMaxGroups][kRaw];
   __shared__ __align__(8) uint64_t s_gbar_g[kMaxGroups][kGatherBufs];
   __shared__ int s_gfail_g[kMaxGroups];   // a bulk gather wait gave up: later tasks are flagged
   constexpr bool use_tc = TC && std::is_same<CT, float2>::value;
@@ -1623,6 +1644,10 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
   tcs.mbar = s_mbar_g[g];
   tcs.sph = 0;
   tcs.failed = false;
+  tcs.maps = &tmaps;
+  tcs.tz = 0;
+  tcs.rbar = s_rbar_g[g];
+  tcs.rph = 0;
   uint64_t* gbar = s_gbar_g[g];
   volatile int& s_gfail = s_gfail_g[g];
   uint32_t gph = 0;   // bit b: parity of the next completion awaited on gather buffer b
@@ -1643,8 +1668,10 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
       tc::tmem_relinquish();
     }
     if (threadIdx.x == 0) {
-      for (int i = 0; i < ngroups; ++i)
+      for (int i = 0; i < ngroups; ++i) {
         for (int j = 0; j < kStages; ++j) tc::mbar_init(&s_mbar_g[i][j], 1);
+        for (int j = 0; j < kRaw; ++j) tc::mbar_init(&s_rbar_g[i][j], 1);
+      }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
@@ -1676,6 +1703,7 @@ __global__ void __launch_bounds__(kThreads * kMaxGroups, 1) eval_kernel(EvalArgs
     // the task's workspace: the group's slot, or (factor-only launches) slot t, which keeps the
     // factors for a later kernel
     unsigned char* ws = static_cast<unsigned char*>(a.work) + a.slot_bytes * (a.factor_only ? t : slot);
+    tcs.tz = a.factor_only ? t : slot;
     CT* A = reinterpret_cast<CT*>(ws + sl.a_off);
     float2* Zs = reinterpret_cast<float2*>(ws + sl.zs_off);
     int* piv = reinterpret_cast<int*>(ws + sl.piv_off);
@@ -2083,6 +2111,37 @@ int groups_for(int ncap, bool tc, bool large) {
   return (2 * gb + kStaticSmemSlack <= static_cast<size_t>(optin_smem())) ? 2 : 1;
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry point (the library
+// does not link against the driver library).
+inline decltype(&cuTensorMapEncodeTiled) tensor_map_encoder() {
+  static decltype(&cuTensorMapEncodeTiled) fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<decltype(&cuTensorMapEncodeTiled)>(p);
+  }();
+  return fn;
+}
+
+// The four operand-tile maps (TmaMaps) over `slots` workspace slots of slot_bytes each, starting
+// at base, each holding a rows x lda complex64 matrix.  Returns false if the encoder is missing or
+// rejects the layout.
+inline bool encode_tile_maps(TmaMaps* t, void* base, int lda, int rows, unsigned long long slots, size_t slot_bytes) {
+  const auto fn = tensor_map_encoder();
+  if (fn == nullptr || base == nullptr) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(lda), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(slots)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(lda) * 8u, static_cast<cuuint64_t>(slot_bytes)};
+  const cuuint32_t boxes[4][3] = {{10, 128, 1}, {72, 8, 1}, {128, 8, 1}, {12, 64, 1}};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int i = 0; i < 4; ++i)
+    if (fn(&t->m[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, boxes[i], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  return true;
+}
+
 template <typename CT, typename ZT, bool MIXED, bool TC, bool LARGE>
 cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
   if (a.ncap < 1 || a.ncap > a.M || a.lda < a.ncap || nslots < 1) return cudaErrorInvalidValue;
@@ -2094,7 +2153,13 @@ cudaError_t launch_eval_t(const EvalArgs& a, int nslots, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   EvalArgs b = a;
   b.nslots = nslots;
-  k<<<(nslots + groups - 1) / groups, kThreads * groups, smem, s>>>(b);
+  TmaMaps maps{};
+  if constexpr (TC && std::is_same<CT, float2>::value) {
+    // slot t of task t in factor-only launches, else the group's slot
+    const unsigned long long slots = a.factor_only ? static_cast<unsigned long long>(a.B) * a.F : nslots;
+    if (!encode_tile_maps(&maps, a.work, a.lda, a.ncap, slots, a.slot_bytes)) return cudaErrorInvalidValue;
+  }
+  k<<<(nslots + groups - 1) / groups, kThreads * groups, smem, s>>>(b, maps);
   return cudaGetLastError();
 }
 

@@ -128,6 +128,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Tiled tensor copy (TMA) of one box of a 3-D tensor map from global to this CTA's shared memory at
+// coordinates {x, y, z} (x in elements of the innermost dimension; x times the element size must
+// be a multiple of 16 bytes, dst 128-byte aligned); completion is counted in bytes on the mbarrier,
+// which the issuing thread first arms with the box bytes.  Parts of the box outside the tensor are
+// filled with zeros.  tmap: a tensor map in kernel-parameter, constant or global memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // 16-byte asynchronous copy global -> shared (L2 only), completion tracked per thread in commit
 // groups; the data is visible to the issuing thread after cp_async_wait<n>, to the others after a
 // following barrier
