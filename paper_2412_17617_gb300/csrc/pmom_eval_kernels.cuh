@@ -316,8 +316,18 @@ struct TmaMaps {
   CUtensorMap m[4];
 };
 enum : int { kMapColX = 0, kMapColY = 1, kMapRowX = 2, kMapRowY = 3 };
-constexpr uint32_t kColBoxBytes = 10 * 128 * 8 + 72 * 8 * 8;   // X + Y of a column-update chunk
-constexpr uint32_t kRowBoxBytes = 128 * 8 * 8 + 12 * 64 * 8;   // X + Y of a row-update chunk
+constexpr uint32_t kBoxW[4] = {10, 72, 128, 12};   // box columns (complex entries) per map
+constexpr uint32_t kBoxH[4] = {128, 8, 8, 64};     // box rows per map
+constexpr uint32_t box_bytes(int m) { return kBoxW[m] * kBoxH[m] * 8u; }
+constexpr uint32_t kColBoxBytes = box_bytes(kMapColX) + box_bytes(kMapColY);   // X + Y of a column-update chunk
+constexpr uint32_t kRowBoxBytes = box_bytes(kMapRowX) + box_bytes(kMapRowY);   // X + Y of a row-update chunk
+static_assert(box_bytes(kMapColX) <= kRawXBytes && box_bytes(kMapRowX) <= kRawXBytes &&
+                  box_bytes(kMapColY) <= kRawBytes - kRawXBytes && box_bytes(kMapRowY) <= kRawBytes - kRawXBytes,
+              "a tensor-copy box overruns its raw-stage region");
+static_assert(kRawXBytes % 128 == 0 && kRawBytes % 128 == 0, "tensor-copy destinations must stay 128-byte aligned");
+static_assert(kBoxW[kMapColX] * 8 == 80 && kBoxW[kMapColY] * 8 == 576 && kBoxW[kMapRowX] * 8 == 1024 &&
+                  kBoxW[kMapRowY] * 8 == 96,
+              "box row pitches must match the raw-stage layouts the conversion reads");
 struct TcState {
   unsigned char* stage;
   uint32_t tmem;
@@ -2133,12 +2143,13 @@ inline bool encode_tile_maps(TmaMaps* t, void* base, int lda, int rows, unsigned
   if (fn == nullptr || base == nullptr) return false;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(lda), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(slots)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(lda) * 8u, static_cast<cuuint64_t>(slot_bytes)};
-  const cuuint32_t boxes[4][3] = {{10, 128, 1}, {72, 8, 1}, {128, 8, 1}, {12, 64, 1}};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (int i = 0; i < 4; ++i)
-    if (fn(&t->m[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, boxes[i], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  for (int i = 0; i < 4; ++i) {
+    const cuuint32_t box[3] = {kBoxW[i], kBoxH[i], 1};
+    if (fn(&t->m[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
+  }
   return true;
 }
 
