@@ -251,7 +251,11 @@ pmom_status pmom_eval_candidates_noalloc(pmom_ctx* ctx, const uint8_t* maps_dev,
 
 /* Single-precision LU variant: on != 0 (default) runs the trailing-matrix updates on the
  * tensor cores (tcgen05, TF32 operands split hi + lo, fp32 accumulation in TMEM); 0 runs them on
- * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning. */
+ * the CUDA cores.  Both meet the same accuracy after refinement; the switch exists for tuning.
+ * The tensor-core variant stages its operand tiles with tensor-map (TMA) copies: each launch
+ * encodes its maps on the host through the CUDA runtime's driver entry point
+ * (cuTensorMapEncodeTiled); if that lookup or encoding fails, the evaluation call returns
+ * PMOM_ERR_CUDA (invalid value) without launching the evaluation kernel. */
 pmom_status pmom_set_tensor_cores(pmom_ctx* ctx, int32_t on);
 
 /* Bordered low-rank evaluation of candidates close to a reference map (the single-pixel changes
