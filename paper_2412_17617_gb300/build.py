@@ -23,17 +23,24 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+PHASES_LIB = os.path.join(BUILD, "libpmom_phases.so")
+
+
+def build(force: bool = False, verbose: bool = False, phases: bool = False) -> str:
+    """Builds libpmom.so; with phases=True the profiling variant libpmom_phases.so instead (phase
+    clocks compiled in with -DPMOM_PHASES, read by paper_2412_17617_gb300/phases.py)."""
+    lib = PHASES_LIB if phases else LIB
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     newest = max(os.path.getmtime(p) for p in srcs + HEADERS)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     objs, procs = [], []
+    extra = ["-DPMOM_PHASES"] if phases else []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + f".{os.getpid()}.o")
+        o = os.path.join(BUILD, os.path.basename(s) + f".{os.getpid()}{'.ph' if phases else ''}.o")
         objs.append(o)
-        cmd = [nvcc()] + ARCH + FLAGS + ["-c", s, "-o", o]
+        cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", s, "-o", o]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for cmd, p in procs:
@@ -48,12 +55,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 os.remove(o)
         msg = "\n".join(" ".join(c) + "\n" + out for c, out in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

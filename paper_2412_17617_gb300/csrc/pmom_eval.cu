@@ -156,3 +156,19 @@ cudaError_t launch_gather_batch(const void* Z, int z_c128, int M, int f, const i
 }
 
 }  // namespace pmom
+
+#ifdef PMOM_PHASES
+// Profiling builds only (compiled with -DPMOM_PHASES; paper_2412_17617_gb300/phases.py builds and
+// reads them): the phase-clock counters of the default-layout evaluation kernels in this
+// translation unit, kPhaseSlots cycle sums (slot kPhTasks counts tasks).  Not part of the public
+// C ABI; the product library is built without them.
+extern "C" int pmom_phase_slots() { return pmom::kPhaseSlots; }
+extern "C" int pmom_phase_read(unsigned long long* out_host) {
+  return static_cast<int>(
+      cudaMemcpyFromSymbol(out_host, pmom::g_phase_cycles, sizeof(unsigned long long) * pmom::kPhaseSlots));
+}
+extern "C" int pmom_phase_reset() {
+  unsigned long long z[pmom::kPhaseSlots] = {0};
+  return static_cast<int>(cudaMemcpyToSymbol(pmom::g_phase_cycles, z, sizeof(z)));
+}
+#endif
