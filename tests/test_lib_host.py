@@ -117,3 +117,22 @@ def test_search_rejects_depth_beyond_the_column_count(lib):
             call(init, seed=1, d_max=8, m_of_d=(1,) * 8, max_evals=10)
         assert e.value.status == 1
     ev.close()
+
+
+def test_phase_profiler_names_match_kernel_slots():
+    """The profiler's phase names follow the kernel's phase-slot enum in order (the profiling build
+    reports cycles by slot index)."""
+    import os
+    import re
+    from paper_2412_17617_gb300 import phases
+    src = open(os.path.join(os.path.dirname(phases.__file__), "csrc", "pmom_eval_kernels.cuh")).read()
+    body = re.search(r"enum Phase : int \{(.*?)\};", src, re.S).group(1)
+    slots = {name: int(v) for name, v in re.findall(r"(kPh\w+)\s*=\s*(\d+)", body)}
+    assert sorted(slots.values()) == list(range(len(slots)))
+    assert len(phases.NAMES) == len(slots)
+    assert slots["kPhTasks"] == phases.TASKS
+    order = [n for n, _ in sorted(slots.items(), key=lambda kv: kv[1])]
+    expect = {"kPhGather": "gather", "kPhLu": "lu", "kPhResid": "resid", "kPhPanelFactor": "panelfactor",
+              "kPhColGemm": "colgemm", "kPhRowGemm": "rowgemm", "kPhInnerUpd": "innerupd", "kPhGemmConv": "g_conv"}
+    for k, n in expect.items():
+        assert phases.NAMES[order.index(k)] == n
