@@ -218,6 +218,7 @@ pmom_status ensure_device(pmom_ctx* c) {
   if (c->d_rules) return PMOM_OK;
   PMOM_CUDA(c, cudaGetDevice(&c->device));
   PMOM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  (void)pmom::tensor_map_encoder_ptr();   // looked up here, outside any stream capture (null: CUDA-core path only)
   std::vector<int4> rules(c->M);
   for (int m = 0; m < c->M; ++m) {
     const int32_t* r = &c->table[static_cast<size_t>(m) * pmom::kTableCols];

@@ -1,6 +1,8 @@
 // Candidate-evaluation launchers for sm_103a: the default-layout evaluation kernels, the
 // activation, ordering, Y -> S, FoM and gather kernels.  The large-support-set variants are
 // compiled in pmom_eval_large.cu (a separate translation unit so the two build in parallel).
+#include <atomic>
+
 #include "pmom_eval_kernels.cuh"
 
 namespace pmom {
@@ -40,6 +42,19 @@ __global__ void wait_selftest_kernel(long long polls, int arrive, int* out) {
 cudaError_t launch_wait_selftest(long long polls, int arrive, int* d_out, cudaStream_t s) {
   wait_selftest_kernel<<<1, 32, 0, s>>>(polls, arrive, d_out);
   return cudaGetLastError();
+}
+
+void* tensor_map_encoder_ptr() {
+  static std::atomic<void*> cached{nullptr};
+  void* p = cached.load(std::memory_order_acquire);
+  if (p == nullptr) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;   // not kept: a later call looks again
+    cached.store(p, std::memory_order_release);
+  }
+  return p;
 }
 
 cudaError_t launch_eval(const EvalArgs& a, int precision, int nslots, cudaStream_t s) {

@@ -2121,18 +2121,10 @@ int groups_for(int ncap, bool tc, bool large) {
   return (2 * gb + kStaticSmemSlack <= static_cast<size_t>(optin_smem())) ? 2 : 1;
 }
 
-// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry point (the library
-// does not link against the driver library).
+// cuTensorMapEncodeTiled through the runtime's driver entry point (tensor_map_encoder_ptr,
+// pmom_eval.cu; the library does not link against the driver library).
 inline decltype(&cuTensorMapEncodeTiled) tensor_map_encoder() {
-  static decltype(&cuTensorMapEncodeTiled) fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      p = nullptr;
-    return reinterpret_cast<decltype(&cuTensorMapEncodeTiled)>(p);
-  }();
-  return fn;
+  return reinterpret_cast<decltype(&cuTensorMapEncodeTiled)>(tensor_map_encoder_ptr());
 }
 
 // The four operand-tile maps (TmaMaps) over `slots` workspace slots of slot_bytes each, starting

@@ -170,6 +170,10 @@ int eval_max_ncap(int precision, int M);
 // Task groups per CTA that the layout of this launch allows (1 or 2).
 int eval_groups_max(int precision, int ncap, int use_tc);
 cudaError_t launch_eval_large(const EvalArgs& a, int precision, int nslots, cudaStream_t s);
+// cuTensorMapEncodeTiled looked up through the runtime's driver entry point (null if unavailable),
+// kept after the first successful lookup.  The tensor-core launches encode their operand maps with
+// it; the first device use of a context looks it up, so a later graph capture makes no lookup.
+void* tensor_map_encoder_ptr();
 int eval_blocks_per_sm_large(int precision, int ncap, int z_c128, int max_groups = 0);
 
 // GPU fill of Z(f) (pmom_fill.cu): allocates *d_Z_out (F*M*M elements of dtype) on success.
